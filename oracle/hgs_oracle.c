@@ -1,0 +1,780 @@
+/*
+ * hgs_oracle.c -- plain FP64 CPU oracle for the hybrid 2D/3D Gaussian
+ * rasterizer of EGGS (Exchangeable 2D/3D Gaussian Splatting).
+ *
+ * TEST INFRASTRUCTURE ONLY.  The product path never calls, links or loads this
+ * file.  Only tests/, __graft_entry__.smoke() and the CPU-baseline leg of
+ * bench.py use it.  It shares no code, header, table or helper with the CUDA
+ * path under paper_2512_02932_gb300/csrc.
+ *
+ * What it computes (each function cites the passage it follows):
+ *   (1) orc_prepare / orc_render -- per pixel, in double precision, over every
+ *       primitive: the unified distance d of Eq. 1 (Sec. 3.1), the
+ *       contribution alpha*exp(-d/2) (Sec. 3.1), and front-to-back
+ *       alpha-blending (Eq. 2).  3D Gaussians use the affine (EWA) projection
+ *       of App. C, Eq. 13; 2D Gaussians use the ray-splat intersection of
+ *       App. C, Eqs. 14-15, which this oracle obtains by solving the 3x3
+ *       ray/plane system directly (Gaussian elimination), not by Eq. 14's
+ *       closed form.  The only acceleration is a uniform grid over
+ *       conservative bounding boxes, which cannot change the result.
+ *   (2) orc_contract_bin -- an FP32 replica of the binning contract: the
+ *       written sequence of single-precision operations that decides each
+ *       primitive's tile rectangle and 32-bit depth key.  Tile lists built
+ *       from it are compared bit for bit with the GPU's.
+ *   (3) orc_sh_basis -- the real spherical-harmonic basis (degree <= 3) that
+ *       decodes view-dependent colour from f (Sec. 3.1).
+ *   (4) orc_exchange -- Adaptive Type Exchange: effective rank (Eq. 3), the
+ *       3D->2D permutation reparameterisation (Eqs. 4-5, App. D Eqs. 17-19)
+ *       and the 2D->3D flag flip (Sec. 3.2).
+ *
+ * Build: gcc -O2 -fopenmp -ffp-contract=off -fPIC -shared (see build.py).
+ * -ffp-contract=off is required: the FP32 contract must round every
+ * multiply and add separately.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* configuration indices (double array passed from Python)                  */
+/* ------------------------------------------------------------------------ */
+enum {
+  CF_NEAR = 0, CF_ALPHA_MIN, CF_ALPHA_MAX, CF_T_MIN, CF_LAMBDA_Z, CF_THETA_Z,
+  CF_T_Z, CF_DILATION, CF_BG0, CF_BG1, CF_BG2, CF_COUNT
+};
+
+/* ambiguity bands: a pixel whose result could legitimately differ between an
+ * FP32 evaluation and this FP64 one is flagged and reported, not compared. */
+#define AMB_ALPHA_REL 2e-4   /* |alpha*G - alpha_min| <= this * alpha_min  */
+#define AMB_T_REL     2e-3   /* |T' - T_min| <= this * T_min               */
+#define AMB_NEAR_REL  1e-5   /* |z - near| <= this * max(1, near)          */
+#define AMB_FLIP      1e-5   /* |n . mu_c| / |mu_c| below this             */
+
+/* ------------------------------------------------------------------------ */
+/* (3) real spherical harmonics, degree <= 3                                 */
+/* Real basis built from the complex Y_l^m (with Condon-Shortley phase):     */
+/*   m>0: sqrt2 Re Y_l^m, m<0: sqrt2 Im Y_l^|m|, m=0: Y_l^0, index l*l+l+m.  */
+/* ------------------------------------------------------------------------ */
+static void sh_basis(int deg, double x, double y, double z, double *Y) {
+  const double PI = 3.14159265358979323846;
+  Y[0] = 0.5 * sqrt(1.0 / PI);
+  if (deg < 1) return;
+  const double k1 = sqrt(3.0 / (4.0 * PI));
+  Y[1] = -k1 * y;
+  Y[2] = k1 * z;
+  Y[3] = -k1 * x;
+  if (deg < 2) return;
+  const double k2a = 0.5 * sqrt(15.0 / PI);
+  const double k2b = 0.25 * sqrt(5.0 / PI);
+  const double k2c = 0.25 * sqrt(15.0 / PI);
+  Y[4] = k2a * x * y;
+  Y[5] = -k2a * y * z;
+  Y[6] = k2b * (2.0 * z * z - x * x - y * y);
+  Y[7] = -k2a * x * z;
+  Y[8] = k2c * (x * x - y * y);
+  if (deg < 3) return;
+  const double k3a = 0.25 * sqrt(35.0 / (2.0 * PI));
+  const double k3b = 0.5 * sqrt(105.0 / PI);
+  const double k3c = 0.25 * sqrt(21.0 / (2.0 * PI));
+  const double k3d = 0.25 * sqrt(7.0 / PI);
+  const double k3e = 0.25 * sqrt(105.0 / PI);
+  Y[9] = -k3a * y * (3.0 * x * x - y * y);
+  Y[10] = k3b * x * y * z;
+  Y[11] = -k3c * y * (4.0 * z * z - x * x - y * y);
+  Y[12] = k3d * z * (2.0 * z * z - 3.0 * x * x - 3.0 * y * y);
+  Y[13] = -k3c * x * (4.0 * z * z - x * x - y * y);
+  Y[14] = k3e * z * (x * x - y * y);
+  Y[15] = -k3a * x * (x * x - 3.0 * y * y);
+}
+
+void orc_sh_basis(int deg, int64_t n, const double *dirs, double *out) {
+  const int nb = (deg + 1) * (deg + 1);
+  for (int64_t i = 0; i < n; ++i) {
+    double Y[16];
+    sh_basis(deg, dirs[3 * i], dirs[3 * i + 1], dirs[3 * i + 2], Y);
+    for (int k = 0; k < nb; ++k) out[i * nb + k] = Y[k];
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* quaternion (w, x, y, z), Hamilton convention, to rotation matrix          */
+/* ------------------------------------------------------------------------ */
+static void quat_to_rot(const double q[4], double R[9]) {
+  double n = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  double w = q[0] / n, x = q[1] / n, y = q[2] / n, z = q[3] / n;
+  R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z); R[2] = 2 * (x * z + w * y);
+  R[3] = 2 * (x * y + w * z); R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+  R[6] = 2 * (x * z - w * y); R[7] = 2 * (y * z + w * x); R[8] = 1 - 2 * (x * x + y * y);
+}
+
+/* ------------------------------------------------------------------------ */
+/* (2) FP32 binning contract replica.  Every operation is a separately      */
+/* rounded binary32 operation (this file is compiled with                   */
+/* -ffp-contract=off); the order of operations is the contract.             */
+/* ------------------------------------------------------------------------ */
+static float f32_from_bits(uint32_t u) { float f; memcpy(&f, &u, 4); return f; }
+static uint32_t bits_from_f32(float f) { uint32_t u; memcpy(&u, &f, 4); return u; }
+
+/* contract exp: Cody-Waite reduction x = k ln2 + r, |r| <= ln2/2, then the
+ * degree-7 Taylor polynomial of e^r by Horner's rule, scaled by 2^k. */
+float orc_c_exp(float x) {
+  if (x != x) return x;
+  if (x < -87.0f) return 0.0f;
+  if (x > 88.0f) x = 88.0f;
+  const float LOG2E = 0x1.715476p+0f;
+  const float LN2_HI = 0x1.62e4p-1f;   /* 16 significant bits: k*LN2_HI exact */
+  const float LN2_LO = 0x1.7f7d1cp-20f; /* ln2 - LN2_HI rounded to binary32 */
+  float k = rintf(x * LOG2E);
+  float r = x - k * LN2_HI;
+  r = r - k * LN2_LO;
+  /* Taylor coefficients 1/n!, n = 7..0, rounded to binary32 */
+  float p = 0x1.a01a02p-13f;
+  p = p * r + 0x1.6c16c2p-10f;
+  p = p * r + 0x1.111112p-7f;
+  p = p * r + 0x1.555556p-5f;
+  p = p * r + 0x1.555556p-3f;
+  p = p * r + 0.5f;
+  p = p * r + 1.0f;
+  p = p * r + 1.0f;
+  int ki = (int)k;
+  float scale = f32_from_bits((uint32_t)(ki + 127) << 23);
+  return p * scale;
+}
+
+/* contract log for normal x > 0: x = m 2^e with m in (sqrt(1/2), sqrt(2)],
+ * ln m = 2 atanh(t), t = (m-1)/(m+1), atanh by its odd series to t^13. */
+float orc_c_log(float x) {
+  if (!(x > 0.0f)) return -INFINITY;
+  uint32_t b = bits_from_f32(x);
+  int e = (int)((b >> 23) & 0xff) - 127;
+  float m = f32_from_bits((b & 0x7fffffu) | 0x3f800000u);
+  if (m > 0x1.6a09e6p+0f) { m = m * 0.5f; e = e + 1; }
+  float t = (m - 1.0f) / (m + 1.0f);
+  float t2 = t * t;
+  /* atanh(t)/t = sum t^(2k)/(2k+1), coefficients rounded to binary32 */
+  float s = 0x1.3b13b2p-4f;
+  s = s * t2 + 0x1.745d18p-4f;
+  s = s * t2 + 0x1.c71c72p-4f;
+  s = s * t2 + 0x1.24924ap-3f;
+  s = s * t2 + 0x1.99999ap-3f;
+  s = s * t2 + 0x1.555556p-2f;
+  s = s * t2 + 1.0f;
+  float lnm = (2.0f * t) * s;
+  float fe = (float)e;
+  return fe * 0x1.62e4p-1f + (fe * 0x1.7f7d1cp-20f + lnm);
+}
+
+static float pad_f(float r) { return r * 1.0009765625f + 0.015625f; }
+
+/* pixel-centre coverage of [lo, hi] -> inclusive pixel range, then tiles */
+static int c_range(float lo, float hi, int extent, int tile, int *t0, int *t1) {
+  float flo = lo - 0.5f, fhi = hi - 0.5f;
+  if (!(flo <= fhi)) return 0;
+  flo = fmaxf(flo, -1.0f);
+  fhi = fminf(fhi, (float)extent);
+  int p0 = (int)ceilf(flo), p1 = (int)floorf(fhi);
+  if (p0 < 0) p0 = 0;
+  if (p1 > extent - 1) p1 = extent - 1;
+  if (p0 > p1) return 0;
+  *t0 = p0 / tile;
+  *t1 = p1 / tile;
+  return 1;
+}
+
+/* One primitive through the contract.  cam: R[9] t[3] fx fy cx cy.
+ * Returns 1 and fills rect {tx0,tx1,ty0,ty1} and depth bits if binned. */
+static int contract_one(const float mu[3], const float ls[3], const float q[4],
+                        float logit, int type, const float *cam, int W, int H,
+                        int tile, float near_z, float alpha_min, float dil,
+                        int rect[4], uint32_t *dbits) {
+  const float *Rc = cam, *tc = cam + 9;
+  const float fx = cam[12], fy = cam[13], cx = cam[14], cy = cam[15];
+  float X = ((Rc[0] * mu[0] + Rc[1] * mu[1]) + Rc[2] * mu[2]) + tc[0];
+  float Y = ((Rc[3] * mu[0] + Rc[4] * mu[1]) + Rc[5] * mu[2]) + tc[1];
+  float Z = ((Rc[6] * mu[0] + Rc[7] * mu[1]) + Rc[8] * mu[2]) + tc[2];
+  *dbits = bits_from_f32(Z);
+  if (!(Z > near_z)) return 0;
+  float alpha = 1.0f / (1.0f + orc_c_exp(-logit));
+  if (!(alpha >= alpha_min)) return 0;
+  float dmax = 2.0f * orc_c_log(alpha / alpha_min);
+  float sx = orc_c_exp(ls[0]), sy = orc_c_exp(ls[1]), sz = orc_c_exp(ls[2]);
+  float qq = ((q[0] * q[0] + q[1] * q[1]) + q[2] * q[2]) + q[3] * q[3];
+  if (!(qq > 0.0f)) return 0;
+  float inv = 1.0f / sqrtf(qq);
+  float w = q[0] * inv, x = q[1] * inv, y = q[2] * inv, z = q[3] * inv;
+  float Rq[9];
+  Rq[0] = 1.0f - 2.0f * (y * y + z * z);
+  Rq[1] = 2.0f * (x * y - w * z);
+  Rq[2] = 2.0f * (x * z + w * y);
+  Rq[3] = 2.0f * (x * y + w * z);
+  Rq[4] = 1.0f - 2.0f * (x * x + z * z);
+  Rq[5] = 2.0f * (y * z - w * x);
+  Rq[6] = 2.0f * (x * z - w * y);
+  Rq[7] = 2.0f * (y * z + w * x);
+  Rq[8] = 1.0f - 2.0f * (x * x + y * y);
+  float a[3][3]; /* a[k][i]: camera-space axis k, component i */
+  for (int k = 0; k < 3; ++k)
+    for (int i = 0; i < 3; ++i)
+      a[k][i] = (Rc[3 * i + 0] * Rq[0 * 3 + k] + Rc[3 * i + 1] * Rq[1 * 3 + k]) +
+                Rc[3 * i + 2] * Rq[2 * 3 + k];
+  float iz = 1.0f / Z;
+  float xz = X * iz, yz = Y * iz;
+  float ctrx, ctry, hx, hy;
+  int whole = 0;
+  if (type == 1) {
+    float c0 = sx * sx, c1 = sy * sy, c2 = sz * sz;
+    float V[3][3];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j)
+        V[i][j] = (c0 * (a[0][i] * a[0][j]) + c1 * (a[1][i] * a[1][j])) +
+                  c2 * (a[2][i] * a[2][j]);
+    float j00 = fx * iz, j02 = -(j00 * xz);
+    float j11 = fy * iz, j12 = -(j11 * yz);
+    float t00 = j00 * V[0][0] + j02 * V[2][0];
+    float t01 = j00 * V[0][1] + j02 * V[2][1];
+    float t02 = j00 * V[0][2] + j02 * V[2][2];
+    float t11 = j11 * V[1][1] + j12 * V[2][1];
+    float t12 = j11 * V[1][2] + j12 * V[2][2];
+    float s00 = (j00 * t00 + j02 * t02) + dil;
+    float s11 = (j11 * t11 + j12 * t12) + dil;
+    float s01 = j11 * t01 + j12 * t02;
+    float det = s00 * s11 - s01 * s01;
+    if (!(det > 0.0f)) return 0;
+    ctrx = fx * xz + cx;
+    ctry = fy * yz + cy;
+    hx = sqrtf(dmax * s00);
+    hy = sqrtf(dmax * s11);
+  } else {
+    float m0x = sx * a[0][0], m0y = sx * a[0][1], m0z = sx * a[0][2];
+    float m1x = sy * a[1][0], m1y = sy * a[1][1], m1z = sy * a[1][2];
+    float g2 = m0z * m0z + m1z * m1z;
+    float zmin = Z - sqrtf(dmax * g2);
+    if (!(zmin > near_z)) {
+      whole = 1;
+    } else {
+      float e0 = m0x - xz * m0z, e1 = m1x - xz * m1z, e2 = X - xz * Z;
+      float f0 = m0y - yz * m0z, f1 = m1y - yz * m1z, f2 = Y - yz * Z;
+      float D22 = dmax * g2 - Z * Z;
+      if (!(D22 < 0.0f)) {
+        whole = 1;
+      } else {
+        float D00 = dmax * (e0 * e0 + e1 * e1) - e2 * e2;
+        float D02 = dmax * (e0 * m0z + e1 * m1z) - e2 * Z;
+        float D11 = dmax * (f0 * f0 + f1 * f1) - f2 * f2;
+        float D12 = dmax * (f0 * m0z + f1 * m1z) - f2 * Z;
+        float qx = D02 * D02 - D00 * D22;
+        float qy = D12 * D12 - D11 * D22;
+        if (!(qx >= 0.0f) || !(qy >= 0.0f)) {
+          whole = 1;
+        } else {
+          float nD = -D22;
+          float ox = D02 / D22, oy = D12 / D22;
+          ctrx = fx * (xz + ox) + cx;
+          ctry = fy * (yz + oy) + cy;
+          hx = fx * (sqrtf(qx) / nD);
+          hy = fy * (sqrtf(qy) / nD);
+        }
+      }
+    }
+  }
+  int tx0, tx1, ty0, ty1;
+  if (whole) {
+    tx0 = 0; tx1 = (W - 1) / tile; ty0 = 0; ty1 = (H - 1) / tile;
+  } else {
+    float px = pad_f(hx), py = pad_f(hy);
+    if (!c_range(ctrx - px, ctrx + px, W, tile, &tx0, &tx1)) return 0;
+    if (!c_range(ctry - py, ctry + py, H, tile, &ty0, &ty1)) return 0;
+  }
+  rect[0] = tx0; rect[1] = tx1; rect[2] = ty0; rect[3] = ty1;
+  return 1;
+}
+
+/* cfg32: near, alpha_min, dilation.  rect: n x 4 (tx0,tx1,ty0,ty1), -1 if not
+ * binned.  touched: tiles covered (0 if not binned). */
+void orc_contract_bin(int64_t n, const float *means, const float *log_scales,
+                      const float *quats, const float *logits, const uint8_t *types,
+                      const float *cam, int W, int H, int tile, const float *cfg32,
+                      uint32_t *depth_bits, int32_t *rect, int64_t *touched) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    int r[4];
+    uint32_t db;
+    int ok = contract_one(means + 3 * i, log_scales + 3 * i, quats + 4 * i, logits[i],
+                          types[i], cam, W, H, tile, cfg32[0], cfg32[1], cfg32[2], r, &db);
+    depth_bits[i] = db;
+    if (ok) {
+      for (int k = 0; k < 4; ++k) rect[4 * i + k] = r[k];
+      touched[i] = (int64_t)(r[1] - r[0] + 1) * (int64_t)(r[3] - r[2] + 1);
+    } else {
+      for (int k = 0; k < 4; ++k) rect[4 * i + k] = -1;
+      touched[i] = 0;
+    }
+  }
+}
+
+float orc_contract_exp(float x) { return orc_c_exp(x); }
+float orc_contract_log(float x) { return orc_c_log(x); }
+
+/* ------------------------------------------------------------------------ */
+/* (1) FP64 per-pixel renderer                                               */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  int type, valid, amb_near;
+  double alpha;                   /* opacity used for contributions */
+  double col[3], nrm[3];
+  double X, Y, Z;                 /* camera-space centre */
+  uint32_t key;                   /* contract FP32 depth bits: the order key */
+  double mx, my, ca, cb, cc;      /* 3D: projected centre and conic */
+  double a[3], b[3];              /* 2D: s_x R_cw r0, s_y R_cw r1 */
+  double ndot;                    /* |n . mu_c| / |mu_c| */
+  double bx0, bx1, by0, by1;      /* padded continuous bbox in pixels */
+  int whole;
+} prim_t;
+
+typedef struct {
+  int64_t n;
+  int W, H, deg, nb;
+  double R[9], t[3], fx, fy, cx, cy;
+  float cam32[16];
+  double cfg[CF_COUNT];
+  prim_t *P;
+  int cell, gx, gy;
+  int64_t *cstart;   /* gx*gy+1 */
+  int32_t *citems;
+  int maxcell;
+} orc_ctx;
+
+static void prep_prim(orc_ctx *C, int64_t i, const double *mu64, const double *ls32,
+                      const double *q32, double logit32, const double *sh32, int type) {
+  prim_t *p = &C->P[i];
+  memset(p, 0, sizeof(*p));
+  p->type = type;
+  const double *Rc = C->R, *tc = C->t;
+  const double mu[3] = {mu64[0], mu64[1], mu64[2]};
+  const float mu32[3] = {(float)mu64[0], (float)mu64[1], (float)mu64[2]};
+  p->X = Rc[0] * mu[0] + Rc[1] * mu[1] + Rc[2] * mu[2] + tc[0];
+  p->Y = Rc[3] * mu[0] + Rc[4] * mu[1] + Rc[5] * mu[2] + tc[1];
+  p->Z = Rc[6] * mu[0] + Rc[7] * mu[1] + Rc[8] * mu[2] + tc[2];
+  {
+    /* the order key: binary32 centre depth by the contract's op order */
+    const float *R32 = C->cam32, *t32 = C->cam32 + 9;
+    float Z32 = ((R32[6] * mu32[0] + R32[7] * mu32[1]) + R32[8] * mu32[2]) + t32[2];
+    p->key = bits_from_f32(Z32);
+  }
+  const double nearz = C->cfg[CF_NEAR], amin = C->cfg[CF_ALPHA_MIN];
+  if (fabs(p->Z - nearz) <= AMB_NEAR_REL * fmax(1.0, nearz)) p->amb_near = 1;
+  if (!(p->Z > nearz) && !p->amb_near) return;
+  /* activations (Sec. 3.1): scale = exp(log s), unit quaternion, sigmoid */
+  double s[3] = {exp((double)ls32[0]), exp((double)ls32[1]), exp((double)ls32[2])};
+  double q[4] = {q32[0], q32[1], q32[2], q32[3]};
+  double qn = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+  if (!(qn > 0)) return;
+  double Rq[9];
+  quat_to_rot(q, Rq);
+  double alpha = 1.0 / (1.0 + exp(-(double)logit32));
+  double alpha_bb = alpha;
+  if (type == 0) {
+    /* scale modulation for 2D Gaussians (Eqs. 6-7) */
+    double sz = s[2];
+    double g = 1.0 / (1.0 + exp(-(sz - C->cfg[CF_THETA_Z]) / C->cfg[CF_T_Z]));
+    alpha *= exp(-C->cfg[CF_LAMBDA_Z] * (g * sz));
+  }
+  p->alpha = alpha;
+  if (!(alpha_bb >= amin * (1.0 - AMB_ALPHA_REL))) return;
+  /* camera-space axes a_k = R_cw r_k */
+  double ax[3][3];
+  for (int k = 0; k < 3; ++k)
+    for (int r = 0; r < 3; ++r)
+      ax[k][r] = Rc[3 * r] * Rq[k] + Rc[3 * r + 1] * Rq[3 + k] + Rc[3 * r + 2] * Rq[6 + k];
+  /* normal: axis of the smallest scale (2D: the z axis), facing the camera */
+  int kn;
+  if (type == 0) kn = 2;
+  else if (ls32[2] <= ls32[0] && ls32[2] <= ls32[1]) kn = 2;
+  else if (ls32[0] <= ls32[1]) kn = 0;
+  else kn = 1;
+  double nd = ax[kn][0] * p->X + ax[kn][1] * p->Y + ax[kn][2] * p->Z;
+  double sg = nd > 0 ? -1.0 : 1.0;
+  for (int r = 0; r < 3; ++r) p->nrm[r] = sg * ax[kn][r];
+  double mun = sqrt(p->X * p->X + p->Y * p->Y + p->Z * p->Z);
+  p->ndot = fabs(nd) / mun;
+  /* colour from SH (Sec. 3.1), view direction from the camera centre */
+  {
+    double cc[3];
+    for (int r = 0; r < 3; ++r)
+      cc[r] = -(C->R[0 + r] * tc[0] + C->R[3 + r] * tc[1] + C->R[6 + r] * tc[2]);
+    double dv[3] = {mu[0] - cc[0], mu[1] - cc[1], mu[2] - cc[2]};
+    double dn = sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+    double Yb[16];
+    sh_basis(C->deg, dv[0] / dn, dv[1] / dn, dv[2] / dn, Yb);
+    for (int ch = 0; ch < 3; ++ch) {
+      double v = 0.5;
+      for (int k = 0; k < C->nb; ++k) v += (double)sh32[3 * k + ch] * Yb[k];
+      p->col[ch] = v > 0 ? v : 0;
+    }
+  }
+  double dmax = 2.0 * log(alpha_bb / amin);
+  if (dmax < 0) dmax = 0;
+  dmax += 1e-3; /* the bbox is an index only: generous */
+  const double fx = C->fx, fy = C->fy, cx = C->cx, cy = C->cy;
+  double X = p->X, Y = p->Y, Z = p->Z;
+  if (type == 1) {
+    /* EWA projection, App. C Eq. 13: Sigma' = J W Sigma W^T J^T */
+    double V[3][3];
+    for (int i2 = 0; i2 < 3; ++i2)
+      for (int j2 = 0; j2 < 3; ++j2) {
+        double v = 0;
+        for (int k = 0; k < 3; ++k) v += s[k] * s[k] * ax[k][i2] * ax[k][j2];
+        V[i2][j2] = v;
+      }
+    double J[2][3] = {{fx / Z, 0, -fx * X / (Z * Z)}, {0, fy / Z, -fy * Y / (Z * Z)}};
+    double S2[2][2];
+    for (int r = 0; r < 2; ++r)
+      for (int c = 0; c < 2; ++c) {
+        double v = 0;
+        for (int i2 = 0; i2 < 3; ++i2)
+          for (int j2 = 0; j2 < 3; ++j2) v += J[r][i2] * V[i2][j2] * J[c][j2];
+        S2[r][c] = v;
+      }
+    S2[0][0] += C->cfg[CF_DILATION];
+    S2[1][1] += C->cfg[CF_DILATION];
+    double det = S2[0][0] * S2[1][1] - S2[0][1] * S2[1][0];
+    if (!(det > 0)) return;
+    p->ca = S2[1][1] / det;
+    p->cb = -S2[0][1] / det;
+    p->cc = S2[0][0] / det;
+    p->mx = fx * X / Z + cx;
+    p->my = fy * Y / Z + cy;
+    double hx = sqrt(dmax * S2[0][0]), hy = sqrt(dmax * S2[1][1]);
+    hx = hx * 1.01 + 2.0;
+    hy = hy * 1.01 + 2.0;
+    p->bx0 = p->mx - hx; p->bx1 = p->mx + hx;
+    p->by0 = p->my - hy; p->by1 = p->my + hy;
+  } else {
+    for (int r = 0; r < 3; ++r) { p->a[r] = s[0] * ax[0][r]; p->b[r] = s[1] * ax[1][r]; }
+    /* bbox of the image of the disc u^2+v^2 <= dmax: whole image unless the
+     * disc lies entirely in front of the camera */
+    double g2 = p->a[2] * p->a[2] + p->b[2] * p->b[2];
+    double zmin = Z - sqrt(dmax * g2);
+    if (!(zmin > 0.5 * nearz)) {
+      p->whole = 1;
+    } else {
+      /* conic of the disc image, via the dual conic in normalised coords */
+      double xz = X / Z, yz = Y / Z;
+      double e0 = p->a[0] - xz * p->a[2], e1 = p->b[0] - xz * p->b[2], e2 = X - xz * Z;
+      double f0 = p->a[1] - yz * p->a[2], f1 = p->b[1] - yz * p->b[2], f2 = Y - yz * Z;
+      double D22 = dmax * g2 - Z * Z;
+      double D00 = dmax * (e0 * e0 + e1 * e1) - e2 * e2;
+      double D02 = dmax * (e0 * p->a[2] + e1 * p->b[2]) - e2 * Z;
+      double D11 = dmax * (f0 * f0 + f1 * f1) - f2 * f2;
+      double D12 = dmax * (f0 * p->a[2] + f1 * p->b[2]) - f2 * Z;
+      double qx = D02 * D02 - D00 * D22, qy = D12 * D12 - D11 * D22;
+      if (!(D22 < 0) || qx < 0 || qy < 0) {
+        p->whole = 1;
+      } else {
+        double ctx = fx * (xz + D02 / D22) + cx, cty = fy * (yz + D12 / D22) + cy;
+        double hx = fx * sqrt(qx) / (-D22), hy = fy * sqrt(qy) / (-D22);
+        hx = hx * 1.01 + 2.0;
+        hy = hy * 1.01 + 2.0;
+        p->bx0 = ctx - hx; p->bx1 = ctx + hx;
+        p->by0 = cty - hy; p->by1 = cty + hy;
+      }
+    }
+  }
+  p->valid = 1;
+}
+
+static void build_grid(orc_ctx *C) {
+  int cell = C->cell;
+  C->gx = (C->W + cell - 1) / cell;
+  C->gy = (C->H + cell - 1) / cell;
+  int64_t ncell = (int64_t)C->gx * C->gy;
+  int64_t *cnt = (int64_t *)calloc(ncell + 1, sizeof(int64_t));
+  for (int pass = 0; pass < 2; ++pass) {
+    if (pass == 1) {
+      int64_t acc = 0;
+      for (int64_t c = 0; c < ncell; ++c) { int64_t v = cnt[c]; C->cstart[c] = acc; acc += v; cnt[c] = 0; }
+      C->cstart[ncell] = acc;
+      C->citems = (int32_t *)malloc(sizeof(int32_t) * (acc > 0 ? acc : 1));
+    }
+    for (int64_t i = 0; i < C->n; ++i) {
+      prim_t *p = &C->P[i];
+      if (!p->valid) continue;
+      int x0, x1, y0, y1;
+      if (p->whole) {
+        x0 = 0; x1 = C->gx - 1; y0 = 0; y1 = C->gy - 1;
+      } else {
+        double lx = floor(p->bx0 / cell), hx = floor(p->bx1 / cell);
+        double ly = floor(p->by0 / cell), hy = floor(p->by1 / cell);
+        if (hx < 0 || hy < 0 || lx > C->gx - 1 || ly > C->gy - 1) continue;
+        x0 = lx < 0 ? 0 : (int)lx; x1 = hx > C->gx - 1 ? C->gx - 1 : (int)hx;
+        y0 = ly < 0 ? 0 : (int)ly; y1 = hy > C->gy - 1 ? C->gy - 1 : (int)hy;
+      }
+      for (int yy = y0; yy <= y1; ++yy)
+        for (int xx = x0; xx <= x1; ++xx) {
+          int64_t c = (int64_t)yy * C->gx + xx;
+          if (pass == 0) cnt[c]++;
+          else C->citems[C->cstart[c] + cnt[c]++] = (int32_t)i;
+        }
+    }
+  }
+  int maxc = 0;
+  for (int64_t c = 0; c < ncell; ++c) {
+    int64_t v = C->cstart[c + 1] - C->cstart[c];
+    if (v > maxc) maxc = (int)v;
+  }
+  C->maxcell = maxc;
+  free(cnt);
+}
+
+/* Parameters are double arrays (float32 inputs widen exactly); the order key
+ * is the contract's binary32 depth of the mean rounded to binary32.
+ * cam: float32 R[9] t[3] fx fy cx cy; cfg: double[CF_COUNT]. */
+void *orc_prepare(int64_t n, const double *means, const double *log_scales, const double *quats,
+                  const double *logits, const double *sh, const uint8_t *types, int sh_deg,
+                  const float *cam, int W, int H, const double *cfg) {
+  orc_ctx *C = (orc_ctx *)calloc(1, sizeof(orc_ctx));
+  C->n = n; C->W = W; C->H = H; C->deg = sh_deg; C->nb = (sh_deg + 1) * (sh_deg + 1);
+  for (int k = 0; k < 9; ++k) C->R[k] = cam[k];
+  for (int k = 0; k < 3; ++k) C->t[k] = cam[9 + k];
+  C->fx = cam[12]; C->fy = cam[13]; C->cx = cam[14]; C->cy = cam[15];
+  memcpy(C->cam32, cam, sizeof(float) * 16);
+  memcpy(C->cfg, cfg, sizeof(double) * CF_COUNT);
+  C->P = (prim_t *)malloc(sizeof(prim_t) * (n > 0 ? n : 1));
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i)
+    prep_prim(C, i, means + 3 * i, log_scales + 3 * i, quats + 4 * i, logits[i],
+              sh + (int64_t)3 * C->nb * i, types[i]);
+  C->cell = 32;
+  C->cstart = (int64_t *)malloc(sizeof(int64_t) * ((int64_t)((W + 31) / 32) * ((H + 31) / 32) + 1));
+  build_grid(C);
+  return C;
+}
+
+/* Re-derive primitive i from new parameters (finite differences).  The grid
+ * is not rebuilt: the bbox padding covers perturbations of ~1e-4 px. */
+void orc_set_prim(void *ctx, int64_t i, const double *mean, const double *ls, const double *q,
+                  double logit, const double *sh, int type) {
+  orc_ctx *C = (orc_ctx *)ctx;
+  prep_prim(C, i, mean, ls, q, logit, sh, type);
+}
+
+void orc_free(void *ctx) {
+  orc_ctx *C = (orc_ctx *)ctx;
+  if (!C) return;
+  free(C->P); free(C->cstart); free(C->citems); free(C);
+}
+
+typedef struct { uint32_t key; int32_t id; double at, z; } contrib_t;
+
+static int cmp_contrib(const void *A, const void *B) {
+  const contrib_t *a = (const contrib_t *)A, *b = (const contrib_t *)B;
+  if (a->key != b->key) return a->key < b->key ? -1 : 1;
+  return a->id < b->id ? -1 : (a->id > b->id);
+}
+
+/* Unified distance (Eq. 1) and contribution (Sec. 3.1) of primitive p at the
+ * pixel centre (px, py).  Returns 1 if it contributes; *amb set if the
+ * decision sits inside an ambiguity band. */
+static int eval_pair(const orc_ctx *C, const prim_t *p, double px, double py,
+                     double *at_out, double *z_out, int *amb) {
+  double d, z;
+  if (p->type == 1) {
+    double dx = px - p->mx, dy = py - p->my;
+    d = p->ca * dx * dx + 2.0 * p->cb * dx * dy + p->cc * dy * dy;
+    z = p->Z;
+  } else {
+    /* ray-splat intersection (App. C): solve mu_c + u a + v b = tau ray */
+    double ray[3] = {(px - C->cx) / C->fx, (py - C->cy) / C->fy, 1.0};
+    double A[3][4] = {{p->a[0], p->b[0], -ray[0], -p->X},
+                      {p->a[1], p->b[1], -ray[1], -p->Y},
+                      {p->a[2], p->b[2], -ray[2], -p->Z}};
+    double scale = sqrt(p->a[0] * p->a[0] + p->a[1] * p->a[1] + p->a[2] * p->a[2]) *
+                   sqrt(p->b[0] * p->b[0] + p->b[1] * p->b[1] + p->b[2] * p->b[2]) *
+                   sqrt(ray[0] * ray[0] + ray[1] * ray[1] + 1.0);
+    double detv = 1.0;
+    for (int c = 0; c < 3; ++c) {
+      int piv = c;
+      for (int r = c + 1; r < 3; ++r)
+        if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
+      if (piv != c) {
+        for (int k = 0; k < 4; ++k) { double tmp = A[c][k]; A[c][k] = A[piv][k]; A[piv][k] = tmp; }
+        detv = -detv;
+      }
+      detv *= A[c][c];
+      if (A[c][c] == 0.0) return 0;
+      for (int r = c + 1; r < 3; ++r) {
+        double f = A[r][c] / A[c][c];
+        for (int k = c; k < 4; ++k) A[r][k] -= f * A[c][k];
+      }
+    }
+    if (fabs(detv) <= 1e-12 * scale) return 0;
+    double sol[3];
+    for (int r = 2; r >= 0; --r) {
+      double v = A[r][3];
+      for (int k = r + 1; k < 3; ++k) v -= A[r][k] * sol[k];
+      sol[r] = v / A[r][r];
+    }
+    double u = sol[0], v = sol[1];
+    z = sol[2];
+    d = u * u + v * v;
+    double nearz = C->cfg[CF_NEAR];
+    if (fabs(z - nearz) <= AMB_NEAR_REL * fmax(1.0, nearz)) {
+      double ag = p->alpha * exp(-0.5 * d);
+      if (ag >= C->cfg[CF_ALPHA_MIN] * (1.0 - AMB_ALPHA_REL)) *amb = 1;
+    }
+    if (!(z > nearz)) return 0;
+  }
+  double ag = p->alpha * exp(-0.5 * d);
+  double amin = C->cfg[CF_ALPHA_MIN];
+  if (fabs(ag - amin) <= AMB_ALPHA_REL * amin) *amb = 1;
+  if (!(ag >= amin)) return 0;
+  if (p->ndot < AMB_FLIP) *amb = 1;
+  if (p->amb_near) {
+    *amb = 1;
+    if (!(p->Z > C->cfg[CF_NEAR])) return 0;
+  }
+  double amax = C->cfg[CF_ALPHA_MAX];
+  *at_out = ag < amax ? ag : amax;
+  *z_out = z;
+  return 1;
+}
+
+/* Render npix pixels (pix: npix x 2 int32 pixel indices, or NULL = full frame
+ * in row-major order).  out: npix x 10 doubles
+ *   [r, g, b, depth, nx, ny, nz, alpha, T_final, n_contrib]
+ * amb: npix flags (1 = ambiguous, see the bands above). */
+void orc_render(void *ctx, int64_t npix, const int32_t *pix, double *out, uint8_t *amb) {
+  orc_ctx *C = (orc_ctx *)ctx;
+  if (!pix) npix = (int64_t)C->W * C->H;
+#pragma omp parallel
+  {
+    contrib_t *buf = (contrib_t *)malloc(sizeof(contrib_t) * (C->maxcell > 0 ? C->maxcell : 1));
+#pragma omp for schedule(dynamic, 64)
+    for (int64_t q = 0; q < npix; ++q) {
+      int ix, iy;
+      if (pix) { ix = pix[2 * q]; iy = pix[2 * q + 1]; }
+      else { ix = (int)(q % C->W); iy = (int)(q / C->W); }
+      double px = ix + 0.5, py = iy + 0.5;
+      int cxi = ix / C->cell, cyi = iy / C->cell;
+      int64_t c = (int64_t)cyi * C->gx + cxi;
+      int cnt = 0, am = 0;
+      for (int64_t k = C->cstart[c]; k < C->cstart[c + 1]; ++k) {
+        int32_t id = C->citems[k];
+        const prim_t *p = &C->P[id];
+        if (!p->valid) continue;
+        double at, z;
+        if (eval_pair(C, p, px, py, &at, &z, &am)) {
+          buf[cnt].key = p->key; buf[cnt].id = id; buf[cnt].at = at; buf[cnt].z = z;
+          cnt++;
+        }
+      }
+      qsort(buf, cnt, sizeof(contrib_t), cmp_contrib);
+      /* front-to-back alpha blending, Eq. 2 */
+      double T = 1.0, Cc[3] = {0, 0, 0}, D = 0, Nn[3] = {0, 0, 0};
+      int used = 0;
+      const double Tmin = C->cfg[CF_T_MIN];
+      for (int k = 0; k < cnt; ++k) {
+        const prim_t *p = &C->P[buf[k].id];
+        double at = buf[k].at;
+        double Tn = T * (1.0 - at);
+        if (fabs(Tn - Tmin) <= AMB_T_REL * Tmin) am = 1;
+        if (Tn < Tmin) break;
+        double w = at * T;
+        for (int r = 0; r < 3; ++r) { Cc[r] += w * p->col[r]; Nn[r] += w * p->nrm[r]; }
+        D += w * buf[k].z;
+        T = Tn;
+        used++;
+      }
+      double *o = out + 10 * q;
+      o[0] = Cc[0] + T * C->cfg[CF_BG0];
+      o[1] = Cc[1] + T * C->cfg[CF_BG1];
+      o[2] = Cc[2] + T * C->cfg[CF_BG2];
+      o[3] = D;
+      o[4] = Nn[0]; o[5] = Nn[1]; o[6] = Nn[2];
+      o[7] = 1.0 - T;
+      o[8] = T;
+      o[9] = used;
+      amb[q] = (uint8_t)am;
+    }
+    free(buf);
+  }
+}
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* (4) Adaptive Type Exchange, Sec. 3.2 and App. D, in FP64.                 */
+/* mode 0: erank rule with threshold theta (Eq. 3): 3D (t=1) with erank <    */
+/*         theta -> 2D; 2D with erank > theta -> 3D.                         */
+/* mode 1: flip exactly the primitives whose mask byte is non-zero.          */
+/* 3D->2D reparameterises S* = P S P^T, R* = R P^T (Eqs. 4-5); 2D->3D keeps  */
+/* every parameter and flips the flag.  Outputs are fresh arrays.            */
+/* ------------------------------------------------------------------------ */
+double orc_erank(double lsx, double lsy, double lsz) {
+  double q[3] = {exp(2 * lsx), exp(2 * lsy), exp(2 * lsz)};
+  double s = q[0] + q[1] + q[2];
+  double H = 0;
+  for (int k = 0; k < 3; ++k) {
+    double p = q[k] / s;
+    if (p > 0) H -= p * log(p);
+  }
+  return exp(H);
+}
+
+static void qmul(const double a[4], const double b[4], double o[4]) {
+  o[0] = a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+  o[1] = a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2];
+  o[2] = a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1];
+  o[3] = a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
+}
+
+int64_t orc_exchange(int64_t n, const float *log_scales, const float *quats, const uint8_t *types,
+                     int mode, double theta, const uint8_t *mask,
+                     double *ls_out, double *q_out, uint8_t *t_out) {
+  int64_t flips = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    double ls[3] = {log_scales[3 * i], log_scales[3 * i + 1], log_scales[3 * i + 2]};
+    double q[4] = {quats[4 * i], quats[4 * i + 1], quats[4 * i + 2], quats[4 * i + 3]};
+    int t = types[i];
+    int flip;
+    if (mode == 0) {
+      double er = orc_erank(ls[0], ls[1], ls[2]);
+      flip = (t == 1) ? (er < theta) : (er > theta);
+    } else {
+      flip = mask[i] != 0;
+    }
+    if (flip && t == 1) {
+      /* move the least significant scale to z */
+      if (ls[2] <= ls[0] && ls[2] <= ls[1]) {
+        /* already on z: identity permutation */
+      } else if (ls[0] <= ls[1]) {
+        /* P_x: S* = diag(sy, sz, sx); R(p) = P_x^T for p = (1/2)(1,1,1,1) */
+        double p[4] = {0.5, 0.5, 0.5, 0.5}, o[4];
+        double nls[3] = {ls[1], ls[2], ls[0]};
+        qmul(q, p, o);
+        memcpy(ls, nls, sizeof(nls)); memcpy(q, o, sizeof(o));
+      } else {
+        /* P_y: S* = diag(sz, sx, sy); R(p) = P_y^T for p = (1/2)(1,-1,-1,-1) */
+        double p[4] = {0.5, -0.5, -0.5, -0.5}, o[4];
+        double nls[3] = {ls[2], ls[0], ls[1]};
+        qmul(q, p, o);
+        memcpy(ls, nls, sizeof(nls)); memcpy(q, o, sizeof(o));
+      }
+    }
+    if (flip) { t = 1 - t; flips++; }
+    for (int k = 0; k < 3; ++k) ls_out[3 * i + k] = ls[k];
+    for (int k = 0; k < 4; ++k) q_out[4 * i + k] = q[k];
+    t_out[i] = (uint8_t)t;
+  }
+  return flips;
+}

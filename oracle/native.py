@@ -1,0 +1,217 @@
+"""ctypes front end of the C oracle (hgs_oracle.c).  Test infrastructure only.
+
+Functions and what pins them (tests/test_oracle_*.py):
+  Oracle.render      FP64 per-pixel renderer, Eq. 1, Sec. 3.1 contribution,
+                     Eq. 2 blending, App. C projections.  Pinned by closed forms
+                     (isotropic 3D Gaussian, face-on surfel), the edge-on surfel
+                     vanishing, 3D->2D convergence as s_z -> 0, brute-force
+                     compositing, order-of-input invariance, and the
+                     independent torch formulation (autograd_ref).
+  contract_bin       FP32 binning contract.  Pinned by conservativeness against
+                     the FP64 renderer and by exp/log accuracy against libm.
+  tile_lists         Sort of the contract's (tile | depth bits, id) pairs:
+                     numpy lexsort, a library primitive.
+  sh_basis           Real SH basis (Sec. 3.1 "decoded from f"), pinned against
+                     scipy's complex spherical harmonics and orthonormality.
+  exchange / erank   Eqs. 3-5, App. D.  Pinned by the erank values the paper
+                     states (3 isotropic, 2 flat, ~2.6 crossing) and by
+                     Sigma* = Sigma, det R* > 0.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        P = C.c_void_p
+        L.orc_prepare.restype = P
+        L.orc_prepare.argtypes = [C.c_int64, P, P, P, P, P, P, C.c_int, P, C.c_int, C.c_int, P]
+        L.orc_render.restype = None
+        L.orc_render.argtypes = [P, C.c_int64, P, P, P]
+        L.orc_set_prim.restype = None
+        L.orc_set_prim.argtypes = [P, C.c_int64, P, P, P, C.c_double, P, C.c_int]
+        L.orc_free.restype = None
+        L.orc_free.argtypes = [P]
+        L.orc_contract_bin.restype = None
+        L.orc_contract_bin.argtypes = [C.c_int64, P, P, P, P, P, P, C.c_int, C.c_int, C.c_int, P, P, P, P]
+        L.orc_contract_exp.restype = C.c_float
+        L.orc_contract_exp.argtypes = [C.c_float]
+        L.orc_contract_log.restype = C.c_float
+        L.orc_contract_log.argtypes = [C.c_float]
+        L.orc_sh_basis.restype = None
+        L.orc_sh_basis.argtypes = [C.c_int, C.c_int64, P, P]
+        L.orc_erank.restype = C.c_double
+        L.orc_erank.argtypes = [C.c_double, C.c_double, C.c_double]
+        L.orc_exchange.restype = C.c_int64
+        L.orc_exchange.argtypes = [C.c_int64, P, P, P, C.c_int, C.c_double, P, P, P, P]
+        L.orc_num_threads.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+OUT_FIELDS = ("r", "g", "b", "depth", "nx", "ny", "nz", "alpha", "T", "n_contrib")
+
+
+class Oracle:
+    """FP64 renderer context for one (scene, camera, config)."""
+
+    def __init__(self, scene, cam, cfg):
+        L = lib()
+        self.n = scene.n
+        self.W, self.H = cam.width, cam.height
+        self.deg = scene.sh_degree
+        self._keep = [np.ascontiguousarray(scene.means, np.float64),
+                      np.ascontiguousarray(scene.log_scales, np.float64),
+                      np.ascontiguousarray(scene.quats, np.float64),
+                      np.ascontiguousarray(scene.opacity_logits, np.float64),
+                      np.ascontiguousarray(scene.sh, np.float64),
+                      np.ascontiguousarray(scene.types, np.uint8),
+                      cam.as_array16(), cfg.as_oracle_array()]
+        m, ls, q, lg, sh, ty, cam16, cf = self._keep
+        self.ctx = L.orc_prepare(self.n, _p(m), _p(ls), _p(q), _p(lg), _p(sh), _p(ty),
+                                 self.deg, _p(cam16), self.W, self.H, _p(cf))
+
+    def close(self):
+        if self.ctx:
+            lib().orc_free(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def render(self, pixels=None):
+        """pixels: (P, 2) int pixel indices (x, y) or None for the full frame
+        (row-major).  Returns (out (P, 10) float64, amb (P,) bool)."""
+        if pixels is None:
+            npix = self.W * self.H
+            pp = None
+        else:
+            pixels = np.ascontiguousarray(pixels, np.int32)
+            npix = len(pixels)
+            pp = _p(pixels)
+        out = np.zeros((npix, 10), np.float64)
+        amb = np.zeros(npix, np.uint8)
+        lib().orc_render(self.ctx, npix, pp, _p(out), _p(amb))
+        return out, amb.astype(bool)
+
+    def render_maps(self):
+        """Full frame as planar maps: dict rgb (3,H,W), depth, normal (3,H,W),
+        alpha, T, n_contrib, amb (H,W)."""
+        out, amb = self.render(None)
+        H, W = self.H, self.W
+        o = out.reshape(H, W, 10)
+        return {"rgb": np.moveaxis(o[..., 0:3], -1, 0), "depth": o[..., 3],
+                "normal": np.moveaxis(o[..., 4:7], -1, 0), "alpha": o[..., 7],
+                "T": o[..., 8], "n_contrib": o[..., 9], "amb": amb.reshape(H, W)}
+
+    def set_prim(self, i, mean, log_scale, quat, logit, sh, type_):
+        a = [np.ascontiguousarray(x, np.float64) for x in (mean, log_scale, quat, sh)]
+        lib().orc_set_prim(self.ctx, int(i), _p(a[0]), _p(a[1]), _p(a[2]), float(logit),
+                           _p(a[3]), int(type_))
+
+
+def contract_bin(scene, cam, cfg):
+    """FP32 binning contract for every primitive: (depth_bits u32 (N,),
+    rect int32 (N,4) = tx0,tx1,ty0,ty1 (-1 if not binned), touched int64)."""
+    n = scene.n
+    arrs = [np.ascontiguousarray(scene.means, np.float32),
+            np.ascontiguousarray(scene.log_scales, np.float32),
+            np.ascontiguousarray(scene.quats, np.float32),
+            np.ascontiguousarray(scene.opacity_logits, np.float32),
+            np.ascontiguousarray(scene.types, np.uint8)]
+    cam16 = cam.as_array16()
+    cfg32 = np.array([cfg.near, cfg.alpha_min, cfg.dilation], np.float32)
+    db = np.zeros(n, np.uint32)
+    rect = np.zeros((n, 4), np.int32)
+    touched = np.zeros(n, np.int64)
+    lib().orc_contract_bin(n, *[_p(a) for a in arrs], _p(cam16), cam.width, cam.height,
+                           cfg.tile, _p(cfg32), _p(db), _p(rect), _p(touched))
+    return db, rect, touched
+
+
+def tile_lists(scene, cam, cfg):
+    """The binned instance list the contract defines: keys (K,) uint64 =
+    tile_id << 32 | depth bits, vals (K,) uint32 primitive ids, sorted by
+    (key, id); ranges (tiles, 2) uint32 [start, end)."""
+    db, rect, touched = contract_bin(scene, cam, cfg)
+    T = cfg.tile
+    TX = (cam.width + T - 1) // T
+    TY = (cam.height + T - 1) // T
+    ids = np.nonzero(touched > 0)[0]
+    cnt = touched[ids]
+    K = int(cnt.sum())
+    rep = np.repeat(ids, cnt)
+    # local index of each instance within its primitive's rectangle
+    start = np.repeat(np.cumsum(cnt) - cnt, cnt)
+    loc = np.arange(K, dtype=np.int64) - start
+    r = rect[rep]
+    wdt = (r[:, 1] - r[:, 0] + 1).astype(np.int64)
+    tx = r[:, 0] + loc % wdt
+    ty = r[:, 2] + loc // wdt
+    tile = ty.astype(np.uint64) * np.uint64(TX) + tx.astype(np.uint64)
+    keys = (tile << np.uint64(32)) | db[rep].astype(np.uint64)
+    order = np.lexsort((rep, keys))
+    keys = keys[order]
+    vals = rep[order].astype(np.uint32)
+    tiles_of = (keys >> np.uint64(32)).astype(np.int64)
+    edges = np.searchsorted(tiles_of, np.arange(TX * TY + 1))
+    ranges = np.stack([edges[:-1], edges[1:]], axis=1).astype(np.uint32)
+    return keys, vals, ranges, (db, rect, touched)
+
+
+def contract_exp(x: float) -> float:
+    return float(lib().orc_contract_exp(float(x)))
+
+
+def contract_log(x: float) -> float:
+    return float(lib().orc_contract_log(float(x)))
+
+
+def sh_basis(deg: int, dirs: np.ndarray) -> np.ndarray:
+    dirs = np.ascontiguousarray(dirs, np.float64)
+    nb = (deg + 1) ** 2
+    out = np.zeros((len(dirs), nb), np.float64)
+    lib().orc_sh_basis(deg, len(dirs), _p(dirs), _p(out))
+    return out
+
+
+def erank(lsx, lsy, lsz) -> float:
+    return float(lib().orc_erank(float(lsx), float(lsy), float(lsz)))
+
+
+def exchange(log_scales, quats, types, mode="erank", theta=2.05, mask=None):
+    """Adaptive Type Exchange in FP64.  Returns (log_scales f64, quats f64,
+    types u8, n_flipped)."""
+    ls = np.ascontiguousarray(log_scales, np.float32)
+    q = np.ascontiguousarray(quats, np.float32)
+    t = np.ascontiguousarray(types, np.uint8)
+    n = len(t)
+    m = np.ascontiguousarray(mask if mask is not None else np.zeros(n), np.uint8)
+    ls_o = np.zeros((n, 3), np.float64)
+    q_o = np.zeros((n, 4), np.float64)
+    t_o = np.zeros(n, np.uint8)
+    nf = lib().orc_exchange(n, _p(ls), _p(q), _p(t), 0 if mode == "erank" else 1, float(theta),
+                            _p(m), _p(ls_o), _p(q_o), _p(t_o))
+    return ls_o, q_o, t_o, int(nf)

@@ -1,0 +1,317 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics,
+not by the oracle itself.  CPU only."""
+import math
+
+import numpy as np
+import pytest
+
+import synthetic as S
+from oracle import autograd_ref as AR
+from oracle import native as O
+
+CFG = S.RenderConfig()
+
+
+def one_prim_scene(mean, log_scales, quat, logit, rgb=(0.8, 0.4, 0.2), type_=1, deg=0):
+    k = (deg + 1) ** 2
+    sh = np.zeros((1, k, 3), np.float32)
+    sh[0, 0, :] = (np.asarray(rgb) - 0.5) / (0.5 / math.sqrt(math.pi))
+    return S.Scene(np.array([mean], np.float32), np.array([log_scales], np.float32),
+                   np.array([quat], np.float32), np.array([logit], np.float32), sh,
+                   np.array([type_], np.uint8), deg)
+
+
+def cat_scenes(scenes):
+    return S.Scene(*(np.concatenate([getattr(s, f) for s in scenes]) for f in
+                     ("means", "log_scales", "quats", "opacity_logits", "sh", "types")),
+                   scenes[0].sh_degree)
+
+
+def pixel_centres(cam):
+    yy, xx = np.mgrid[0:cam.height, 0:cam.width]
+    return xx + 0.5, yy + 0.5
+
+
+# ---------------------------------------------------------------------------
+# contract exp / log against libm (error bound, not self-consistency)
+# ---------------------------------------------------------------------------
+def test_contract_exp_log_accuracy():
+    rng = np.random.default_rng(0)
+    xs = np.concatenate([rng.uniform(-87, 88, 4000), rng.uniform(-1, 1, 2000),
+                         [0.0, 1.0, -1.0, 0.5, -87.0, 88.0]]).astype(np.float32)
+    for x in xs:
+        got = O.contract_exp(x)
+        ref = math.exp(float(x))
+        assert abs(got - ref) <= 4 * np.spacing(np.float32(ref)), (x, got, ref)
+    ys = np.concatenate([rng.uniform(1, 255, 4000), np.exp(rng.uniform(-30, 30, 2000)),
+                         [1.0, 2.0, 255.0, math.sqrt(2)]]).astype(np.float32)
+    for y in ys:
+        got = O.contract_log(y)
+        ref = math.log(float(y))
+        # absolute bound near 1 (log -> 0), relative elsewhere
+        assert abs(got - ref) <= 4 * np.spacing(np.float32(max(abs(ref), 1e-3))) + 2e-8, (y, got, ref)
+    assert O.contract_exp(0.0) == 1.0 and O.contract_log(1.0) == 0.0
+
+
+# ---------------------------------------------------------------------------
+# SH basis: scipy's complex harmonics and orthonormality
+# ---------------------------------------------------------------------------
+def _scipy_real_sh(deg, dirs):
+    from scipy.special import sph_harm_y
+    theta = np.arccos(np.clip(dirs[:, 2], -1, 1))
+    phi = np.mod(np.arctan2(dirs[:, 1], dirs[:, 0]), 2 * np.pi)
+    cols = []
+    for l in range(deg + 1):
+        for m in range(-l, l + 1):
+            Y = sph_harm_y(l, abs(m), theta, phi)
+            if m > 0:
+                cols.append(math.sqrt(2) * Y.real)
+            elif m < 0:
+                cols.append(math.sqrt(2) * Y.imag)
+            else:
+                cols.append(Y.real)
+    return np.stack(cols, 1)
+
+
+def test_sh_basis_matches_scipy_and_is_orthonormal():
+    rng = np.random.default_rng(1)
+    d = rng.normal(size=(500, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    ref = _scipy_real_sh(3, d)
+    c_basis = O.sh_basis(3, d)
+    import torch
+    t_basis = AR.sh_basis(3, torch.tensor(d)).numpy()
+    np.testing.assert_allclose(c_basis, ref, atol=1e-12)
+    np.testing.assert_allclose(t_basis, ref, atol=1e-12)
+    # orthonormality on the sphere: Gauss-Legendre in cos(theta) x uniform phi
+    xg, wg = np.polynomial.legendre.leggauss(16)
+    nphi = 32
+    phi = (np.arange(nphi) + 0.5) * 2 * np.pi / nphi
+    ct, ph = np.meshgrid(xg, phi, indexing="ij")
+    st = np.sqrt(1 - ct ** 2)
+    dirs = np.stack([st * np.cos(ph), st * np.sin(ph), ct], -1).reshape(-1, 3)
+    w = (wg[:, None] * np.full(nphi, 2 * np.pi / nphi)[None]).reshape(-1)
+    B = O.sh_basis(3, dirs)
+    G = (B * w[:, None]).T @ B
+    np.testing.assert_allclose(G, np.eye(16), atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# closed forms
+# ---------------------------------------------------------------------------
+def test_isotropic_3d_gaussian_closed_form():
+    """On the optical axis at depth z with isotropic scale s the EWA
+    covariance is (f s / z)^2 I exactly (App. C, Eq. 13), so each pixel is
+    alpha exp(-r^2 / (2 sigma^2)) up to the 1/255 cutoff (Sec. 3.1)."""
+    cam = S.pinhole(96, 96, 60.0)
+    z, s, logit = 3.0, 0.05, 1.2
+    sc = one_prim_scene((0.0, 0.0, z), (math.log(s),) * 3, (1, 0, 0, 0), logit)
+    m = O.Oracle(sc, cam, CFG).render_maps()
+    X, Y = pixel_centres(cam)
+    sig = cam.fx * np.float64(np.float32(s)) / z
+    # exp(log s) in float32 -> double: use the same s the oracle sees
+    s64 = math.exp(float(np.float32(math.log(s))))
+    sig = cam.fx * s64 / z
+    r2 = (X - cam.cx) ** 2 + (Y - cam.cy) ** 2
+    alpha = 1 / (1 + math.exp(-float(np.float32(logit))))
+    a = alpha * np.exp(-r2 / (2 * sig ** 2))
+    a = np.where(a >= CFG.alpha_min, np.minimum(a, CFG.alpha_max), 0.0)
+    assert not m["amb"].any()
+    np.testing.assert_allclose(m["alpha"], a, atol=1e-12)
+    np.testing.assert_allclose(m["depth"], a * z, atol=1e-12)
+    col = 0.5 + (0.5 / math.sqrt(math.pi)) * float(np.float32((0.8 - 0.5) / (0.5 / math.sqrt(math.pi))))
+    np.testing.assert_allclose(m["rgb"][0], a * col, atol=1e-12)
+    # isotropic: the normal is the z axis (tie rule) facing the camera
+    np.testing.assert_allclose(m["normal"][2], -a, atol=1e-12)
+
+
+@pytest.mark.parametrize("twist", [0.0, 0.7])
+def test_face_on_surfel_closed_form(twist):
+    """A surfel facing the camera at depth z: the ray through pixel p meets the
+    plane at ((p-c) z / f); (u, v) are that point in the splat's frame divided
+    by (s_u, s_v) (App. C), so d = u^2 + v^2 in closed form per axis."""
+    cam = S.pinhole(80, 64, 55.0)
+    z, su, sv, logit = 2.5, 0.08, 0.03, 2.0
+    cx0, cy0 = 0.1, -0.05
+    q = (math.cos(twist / 2), 0.0, 0.0, math.sin(twist / 2))
+    sc = one_prim_scene((cx0, cy0, z), (math.log(su), math.log(sv), S.SURFEL_LOG_SZ), q, logit, type_=0)
+    m = O.Oracle(sc, cam, CFG).render_maps()
+    X, Y = pixel_centres(cam)
+    mu = sc.means[0].astype(np.float64)
+    PX = (X - cam.cx) / cam.fx * mu[2] - mu[0]
+    PY = (Y - cam.cy) / cam.fy * mu[2] - mu[1]
+    q64 = sc.quats[0].astype(np.float64)
+    q64 /= np.linalg.norm(q64)
+    ang = 2 * math.atan2(q64[3], q64[0])
+    u = (math.cos(ang) * PX + math.sin(ang) * PY) / math.exp(float(sc.log_scales[0, 0]))
+    v = (-math.sin(ang) * PX + math.cos(ang) * PY) / math.exp(float(sc.log_scales[0, 1]))
+    alpha = 1 / (1 + math.exp(-float(sc.opacity_logits[0])))
+    a = alpha * np.exp(-0.5 * (u * u + v * v))
+    a = np.where(a >= CFG.alpha_min, np.minimum(a, CFG.alpha_max), 0.0)
+    ok = ~m["amb"]
+    assert ok.mean() > 0.99
+    np.testing.assert_allclose(m["alpha"][ok], a[ok], atol=1e-12)
+    np.testing.assert_allclose(m["depth"][ok], (a * mu[2])[ok], atol=1e-11)
+    np.testing.assert_allclose(m["normal"][2][ok], -a[ok], atol=1e-12)
+
+
+def test_edge_on_surfel_vanishes():
+    """A surfel whose plane contains the camera centre: every ray meets the
+    plane at the camera centre (depth 0) or lies in it, so the contribution is
+    exactly zero everywhere."""
+    cam = S.pinhole(64, 64, 60.0)
+    # plane x = 0 (normal along x): local z axis -> world x
+    q = (math.cos(math.pi / 4), 0.0, math.sin(math.pi / 4), 0.0)
+    sc = one_prim_scene((0.0, 0.05, 3.0), (math.log(0.5), math.log(0.5), S.SURFEL_LOG_SZ), q, 3.0, type_=0)
+    m = O.Oracle(sc, cam, CFG).render_maps()
+    assert np.all(m["alpha"] == 0.0) and np.all(m["rgb"] == 0.0)
+    # same splat rotated a little: now visible
+    q2 = (math.cos(math.pi / 4 - 0.05), 0.0, math.sin(math.pi / 4 - 0.05), 0.0)
+    sc2 = one_prim_scene((0.0, 0.05, 3.0), (math.log(0.5), math.log(0.5), S.SURFEL_LOG_SZ), q2, 3.0, type_=0)
+    assert O.Oracle(sc2, cam, CFG).render_maps()["alpha"].max() > 0.5
+
+
+def test_3d_converges_to_surfel_when_fronto_parallel():
+    """A fronto-parallel 3D Gaussian whose z scale tends to 0 renders as the
+    surfel with the same parameters: on a plane of constant depth the affine
+    projection is exact.  Off the optical axis the difference is O(s_z^2)."""
+    cam = S.pinhole(96, 80, 60.0)
+    mean, q = (0.35, -0.2, 3.0), (math.cos(0.3), 0.0, 0.0, math.sin(0.3))
+    ls = [math.log(0.06), math.log(0.025), 0.0]
+    diffs = []
+    for sz in (1e-2, 1e-3, 1e-4):
+        ls[2] = math.log(sz)
+        g3 = O.Oracle(one_prim_scene(mean, ls, q, 1.5, type_=1), cam, CFG).render_maps()
+        g2 = O.Oracle(one_prim_scene(mean, ls, q, 1.5, type_=0), cam, CFG).render_maps()
+        ok = ~(g3["amb"] | g2["amb"])
+        diffs.append(np.abs(g3["alpha"] - g2["alpha"])[ok].max())
+    assert diffs[-1] < 1e-6
+    assert diffs[0] > diffs[1] > diffs[2]
+
+
+def test_oblique_flat_gaussian_differs_from_surfel_except_at_centre():
+    """The affine projection distorts everywhere except at the centre
+    (Sec. 3.1): an oblique flat 3D Gaussian and the surfel with the same
+    parameters agree at the centre pixel and differ around it."""
+    cam = S.pinhole(128, 128, 70.0)
+    z = 2.0
+    # centre projects exactly onto the centre of pixel (70, 58)
+    px, py = 70.5, 58.5
+    mean = ((px - cam.cx) / cam.fx * z, (py - cam.cy) / cam.fy * z, z)
+    mean = tuple(float(np.float32(v)) for v in mean)
+    ang = 1.1  # strong tilt about the x axis
+    q = (math.cos(ang / 2), math.sin(ang / 2), 0.0, 0.0)
+    ls = (math.log(0.25), math.log(0.25), math.log(1e-6))
+    g3 = O.Oracle(one_prim_scene(mean, ls, q, 2.0, type_=1), cam, CFG).render_maps()
+    g2 = O.Oracle(one_prim_scene(mean, ls, q, 2.0, type_=0), cam, CFG).render_maps()
+    assert abs(g3["alpha"][58, 70] - g2["alpha"][58, 70]) < 1e-6
+    assert np.abs(g3["alpha"] - g2["alpha"]).max() > 0.05
+
+
+def test_bruteforce_blend_eq2():
+    """Eq. 2 enumerated term by term, C = sum_i c_i a_i prod_{j<i}(1 - a_j),
+    over up to 8 face-on surfels with closed-form contributions, sorted by
+    depth; no transmittance termination is reached."""
+    cam = S.pinhole(16, 16, 60.0)
+    rng = np.random.default_rng(5)
+    prims, closed = [], []
+    X, Y = pixel_centres(cam)
+    for i in range(8):
+        z = 2.0 + 0.25 * i
+        mu = (rng.uniform(-0.2, 0.2), rng.uniform(-0.2, 0.2), z)
+        s = (rng.uniform(0.1, 0.3), rng.uniform(0.1, 0.3))
+        logit = rng.uniform(-1.5, 0.0)
+        rgb = rng.uniform(0, 1, 3)
+        sc = one_prim_scene(mu, (math.log(s[0]), math.log(s[1]), S.SURFEL_LOG_SZ), (1, 0, 0, 0), logit, rgb, type_=0)
+        prims.append(sc)
+        m = sc.means[0].astype(np.float64)
+        u = ((X - cam.cx) / cam.fx * m[2] - m[0]) / math.exp(float(sc.log_scales[0, 0]))
+        v = ((Y - cam.cy) / cam.fy * m[2] - m[1]) / math.exp(float(sc.log_scales[0, 1]))
+        a = (1 / (1 + math.exp(-float(sc.opacity_logits[0])))) * np.exp(-0.5 * (u * u + v * v))
+        a = np.where(a >= CFG.alpha_min, np.minimum(a, CFG.alpha_max), 0.0)
+        col = 0.5 + (0.5 / math.sqrt(math.pi)) * sc.sh[0, 0].astype(np.float64)
+        closed.append((z, a, col))
+    order = rng.permutation(8)
+    scene = cat_scenes([prims[i] for i in order])
+    m = O.Oracle(scene, cam, CFG).render_maps()
+    closed.sort(key=lambda t: t[0])
+    C = np.zeros((3, 16, 16))
+    for i, (z, a, col) in enumerate(closed):
+        trans = np.ones((16, 16))
+        for j in range(i):
+            trans = trans * (1 - closed[j][1])
+        C += col[:, None, None] * a * trans
+    assert not m["amb"].any()
+    np.testing.assert_allclose(m["rgb"], C, atol=1e-12)
+
+
+def test_order_of_input_invariance():
+    sc, cam = S.tiny_scene(0)
+    m0 = O.Oracle(sc, cam, CFG).render_maps()
+    perm = np.random.default_rng(9).permutation(sc.n)
+    m1 = O.Oracle(sc.subset(perm), cam, CFG).render_maps()
+    ok = ~(m0["amb"] | m1["amb"])
+    for k in ("rgb", "depth", "normal", "alpha"):
+        np.testing.assert_allclose(m0[k][..., ok], m1[k][..., ok], atol=1e-13)
+    # the contract's lists are identical up to the relabelling
+    k0, v0, r0, _ = O.tile_lists(sc, cam, CFG)
+    k1, v1, r1, _ = O.tile_lists(sc.subset(perm), cam, CFG)
+    np.testing.assert_array_equal(k0, k1)
+    np.testing.assert_array_equal(r0, r1)
+    np.testing.assert_array_equal(v0, perm[v1])
+
+
+def test_torch_formulation_matches_c_oracle():
+    """Two independent FP64 formulations of the same image function."""
+    sc, cam = S.tiny_scene(0)
+    m = O.Oracle(sc, cam, CFG).render_maps()
+    r = AR.render(sc, cam, CFG)
+    H, W = cam.height, cam.width
+    np.testing.assert_allclose(r["rgb"].detach().numpy().T.reshape(3, H, W), m["rgb"], atol=1e-12)
+    np.testing.assert_allclose(r["depth"].detach().numpy().reshape(H, W), m["depth"], atol=1e-12)
+    np.testing.assert_allclose(r["normal"].detach().numpy().T.reshape(3, H, W), m["normal"], atol=1e-12)
+    np.testing.assert_allclose(r["alpha"].detach().numpy().reshape(H, W), m["alpha"], atol=1e-12)
+
+
+def test_contract_is_conservative():
+    """Every (pixel, primitive) pair whose FP64 contribution clears the 1/255
+    threshold outside the ambiguity band lies in a tile of the primitive's
+    FP32 contract rectangle."""
+    for seed in (0, 1):
+        sc, cam = S.tiny_scene(seed)
+        db, rect, touched = O.contract_bin(sc, cam, CFG)
+        yy, xx = np.mgrid[0:cam.height, 0:cam.width]
+        pix = np.stack([xx.ravel(), yy.ravel()], 1)
+        araw, ok = AR.pair_alpha(sc, cam, CFG, pix)
+        sure = ok & (araw >= CFG.alpha_min * (1 + 2e-4))
+        p_idx, g_idx = np.nonzero(sure)
+        tx = pix[p_idx, 0] // CFG.tile
+        ty = pix[p_idx, 1] // CFG.tile
+        r = rect[g_idx]
+        inside = (r[:, 0] <= tx) & (tx <= r[:, 1]) & (r[:, 2] <= ty) & (ty <= r[:, 3])
+        assert inside.all(), (seed, np.count_nonzero(~inside))
+        assert len(p_idx) > 1000
+
+
+def test_tile_list_structure():
+    sc, cam = S.tiny_scene(2)
+    keys, vals, ranges, (db, rect, touched) = O.tile_lists(sc, cam, CFG)
+    assert len(keys) == touched.sum()
+    assert np.all(np.diff(keys.astype(np.float64)) >= 0)
+    TX = (cam.width + 15) // 16
+    for t in range(len(ranges)):
+        s, e = ranges[t]
+        assert np.all((keys[s:e] >> np.uint64(32)) == t)
+        d = (keys[s:e] & np.uint64(0xffffffff)).view(np.uint64)
+        assert np.all(d == db[vals[s:e]])
+        tx, ty = t % TX, t // TX
+        rr = rect[vals[s:e]]
+        assert np.all((rr[:, 0] <= tx) & (tx <= rr[:, 1]) & (rr[:, 2] <= ty) & (ty <= rr[:, 3]))
+
+
+def test_contract_depth_order_matches_fp64_depth():
+    sc, cam = S.tiny_scene(3)
+    db, _, _ = O.contract_bin(sc, cam, CFG)
+    z32 = db.view(np.float32).astype(np.float64)
+    z64 = sc.means.astype(np.float64) @ np.asarray(cam.R, np.float64)[2] + float(cam.t[2])
+    np.testing.assert_allclose(z32, z64, rtol=2e-7)
