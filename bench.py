@@ -1,0 +1,373 @@
+"""Benchmark of the hybrid 2D/3D Gaussian rasterizer on GB300.
+
+Default workload: the scene-scale training step -- 3,000,000 primitives (70%
+3D Gaussians, 30% 2D surfels, SH degree 3) on a unit-sphere shell plus ground
+plane, one 1600x1064 pinhole view (fov 50 deg), forward + backward through the
+autograd Function on an L1 loss against a random target image, with a
+mask-mode type exchange of 1% of the flags every 100 steps.  One step is one
+pass of the whole hot path: preprocess, binning (scan, emit, radix sort, tile
+ranges), blend forward, blend backward, preprocess backward (+ exchange).
+
+Prints one JSON line (see the keys below).  `--impl reference` times the CPU
+oracle instead (the reference arm of this build).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd ms/iter @3M prims 1600x1064; served frames/s + p50/p99 latency"
+WORKLOAD = "scene-scale training step: 3M prims (70% 3D / 30% 2D, SH deg 3), 1600x1064, fwd+bwd, L1 loss"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=3_000_000)
+    p.add_argument("--width", type=int, default=1600)
+    p.add_argument("--height", type=int, default=1064)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-sample-pixels", type=int, default=20000)
+    p.add_argument("--profile-phases", action="store_true", default=True)
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed
+    region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.samples = []
+        self.proc = None
+        self.gpu_index = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu_index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            for k, nm in enumerate(names):
+                if s[5 + k].lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+# ---------------------------------------------------------------------------
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world, device=None):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+def cpu_baseline(scene, cam, cfg, sample_pixels, seed=0):
+    """The oracle as it stands, on a bounded sample: FP64 per-primitive
+    preparation of all N primitives plus the per-pixel render of a random pixel
+    sample, extrapolated to one full-frame forward."""
+    from oracle import native as O
+    rng = np.random.default_rng(seed)
+    W, H = cam.width, cam.height
+    pix = np.stack([rng.integers(0, W, sample_pixels), rng.integers(0, H, sample_pixels)], 1)
+    t0 = time.perf_counter()
+    orc = O.Oracle(scene, cam, cfg)
+    t1 = time.perf_counter()
+    orc.render(pix)
+    t2 = time.perf_counter()
+    orc.close()
+    per_frame = (t1 - t0) + (t2 - t1) * (W * H) / sample_pixels
+    return {
+        "value": round(per_frame * 1e3, 3), "unit": "ms", "cores": O.num_threads(),
+        "kind": "oracle",
+        "sample": (f"FP64 C oracle: prepare all {scene.n} prims ({t1 - t0:.2f} s) + render "
+                   f"{sample_pixels} random pixels ({t2 - t1:.2f} s), extrapolated to one "
+                   f"{W}x{H} forward; backward not included (the oracle's gradients are "
+                   f"finite differences / FP64 autograd on small scenes)"),
+        "host_cpus": os.cpu_count(),
+    }
+
+
+def reference_arm(args, world, rank):
+    import synthetic as S
+    if rank != 0:
+        return
+    scene, cam = S.scene_scale(args.n, seed=1)
+    cam = S.orbit_camera(30.0, 20.0, 3.0, args.width, args.height, 50.0)
+    cfg = S.RenderConfig()
+    per_step = []
+    sample = max(2000, args.cpu_sample_pixels // max(1, args.steps))
+    res = None
+    for k in range(args.warmup + args.steps):
+        res = cpu_baseline(scene, cam, cfg, sample, seed=k)
+        if k >= args.warmup:
+            per_step.append(res["value"])
+    v = float(np.median(per_step))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD + " (CPU oracle, forward, sampled pixels extrapolated)"},
+            "cpu_baseline": {"value": v, "unit": "ms", "cores": res["cores"], "kind": "oracle",
+                             "sample": res["sample"]},
+            "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def launches_per_step(rast, exchange_steps, steps):
+    tiles = rast.ranges.shape[0]
+    tile_bits = max(1, math.ceil(math.log2(tiles))) if tiles > 1 else 1
+    passes = (tile_bits + 7) // 8
+    bin_sort = 3 * (4 + passes) + 3 + 1 + 1 + (1 if rast.keys is not None else 0)
+    per = 1 + bin_sort + 1 + 2
+    return per * steps + exchange_steps
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_init(args)
+    if args.impl == "reference":
+        reference_arm(args, world, rank)
+        return
+    import torch
+
+    import synthetic as S
+    from paper_2512_02932_gb300 import Rasterizer, SceneTensors, exchange_types, rasterize
+    from paper_2512_02932_gb300.rasterizer import RasterizeFunction
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    scene, _ = S.scene_scale(args.n, seed=1 + rank)
+    cam = S.orbit_camera(30.0 + 10 * rank, 20.0, 3.0, args.width, args.height, 50.0)
+    cfg = S.RenderConfig()
+    st = SceneTensors.from_numpy(scene, dev)
+    for t in (st.means, st.log_scales, st.quats, st.opacity_logits, st.sh):
+        t.requires_grad_(True)
+    target = torch.rand((3, args.height, args.width), device=dev, generator=torch.Generator(device=dev).manual_seed(7))
+    mask_rng = torch.Generator(device=dev).manual_seed(11)
+
+    # capacity from one checked frame, then no per-step host sync
+    probe = Rasterizer(dev, sync_check=True)
+    probe.forward(SceneTensors(st.means.detach(), st.log_scales.detach(), st.quats.detach(),
+                               st.opacity_logits.detach(), st.sh.detach(), st.types, 3), cam, cfg)
+    K0 = probe.last_K
+    del probe
+    rast = Rasterizer(dev, capacity=int(K0 * 1.5) + (1 << 20), sync_check=False)
+
+    n_exchange = [0]
+
+    def step(k):
+        rgb, depth, normal, alpha = rasterize(st, cam, cfg, rast)
+        loss = (rgb - target).abs().mean()
+        loss.backward()
+        if k % 100 == 0:
+            with torch.no_grad():
+                mask = (torch.rand(st.n, device=dev, generator=mask_rng) < 0.01).to(torch.uint8)
+                exchange_types(SceneTensors(st.means.detach(), st.log_scales.detach(), st.quats.detach(),
+                                            st.opacity_logits.detach(), st.sh.detach(), st.types, 3),
+                               mode="mask", mask=mask)
+                n_exchange[0] += 1
+        for t in (st.means, st.log_scales, st.quats, st.opacity_logits, st.sh):
+            t.grad = None
+        return loss
+
+    # warm-up covers one exchange too (its first call pays one-time module loads)
+    for k in range(args.warmup):
+        step(0 if k == 0 else k + 100)
+    torch.cuda.synchronize()
+    rast.check()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    n_exchange[0] = 0
+    step_ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev0.record()
+    step_ev[0].record()
+    for k in range(args.steps):
+        step(k)
+        step_ev[k + 1].record()
+    ev1.record()
+    torch.cuda.synchronize()
+    barrier(world)
+    ms_total = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    rast.check()
+    ms_total = max_over_ranks(ms_total, world, dev)
+    ms_per_step = ms_total / args.steps
+    step_ms = [step_ev[k].elapsed_time(step_ev[k + 1]) for k in range(args.steps)]
+    K = int(rast.d_count.item())
+    n_last_sum = int(rast.n_last.to(torch.int64).sum().item())
+
+    # per-phase timing on the launching stream (same workload, separate loop)
+    phases = {}
+    if args.profile_phases:
+        s = torch.cuda.current_stream()
+        dsc = SceneTensors(st.means.detach(), st.log_scales.detach(), st.quats.detach(),
+                           st.opacity_logits.detach(), st.sh.detach(), st.types, 3)
+        g = torch.sign(torch.randn((3, args.height, args.width), device=dev)) / target.numel()
+        names = ["preprocess", "bin_sort", "render_fwd", "render_bwd+preprocess_bwd"]
+        acc = {n: 0.0 for n in names}
+        reps = max(3, min(10, args.steps))
+        for _ in range(reps):
+            evs = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+            evs[0].record(s)
+            rast.preprocess(dsc, cam, cfg)
+            evs[1].record(s)
+            rast.bin_sort(sync_check=False)
+            evs[2].record(s)
+            rast.render()
+            evs[3].record(s)
+            rast.backward(g, None, None, None)
+            evs[4].record(s)
+            torch.cuda.synchronize()
+            for i, n in enumerate(names):
+                acc[n] += evs[i].elapsed_time(evs[i + 1])
+        phases = {n: round(v / reps, 4) for n, v in acc.items()}
+
+    # end to end through the public API with host buffers: H2D of the step's
+    # inputs (scene parameters + target) from pinned memory, D2H of the loss
+    e2e = None
+    if not args.no_e2e:
+        host = {k: torch.from_numpy(np.ascontiguousarray(getattr(scene, k))).pin_memory()
+                for k in ("means", "log_scales", "quats", "opacity_logits", "sh", "types")}
+        host_target = target.cpu().pin_memory()
+        h2d = sum(v.numel() * v.element_size() for v in host.values()) + host_target.numel() * 4
+        dev_in = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
+        dev_target = torch.empty_like(host_target, device=dev)
+        loss_host = torch.empty(1, dtype=torch.float32).pin_memory()
+
+        def e2e_step():
+            for k, v in host.items():
+                dev_in[k].copy_(v, non_blocking=True)
+            dev_target.copy_(host_target, non_blocking=True)
+            sc = SceneTensors(*(dev_in[k] for k in ("means", "log_scales", "quats", "opacity_logits", "sh",
+                                                   "types")), 3)
+            params = [sc.means, sc.log_scales, sc.quats, sc.opacity_logits, sc.sh]
+            for p in params:
+                p.requires_grad_(True)
+            rgb, depth, normal, alpha = RasterizeFunction.apply(*params, sc.types, rast, cam, cfg, 3)
+            loss = (rgb - dev_target).abs().mean()
+            loss.backward()
+            loss_host.copy_(loss.detach().reshape(1), non_blocking=True)
+            for p in params:
+                p.requires_grad_(False)
+                p.grad = None
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        ksteps = max(3, args.steps // 2)
+        barrier(world)
+        e0.record()
+        for _ in range(ksteps):
+            e2e_step()
+        e1.record()
+        torch.cuda.synchronize()
+        e2e_ms = max_over_ranks(e0.elapsed_time(e1) / ksteps, world, dev)
+        e2e = {"value": round(e2e_ms, 4), "unit": "ms", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": 4, "steps": ksteps}
+
+    line = {
+        "metric": METRIC, "value": round(ms_per_step, 4), "unit": "ms", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_prims": args.n, "width": args.width, "height": args.height,
+                   "sh_degree": 3, "instances_K": K, "pixel_list_entries": n_last_sum,
+                   "l2": "inputs larger than L2 (scene 708 MB, records 192 MB, lists > 100 MB)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "phases_ms": phases,
+        "step_ms": {"min": round(min(step_ms), 4), "median": round(statistics.median(step_ms), 4),
+                    "max": round(max(step_ms), 4), "first": round(step_ms[0], 4)},
+        "gpu_launches": launches_per_step(rast, n_exchange[0], args.steps),
+        "clocks": clk,
+        "e2e": e2e,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            line["cpu_baseline"] = cpu_baseline(scene, cam, cfg, args.cpu_sample_pixels)
+        except Exception as exc:  # the checker is optional for the GPU number
+            line["cpu_baseline"] = {"error": repr(exc)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

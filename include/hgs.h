@@ -1,0 +1,253 @@
+/*
+ * hgs.h -- C ABI of the hybrid 2D/3D Gaussian rasterizer for GB300 (sm_103a).
+ *
+ * The operation is the Hybrid Gaussian Rasterization of EGGS (Exchangeable
+ * 2D/3D Gaussian Splatting, arXiv 2512.02932): each primitive carries a type
+ * flag t (Sec. 3.1: t = 0 a 2D surfel, t = 1 a 3D Gaussian); 3D Gaussians are
+ * projected affinely (App. C, Eq. 13), 2D surfels by ray-splat intersection
+ * (App. C, Eqs. 14-15); both give a distance d (Eq. 1), a contribution
+ * alpha * exp(-d/2) (Sec. 3.1) and are alpha-blended in one front-to-back
+ * pass (Eq. 2).  Adaptive Type Exchange (Sec. 3.2, Eqs. 3-7) switches types
+ * in place.
+ *
+ * Conventions (every entry point):
+ *   - Every data pointer is a DEVICE pointer owned by the caller.  The library
+ *     allocates nothing and frees nothing.  Structs themselves are read on the
+ *     host during the call and may be discarded when it returns.
+ *   - Calls are asynchronous on the given stream and do not synchronise,
+ *     except hgs_check, which says so.
+ *   - Return value: HGS_OK (0) or a negative hgs_status.  Host-side argument
+ *     validation happens before anything is enqueued; on a non-zero return
+ *     nothing was launched.
+ *   - dev_err points to one device int32 the caller zeroes once; a kernel that
+ *     detects a data-dependent error (capacity exceeded, a bounded wait that
+ *     ran out) stores the first such status there.  hgs_check reads it.
+ *   - No call prints, aborts or exits.
+ *   - Float buffers are IEEE binary32, C-contiguous, 16-byte aligned where
+ *     marked (A16).
+ *
+ * Camera: OpenCV convention (x right, y down, z forward), world-to-camera
+ * x_c = R x_w + t, pinhole intrinsics fx, fy, cx, cy in pixels; pixel (i, j)
+ * has its centre at (i + 0.5, j + 0.5).
+ */
+#ifndef HGS_H
+#define HGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* a cudaStream_t (same underlying type); NULL = the legacy default stream */
+typedef struct CUstream_st *hgs_stream_t;
+
+typedef enum {
+  HGS_OK = 0,
+  HGS_ERR_INVALID_ARG = -1, /* a pointer, size or setting is invalid */
+  HGS_ERR_CAPACITY = -2,    /* instance buffer too small; required size written */
+  HGS_ERR_CUDA = -3,        /* a CUDA launch or runtime call failed */
+  HGS_ERR_TIMEOUT = -4,     /* a bounded device-side wait ran out */
+  HGS_ERR_UNSUPPORTED = -5  /* a setting this build does not implement */
+} hgs_status;
+
+/* Scene parameters, one row per primitive (Sec. 3.1): centre mu, scale s
+ * (stored as log s), rotation quaternion r (w, x, y, z; normalised on use),
+ * opacity (stored as a logit; alpha = sigmoid), SH colour coefficients f of
+ * degree l, and the type flag t.  SH layout: [n][(l+1)^2][3] (coefficient
+ * major, RGB minor).  A 2D surfel's s_z is ignored by the rasterizer except
+ * in the scale modulation of Eqs. 6-7. */
+typedef struct {
+  const float *means;          /* [n,3] */
+  const float *log_scales;     /* [n,3] */
+  const float *quats;          /* [n,4] */
+  const float *opacity_logits; /* [n] */
+  const float *sh;             /* [n,(l+1)^2,3] */
+  const uint8_t *types;        /* [n] 0 = 2D surfel, 1 = 3D Gaussian */
+  int64_t n;                   /* 0 <= n < 2^31 */
+  int32_t sh_degree;           /* 0..3 */
+} hgs_scene;
+
+/* The same arrays, writable: the exchange remaps them in place. */
+typedef struct {
+  float *log_scales; /* [n,3] */
+  float *quats;      /* [n,4] */
+  uint8_t *types;    /* [n] */
+  int64_t n;
+} hgs_scene_mut;
+
+typedef struct {
+  float R[9]; /* world-to-camera rotation, row major */
+  float t[3];
+  float fx, fy, cx, cy;
+  int32_t width, height; /* 1 .. 16384 */
+} hgs_camera;
+
+/* Render settings.  The paper fixes theta_z = 1.05 and T_z = 0.001 (App. A);
+ * the rest are unstated and default to the 3DGS practice the paper builds on
+ * (hgs_default_config). */
+typedef struct {
+  float near_z;    /* cull centres with z <= near_z; surfel hits need z > near_z */
+  float alpha_min; /* a pair contributes iff alpha*exp(-d/2) >= alpha_min */
+  float alpha_max; /* contribution clamp */
+  float T_min;     /* stop before a contributor that takes T below T_min */
+  float lambda_z;  /* scale modulation weight of Eq. 6 (not given in the paper) */
+  float theta_z;   /* Eq. 7 threshold */
+  float T_z;       /* Eq. 7 temperature */
+  float dilation;  /* added to the diagonal of the projected 3D covariance */
+  float bg[3];     /* background colour */
+  int32_t tile;    /* tile edge in pixels; this build supports 16 only */
+} hgs_config;
+
+/* Per-primitive output of hgs_preprocess (caller-allocated, n rows each):
+ *   rec        [n,16] float, A16: the render record (centre, depth, signed
+ *              opacity, conic or surfel homography, colour, normal); its
+ *              content is private to the library and valid for one camera.
+ *   depth_key  [n] uint32: bits of the binary32 camera-space centre depth.
+ *   rect       [n,4] uint16: covered tile rectangle tx0, tx1, ty0, ty1.
+ *   touched    [n] uint32: tiles covered (0 = not binned). */
+typedef struct {
+  float *rec;
+  uint32_t *depth_key;
+  uint16_t *rect;
+  uint32_t *touched;
+} hgs_projected;
+
+/* Output of hgs_bin_sort.
+ *   vals    [capacity] uint32: primitive ids of the tile instances, grouped by
+ *           tile (row-major tile id), ordered inside a tile by (depth key, id).
+ *   keys    [capacity] uint64, optional (may be NULL): tile_id << 32 | depth
+ *           key of each instance -- the 64-bit sort key the list is ordered by.
+ *   ranges  [tiles,2] uint32: [start, end) of each tile's instances in vals;
+ *           an empty tile is [0, 0).
+ *   d_count [1] int64: K, the number of instances, written even when K
+ *           exceeds the capacity. */
+typedef struct {
+  uint32_t *vals;
+  uint64_t *keys;
+  uint32_t *ranges;
+  int64_t *d_count;
+} hgs_binning;
+
+/* Planar per-pixel output of hgs_render_fwd (each [H,W] plane, row major). */
+typedef struct {
+  float *rgb;       /* [3,H,W] C + T_final * bg (Eq. 2) */
+  float *depth;     /* [H,W] sum of w_i z_i: 3D centre depth, 2D hit depth */
+  float *normal;    /* [3,H,W] sum of w_i n_i, camera space */
+  float *alpha;     /* [H,W] 1 - T_final */
+  float *T_final;   /* [H,W] final transmittance (needed by the backward) */
+  uint32_t *n_last; /* [H,W] list entries consumed (needed by the backward) */
+} hgs_image;
+
+/* Upstream gradients dL/d(outputs), same shapes as hgs_image; any may be NULL
+ * (treated as zero). */
+typedef struct {
+  const float *rgb;
+  const float *depth;
+  const float *normal;
+  const float *alpha;
+} hgs_image_grad;
+
+/* Gradients with respect to the raw parameters (overwritten, not added). */
+typedef struct {
+  float *means;          /* [n,3] */
+  float *log_scales;     /* [n,3] */
+  float *quats;          /* [n,4] */
+  float *opacity_logits; /* [n] */
+  float *sh;             /* [n,(l+1)^2,3] */
+} hgs_scene_grad;
+
+typedef enum { HGS_EXCHANGE_ERANK = 0, HGS_EXCHANGE_MASK = 1 } hgs_exchange_mode;
+
+typedef struct {
+  int32_t mode;          /* hgs_exchange_mode */
+  float theta_e;         /* erank threshold (paper: 2.05) */
+  const uint8_t *mask;   /* [n] device, MASK mode: flip where non-zero */
+} hgs_exchange_cfg;
+
+/* Fill *cfg with the defaults: near 0.2, alpha_min 1/255, alpha_max 0.99,
+ * T_min 1e-4, lambda_z 1, theta_z 1.05, T_z 1e-3, dilation 0, bg 0, tile 16. */
+void hgs_default_config(hgs_config *cfg);
+
+/* Name of a status code (static string). */
+const char *hgs_status_string(int status);
+
+/* Synchronise `stream`, then copy the device error word to *host_err (may be
+ * NULL) and return it (HGS_OK if none).  HGS_ERR_CUDA if the stream itself
+ * reports an error. */
+int hgs_check(const int32_t *dev_err, int32_t *host_err, hgs_stream_t stream);
+
+/* hgs_preprocess -- per-primitive projection (Sec. 3.1, App. C).
+ * For each primitive: activations (exp of log s, normalised r, sigmoid
+ * opacity), camera-space centre, cull at z <= near_z, SH colour, and
+ *   t = 1: projected 2D covariance Sigma' = J W Sigma W^T J^T (Eq. 13) and
+ *          its inverse (the conic of Eq. 1);
+ *   t = 0: the surfel's splat-to-screen homography (the WH of Eq. 15),
+ *          inverted and re-centred so Eq. 14's (u, v) are affine functions
+ *          of the pixel offset up to one perspective divide;
+ * the scale-modulated opacity for t = 0 (Eqs. 6-7), the normal, and the
+ * binning contract: depth key and covered tile rectangle from one fixed
+ * sequence of binary32 operations (exact rounding, no fused multiply-add).
+ * Errors: HGS_ERR_INVALID_ARG for NULL pointers, n < 0, sh_degree outside
+ * 0..3, a camera with non-positive size or focal, tile != 16 (UNSUPPORTED). */
+int hgs_preprocess(const hgs_scene *scene, const hgs_camera *cam, const hgs_config *cfg,
+                   hgs_projected *out, int32_t *dev_err, hgs_stream_t stream);
+
+/* Bytes of device workspace hgs_bin_sort needs for n primitives, `capacity`
+ * instances and `tiles` tiles.  Host only. */
+int hgs_bin_sort_workspace(int64_t n, int64_t capacity, int32_t tiles, size_t *bytes);
+
+/* hgs_bin_sort -- duplicate each binned primitive into the tiles of its
+ * rectangle and order the instances by the 64-bit key tile << 32 | depth key,
+ * ties by primitive id.  Implemented as an LSD radix sort whose low (depth)
+ * digits are sorted once per primitive and whose high (tile) digits are
+ * sorted per instance; the resulting order is that of the 64-bit key.
+ * If K > capacity: writes K to out->d_count, stores HGS_ERR_CAPACITY in
+ * *dev_err, zeroes the ranges, and writes no instance (no out-of-bounds
+ * write).  The caller grows the buffers and calls again.
+ * ws: device workspace of at least hgs_bin_sort_workspace() bytes, A16.
+ * Errors: INVALID_ARG for NULL pointers, ws_bytes too small, capacity < 0. */
+int hgs_bin_sort(int64_t n, const hgs_projected *proj, const hgs_camera *cam,
+                 const hgs_config *cfg, void *ws, size_t ws_bytes, int64_t capacity,
+                 hgs_binning *out, int32_t *dev_err, hgs_stream_t stream);
+
+/* hgs_render_fwd -- per 16x16 tile, front-to-back blending over the tile's
+ * sorted list (Eq. 2): per pair the unified distance of Eq. 1, contribution
+ * a = min(alpha_max, alpha exp(-d/2)), skipped if a < alpha_min; stop before
+ * the first contributor with T (1 - a) < T_min.  Writes every field of *out. */
+int hgs_render_fwd(int64_t n, const hgs_projected *proj, const hgs_binning *bins,
+                   const hgs_camera *cam, const hgs_config *cfg, hgs_image *out,
+                   int32_t *dev_err, hgs_stream_t stream);
+
+/* hgs_render_bwd -- gradients of a scalar loss with respect to the raw scene
+ * parameters, given dL/d(outputs).  Replays each tile's list in reverse from
+ * n_last, recovering the transmittance by division (T_i = T_{i+1}/(1 - a_i)),
+ * accumulates per-primitive gradients of the render record (warp-reduced
+ * atomics into grad_ws), then chains them through the projection, the SH
+ * decode, the activations and the scale modulation.
+ * grad_ws: [n,16] float device scratch, A16, zeroed by this call.
+ * `fwd` must be the output of hgs_render_fwd for the same inputs. */
+int hgs_render_bwd(const hgs_scene *scene, const hgs_projected *proj,
+                   const hgs_binning *bins, const hgs_camera *cam, const hgs_config *cfg,
+                   const hgs_image *fwd, const hgs_image_grad *dL, float *grad_ws,
+                   hgs_scene_grad *out, int32_t *dev_err, hgs_stream_t stream);
+
+/* hgs_exchange_types -- Adaptive Type Exchange (Sec. 3.2) in place.
+ * ERANK mode: erank = exp(-sum p_i log p_i), p = q / |q|_1, q = (s_x^2,
+ * s_y^2, s_z^2) (Eq. 3); a 3D Gaussian with erank < theta_e becomes 2D, a 2D
+ * one with erank > theta_e becomes 3D (the comparison is decided in binary64
+ * whenever binary32 cannot decide it).  MASK mode: flip where mask != 0.
+ * 3D -> 2D reparameterises S* = P S P^T, R* = R P^T (Eqs. 4-5) with P = P_x
+ * if s_x is the smallest scale, P_y if s_y is (ties: x), identity if s_z is
+ * already the smallest; the quaternion becomes r (x) p with R(p) = P^T.
+ * 2D -> 3D flips the flag only (Sec. 3.2).  No buffer is reallocated or
+ * reordered.  *d_n_flipped (device int64, may be NULL) receives the count.
+ * Errors: INVALID_ARG for NULL arrays or a NULL mask in MASK mode. */
+int hgs_exchange_types(hgs_scene_mut *scene, const hgs_exchange_cfg *xcfg,
+                       int64_t *d_n_flipped, int32_t *dev_err, hgs_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HGS_H */

@@ -48,9 +48,13 @@ enum {
 };
 
 /* ambiguity bands: a pixel whose result could legitimately differ between an
- * FP32 evaluation and this FP64 one is flagged and reported, not compared. */
-#define AMB_ALPHA_REL 2e-4   /* |alpha*G - alpha_min| <= this * alpha_min  */
-#define AMB_T_REL     2e-3   /* |T' - T_min| <= this * T_min               */
+ * FP32 evaluation and this FP64 one is flagged and reported, not compared.
+ * In binary32 a contribution alpha*exp(-d/2) carries a relative error of
+ * about 1e-5 (d ~ 11 near the cutoff, ~1e-6 relative error in d), and the
+ * transmittance after a few hundred contributors about 1e-4; the bands are
+ * five to ten times wider. */
+#define AMB_ALPHA_REL 5e-5   /* |alpha*G - alpha_min| <= this * alpha_min  */
+#define AMB_T_REL     1e-3   /* |T' - T_min| <= this * T_min               */
 #define AMB_NEAR_REL  1e-5   /* |z - near| <= this * max(1, near)          */
 #define AMB_FLIP      1e-5   /* |n . mu_c| / |mu_c| below this             */
 
@@ -568,7 +572,7 @@ void orc_free(void *ctx) {
   free(C->P); free(C->cstart); free(C->citems); free(C);
 }
 
-typedef struct { uint32_t key; int32_t id; double at, z; } contrib_t;
+typedef struct { uint32_t key; int32_t id; int amb; double at, z; } contrib_t;
 
 static int cmp_contrib(const void *A, const void *B) {
   const contrib_t *a = (const contrib_t *)A, *b = (const contrib_t *)B;
@@ -577,11 +581,16 @@ static int cmp_contrib(const void *A, const void *B) {
 }
 
 /* Unified distance (Eq. 1) and contribution (Sec. 3.1) of primitive p at the
- * pixel centre (px, py).  Returns 1 if it contributes; *amb set if the
- * decision sits inside an ambiguity band. */
+ * pixel centre (px, py).  Returns 1 if the pair must be listed: it
+ * contributes (*at_out > 0), or its contribution decision sits inside an
+ * ambiguity band (*amb = 1; *at_out = 0 if it does not contribute).  Whether
+ * an ambiguous pair matters is decided by the blend: only pairs reached
+ * before the pixel terminates can change the result. */
 static int eval_pair(const orc_ctx *C, const prim_t *p, double px, double py,
                      double *at_out, double *z_out, int *amb) {
   double d, z;
+  int a = 0;
+  const double amin = C->cfg[CF_ALPHA_MIN], nearz = C->cfg[CF_NEAR];
   if (p->type == 1) {
     double dx = px - p->mx, dy = py - p->my;
     d = p->ca * dx * dx + 2.0 * p->cb * dx * dy + p->cc * dy * dy;
@@ -621,32 +630,36 @@ static int eval_pair(const orc_ctx *C, const prim_t *p, double px, double py,
     double u = sol[0], v = sol[1];
     z = sol[2];
     d = u * u + v * v;
-    double nearz = C->cfg[CF_NEAR];
     if (fabs(z - nearz) <= AMB_NEAR_REL * fmax(1.0, nearz)) {
-      double ag = p->alpha * exp(-0.5 * d);
-      if (ag >= C->cfg[CF_ALPHA_MIN] * (1.0 - AMB_ALPHA_REL)) *amb = 1;
+      if (p->alpha * exp(-0.5 * d) >= amin * (1.0 - AMB_ALPHA_REL)) a = 1;
     }
-    if (!(z > nearz)) return 0;
+    if (!(z > nearz)) {
+      if (!a) return 0;
+      *at_out = 0.0; *z_out = z; *amb = 1;
+      return 1;
+    }
   }
   double ag = p->alpha * exp(-0.5 * d);
-  double amin = C->cfg[CF_ALPHA_MIN];
-  if (fabs(ag - amin) <= AMB_ALPHA_REL * amin) *amb = 1;
-  if (!(ag >= amin)) return 0;
-  if (p->ndot < AMB_FLIP) *amb = 1;
-  if (p->amb_near) {
-    *amb = 1;
-    if (!(p->Z > C->cfg[CF_NEAR])) return 0;
+  if (fabs(ag - amin) <= AMB_ALPHA_REL * amin) a = 1;
+  int contributes = ag >= amin;
+  if (contributes && p->ndot < AMB_FLIP) a = 1;
+  if (p->amb_near && (contributes || a)) {
+    a = 1;
+    if (!(p->Z > nearz)) contributes = 0;
   }
+  if (!contributes && !a) return 0;
   double amax = C->cfg[CF_ALPHA_MAX];
-  *at_out = ag < amax ? ag : amax;
+  *at_out = contributes ? (ag < amax ? ag : amax) : 0.0;
   *z_out = z;
+  *amb = a;
   return 1;
 }
 
 /* Render npix pixels (pix: npix x 2 int32 pixel indices, or NULL = full frame
  * in row-major order).  out: npix x 10 doubles
  *   [r, g, b, depth, nx, ny, nz, alpha, T_final, n_contrib]
- * amb: npix flags (1 = ambiguous, see the bands above). */
+ * amb: npix flags (1 = ambiguous: a pair reached before termination sits in
+ * one of the bands above). */
 void orc_render(void *ctx, int64_t npix, const int32_t *pix, double *out, uint8_t *amb) {
   orc_ctx *C = (orc_ctx *)ctx;
   if (!pix) npix = (int64_t)C->W * C->H;
@@ -666,9 +679,11 @@ void orc_render(void *ctx, int64_t npix, const int32_t *pix, double *out, uint8_
         int32_t id = C->citems[k];
         const prim_t *p = &C->P[id];
         if (!p->valid) continue;
-        double at, z;
-        if (eval_pair(C, p, px, py, &at, &z, &am)) {
+        double at = 0, z = 0;
+        int a = 0;
+        if (eval_pair(C, p, px, py, &at, &z, &a)) {
           buf[cnt].key = p->key; buf[cnt].id = id; buf[cnt].at = at; buf[cnt].z = z;
+          buf[cnt].amb = a;
           cnt++;
         }
       }
@@ -679,7 +694,9 @@ void orc_render(void *ctx, int64_t npix, const int32_t *pix, double *out, uint8_
       const double Tmin = C->cfg[CF_T_MIN];
       for (int k = 0; k < cnt; ++k) {
         const prim_t *p = &C->P[buf[k].id];
+        if (buf[k].amb) am = 1;
         double at = buf[k].at;
+        if (at <= 0.0) continue;
         double Tn = T * (1.0 - at);
         if (fabs(Tn - Tmin) <= AMB_T_REL * Tmin) am = 1;
         if (Tn < Tmin) break;

@@ -178,6 +178,7 @@ def tile_lists(scene, cam, cfg):
     tiles_of = (keys >> np.uint64(32)).astype(np.int64)
     edges = np.searchsorted(tiles_of, np.arange(TX * TY + 1))
     ranges = np.stack([edges[:-1], edges[1:]], axis=1).astype(np.uint32)
+    ranges[ranges[:, 0] == ranges[:, 1]] = 0  # an empty tile is [0, 0)
     return keys, vals, ranges, (db, rect, touched)
 
 

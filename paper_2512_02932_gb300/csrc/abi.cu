@@ -1,0 +1,275 @@
+// abi.cu -- extern "C" entry points of libhgs (declared in include/hgs.h).
+// Host-side validation, conversion of the ABI structs to kernel argument
+// blocks, and launches on the caller's stream.  Nothing here allocates,
+// synchronises (except hgs_check) or prints.
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+using namespace hgs;
+
+namespace {
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+int cam_to_kernel(const hgs_camera *c, CamK *k) {
+  if (!c) return HGS_ERR_INVALID_ARG;
+  if (c->width <= 0 || c->height <= 0 || c->width > 16384 || c->height > 16384) return HGS_ERR_INVALID_ARG;
+  if (!(c->fx > 0.f) || !(c->fy > 0.f) || !std::isfinite(c->cx) || !std::isfinite(c->cy))
+    return HGS_ERR_INVALID_ARG;
+  for (int i = 0; i < 9; ++i)
+    if (!std::isfinite(c->R[i])) return HGS_ERR_INVALID_ARG;
+  for (int i = 0; i < 3; ++i)
+    if (!std::isfinite(c->t[i])) return HGS_ERR_INVALID_ARG;
+  std::memcpy(k->R, c->R, sizeof(k->R));
+  std::memcpy(k->t, c->t, sizeof(k->t));
+  k->fx = c->fx; k->fy = c->fy; k->cx = c->cx; k->cy = c->cy;
+  for (int i = 0; i < 3; ++i)
+    k->campos[i] = -(c->R[i] * c->t[0] + c->R[3 + i] * c->t[1] + c->R[6 + i] * c->t[2]);
+  k->W = c->width; k->H = c->height;
+  k->TX = (c->width + kTile - 1) / kTile;
+  k->TY = (c->height + kTile - 1) / kTile;
+  return HGS_OK;
+}
+
+int cfg_to_kernel(const hgs_config *c, CfgK *k) {
+  if (!c) return HGS_ERR_INVALID_ARG;
+  if (c->tile != kTile) return HGS_ERR_UNSUPPORTED;
+  if (!(c->alpha_min > 0.f) || !(c->alpha_max >= c->alpha_min) || !(c->alpha_max < 1.f) ||
+      !(c->T_min > 0.f) || !(c->T_z > 0.f) || !(c->near_z > 0.f) || !(c->dilation >= 0.f) ||
+      !std::isfinite(c->lambda_z) || !std::isfinite(c->theta_z))
+    return HGS_ERR_INVALID_ARG;
+  k->near_z = c->near_z; k->alpha_min = c->alpha_min; k->alpha_max = c->alpha_max;
+  k->T_min = c->T_min; k->lambda_z = c->lambda_z; k->theta_z = c->theta_z; k->T_z = c->T_z;
+  k->dilation = c->dilation;
+  for (int i = 0; i < 3; ++i) k->bg[i] = c->bg[i];
+  return HGS_OK;
+}
+
+int scene_ok(const hgs_scene *s) {
+  if (!s || s->n < 0 || s->n >= (int64_t(1) << 31)) return HGS_ERR_INVALID_ARG;
+  if (s->sh_degree < 0 || s->sh_degree > 3) return HGS_ERR_INVALID_ARG;
+  if (s->n == 0) return HGS_OK;
+  if (!s->means || !s->log_scales || !s->quats || !s->opacity_logits || !s->sh || !s->types)
+    return HGS_ERR_INVALID_ARG;
+  if (!aligned16(s->quats)) return HGS_ERR_INVALID_ARG;
+  if ((s->sh_degree == 1 || s->sh_degree == 3) && !aligned16(s->sh)) return HGS_ERR_INVALID_ARG;
+  return HGS_OK;
+}
+
+int proj_ok(const hgs_projected *p, int64_t n) {
+  if (!p) return HGS_ERR_INVALID_ARG;
+  if (n == 0) return HGS_OK;
+  if (!p->rec || !p->depth_key || !p->rect || !p->touched) return HGS_ERR_INVALID_ARG;
+  if (!aligned16(p->rec) || (reinterpret_cast<uintptr_t>(p->rect) & 7u)) return HGS_ERR_INVALID_ARG;
+  return HGS_OK;
+}
+
+int tile_bits_for(int tiles) {
+  int b = 1;
+  while ((1 << b) < tiles) ++b;
+  return b;
+}
+
+int launched() { return cudaGetLastError() == cudaSuccess ? HGS_OK : HGS_ERR_CUDA; }
+
+PrepArgs prep_args(const hgs_scene *s, const CamK &ck, const CfgK &fk, const hgs_projected *p) {
+  PrepArgs a;
+  a.means = s->means; a.log_scales = s->log_scales; a.quats = s->quats;
+  a.logits = s->opacity_logits; a.sh = s->sh; a.types = s->types; a.n = s->n;
+  a.cam = ck; a.cfg = fk;
+  a.rec = p->rec; a.depth_key = p->depth_key; a.rect = p->rect; a.touched = p->touched;
+  return a;
+}
+
+}  // namespace
+
+extern "C" {
+
+void hgs_default_config(hgs_config *c) {
+  if (!c) return;
+  c->near_z = 0.2f;
+  c->alpha_min = 1.0f / 255.0f;
+  c->alpha_max = 0.99f;
+  c->T_min = 1e-4f;
+  c->lambda_z = 1.0f;
+  c->theta_z = 1.05f;
+  c->T_z = 1e-3f;
+  c->dilation = 0.0f;
+  c->bg[0] = c->bg[1] = c->bg[2] = 0.0f;
+  c->tile = kTile;
+}
+
+const char *hgs_status_string(int s) {
+  switch (s) {
+    case HGS_OK: return "HGS_OK";
+    case HGS_ERR_INVALID_ARG: return "HGS_ERR_INVALID_ARG";
+    case HGS_ERR_CAPACITY: return "HGS_ERR_CAPACITY";
+    case HGS_ERR_CUDA: return "HGS_ERR_CUDA";
+    case HGS_ERR_TIMEOUT: return "HGS_ERR_TIMEOUT";
+    case HGS_ERR_UNSUPPORTED: return "HGS_ERR_UNSUPPORTED";
+    default: return "HGS_ERR_UNKNOWN";
+  }
+}
+
+int hgs_check(const int32_t *dev_err, int32_t *host_err, hgs_stream_t stream) {
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return HGS_ERR_CUDA;
+  int32_t e = 0;
+  if (dev_err && cudaMemcpy(&e, dev_err, sizeof(e), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return HGS_ERR_CUDA;
+  if (host_err) *host_err = e;
+  return e;
+}
+
+int hgs_preprocess(const hgs_scene *scene, const hgs_camera *cam, const hgs_config *cfg,
+                   hgs_projected *out, int32_t *dev_err, hgs_stream_t stream) {
+  (void)dev_err;
+  int st;
+  if ((st = scene_ok(scene)) != HGS_OK) return st;
+  CamK ck;
+  CfgK fk;
+  if ((st = cam_to_kernel(cam, &ck)) != HGS_OK) return st;
+  if ((st = cfg_to_kernel(cfg, &fk)) != HGS_OK) return st;
+  if ((st = proj_ok(out, scene->n)) != HGS_OK) return st;
+  if (scene->n == 0) return HGS_OK;
+  launch_preprocess_fwd(prep_args(scene, ck, fk, out), scene->sh_degree,
+                        reinterpret_cast<cudaStream_t>(stream));
+  return launched();
+}
+
+int hgs_bin_sort_workspace(int64_t n, int64_t capacity, int32_t tiles, size_t *bytes) {
+  if (!bytes || n < 0 || capacity < 0 || tiles <= 0) return HGS_ERR_INVALID_ARG;
+  BinWorkspace ws;
+  *bytes = bin_layout(nullptr, n, capacity, &ws);
+  return HGS_OK;
+}
+
+int hgs_bin_sort(int64_t n, const hgs_projected *proj, const hgs_camera *cam, const hgs_config *cfg,
+                 void *ws, size_t ws_bytes, int64_t capacity, hgs_binning *out, int32_t *dev_err,
+                 hgs_stream_t stream) {
+  int st;
+  if (n < 0 || n >= (int64_t(1) << 31) || capacity < 0 || !out || !out->ranges || !out->d_count)
+    return HGS_ERR_INVALID_ARG;
+  if (capacity > 0 && !out->vals) return HGS_ERR_INVALID_ARG;
+  CamK ck;
+  CfgK fk;
+  if ((st = cam_to_kernel(cam, &ck)) != HGS_OK) return st;
+  if ((st = cfg_to_kernel(cfg, &fk)) != HGS_OK) return st;
+  if ((st = proj_ok(proj, n)) != HGS_OK) return st;
+  if (!ws || !aligned16(ws)) return HGS_ERR_INVALID_ARG;
+  BinWorkspace w;
+  const size_t need = bin_layout(ws, n, capacity, &w);
+  if (ws_bytes < need) return HGS_ERR_INVALID_ARG;
+  BinArgs a;
+  a.n = n;
+  a.capacity = capacity;
+  a.tiles = ck.TX * ck.TY;
+  a.tile_bits = tile_bits_for(a.tiles);
+  a.TX = ck.TX;
+  a.depth_key = proj->depth_key;
+  a.touched = proj->touched;
+  a.rect = proj->rect;
+  a.vals = out->vals;
+  a.keys = out->keys;
+  a.ranges = out->ranges;
+  a.d_count = out->d_count;
+  a.dev_err = dev_err;
+  launch_bin_sort(a, w, reinterpret_cast<cudaStream_t>(stream));
+  return launched();
+}
+
+int hgs_render_fwd(int64_t n, const hgs_projected *proj, const hgs_binning *bins, const hgs_camera *cam,
+                   const hgs_config *cfg, hgs_image *out, int32_t *dev_err, hgs_stream_t stream) {
+  (void)dev_err;
+  int st;
+  CamK ck;
+  CfgK fk;
+  if ((st = cam_to_kernel(cam, &ck)) != HGS_OK) return st;
+  if ((st = cfg_to_kernel(cfg, &fk)) != HGS_OK) return st;
+  if ((st = proj_ok(proj, n)) != HGS_OK) return st;
+  if (!bins || !bins->ranges || (n > 0 && !bins->vals)) return HGS_ERR_INVALID_ARG;
+  if (!out || !out->rgb || !out->depth || !out->normal || !out->alpha || !out->T_final || !out->n_last)
+    return HGS_ERR_INVALID_ARG;
+  RenderArgs a;
+  a.rec = proj->rec;
+  a.vals = bins->vals;
+  a.ranges = bins->ranges;
+  a.cam = ck;
+  a.cfg = fk;
+  a.rgb = out->rgb; a.depth = out->depth; a.normal = out->normal; a.alpha = out->alpha;
+  a.T_final = out->T_final; a.n_last = out->n_last;
+  launch_render_fwd(a, reinterpret_cast<cudaStream_t>(stream));
+  return launched();
+}
+
+int hgs_render_bwd(const hgs_scene *scene, const hgs_projected *proj, const hgs_binning *bins,
+                   const hgs_camera *cam, const hgs_config *cfg, const hgs_image *fwd,
+                   const hgs_image_grad *dL, float *grad_ws, hgs_scene_grad *out, int32_t *dev_err,
+                   hgs_stream_t stream) {
+  (void)dev_err;
+  int st;
+  if ((st = scene_ok(scene)) != HGS_OK) return st;
+  CamK ck;
+  CfgK fk;
+  if ((st = cam_to_kernel(cam, &ck)) != HGS_OK) return st;
+  if ((st = cfg_to_kernel(cfg, &fk)) != HGS_OK) return st;
+  if ((st = proj_ok(proj, scene->n)) != HGS_OK) return st;
+  if (!bins || !bins->ranges || (scene->n > 0 && !bins->vals)) return HGS_ERR_INVALID_ARG;
+  if (!fwd || !fwd->T_final || !fwd->n_last || !dL) return HGS_ERR_INVALID_ARG;
+  if (!out || (scene->n > 0 && (!out->means || !out->log_scales || !out->quats ||
+                                !out->opacity_logits || !out->sh)))
+    return HGS_ERR_INVALID_ARG;
+  if (scene->n > 0 && (!grad_ws || !aligned16(grad_ws) || !aligned16(out->quats)))
+    return HGS_ERR_INVALID_ARG;
+  if (scene->n == 0) return HGS_OK;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaMemsetAsync(grad_ws, 0, sizeof(float) * kGradW * (size_t)scene->n, s);
+  RenderBwdArgs r;
+  r.rec = proj->rec;
+  r.vals = bins->vals;
+  r.ranges = bins->ranges;
+  r.cam = ck;
+  r.cfg = fk;
+  r.T_final = fwd->T_final;
+  r.n_last = fwd->n_last;
+  r.g_rgb = dL->rgb; r.g_depth = dL->depth; r.g_normal = dL->normal; r.g_alpha = dL->alpha;
+  r.rec_grad = grad_ws;
+  launch_render_bwd(r, s);
+  PrepGradArgs g;
+  g.rec_grad = grad_ws;
+  g.means = out->means; g.log_scales = out->log_scales; g.quats = out->quats;
+  g.logits = out->opacity_logits; g.sh = out->sh;
+  hgs_projected pcopy = *proj;
+  launch_preprocess_bwd(prep_args(scene, ck, fk, &pcopy), g, scene->sh_degree, s);
+  return launched();
+}
+
+int hgs_exchange_types(hgs_scene_mut *scene, const hgs_exchange_cfg *xcfg, int64_t *d_n_flipped,
+                       int32_t *dev_err, hgs_stream_t stream) {
+  (void)dev_err;
+  if (!scene || !xcfg || scene->n < 0) return HGS_ERR_INVALID_ARG;
+  if (xcfg->mode != HGS_EXCHANGE_ERANK && xcfg->mode != HGS_EXCHANGE_MASK) return HGS_ERR_INVALID_ARG;
+  if (scene->n == 0) return HGS_OK;
+  if (!scene->log_scales || !scene->quats || !scene->types || !aligned16(scene->quats))
+    return HGS_ERR_INVALID_ARG;
+  if (xcfg->mode == HGS_EXCHANGE_MASK && !xcfg->mask) return HGS_ERR_INVALID_ARG;
+  if (xcfg->mode == HGS_EXCHANGE_ERANK && !(xcfg->theta_e > 0.f)) return HGS_ERR_INVALID_ARG;
+  ExchangeArgs a;
+  a.log_scales = scene->log_scales;
+  a.quats = scene->quats;
+  a.types = scene->types;
+  a.n = scene->n;
+  a.mode = xcfg->mode;
+  a.theta = xcfg->theta_e;
+  a.mask = xcfg->mask;
+  a.n_flipped = reinterpret_cast<unsigned long long *>(d_n_flipped);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (d_n_flipped) cudaMemsetAsync(d_n_flipped, 0, sizeof(int64_t), s);
+  launch_exchange(a, s);
+  return launched();
+}
+
+}  // extern "C"

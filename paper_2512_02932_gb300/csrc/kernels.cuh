@@ -1,0 +1,104 @@
+// kernels.cuh -- kernel argument blocks and launchers (internal to libhgs).
+#pragma once
+#include "common.cuh"
+
+namespace hgs {
+
+struct PrepArgs {
+  const float *means, *log_scales, *quats, *logits, *sh;
+  const uint8_t *types;
+  int64_t n;
+  CamK cam;
+  CfgK cfg;
+  // outputs (forward) / inputs (backward)
+  float *rec;
+  uint32_t *depth_key;
+  uint16_t *rect;
+  uint32_t *touched;
+};
+
+struct PrepGradArgs {
+  const float *rec_grad;  // [n,16]
+  float *means, *log_scales, *quats, *logits, *sh;
+};
+
+int launch_preprocess_fwd(const PrepArgs &a, int deg, cudaStream_t s);
+int launch_preprocess_bwd(const PrepArgs &a, const PrepGradArgs &g, int deg, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// binning
+// ---------------------------------------------------------------------------
+struct BinWorkspace {
+  // carved from the caller's workspace by bin_layout()
+  uint32_t *hist;        // [256 * kSortBlocks]
+  uint64_t *blk;         // [kSortBlocks] scan partials
+  int64_t *counters;     // [8]: 0 = n_visible, 1 = K, 2 = overflow flag
+  uint32_t *dk[2], *dv[2];  // depth sort ping-pong, [n] each
+  uint32_t *offs;        // [n] instance offsets in depth order
+  uint32_t *tk[2];       // tile keys ping-pong, [capacity]
+  uint32_t *tv;          // tile vals scratch, [capacity]
+  size_t bytes;
+};
+
+constexpr int kSortBlocks = 1024;  // fixed grid of every sort/scan pass
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;      // per thread per tile (tile = 2048 keys)
+
+size_t bin_layout(void *base, int64_t n, int64_t capacity, BinWorkspace *ws);
+
+struct BinArgs {
+  int64_t n, capacity;
+  int tiles, tile_bits, TX;
+  const uint32_t *depth_key, *touched;
+  const uint16_t *rect;
+  uint32_t *vals;
+  uint64_t *keys;   // optional
+  uint32_t *ranges;
+  int64_t *d_count;
+  int32_t *dev_err;
+};
+
+int launch_bin_sort(const BinArgs &a, const BinWorkspace &ws, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// render
+// ---------------------------------------------------------------------------
+struct RenderArgs {
+  const float *rec;
+  const uint32_t *vals, *ranges;
+  CamK cam;
+  CfgK cfg;
+  float *rgb, *depth, *normal, *alpha, *T_final;
+  uint32_t *n_last;
+};
+
+struct RenderBwdArgs {
+  const float *rec;
+  const uint32_t *vals, *ranges;
+  CamK cam;
+  CfgK cfg;
+  const float *T_final;
+  const uint32_t *n_last;
+  const float *g_rgb, *g_depth, *g_normal, *g_alpha;
+  float *rec_grad;  // [n,16], zeroed before launch
+};
+
+int launch_render_fwd(const RenderArgs &a, cudaStream_t s);
+int launch_render_bwd(const RenderBwdArgs &a, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// exchange
+// ---------------------------------------------------------------------------
+struct ExchangeArgs {
+  float *log_scales, *quats;
+  uint8_t *types;
+  int64_t n;
+  int mode;
+  float theta;
+  const uint8_t *mask;
+  unsigned long long *n_flipped;
+};
+
+int launch_exchange(const ExchangeArgs &a, cudaStream_t s);
+
+}  // namespace hgs

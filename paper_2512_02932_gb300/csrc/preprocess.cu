@@ -1,0 +1,645 @@
+// preprocess.cu -- per-primitive projection of the hybrid rasterizer and its
+// backward (EGGS Sec. 3.1, App. C; scale modulation Eqs. 6-7).
+//
+// Forward, one thread per primitive:
+//   binning contract (exact binary32 sequence): camera-space centre, opacity,
+//   activated scales, rotation, covered tile rectangle and depth key;
+//   render record: projected centre, conic (t=1, Eq. 13) or re-centred
+//   inverse homography (t=0, Eqs. 14-15), modulated opacity, SH colour,
+//   camera-space normal.
+// Backward, one thread per primitive: the record gradient accumulated by
+//   render_bwd, chained through the same forward quantities to the raw
+//   parameters (means, log-scales, quaternion, opacity logit, SH).
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace hgs {
+
+// ---------------------------------------------------------------------------
+// binning contract
+// ---------------------------------------------------------------------------
+struct Contract {
+  float X, Y, Z, iz, xz, yz;
+  float alpha, dmax;
+  float s[3];
+  float qn[4], qinv;  // normalised quaternion, 1/|q|
+  float Rq[9];        // rotation of the primitive (row major)
+  float a[3][3];      // camera-space axes a[k] = R_cw * column k of Rq
+  float s00, s01, s11;                 // t=1: projected covariance
+  float e0, e1, f0, f1;                // t=0: re-centred homography block
+  uint32_t dbits;
+  int tx0, tx1, ty0, ty1;
+};
+
+__device__ __forceinline__ float pad_extent(float r) {
+  return cadd(cmul(r, 1.0009765625f), 0.015625f);
+}
+
+__device__ __forceinline__ bool pixel_tiles(float lo, float hi, int extent, int *t0, int *t1) {
+  float flo = csub(lo, 0.5f), fhi = csub(hi, 0.5f);
+  if (!(flo <= fhi)) return false;
+  flo = fmaxf(flo, -1.0f);
+  fhi = fminf(fhi, (float)extent);
+  int p0 = (int)ceilf(flo), p1 = (int)floorf(fhi);
+  if (p0 < 0) p0 = 0;
+  if (p1 > extent - 1) p1 = extent - 1;
+  if (p0 > p1) return false;
+  *t0 = p0 / kTile;
+  *t1 = p1 / kTile;
+  return true;
+}
+
+// The contract: a fixed sequence of correctly rounded binary32 operations.
+// Returns true if the primitive is binned.
+__device__ bool run_contract(const float mu[3], const float ls[3], const float q[4], float logit,
+                             int type, const CamK &c, const CfgK &f, Contract &o) {
+  const float *Rc = c.R;
+  o.X = cadd(cadd(cadd(cmul(Rc[0], mu[0]), cmul(Rc[1], mu[1])), cmul(Rc[2], mu[2])), c.t[0]);
+  o.Y = cadd(cadd(cadd(cmul(Rc[3], mu[0]), cmul(Rc[4], mu[1])), cmul(Rc[5], mu[2])), c.t[1]);
+  o.Z = cadd(cadd(cadd(cmul(Rc[6], mu[0]), cmul(Rc[7], mu[1])), cmul(Rc[8], mu[2])), c.t[2]);
+  o.dbits = __float_as_uint(o.Z);
+  if (!(o.Z > f.near_z)) return false;
+  o.alpha = cdiv(1.0f, cadd(1.0f, contract_exp(-logit)));
+  if (!(o.alpha >= f.alpha_min)) return false;
+  o.dmax = cmul(2.0f, contract_log(cdiv(o.alpha, f.alpha_min)));
+  o.s[0] = contract_exp(ls[0]);
+  o.s[1] = contract_exp(ls[1]);
+  o.s[2] = contract_exp(ls[2]);
+  const float qq = cadd(cadd(cadd(cmul(q[0], q[0]), cmul(q[1], q[1])), cmul(q[2], q[2])),
+                        cmul(q[3], q[3]));
+  if (!(qq > 0.0f)) return false;
+  o.qinv = cdiv(1.0f, csqrt(qq));
+  const float w = cmul(q[0], o.qinv), x = cmul(q[1], o.qinv), y = cmul(q[2], o.qinv),
+              z = cmul(q[3], o.qinv);
+  o.qn[0] = w; o.qn[1] = x; o.qn[2] = y; o.qn[3] = z;
+  float *Rq = o.Rq;
+  Rq[0] = csub(1.0f, cmul(2.0f, cadd(cmul(y, y), cmul(z, z))));
+  Rq[1] = cmul(2.0f, csub(cmul(x, y), cmul(w, z)));
+  Rq[2] = cmul(2.0f, cadd(cmul(x, z), cmul(w, y)));
+  Rq[3] = cmul(2.0f, cadd(cmul(x, y), cmul(w, z)));
+  Rq[4] = csub(1.0f, cmul(2.0f, cadd(cmul(x, x), cmul(z, z))));
+  Rq[5] = cmul(2.0f, csub(cmul(y, z), cmul(w, x)));
+  Rq[6] = cmul(2.0f, csub(cmul(x, z), cmul(w, y)));
+  Rq[7] = cmul(2.0f, cadd(cmul(y, z), cmul(w, x)));
+  Rq[8] = csub(1.0f, cmul(2.0f, cadd(cmul(x, x), cmul(y, y))));
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      o.a[k][i] = cadd(cadd(cmul(Rc[3 * i + 0], Rq[0 * 3 + k]), cmul(Rc[3 * i + 1], Rq[1 * 3 + k])),
+                       cmul(Rc[3 * i + 2], Rq[2 * 3 + k]));
+  o.iz = cdiv(1.0f, o.Z);
+  o.xz = cmul(o.X, o.iz);
+  o.yz = cmul(o.Y, o.iz);
+  const float fx = c.fx, fy = c.fy, cx = c.cx, cy = c.cy;
+  float ctrx = 0.f, ctry = 0.f, hx = 0.f, hy = 0.f;
+  bool whole = false;
+  if (type == 1) {
+    const float c0 = cmul(o.s[0], o.s[0]), c1 = cmul(o.s[1], o.s[1]), c2 = cmul(o.s[2], o.s[2]);
+    float V[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        V[i][j] = cadd(cadd(cmul(c0, cmul(o.a[0][i], o.a[0][j])), cmul(c1, cmul(o.a[1][i], o.a[1][j]))),
+                       cmul(c2, cmul(o.a[2][i], o.a[2][j])));
+    const float j00 = cmul(fx, o.iz), j02 = -(cmul(j00, o.xz));
+    const float j11 = cmul(fy, o.iz), j12 = -(cmul(j11, o.yz));
+    const float t00 = cadd(cmul(j00, V[0][0]), cmul(j02, V[2][0]));
+    const float t01 = cadd(cmul(j00, V[0][1]), cmul(j02, V[2][1]));
+    const float t02 = cadd(cmul(j00, V[0][2]), cmul(j02, V[2][2]));
+    const float t11 = cadd(cmul(j11, V[1][1]), cmul(j12, V[2][1]));
+    const float t12 = cadd(cmul(j11, V[1][2]), cmul(j12, V[2][2]));
+    o.s00 = cadd(cadd(cmul(j00, t00), cmul(j02, t02)), f.dilation);
+    o.s11 = cadd(cadd(cmul(j11, t11), cmul(j12, t12)), f.dilation);
+    o.s01 = cadd(cmul(j11, t01), cmul(j12, t02));
+    const float det = csub(cmul(o.s00, o.s11), cmul(o.s01, o.s01));
+    if (!(det > 0.0f)) return false;
+    ctrx = cadd(cmul(fx, o.xz), cx);
+    ctry = cadd(cmul(fy, o.yz), cy);
+    hx = csqrt(cmul(o.dmax, o.s00));
+    hy = csqrt(cmul(o.dmax, o.s11));
+  } else {
+    const float m0x = cmul(o.s[0], o.a[0][0]), m0y = cmul(o.s[0], o.a[0][1]), m0z = cmul(o.s[0], o.a[0][2]);
+    const float m1x = cmul(o.s[1], o.a[1][0]), m1y = cmul(o.s[1], o.a[1][1]), m1z = cmul(o.s[1], o.a[1][2]);
+    o.e0 = csub(m0x, cmul(o.xz, m0z));
+    o.e1 = csub(m1x, cmul(o.xz, m1z));
+    o.f0 = csub(m0y, cmul(o.yz, m0z));
+    o.f1 = csub(m1y, cmul(o.yz, m1z));
+    const float g2 = cadd(cmul(m0z, m0z), cmul(m1z, m1z));
+    const float zmin = csub(o.Z, csqrt(cmul(o.dmax, g2)));
+    if (!(zmin > f.near_z)) {
+      whole = true;
+    } else {
+      const float e2 = csub(o.X, cmul(o.xz, o.Z));
+      const float f2 = csub(o.Y, cmul(o.yz, o.Z));
+      const float D22 = csub(cmul(o.dmax, g2), cmul(o.Z, o.Z));
+      if (!(D22 < 0.0f)) {
+        whole = true;
+      } else {
+        const float D00 = csub(cmul(o.dmax, cadd(cmul(o.e0, o.e0), cmul(o.e1, o.e1))), cmul(e2, e2));
+        const float D02 = csub(cmul(o.dmax, cadd(cmul(o.e0, m0z), cmul(o.e1, m1z))), cmul(e2, o.Z));
+        const float D11 = csub(cmul(o.dmax, cadd(cmul(o.f0, o.f0), cmul(o.f1, o.f1))), cmul(f2, f2));
+        const float D12 = csub(cmul(o.dmax, cadd(cmul(o.f0, m0z), cmul(o.f1, m1z))), cmul(f2, o.Z));
+        const float qx = csub(cmul(D02, D02), cmul(D00, D22));
+        const float qy = csub(cmul(D12, D12), cmul(D11, D22));
+        if (!(qx >= 0.0f) || !(qy >= 0.0f)) {
+          whole = true;
+        } else {
+          const float nD = -D22;
+          const float ox = cdiv(D02, D22), oy = cdiv(D12, D22);
+          ctrx = cadd(cmul(fx, cadd(o.xz, ox)), cx);
+          ctry = cadd(cmul(fy, cadd(o.yz, oy)), cy);
+          hx = cmul(fx, cdiv(csqrt(qx), nD));
+          hy = cmul(fy, cdiv(csqrt(qy), nD));
+        }
+      }
+    }
+  }
+  if (whole) {
+    o.tx0 = 0; o.tx1 = (c.W - 1) / kTile;
+    o.ty0 = 0; o.ty1 = (c.H - 1) / kTile;
+  } else {
+    const float px = pad_extent(hx), py = pad_extent(hy);
+    if (!pixel_tiles(csub(ctrx, px), cadd(ctrx, px), c.W, &o.tx0, &o.tx1)) return false;
+    if (!pixel_tiles(csub(ctry, py), cadd(ctry, py), c.H, &o.ty0, &o.ty1)) return false;
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// real spherical harmonics (degree <= 3), as homogeneous polynomials in the
+// unit view direction (x, y, z); constants are the real-SH normalisations
+// (Condon-Shortley phase kept), e.g. k1 = sqrt(3/(4 pi)).
+// ---------------------------------------------------------------------------
+#define SH_K0 0.28209479177387814f   /* 1/(2 sqrt(pi)) */
+#define SH_K1 0.48860251190291992f   /* sqrt(3/(4 pi)) */
+#define SH_K2A 1.0925484305920792f   /* sqrt(15/pi)/2 */
+#define SH_K2B 0.31539156525252005f  /* sqrt(5/pi)/4 */
+#define SH_K2C 0.54627421529603959f  /* sqrt(15/pi)/4 */
+#define SH_K3A 0.59004358992664352f  /* sqrt(35/(2 pi))/4 */
+#define SH_K3B 2.8906114426405538f   /* sqrt(105/pi)/2 */
+#define SH_K3C 0.45704579946446572f  /* sqrt(21/(2 pi))/4 */
+#define SH_K3D 0.37317633259011540f  /* sqrt(7/pi)/4 */
+#define SH_K3E 1.4453057213202769f   /* sqrt(105/pi)/4 */
+
+template <int DEG>
+__device__ __forceinline__ void sh_eval(float x, float y, float z, float *Y) {
+  Y[0] = SH_K0;
+  if (DEG >= 1) {
+    Y[1] = -SH_K1 * y;
+    Y[2] = SH_K1 * z;
+    Y[3] = -SH_K1 * x;
+  }
+  if (DEG >= 2) {
+    const float xx = x * x, yy = y * y, zz = z * z;
+    Y[4] = SH_K2A * x * y;
+    Y[5] = -SH_K2A * y * z;
+    Y[6] = SH_K2B * (2.f * zz - xx - yy);
+    Y[7] = -SH_K2A * x * z;
+    Y[8] = SH_K2C * (xx - yy);
+    if (DEG >= 3) {
+      Y[9] = -SH_K3A * y * (3.f * xx - yy);
+      Y[10] = SH_K3B * x * y * z;
+      Y[11] = -SH_K3C * y * (4.f * zz - xx - yy);
+      Y[12] = SH_K3D * z * (2.f * zz - 3.f * xx - 3.f * yy);
+      Y[13] = -SH_K3C * x * (4.f * zz - xx - yy);
+      Y[14] = SH_K3E * z * (xx - yy);
+      Y[15] = -SH_K3A * x * (xx - 3.f * yy);
+    }
+  }
+}
+
+// d/d(x,y,z) of sum_k w_k Y_k
+template <int DEG>
+__device__ __forceinline__ void sh_grad(float x, float y, float z, const float *w, float g[3]) {
+  g[0] = g[1] = g[2] = 0.f;
+  if (DEG >= 1) {
+    g[1] += -SH_K1 * w[1];
+    g[2] += SH_K1 * w[2];
+    g[0] += -SH_K1 * w[3];
+  }
+  if (DEG >= 2) {
+    const float xx = x * x, yy = y * y, zz = z * z;
+    g[0] += SH_K2A * y * w[4];
+    g[1] += SH_K2A * x * w[4];
+    g[1] += -SH_K2A * z * w[5];
+    g[2] += -SH_K2A * y * w[5];
+    g[0] += -2.f * SH_K2B * x * w[6];
+    g[1] += -2.f * SH_K2B * y * w[6];
+    g[2] += 4.f * SH_K2B * z * w[6];
+    g[0] += -SH_K2A * z * w[7];
+    g[2] += -SH_K2A * x * w[7];
+    g[0] += 2.f * SH_K2C * x * w[8];
+    g[1] += -2.f * SH_K2C * y * w[8];
+    if (DEG >= 3) {
+      g[0] += -6.f * SH_K3A * x * y * w[9];
+      g[1] += -SH_K3A * (3.f * xx - 3.f * yy) * w[9];
+      g[0] += SH_K3B * y * z * w[10];
+      g[1] += SH_K3B * x * z * w[10];
+      g[2] += SH_K3B * x * y * w[10];
+      g[0] += 2.f * SH_K3C * x * y * w[11];
+      g[1] += -SH_K3C * (4.f * zz - xx - 3.f * yy) * w[11];
+      g[2] += -8.f * SH_K3C * y * z * w[11];
+      g[0] += -6.f * SH_K3D * x * z * w[12];
+      g[1] += -6.f * SH_K3D * y * z * w[12];
+      g[2] += SH_K3D * (6.f * zz - 3.f * xx - 3.f * yy) * w[12];
+      g[0] += -SH_K3C * (4.f * zz - 3.f * xx - yy) * w[13];
+      g[1] += 2.f * SH_K3C * x * y * w[13];
+      g[2] += -8.f * SH_K3C * x * z * w[13];
+      g[0] += 2.f * SH_K3E * x * z * w[14];
+      g[1] += -2.f * SH_K3E * y * z * w[14];
+      g[2] += SH_K3E * (xx - yy) * w[14];
+      g[0] += -SH_K3A * (3.f * xx - 3.f * yy) * w[15];
+      g[1] += 6.f * SH_K3A * x * y * w[15];
+    }
+  }
+}
+
+template <int DEG>
+__device__ __forceinline__ void load_sh(const float *sh, int64_t i, float *f) {
+  constexpr int NB = (DEG + 1) * (DEG + 1);
+  const float *p = sh + (int64_t)i * NB * 3;
+  if constexpr (DEG == 0) {
+    f[0] = __ldg(p); f[1] = __ldg(p + 1); f[2] = __ldg(p + 2);
+  } else {
+    // (DEG+1)^2 * 3 floats = 12, 27 or 48; rows are 16-byte aligned only for
+    // degrees 1 and 3 (48 and 192 bytes); degree 2 (108 bytes) loads scalars
+    if constexpr ((NB * 3) % 4 == 0) {
+      const float4 *p4 = reinterpret_cast<const float4 *>(p);
+#pragma unroll
+      for (int k = 0; k < NB * 3 / 4; ++k) {
+        const float4 v = __ldg(p4 + k);
+        f[4 * k] = v.x; f[4 * k + 1] = v.y; f[4 * k + 2] = v.z; f[4 * k + 3] = v.w;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < NB * 3; ++k) f[k] = __ldg(p + k);
+    }
+  }
+}
+
+__device__ __forceinline__ int normal_axis(int type, const float ls[3]) {
+  if (type == 0) return 2;
+  if (ls[2] <= ls[0] && ls[2] <= ls[1]) return 2;
+  return ls[0] <= ls[1] ? 0 : 1;
+}
+
+__device__ __forceinline__ void load_params(const PrepArgs &a, int64_t i, float mu[3], float ls[3],
+                                            float q[4], float &logit, int &type) {
+  mu[0] = __ldg(a.means + 3 * i); mu[1] = __ldg(a.means + 3 * i + 1); mu[2] = __ldg(a.means + 3 * i + 2);
+  ls[0] = __ldg(a.log_scales + 3 * i); ls[1] = __ldg(a.log_scales + 3 * i + 1);
+  ls[2] = __ldg(a.log_scales + 3 * i + 2);
+  const float4 qv = __ldg(reinterpret_cast<const float4 *>(a.quats) + i);
+  q[0] = qv.x; q[1] = qv.y; q[2] = qv.z; q[3] = qv.w;
+  logit = __ldg(a.logits + i);
+  type = __ldg(a.types + i) ? 1 : 0;
+}
+
+// 2D opacity modulation (Eqs. 6-7): alpha* = alpha exp(-lambda s_z*),
+// s_z* = sigmoid((s_z - theta_z)/T_z) s_z.  Returns alpha*, and the factors
+// the backward needs.
+__device__ __forceinline__ float modulate(float alpha, float sz, const CfgK &f, float *gate,
+                                          float *fac) {
+  const float g = 1.0f / (1.0f + expf(-(sz - f.theta_z) / f.T_z));
+  const float e = expf(-f.lambda_z * (g * sz));
+  *gate = g;
+  *fac = e;
+  return alpha * e;
+}
+
+// ---------------------------------------------------------------------------
+// forward kernel
+// ---------------------------------------------------------------------------
+template <int DEG>
+__global__ void __launch_bounds__(256) preprocess_fwd_kernel(PrepArgs a) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  float mu[3], ls[3], q[4], logit;
+  int type;
+  load_params(a, i, mu, ls, q, logit, type);
+  Contract o;
+  const bool binned = run_contract(mu, ls, q, logit, type, a.cam, a.cfg, o);
+  a.depth_key[i] = o.dbits;
+  if (!binned) {
+    a.touched[i] = 0u;
+    reinterpret_cast<uint2 *>(a.rect)[i] = make_uint2(0u, 0u);
+    return;
+  }
+  a.touched[i] = (uint32_t)((o.tx1 - o.tx0 + 1) * (o.ty1 - o.ty0 + 1));
+  reinterpret_cast<uint2 *>(a.rect)[i] =
+      make_uint2((uint32_t)o.tx0 | ((uint32_t)o.tx1 << 16), (uint32_t)o.ty0 | ((uint32_t)o.ty1 << 16));
+
+  const CamK &c = a.cam;
+  // colour (Sec. 3.1): SH decoded along the view direction
+  constexpr int NB = (DEG + 1) * (DEG + 1);
+  float f[NB * 3];
+  load_sh<DEG>(a.sh, i, f);
+  float dx = mu[0] - c.campos[0], dy = mu[1] - c.campos[1], dz = mu[2] - c.campos[2];
+  const float il = rsqrtf(dx * dx + dy * dy + dz * dz);
+  dx *= il; dy *= il; dz *= il;
+  float Y[NB];
+  sh_eval<DEG>(dx, dy, dz, Y);
+  float col[3];
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch) {
+    float v = 0.5f;
+#pragma unroll
+    for (int k = 0; k < NB; ++k) v = fmaf(f[3 * k + ch], Y[k], v);
+    col[ch] = fmaxf(v, 0.0f);
+  }
+  // normal: smallest-scale axis (z for a surfel), facing the camera
+  const int kn = normal_axis(type, ls);
+  float n0 = o.a[kn][0], n1 = o.a[kn][1], n2 = o.a[kn][2];
+  if (n0 * o.X + n1 * o.Y + n2 * o.Z > 0.0f) { n0 = -n0; n1 = -n1; n2 = -n2; }
+  const float ctrx = fmaf(c.fx, o.xz, c.cx), ctry = fmaf(c.fy, o.yz, c.cy);
+  Rec r;
+  if (type == 1) {
+    const float det = o.s00 * o.s11 - o.s01 * o.s01;
+    const float id = 1.0f / det;
+    r.r0 = make_float4(ctrx, ctry, o.Z, o.alpha);
+    r.r1 = make_float4(o.s11 * id, -o.s01 * id, o.s00 * id, 0.0f);
+    r.r2 = make_float4(0.0f, 0.0f, col[0], col[1]);
+  } else {
+    float gate, fac;
+    const float am = modulate(o.alpha, o.s[2], a.cfg, &gate, &fac);
+    const float m0z = o.s[0] * o.a[0][2], m1z = o.s[1] * o.a[1][2];
+    const float detE = o.e0 * o.f1 - o.e1 * o.f0;
+    const float ie = 1.0f / detE;
+    const float E00 = o.f1 * ie, E01 = -o.e1 * ie, E10 = -o.f0 * ie, E11 = o.e0 * ie;
+    const float ifx = 1.0f / c.fx, ify = 1.0f / c.fy;
+    float Q00 = o.Z * E00 * ifx, Q01 = o.Z * E01 * ify, Q10 = o.Z * E10 * ifx, Q11 = o.Z * E11 * ify;
+    float Q20 = -(m0z * E00 + m1z * E10) * ifx, Q21 = -(m0z * E01 + m1z * E11) * ify;
+    float as = -am;
+    const bool finite = isfinite(Q00) && isfinite(Q01) && isfinite(Q10) && isfinite(Q11) &&
+                        isfinite(Q20) && isfinite(Q21);
+    if (!finite) {
+      // edge-on surfel (plane through the camera centre): it covers no pixel;
+      // a zero-opacity record keeps the binned list intact
+      Q00 = Q01 = Q10 = Q11 = Q20 = Q21 = 0.0f;
+      as = -0.0f;
+    }
+    r.r0 = make_float4(ctrx, ctry, o.Z, as);
+    r.r1 = make_float4(Q00, Q01, Q10, Q11);
+    r.r2 = make_float4(Q20, Q21, col[0], col[1]);
+  }
+  r.r3 = make_float4(col[2], n0, n1, n2);
+  float4 *dst = reinterpret_cast<float4 *>(a.rec) + 4 * i;
+  dst[0] = r.r0; dst[1] = r.r1; dst[2] = r.r2; dst[3] = r.r3;
+}
+
+// ---------------------------------------------------------------------------
+// backward kernel
+// ---------------------------------------------------------------------------
+template <int DEG>
+__global__ void __launch_bounds__(256) preprocess_bwd_kernel(PrepArgs a, PrepGradArgs g) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  constexpr int NB = (DEG + 1) * (DEG + 1);
+  float *gsh = g.sh + (int64_t)i * NB * 3;
+  if (__ldg(a.touched + i) == 0u) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) { g.means[3 * i + k] = 0.f; g.log_scales[3 * i + k] = 0.f; }
+    reinterpret_cast<float4 *>(g.quats)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    g.logits[i] = 0.f;
+    for (int k = 0; k < NB * 3; ++k) gsh[k] = 0.f;
+    return;
+  }
+  float mu[3], ls[3], q[4], logit;
+  int type;
+  load_params(a, i, mu, ls, q, logit, type);
+  Contract o;
+  run_contract(mu, ls, q, logit, type, a.cam, a.cfg, o);
+  const CamK &c = a.cam;
+  float G[kGradW];
+  {
+    const float4 *src = reinterpret_cast<const float4 *>(g.rec_grad) + 4 * i;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float4 v = src[k];
+      G[4 * k] = v.x; G[4 * k + 1] = v.y; G[4 * k + 2] = v.z; G[4 * k + 3] = v.w;
+    }
+  }
+  float dX = 0.f, dY = 0.f, dZ = G[6];
+  float dA[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+  float dls[3] = {0.f, 0.f, 0.f};
+  float dalpha = 0.f;
+  const float fx = c.fx, fy = c.fy;
+  const float X = o.X, Y = o.Y, Z = o.Z, iz = o.iz;
+
+  // normal
+  {
+    const int kn = normal_axis(type, ls);
+    const float sg = (o.a[kn][0] * X + o.a[kn][1] * Y + o.a[kn][2] * Z > 0.0f) ? -1.f : 1.f;
+    dA[kn][0] += sg * G[13];
+    dA[kn][1] += sg * G[14];
+    dA[kn][2] += sg * G[15];
+  }
+  const float dxc = G[4], dyc = G[5];
+  if (type == 1) {
+    dalpha = G[0];
+    // conic (a, b, c) = inverse of (s00, s01; s01, s11)
+    const float det = o.s00 * o.s11 - o.s01 * o.s01;
+    const float id = 1.0f / det;
+    const float ca = o.s11 * id, cb = -o.s01 * id, cc = o.s00 * id;
+    const float ga = G[7], gb = G[8], gc = G[9];
+    const float ds00 = -(ga * ca * ca + gb * ca * cb + gc * cb * cb);
+    const float ds11 = -(ga * cb * cb + gb * cb * cc + gc * cc * cc);
+    const float ds01 = -(2.f * ga * ca * cb + gb * (ca * cc + cb * cb) + 2.f * gc * cb * cc);
+    // Sigma' = J V J^T,  J0 = (j00, 0, j02), J1 = (0, j11, j12)
+    const float j00 = fx * iz, j02 = -fx * X * iz * iz, j11 = fy * iz, j12 = -fy * Y * iz * iz;
+    const float cs0 = o.s[0] * o.s[0], cs1 = o.s[1] * o.s[1], cs2 = o.s[2] * o.s[2];
+    float V[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int s = 0; s < 3; ++s)
+        V[r][s] = cs0 * o.a[0][r] * o.a[0][s] + cs1 * o.a[1][r] * o.a[1][s] + cs2 * o.a[2][r] * o.a[2][s];
+    const float J0[3] = {j00, 0.f, j02}, J1[3] = {0.f, j11, j12};
+    float VJ0[3], VJ1[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      VJ0[r] = V[r][0] * J0[0] + V[r][1] * J0[1] + V[r][2] * J0[2];
+      VJ1[r] = V[r][0] * J1[0] + V[r][1] * J1[1] + V[r][2] * J1[2];
+    }
+    // dL/dV (full matrix): ds00 J0 J0^T + ds01 J0 J1^T + ds11 J1 J1^T
+    float dV[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int s = 0; s < 3; ++s)
+        dV[r][s] = ds00 * J0[r] * J0[s] + ds01 * J0[r] * J1[s] + ds11 * J1[r] * J1[s];
+    // dJ0 = 2 ds00 V J0 + ds01 V J1;  dJ1 = ds01 V J0 + 2 ds11 V J1
+    const float dj00 = 2.f * ds00 * VJ0[0] + ds01 * VJ1[0];
+    const float dj02 = 2.f * ds00 * VJ0[2] + ds01 * VJ1[2];
+    const float dj11 = ds01 * VJ0[1] + 2.f * ds11 * VJ1[1];
+    const float dj12 = ds01 * VJ0[2] + 2.f * ds11 * VJ1[2];
+    const float iz2 = iz * iz, iz3 = iz2 * iz;
+    dX += dj02 * (-fx * iz2);
+    dY += dj12 * (-fy * iz2);
+    dZ += dj00 * (-fx * iz2) + dj02 * (2.f * fx * X * iz3) + dj11 * (-fy * iz2) + dj12 * (2.f * fy * Y * iz3);
+    // V = sum_k s_k^2 a_k a_k^T
+    const float csk[3] = {cs0, cs1, cs2};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      float dcs = 0.f;
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int s = 0; s < 3; ++s) dcs += dV[r][s] * o.a[k][r] * o.a[k][s];
+      dls[k] += 2.f * csk[k] * dcs;  // d/dlog s_k of s_k^2 = 2 s_k^2
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        float acc = 0.f;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) acc += (dV[m][r] + dV[r][m]) * o.a[k][r];
+        dA[k][m] += csk[k] * acc;
+      }
+    }
+  } else {
+    // re-centred homography block and its inverse
+    const float m0z = o.s[0] * o.a[0][2], m1z = o.s[1] * o.a[1][2];
+    const float detE = o.e0 * o.f1 - o.e1 * o.f0;
+    const float ie = 1.0f / detE;
+    const float E00 = o.f1 * ie, E01 = -o.e1 * ie, E10 = -o.f0 * ie, E11 = o.e0 * ie;
+    const float ifx = 1.0f / fx, ify = 1.0f / fy;
+    const bool ok = isfinite(ie) && isfinite(E00) && isfinite(E01) && isfinite(E10) && isfinite(E11);
+    float dm0[3] = {0.f, 0.f, 0.f}, dm1[3] = {0.f, 0.f, 0.f};
+    float dxz = dxc * fx, dyz = dyc * fy;
+    if (ok) {
+      const float Q00 = Z * E00 * ifx, Q01 = Z * E01 * ify, Q10 = Z * E10 * ifx, Q11 = Z * E11 * ify;
+      const float gQ00 = G[7], gQ01 = G[8], gQ10 = G[9], gQ11 = G[10], gQ20 = G[11], gQ21 = G[12];
+      float dE00 = gQ00 * Z * ifx, dE01 = gQ01 * Z * ify, dE10 = gQ10 * Z * ifx, dE11 = gQ11 * Z * ify;
+      dZ += (gQ00 * Q00 + gQ01 * Q01 + gQ10 * Q10 + gQ11 * Q11) * iz;
+      const float dh0 = -gQ20 * ifx, dh1 = -gQ21 * ify;
+      dm0[2] += dh0 * E00 + dh1 * E01;
+      dm1[2] += dh0 * E10 + dh1 * E11;
+      dE00 += dh0 * m0z; dE10 += dh0 * m1z; dE01 += dh1 * m0z; dE11 += dh1 * m1z;
+      // dE = -Einv^T dEinv Einv^T
+      const float de0 = -(E00 * (dE00 * E00 + dE01 * E01) + E10 * (dE10 * E00 + dE11 * E01));
+      const float de1 = -(E00 * (dE00 * E10 + dE01 * E11) + E10 * (dE10 * E10 + dE11 * E11));
+      const float df0 = -(E01 * (dE00 * E00 + dE01 * E01) + E11 * (dE10 * E00 + dE11 * E01));
+      const float df1 = -(E01 * (dE00 * E10 + dE01 * E11) + E11 * (dE10 * E10 + dE11 * E11));
+      // e0 = m0x - xz m0z, e1 = m1x - xz m1z, f0 = m0y - yz m0z, f1 = m1y - yz m1z
+      dm0[0] += de0; dm0[2] += -de0 * o.xz; dxz += -de0 * m0z;
+      dm1[0] += de1; dm1[2] += -de1 * o.xz; dxz += -de1 * m1z;
+      dm0[1] += df0; dm0[2] += -df0 * o.yz; dyz += -df0 * m0z;
+      dm1[1] += df1; dm1[2] += -df1 * o.yz; dyz += -df1 * m1z;
+    }
+    dX += dxz * iz;
+    dY += dyz * iz;
+    dZ += -(dxz * X + dyz * Y) * iz * iz;
+    // m0 = s_x a0, m1 = s_y a1
+    dls[0] += o.s[0] * (dm0[0] * o.a[0][0] + dm0[1] * o.a[0][1] + dm0[2] * o.a[0][2]);
+    dls[1] += o.s[1] * (dm1[0] * o.a[1][0] + dm1[1] * o.a[1][1] + dm1[2] * o.a[1][2]);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      dA[0][m] += o.s[0] * dm0[m];
+      dA[1][m] += o.s[1] * dm1[m];
+    }
+    // scale modulation (Eqs. 6-7)
+    float gate, fac;
+    const float am = modulate(o.alpha, o.s[2], a.cfg, &gate, &fac);
+    dalpha = G[0] * fac;
+    const float dszs = G[0] * am * (-a.cfg.lambda_z);
+    const float dsz = dszs * (gate + o.s[2] * gate * (1.f - gate) / a.cfg.T_z);
+    dls[2] += dsz * o.s[2];
+  }
+  // projected centre (x_c = fx X/Z + cx) for 3D; 2D folded it into dxz above
+  if (type == 1) {
+    dX += dxc * fx * iz;
+    dY += dyc * fy * iz;
+    dZ += -(dxc * fx * X + dyc * fy * Y) * iz * iz;
+  }
+  // camera: mu_c = R_cw mu + t
+  float dmu[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) dmu[k] = c.R[k] * dX + c.R[3 + k] * dY + c.R[6 + k] * dZ;
+  // axes: a_k = R_cw Rq[:,k]  ->  dRq[:,k] = R_cw^T dA[k]
+  float dR[9];
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+      dR[3 * r + k] = c.R[r] * dA[k][0] + c.R[3 + r] * dA[k][1] + c.R[6 + r] * dA[k][2];
+  const float w = o.qn[0], x = o.qn[1], y = o.qn[2], z = o.qn[3];
+  float dq[4];
+  dq[0] = 2.f * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
+  dq[1] = 2.f * (y * dR[1] + z * dR[2] + y * dR[3] - 2.f * x * dR[4] - w * dR[5] + z * dR[6] + w * dR[7] - 2.f * x * dR[8]);
+  dq[2] = 2.f * (-2.f * y * dR[0] + x * dR[1] + w * dR[2] + x * dR[3] + z * dR[5] - w * dR[6] + z * dR[7] - 2.f * y * dR[8]);
+  dq[3] = 2.f * (-2.f * z * dR[0] - w * dR[1] + x * dR[2] + w * dR[3] - 2.f * z * dR[4] + y * dR[5] + x * dR[6] + y * dR[7]);
+  const float qd = w * dq[0] + x * dq[1] + y * dq[2] + z * dq[3];
+  float4 gq;
+  gq.x = (dq[0] - w * qd) * o.qinv;
+  gq.y = (dq[1] - x * qd) * o.qinv;
+  gq.z = (dq[2] - y * qd) * o.qinv;
+  gq.w = (dq[3] - z * qd) * o.qinv;
+  // colour
+  float f[NB * 3];
+  load_sh<DEG>(a.sh, i, f);
+  float vx = mu[0] - c.campos[0], vy = mu[1] - c.campos[1], vz = mu[2] - c.campos[2];
+  const float il = rsqrtf(vx * vx + vy * vy + vz * vz);
+  const float ux = vx * il, uy = vy * il, uz = vz * il;
+  float Yb[NB];
+  sh_eval<DEG>(ux, uy, uz, Yb);
+  float dv[3];
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch) {
+    float v = 0.5f;
+#pragma unroll
+    for (int k = 0; k < NB; ++k) v = fmaf(f[3 * k + ch], Yb[k], v);
+    dv[ch] = v > 0.0f ? G[1 + ch] : 0.0f;
+  }
+#pragma unroll
+  for (int k = 0; k < NB; ++k)
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) gsh[3 * k + ch] = dv[ch] * Yb[k];
+  if (DEG > 0) {
+    float wk[NB];
+#pragma unroll
+    for (int k = 0; k < NB; ++k) wk[k] = dv[0] * f[3 * k] + dv[1] * f[3 * k + 1] + dv[2] * f[3 * k + 2];
+    float gd[3];
+    sh_grad<DEG>(ux, uy, uz, wk, gd);
+    const float dotp = gd[0] * ux + gd[1] * uy + gd[2] * uz;
+    dmu[0] += (gd[0] - ux * dotp) * il;
+    dmu[1] += (gd[1] - uy * dotp) * il;
+    dmu[2] += (gd[2] - uz * dotp) * il;
+  }
+  const float dlogit = dalpha * o.alpha * (1.f - o.alpha);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    g.means[3 * i + k] = dmu[k];
+    g.log_scales[3 * i + k] = dls[k];
+  }
+  reinterpret_cast<float4 *>(g.quats)[i] = gq;
+  g.logits[i] = dlogit;
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+int launch_preprocess_fwd(const PrepArgs &a, int deg, cudaStream_t s) {
+  if (a.n == 0) return 0;
+  const unsigned grid = (unsigned)((a.n + 255) / 256);
+  switch (deg) {
+    case 0: preprocess_fwd_kernel<0><<<grid, 256, 0, s>>>(a); break;
+    case 1: preprocess_fwd_kernel<1><<<grid, 256, 0, s>>>(a); break;
+    case 2: preprocess_fwd_kernel<2><<<grid, 256, 0, s>>>(a); break;
+    default: preprocess_fwd_kernel<3><<<grid, 256, 0, s>>>(a); break;
+  }
+  return 0;
+}
+
+int launch_preprocess_bwd(const PrepArgs &a, const PrepGradArgs &g, int deg, cudaStream_t s) {
+  if (a.n == 0) return 0;
+  const unsigned grid = (unsigned)((a.n + 255) / 256);
+  switch (deg) {
+    case 0: preprocess_bwd_kernel<0><<<grid, 256, 0, s>>>(a, g); break;
+    case 1: preprocess_bwd_kernel<1><<<grid, 256, 0, s>>>(a, g); break;
+    case 2: preprocess_bwd_kernel<2><<<grid, 256, 0, s>>>(a, g); break;
+    default: preprocess_bwd_kernel<3><<<grid, 256, 0, s>>>(a, g); break;
+  }
+  return 0;
+}
+
+}  // namespace hgs

@@ -1,0 +1,348 @@
+// render.cu -- per-tile blending of the hybrid rasterizer (EGGS Sec. 3.1,
+// Eq. 1, Eq. 2) and its backward.
+//
+// One CTA per 16x16 tile, 8 warps; each warp owns an 8x4 pixel block and
+// walks the tile's sorted list on its own: it stages the list 32 records at a
+// time into a private double buffer in shared memory with cp.async, and
+// leaves as soon as a ballot says every one of its pixels has terminated
+// (transmittance below T_min).  No CTA-wide barrier is ever taken, so warps
+// of a tile never wait for each other.
+//
+// The per-pair evaluation (eval_pair) is written with explicitly rounded
+// operations so the backward kernel reproduces the forward's contribution
+// decisions bit for bit.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace hgs {
+
+constexpr int kRW = 8;   // warps per CTA
+constexpr int kCh = 32;  // records per staged chunk
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+struct PairEval {
+  float dx, dy, z, q, g, araw, at, alpha, u, v, inv;
+};
+
+// Unified distance (Eq. 1) and contribution (Sec. 3.1) of one record at the
+// pixel centre (px, py).  Returns true iff the pair contributes.
+__device__ __forceinline__ bool eval_pair(const float4 &r0, const float4 &r1, const float4 &r2,
+                                          float px, float py, const CfgK &f, PairEval &e) {
+  e.dx = __fsub_rn(px, r0.x);
+  e.dy = __fsub_rn(py, r0.y);
+  float q;
+  if (r0.w > 0.0f) {
+    // 3D: d = a dx^2 + 2 b dx dy + c dy^2 with the conic of Eq. 13
+    const float h = __fmaf_rn(r1.x, e.dx, __fmul_rn(__fadd_rn(r1.y, r1.y), e.dy));
+    q = __fmaf_rn(__fmul_rn(r1.z, e.dy), e.dy, __fmul_rn(h, e.dx));
+    e.alpha = r0.w;
+    e.z = r0.z;
+  } else {
+    // 2D: ray-splat intersection (Eq. 14), re-centred on the projected centre
+    const float p0 = __fmaf_rn(r1.x, e.dx, __fmul_rn(r1.y, e.dy));
+    const float p1 = __fmaf_rn(r1.z, e.dx, __fmul_rn(r1.w, e.dy));
+    const float p2 = __fmaf_rn(r2.x, e.dx, __fmaf_rn(r2.y, e.dy, 1.0f));
+    if (!(p2 > 0.0f)) return false;
+    e.inv = rcp_approx(p2);
+    e.z = __fmul_rn(r0.z, e.inv);
+    if (!(e.z > f.near_z)) return false;
+    e.u = __fmul_rn(p0, e.inv);
+    e.v = __fmul_rn(p1, e.inv);
+    q = __fmaf_rn(e.u, e.u, __fmul_rn(e.v, e.v));
+    e.alpha = -r0.w;
+  }
+  e.q = q;
+  e.g = ex2_approx(__fmul_rn(q, -0.5f * kLog2e));
+  e.araw = __fmul_rn(e.alpha, e.g);
+  if (!(e.araw >= f.alpha_min)) return false;
+  e.at = fminf(e.araw, f.alpha_max);
+  return true;
+}
+
+__device__ __forceinline__ void pixel_of(int tile, int TX, int warp, int lane, int &px, int &py) {
+  const int tx = tile % TX, ty = tile / TX;
+  px = tx * kTile + (warp & 1) * 8 + (lane & 7);
+  py = ty * kTile + (warp >> 1) * 4 + (lane >> 3);
+}
+
+// ---------------------------------------------------------------------------
+// forward
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kRW * 32) render_fwd_kernel(RenderArgs a) {
+  __shared__ __align__(16) float4 sm[kRW][2][kCh * 4];
+  const int tile = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int pxi, pyi;
+  pixel_of(tile, a.cam.TX, warp, lane, pxi, pyi);
+  const bool inside = pxi < a.cam.W && pyi < a.cam.H;
+  const float px = (float)pxi + 0.5f, py = (float)pyi + 0.5f;
+  const uint32_t start = a.ranges[2 * tile], end = a.ranges[2 * tile + 1];
+  const float4 *rec = reinterpret_cast<const float4 *>(a.rec);
+  float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f, N0 = 0.f, N1 = 0.f, N2 = 0.f;
+  uint32_t last = 0;
+  bool done = !inside;
+  if (__all_sync(0xffffffffu, done)) return;
+
+  if (start < end) {
+    const uint32_t idx = start + lane;
+    if (idx < end) {
+      const float4 *src = rec + 4 * (size_t)__ldg(a.vals + idx);
+      float4 *dst = &sm[warp][0][lane * 4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) cp_async16(dst + k, src + k);
+    }
+    cp_async_commit();
+  }
+  int buf = 0;
+  for (uint32_t base = start; base < end; base += kCh) {
+    const bool has_next = base + kCh < end;
+    if (has_next) {
+      const uint32_t idx = base + kCh + lane;
+      if (idx < end) {
+        const float4 *src = rec + 4 * (size_t)__ldg(a.vals + idx);
+        float4 *dst = &sm[warp][buf ^ 1][lane * 4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) cp_async16(dst + k, src + k);
+      }
+      cp_async_commit();
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncwarp();
+    const int cnt = (int)min((uint32_t)kCh, end - base);
+    if (!done) {
+      const float4 *chunk = &sm[warp][buf][0];
+      for (int j = 0; j < cnt; ++j) {
+        const float4 r0 = chunk[4 * j], r1 = chunk[4 * j + 1], r2 = chunk[4 * j + 2];
+        PairEval e;
+        if (!eval_pair(r0, r1, r2, px, py, a.cfg, e)) continue;
+        const float Tn = T * (1.0f - e.at);
+        if (Tn < a.cfg.T_min) {
+          done = true;
+          break;
+        }
+        const float w = e.at * T;
+        const float4 r3 = chunk[4 * j + 3];
+        C0 = fmaf(w, r2.z, C0);
+        C1 = fmaf(w, r2.w, C1);
+        C2 = fmaf(w, r3.x, C2);
+        D = fmaf(w, e.z, D);
+        N0 = fmaf(w, r3.y, N0);
+        N1 = fmaf(w, r3.z, N1);
+        N2 = fmaf(w, r3.w, N2);
+        T = Tn;
+        last = base - start + (uint32_t)j + 1u;
+      }
+    }
+    if (__all_sync(0xffffffffu, done)) break;
+    __syncwarp();
+    buf ^= 1;
+  }
+  cp_async_wait<0>();
+  if (!inside) return;
+  const size_t HW = (size_t)a.cam.W * a.cam.H;
+  const size_t p = (size_t)pyi * a.cam.W + pxi;
+  a.rgb[p] = C0 + T * a.cfg.bg[0];
+  a.rgb[p + HW] = C1 + T * a.cfg.bg[1];
+  a.rgb[p + 2 * HW] = C2 + T * a.cfg.bg[2];
+  a.depth[p] = D;
+  a.normal[p] = N0;
+  a.normal[p + HW] = N1;
+  a.normal[p + 2 * HW] = N2;
+  a.alpha[p] = 1.0f - T;
+  a.T_final[p] = T;
+  a.n_last[p] = last;
+}
+
+// ---------------------------------------------------------------------------
+// backward
+// ---------------------------------------------------------------------------
+// Sum 16 per-lane values over the warp by recursive halving: after five
+// exchange steps lane l holds the total of component
+// 8 b4 + 4 b3 + 2 b2 + b1 (b = bits of l); lanes l and l^1 hold the same one.
+__device__ __forceinline__ float warp_sum16(float (&v)[16], int lane, int &comp) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const bool hi = lane & 16;
+    const float send = hi ? v[i] : v[i + 8];
+    const float keep = hi ? v[i + 8] : v[i];
+    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const bool hi = lane & 8;
+    const float send = hi ? v[i] : v[i + 4];
+    const float keep = hi ? v[i + 4] : v[i];
+    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const bool hi = lane & 4;
+    const float send = hi ? v[i] : v[i + 2];
+    const float keep = hi ? v[i + 2] : v[i];
+    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  {
+    const bool hi = lane & 2;
+    const float send = hi ? v[0] : v[1];
+    const float keep = hi ? v[1] : v[0];
+    v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+  }
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+  comp = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+  return v[0];
+}
+
+__global__ void __launch_bounds__(kRW * 32) render_bwd_kernel(RenderBwdArgs a) {
+  __shared__ __align__(16) float4 sm[kRW][2][kCh * 4];
+  __shared__ uint32_t sid[kRW][2][kCh];
+  const int tile = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int pxi, pyi;
+  pixel_of(tile, a.cam.TX, warp, lane, pxi, pyi);
+  const bool inside = pxi < a.cam.W && pyi < a.cam.H;
+  const float px = (float)pxi + 0.5f, py = (float)pyi + 0.5f;
+  const uint32_t start = a.ranges[2 * tile];
+  const size_t HW = (size_t)a.cam.W * a.cam.H;
+  const size_t p = inside ? (size_t)pyi * a.cam.W + pxi : 0;
+  float T = 1.0f;
+  uint32_t last = 0;
+  float dC0 = 0.f, dC1 = 0.f, dC2 = 0.f, dD = 0.f, dN0 = 0.f, dN1 = 0.f, dN2 = 0.f, dA = 0.f;
+  if (inside) {
+    T = a.T_final[p];
+    last = a.n_last[p];
+    if (a.g_rgb) { dC0 = a.g_rgb[p]; dC1 = a.g_rgb[p + HW]; dC2 = a.g_rgb[p + 2 * HW]; }
+    if (a.g_depth) dD = a.g_depth[p];
+    if (a.g_normal) { dN0 = a.g_normal[p]; dN1 = a.g_normal[p + HW]; dN2 = a.g_normal[p + 2 * HW]; }
+    if (a.g_alpha) dA = a.g_alpha[p];
+  }
+  // accumulated colour / depth / normal / alpha of everything behind
+  float ac0 = a.cfg.bg[0], ac1 = a.cfg.bg[1], ac2 = a.cfg.bg[2];
+  float az = 0.f, an0 = 0.f, an1 = 0.f, an2 = 0.f, aa = 0.f;
+  const uint32_t wmax = __reduce_max_sync(0xffffffffu, last);
+  if (wmax == 0) return;
+  const float4 *rec = reinterpret_cast<const float4 *>(a.rec);
+
+  uint32_t ce = start + wmax;
+  uint32_t cs = ce - min((uint32_t)kCh, wmax);
+  {
+    const uint32_t idx = cs + lane;
+    if (idx < ce) {
+      const uint32_t id = __ldg(a.vals + idx);
+      sid[warp][0][lane] = id;
+      const float4 *src = rec + 4 * (size_t)id;
+      float4 *dst = &sm[warp][0][lane * 4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) cp_async16(dst + k, src + k);
+    }
+    cp_async_commit();
+  }
+  int buf = 0;
+  while (true) {
+    const bool has_next = cs > start;
+    const uint32_t ncs = has_next ? cs - min((uint32_t)kCh, cs - start) : cs;
+    if (has_next) {
+      const uint32_t idx = ncs + lane;
+      if (idx < cs) {
+        const uint32_t id = __ldg(a.vals + idx);
+        sid[warp][buf ^ 1][lane] = id;
+        const float4 *src = rec + 4 * (size_t)id;
+        float4 *dst = &sm[warp][buf ^ 1][lane * 4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) cp_async16(dst + k, src + k);
+      }
+      cp_async_commit();
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncwarp();
+    const float4 *chunk = &sm[warp][buf][0];
+    for (int jj = (int)(ce - cs) - 1; jj >= 0; --jj) {
+      const uint32_t j = cs + (uint32_t)jj;
+      const float4 r0 = chunk[4 * jj], r1 = chunk[4 * jj + 1], r2 = chunk[4 * jj + 2];
+      PairEval e;
+      const bool contrib = inside && (j - start) < last && eval_pair(r0, r1, r2, px, py, a.cfg, e);
+      if (!__any_sync(0xffffffffu, contrib)) continue;
+      float g[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) g[k] = 0.f;
+      if (contrib) {
+        const float4 r3 = chunk[4 * jj + 3];
+        const float c0 = r2.z, c1 = r2.w, c2 = r3.x, n0 = r3.y, n1 = r3.z, n2 = r3.w;
+        const float om = 1.0f - e.at;
+        const float Ti = __fdividef(T, om);
+        const float w = e.at * Ti;
+        const float fsum = (c0 - ac0) * dC0 + (c1 - ac1) * dC1 + (c2 - ac2) * dC2 + (e.z - az) * dD +
+                           (n0 - an0) * dN0 + (n1 - an1) * dN1 + (n2 - an2) * dN2 + (1.0f - aa) * dA;
+        const float dat = Ti * fsum;
+        ac0 += e.at * (c0 - ac0); ac1 += e.at * (c1 - ac1); ac2 += e.at * (c2 - ac2);
+        az += e.at * (e.z - az);
+        an0 += e.at * (n0 - an0); an1 += e.at * (n1 - an1); an2 += e.at * (n2 - an2);
+        aa += e.at * (1.0f - aa);
+        T = Ti;
+        g[1] = w * dC0; g[2] = w * dC1; g[3] = w * dC2;
+        g[13] = w * dN0; g[14] = w * dN1; g[15] = w * dN2;
+        const float dzp = w * dD;
+        float dd = 0.f;
+        if (e.araw <= a.cfg.alpha_max) {
+          g[0] = dat * e.g;
+          dd = dat * (-0.5f * e.at);
+        }
+        if (r0.w > 0.0f) {
+          g[7] = dd * e.dx * e.dx;
+          g[8] = dd * 2.0f * e.dx * e.dy;
+          g[9] = dd * e.dy * e.dy;
+          const float ddx = dd * 2.0f * (r1.x * e.dx + r1.y * e.dy);
+          const float ddy = dd * 2.0f * (r1.y * e.dx + r1.z * e.dy);
+          g[4] = -ddx; g[5] = -ddy; g[6] = dzp;
+        } else {
+          const float du = 2.0f * e.u * dd, dv = 2.0f * e.v * dd;
+          const float dp0 = du * e.inv, dp1 = dv * e.inv;
+          const float dp2 = -(du * e.u + dv * e.v + dzp * e.z) * e.inv;
+          g[7] = dp0 * e.dx; g[8] = dp0 * e.dy;
+          g[9] = dp1 * e.dx; g[10] = dp1 * e.dy;
+          g[11] = dp2 * e.dx; g[12] = dp2 * e.dy;
+          const float ddx = dp0 * r1.x + dp1 * r1.z + dp2 * r2.x;
+          const float ddy = dp0 * r1.y + dp1 * r1.w + dp2 * r2.y;
+          g[4] = -ddx; g[5] = -ddy; g[6] = dzp * e.inv;
+        }
+      }
+      int comp;
+      const float s = warp_sum16(g, lane, comp);
+      if ((lane & 1) == 0) atomicAdd(a.rec_grad + (size_t)sid[warp][buf][jj] * kGradW + comp, s);
+    }
+    if (!has_next) break;
+    __syncwarp();
+    buf ^= 1;
+    ce = cs;
+    cs = ncs;
+  }
+  cp_async_wait<0>();
+}
+
+int launch_render_fwd(const RenderArgs &a, cudaStream_t s) {
+  const int tiles = a.cam.TX * a.cam.TY;
+  if (tiles <= 0) return 0;
+  render_fwd_kernel<<<tiles, kRW * 32, 0, s>>>(a);
+  return 0;
+}
+
+int launch_render_bwd(const RenderBwdArgs &a, cudaStream_t s) {
+  const int tiles = a.cam.TX * a.cam.TY;
+  if (tiles <= 0) return 0;
+  render_bwd_kernel<<<tiles, kRW * 32, 0, s>>>(a);
+  return 0;
+}
+
+}  // namespace hgs
