@@ -212,6 +212,29 @@ int hgs_bin_sort(int64_t n, const hgs_projected *proj, const hgs_camera *cam,
                  const hgs_config *cfg, void *ws, size_t ws_bytes, int64_t capacity,
                  hgs_binning *out, int32_t *dev_err, hgs_stream_t stream);
 
+/* hgs_bin_sort_static -- hgs_bin_sort without a caller-supplied workspace,
+ * for callers that cannot allocate device memory while they render: a host
+ * application that owns the GPU allocator and forbids other cudaMalloc calls,
+ * or a real-time loop that must avoid cudaMalloc/cudaFree because they can
+ * synchronise the device.  The paper has no counterpart; this is a deployment
+ * convenience.  Inputs and outputs are exactly those of hgs_bin_sort (the
+ * caller still owns proj and out); the sort's scratch is a library-owned
+ * device array of HGS_BIN_SORT_STATIC_BYTES that every GPU loading the
+ * library reserves until the process exits.
+ * Limits: returns HGS_ERR_INVALID_ARG, launching nothing, when
+ * hgs_bin_sort_workspace(n, capacity, tiles) exceeds HGS_BIN_SORT_STATIC_BYTES
+ * (for example n = 1M with capacity 3.5M fits; the 3M-primitive scene does
+ * not).  The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array and it keeps the
+ * previous call's contents (the kernels clear what must start at zero): calls
+ * whose work can overlap on the GPU race, so serialise them.  Allocates
+ * nothing; HGS_ERR_CUDA if the address lookup or a launch fails. */
+#define HGS_BIN_SORT_STATIC_BYTES ((size_t)64 << 20)
+int hgs_bin_sort_static(int64_t n, const hgs_projected *proj, const hgs_camera *cam,
+                        const hgs_config *cfg, int64_t capacity, hgs_binning *out,
+                        int32_t *dev_err, hgs_stream_t stream);
+
 /* hgs_render_fwd -- per 16x16 tile, front-to-back blending over the tile's
  * sorted list (Eq. 2): per pair the unified distance of Eq. 1, contribution
  * a = min(alpha_max, alpha exp(-d/2)), skipped if a < alpha_min; stop before

@@ -18,6 +18,7 @@ HGS_ERR_TIMEOUT = -4
 HGS_ERR_UNSUPPORTED = -5
 HGS_EXCHANGE_ERANK = 0
 HGS_EXCHANGE_MASK = 1
+HGS_BIN_SORT_STATIC_BYTES = 64 << 20
 
 P = C.c_void_p
 
@@ -77,6 +78,8 @@ SYMBOLS = {
     "hgs_bin_sort": (C.c_int, [C.c_int64, C.POINTER(hgs_projected), C.POINTER(hgs_camera),
                                C.POINTER(hgs_config), P, C.c_size_t, C.c_int64, C.POINTER(hgs_binning),
                                P, P]),
+    "hgs_bin_sort_static": (C.c_int, [C.c_int64, C.POINTER(hgs_projected), C.POINTER(hgs_camera),
+                                      C.POINTER(hgs_config), C.c_int64, C.POINTER(hgs_binning), P, P]),
     "hgs_render_fwd": (C.c_int, [C.c_int64, C.POINTER(hgs_projected), C.POINTER(hgs_binning),
                                  C.POINTER(hgs_camera), C.POINTER(hgs_config), C.POINTER(hgs_image), P, P]),
     "hgs_render_bwd": (C.c_int, [C.POINTER(hgs_scene), C.POINTER(hgs_projected), C.POINTER(hgs_binning),
@@ -139,6 +142,7 @@ hgs_check = _fwd("hgs_check")
 hgs_preprocess = _fwd("hgs_preprocess")
 hgs_bin_sort_workspace = _fwd("hgs_bin_sort_workspace")
 hgs_bin_sort = _fwd("hgs_bin_sort")
+hgs_bin_sort_static = _fwd("hgs_bin_sort_static")
 hgs_render_fwd = _fwd("hgs_render_fwd")
 hgs_render_bwd = _fwd("hgs_render_bwd")
 hgs_exchange_types = _fwd("hgs_exchange_types")
