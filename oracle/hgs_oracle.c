@@ -284,6 +284,27 @@ static int contract_one(const float mu[3], const float ls[3], const float q[4],
         }
       }
     }
+    if (whole) {
+      /* the disc reaches the near plane: a contributing hit lies in the disc
+       * (camera-space extents R) at depth in (near, Z + Rz], so x/z and y/z
+       * are bounded by the extents divided by the depth bounds */
+      float sd = sqrtf(dmax);
+      float Rx = sd * sqrtf(m0x * m0x + m1x * m1x);
+      float Ry = sd * sqrtf(m0y * m0y + m1y * m1y);
+      float zhi = Z + sd * sqrtf(g2);
+      float xl = X - Rx, xh = X + Rx, yl = Y - Ry, yh = Y + Ry;
+      float nxl = xl >= 0.0f ? xl / zhi : xl / near_z;
+      float nxh = xh >= 0.0f ? xh / near_z : xh / zhi;
+      float nyl = yl >= 0.0f ? yl / zhi : yl / near_z;
+      float nyh = yh >= 0.0f ? yh / near_z : yh / zhi;
+      float ilx = fx * nxl + cx, ihx = fx * nxh + cx;
+      float ily = fy * nyl + cy, ihy = fy * nyh + cy;
+      ctrx = 0.5f * (ilx + ihx);
+      ctry = 0.5f * (ily + ihy);
+      hx = 0.5f * (ihx - ilx);
+      hy = 0.5f * (ihy - ily);
+      whole = 0;
+    }
   }
   int tx0, tx1, ty0, ty1;
   if (whole) {

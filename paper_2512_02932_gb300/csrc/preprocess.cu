@@ -155,6 +155,27 @@ __device__ bool run_contract(const float mu[3], const float ls[3], const float q
         }
       }
     }
+    if (whole) {
+      // The disc reaches the near plane (or its image conic is degenerate):
+      // a contributing hit lies inside the disc's camera-space extents R at a
+      // depth in (near, Z + R_z], which bounds x/z and y/z.
+      const float sd = csqrt(o.dmax);
+      const float Rx = cmul(sd, csqrt(cadd(cmul(m0x, m0x), cmul(m1x, m1x))));
+      const float Ry = cmul(sd, csqrt(cadd(cmul(m0y, m0y), cmul(m1y, m1y))));
+      const float zhi = cadd(o.Z, cmul(sd, csqrt(g2)));
+      const float xl = csub(o.X, Rx), xh = cadd(o.X, Rx), yl = csub(o.Y, Ry), yh = cadd(o.Y, Ry);
+      const float nxl = xl >= 0.0f ? cdiv(xl, zhi) : cdiv(xl, f.near_z);
+      const float nxh = xh >= 0.0f ? cdiv(xh, f.near_z) : cdiv(xh, zhi);
+      const float nyl = yl >= 0.0f ? cdiv(yl, zhi) : cdiv(yl, f.near_z);
+      const float nyh = yh >= 0.0f ? cdiv(yh, f.near_z) : cdiv(yh, zhi);
+      const float ilx = cadd(cmul(fx, nxl), cx), ihx = cadd(cmul(fx, nxh), cx);
+      const float ily = cadd(cmul(fy, nyl), cy), ihy = cadd(cmul(fy, nyh), cy);
+      ctrx = cmul(0.5f, cadd(ilx, ihx));
+      ctry = cmul(0.5f, cadd(ily, ihy));
+      hx = cmul(0.5f, csub(ihx, ilx));
+      hy = cmul(0.5f, csub(ihy, ily));
+      whole = false;
+    }
   }
   if (whole) {
     o.tx0 = 0; o.tx1 = (c.W - 1) / kTile;

@@ -219,3 +219,26 @@ def test_exchange_mask_matches_oracle():
     assert nf == nf_o == int(mask.sum())
     np.testing.assert_array_equal(ls.astype(np.float64), ls_o)
     np.testing.assert_allclose(q, q_o, atol=2e-7)
+
+
+def test_surfels_reaching_the_near_plane():
+    """Large surfels crossing the near plane (the contract's extent-bound
+    branch): lists bit-exact, images and gradients within tolerance."""
+    rng = np.random.default_rng(8)
+    n = 300
+    means = np.stack([rng.uniform(-0.4, 0.4, n), rng.uniform(-0.4, 0.4, n), rng.uniform(0.22, 1.2, n)], 1)
+    ls = np.stack([rng.normal(-1.2, 0.4, n), rng.normal(-1.2, 0.4, n), np.full(n, S.SURFEL_LOG_SZ)], 1)
+    q = rng.normal(size=(n, 4))
+    sh = np.zeros((n, 1, 3))
+    sh[:, 0] = rng.uniform(-1.7, 1.7, (n, 3))
+    scene = S.Scene(means.astype(np.float32), ls.astype(np.float32), q.astype(np.float32),
+                    rng.normal(1.0, 1.0, n).astype(np.float32), sh.astype(np.float32), np.zeros(n, np.uint8), 0)
+    cam = S.pinhole(96, 80, 70.0)
+    r, st, g = gpu_forward(scene, cam)
+    assert_lists_bitexact(r, scene, cam)
+    m = _oracle_maps(scene, cam)
+    assert_images_match(g, m, m["amb"], max_amb_frac=0.02)
+    cot = _masked_cot(4, cam, m["amb"])
+    _, ref = AR.vjp(scene, cam, CFG, cot)
+    _, got = _gpu_vjp(scene, cam, cot)
+    assert_grads_match(got, ref)

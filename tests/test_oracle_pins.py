@@ -293,6 +293,36 @@ def test_contract_is_conservative():
         assert len(p_idx) > 1000
 
 
+def test_contract_is_conservative_for_surfels_reaching_the_near_plane():
+    """Large surfels whose discs cross the near plane take the contract's
+    extent bound (contributing hits need depth > near); it must still cover
+    every contributing pair."""
+    rng = np.random.default_rng(8)
+    n = 300
+    means = np.stack([rng.uniform(-0.4, 0.4, n), rng.uniform(-0.4, 0.4, n), rng.uniform(0.22, 1.2, n)], 1)
+    ls = np.stack([rng.normal(-1.2, 0.4, n), rng.normal(-1.2, 0.4, n), np.full(n, S.SURFEL_LOG_SZ)], 1)
+    q = rng.normal(size=(n, 4))
+    sh = np.zeros((n, 1, 3))
+    scene = S.Scene(means.astype(np.float32), ls.astype(np.float32), q.astype(np.float32),
+                    rng.normal(1.0, 1.0, n).astype(np.float32), sh.astype(np.float32),
+                    np.zeros(n, np.uint8), 0)
+    cam = S.pinhole(96, 80, 70.0)
+    db, rect, touched = O.contract_bin(scene, cam, CFG)
+    yy, xx = np.mgrid[0:cam.height, 0:cam.width]
+    pix = np.stack([xx.ravel(), yy.ravel()], 1)
+    araw, ok = AR.pair_alpha(scene, cam, CFG, pix)
+    sure = ok & (araw >= CFG.alpha_min * (1 + 2e-4))
+    p_idx, g_idx = np.nonzero(sure)
+    tx, ty = pix[p_idx, 0] // CFG.tile, pix[p_idx, 1] // CFG.tile
+    r = rect[g_idx]
+    inside = (r[:, 0] <= tx) & (tx <= r[:, 1]) & (r[:, 2] <= ty) & (ty <= r[:, 3])
+    assert inside.all(), np.count_nonzero(~inside)
+    # the branch is exercised: many discs reach the near plane
+    m = means.astype(np.float64)
+    assert (m[:, 2] - 3 * np.exp(ls[:, :2]).max(1) < CFG.near).sum() > 30
+    assert len(p_idx) > 1000
+
+
 def test_tile_list_structure():
     sc, cam = S.tiny_scene(2)
     keys, vals, ranges, (db, rect, touched) = O.tile_lists(sc, cam, CFG)
