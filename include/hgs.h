@@ -101,9 +101,10 @@ typedef struct {
 } hgs_config;
 
 /* Per-primitive output of hgs_preprocess (caller-allocated, n rows each):
- *   rec        [n,16] float, A16: the render record (centre, depth, signed
- *              opacity, conic or surfel homography, colour, normal); its
- *              content is private to the library and valid for one camera.
+ *   rec        [n,20] float, A16: the render record (centre, depth, signed
+ *              opacity, conic or surfel homography, colour, normal, pixel
+ *              box); its content is private to the library and valid for one
+ *              camera.
  *   depth_key  [n] uint32: bits of the binary32 camera-space centre depth.
  *   rect       [n,4] uint16: covered tile rectangle tx0, tx1, ty0, ty1.
  *   touched    [n] uint32: tiles covered (0 = not binned). */

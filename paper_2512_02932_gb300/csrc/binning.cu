@@ -125,7 +125,32 @@ __global__ void __launch_bounds__(256) k_hist_scan(uint32_t *__restrict__ hist, 
   if (tid == 255) dtot[d] = wbase + incl;
 }
 
-// stable scatter: ranks by warp-local match + per-warp digit counters
+// stable scatter: ranks by warp-local match + per-warp digit counters.
+// The next tile's keys and values are loaded while the current one is ranked
+// (register double buffer); the per-digit bases are double-buffered so a tile
+// takes two barriers.
+struct TileRegs {
+  uint32_t key[kSortItems], val[kSortItems], dig[kSortItems];
+};
+
+__device__ __forceinline__ void load_tile(TileRegs &t, const uint32_t *__restrict__ keys_in,
+                                          const uint32_t *__restrict__ vals_in,
+                                          const uint32_t *__restrict__ valid, int64_t tb, int64_t b1,
+                                          int warp, int lane, int shift, uint32_t mask) {
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    const int64_t e = tb + warp * (32 * kSortItems) + r * 32 + lane;
+    t.dig[r] = kNoDigit;
+    t.key[r] = 0u;
+    t.val[r] = 0u;
+    if (e < b1) {
+      t.key[r] = __ldg(keys_in + e);
+      t.val[r] = vals_in ? __ldg(vals_in + e) : (uint32_t)e;
+      if (!valid || __ldg(valid + e) != 0u) t.dig[r] = (t.key[r] >> shift) & mask;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kSortThreads)
     k_scatter(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
               const uint32_t *__restrict__ valid, const int64_t *d_n, int64_t n_host,
@@ -133,9 +158,12 @@ __global__ void __launch_bounds__(kSortThreads)
               const uint32_t *__restrict__ dtot, uint32_t *__restrict__ keys_out,
               uint32_t *__restrict__ vals_out, int64_t *count_out) {
   constexpr int W = kSortThreads / 32;
-  __shared__ uint32_t base[256];
+  __shared__ uint32_t base[2][256];
   __shared__ uint32_t wcnt[W][256];
+  __shared__ uint32_t tdig[256];     // tile-local exclusive start of each digit
   __shared__ uint32_t scan_tmp[W];
+  __shared__ uint32_t stage_k[kTileElems], stage_v[kTileElems];
+  __shared__ uint32_t tile_count;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const bool aborted = d_abort && *d_abort;
   const int64_t n = aborted ? 0 : read_n(d_n, n_host);
@@ -153,7 +181,7 @@ __global__ void __launch_bounds__(kSortThreads)
     uint32_t wb = 0;
     for (int w = 0; w < warp; ++w) wb += scan_tmp[w];
     const uint32_t excl = wb + incl - t;
-    base[tid] = excl + (tid < (1 << bits) ? hist[(size_t)tid * gridDim.x + blockIdx.x] : 0u);
+    base[0][tid] = excl + (tid < (1 << bits) ? hist[(size_t)tid * gridDim.x + blockIdx.x] : 0u);
     if (count_out && blockIdx.x == 0 && tid == 255) *count_out = aborted ? 0 : (int64_t)(wb + incl);
   }
   __syncthreads();
@@ -161,35 +189,35 @@ __global__ void __launch_bounds__(kSortThreads)
   block_range(n, b0, b1);
   const uint32_t mask = (1u << bits) - 1u;
   const uint32_t lt = lanemask_lt();
+  TileRegs cur, nxt;
+  if (b0 < b1) load_tile(cur, keys_in, vals_in, valid, b0, b1, warp, lane, shift, mask);
+  int cb = 0;
   for (int64_t tb = b0; tb < b1; tb += kTileElems) {
-    uint32_t key[kSortItems], val[kSortItems], dig[kSortItems], loc[kSortItems];
-#pragma unroll
-    for (int r = 0; r < kSortItems; ++r) {
-      const int64_t e = tb + warp * (32 * kSortItems) + r * 32 + lane;
-      dig[r] = kNoDigit;
-      if (e < b1 && (!valid || __ldg(valid + e) != 0u)) {
-        key[r] = __ldg(keys_in + e);
-        val[r] = vals_in ? __ldg(vals_in + e) : (uint32_t)e;
-        dig[r] = (key[r] >> shift) & mask;
-      }
-    }
+    if (tb + kTileElems < b1)
+      load_tile(nxt, keys_in, vals_in, valid, tb + kTileElems, b1, warp, lane, shift, mask);
+    __syncwarp();
 #pragma unroll
     for (int k = 0; k < 256 / 32; ++k) wcnt[warp][lane * 8 + k] = 0u;
     __syncwarp();
+    // 1) warp-local stable ranks
+    uint32_t loc[kSortItems];
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
-      const uint32_t peers = __match_any_sync(0xffffffffu, dig[r]);
+      const uint32_t d = cur.dig[r];
+      const uint32_t peers = __match_any_sync(0xffffffffu, d);
       const int leader = __ffs(peers) - 1;
       uint32_t old = 0;
-      if (lane == leader && dig[r] != kNoDigit) {
-        old = wcnt[warp][dig[r]];
-        wcnt[warp][dig[r]] = old + __popc(peers);
+      if (lane == leader && d != kNoDigit) {
+        old = wcnt[warp][d];
+        wcnt[warp][d] = old + __popc(peers);
       }
       old = __shfl_sync(0xffffffffu, old, leader);
       loc[r] = old + __popc(peers & lt);
       __syncwarp();
     }
     __syncthreads();
+    // 2) per digit: prefix over warps, then a tile-wide exclusive scan over
+    //    digits (where each digit's run starts in the staged tile)
     uint32_t tot = 0;
     {
       uint32_t run = 0;
@@ -201,18 +229,46 @@ __global__ void __launch_bounds__(kSortThreads)
       }
       tot = run;
     }
+    uint32_t incl = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    if (lane == 31) scan_tmp[warp] = incl;
     __syncthreads();
+    {
+      uint32_t wb = 0;
+#pragma unroll
+      for (int w = 0; w < W; ++w)
+        if (w < warp) wb += scan_tmp[w];
+      tdig[tid] = wb + incl - tot;
+      base[cb ^ 1][tid] = base[cb][tid] + tot;
+      if (tid == 255) tile_count = wb + incl;
+    }
+    __syncthreads();
+    // 3) stage the tile in digit order
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
-      if (dig[r] != kNoDigit) {
-        const uint32_t pos = base[dig[r]] + wcnt[warp][dig[r]] + loc[r];
-        keys_out[pos] = key[r];
-        vals_out[pos] = val[r];
+      const uint32_t d = cur.dig[r];
+      if (d != kNoDigit) {
+        const uint32_t lpos = tdig[d] + wcnt[warp][d] + loc[r];
+        stage_k[lpos] = cur.key[r];
+        stage_v[lpos] = cur.val[r];
       }
     }
     __syncthreads();
-    base[tid] += tot;
-    __syncthreads();
+    // 4) write the digit runs out: consecutive threads, consecutive addresses
+    const uint32_t cnt = tile_count;
+    for (uint32_t i = tid; i < cnt; i += kSortThreads) {
+      const uint32_t key = stage_k[i];
+      const uint32_t d = (key >> shift) & mask;
+      const uint32_t pos = base[cb][d] + (i - tdig[d]);
+      keys_out[pos] = key;
+      vals_out[pos] = stage_v[i];
+    }
+    cb ^= 1;
+    cur = nxt;
   }
 }
 
@@ -305,52 +361,95 @@ __global__ void __launch_bounds__(kSortThreads)
 
 // ---------------------------------------------------------------------------
 // emit (tile id, primitive id) for every tile of each binned primitive,
-// primitives in depth order
+// primitives in depth order.  A warp takes 32 consecutive primitives, whose
+// instances form one contiguous output range; lanes write that range in
+// order (coalesced), each output slot finding its owner lane by a binary
+// search over the lanes' exclusive prefix.
 // ---------------------------------------------------------------------------
+constexpr uint32_t kBigRect = 256;  // tiles; larger rectangles go to k_emit_big
+
 __global__ void __launch_bounds__(256)
     k_emit(const uint32_t *__restrict__ ids, const uint32_t *__restrict__ offs,
-           const uint16_t *__restrict__ rect, const int64_t *counters, int TX,
-           uint32_t *__restrict__ tkeys, uint32_t *__restrict__ tvals) {
+           const uint16_t *__restrict__ rect, int64_t *counters, int TX,
+           uint32_t *__restrict__ tkeys, uint32_t *__restrict__ tvals, uint32_t *__restrict__ bigq) {
   if (counters[2]) return;
   const int64_t M = counters[0];
   const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  // grid-stride with whole warps alive so the cooperative path can shuffle
   for (int64_t jb = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); jb < M; jb += stride) {
     const int64_t j = jb + lane;
-    uint32_t p = 0, off = 0, tx0 = 0, tx1 = 0, ty0 = 0, ty1 = 0, cnt = 0;
+    uint32_t p = 0, off = 0, tx0 = 0, ty0 = 0, w = 1, cnt = 0;
     if (j < M) {
       p = __ldg(ids + j);
       off = __ldg(offs + j);
       const uint2 r = __ldg(reinterpret_cast<const uint2 *>(rect) + p);
-      tx0 = r.x & 0xffffu; tx1 = r.x >> 16; ty0 = r.y & 0xffffu; ty1 = r.y >> 16;
-      cnt = (tx1 - tx0 + 1) * (ty1 - ty0 + 1);
-    }
-    const bool big = cnt > 32;
-    if (!big) {
-      uint32_t k = off;
-      for (uint32_t ty = ty0; ty <= ty1 && cnt; ++ty)
-        for (uint32_t tx = tx0; tx <= tx1; ++tx, ++k) {
-          tkeys[k] = ty * TX + tx;
-          tvals[k] = p;
-        }
-    }
-    uint32_t bigmask = __ballot_sync(0xffffffffu, big);
-    while (bigmask) {
-      const int src = __ffs(bigmask) - 1;
-      bigmask &= bigmask - 1;
-      const uint32_t bp = __shfl_sync(0xffffffffu, p, src);
-      const uint32_t boff = __shfl_sync(0xffffffffu, off, src);
-      const uint32_t btx0 = __shfl_sync(0xffffffffu, tx0, src);
-      const uint32_t btx1 = __shfl_sync(0xffffffffu, tx1, src);
-      const uint32_t bty0 = __shfl_sync(0xffffffffu, ty0, src);
-      const uint32_t bcnt = __shfl_sync(0xffffffffu, cnt, src);
-      const uint32_t w = btx1 - btx0 + 1;
-      for (uint32_t k = lane; k < bcnt; k += 32) {
-        const uint32_t ty = bty0 + k / w, tx = btx0 + k % w;
-        tkeys[boff + k] = ty * TX + tx;
-        tvals[boff + k] = bp;
+      tx0 = r.x & 0xffffu;
+      ty0 = r.y & 0xffffu;
+      w = (r.x >> 16) - tx0 + 1;
+      cnt = w * ((r.y >> 16) - ty0 + 1);
+      if (cnt > kBigRect) {  // deferred: written by one block in k_emit_big
+        const unsigned long long slot = atomicAdd(reinterpret_cast<unsigned long long *>(&counters[3]), 1ull);
+        bigq[slot] = (uint32_t)j;
+        cnt = 0;
       }
+    }
+    // exclusive prefix of the small counts within the warp
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    const uint32_t rel = j < M ? incl - cnt : 0xffffffffu;
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    const float inv_w = 1.0f / (float)w;
+    for (uint32_t kb = 0; kb < total; kb += 32) {  // warp-uniform trip count
+      const uint32_t k = kb + lane;
+      // owner: the last lane with prefix <= k and a non-empty range
+      int lo = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const uint32_t pr = __shfl_sync(0xffffffffu, rel, lo + step);
+        if (pr <= k) lo += step;
+      }
+      const uint32_t own_rel = __shfl_sync(0xffffffffu, rel, lo);
+      const uint32_t own_off = __shfl_sync(0xffffffffu, off, lo);
+      const uint32_t own_w = __shfl_sync(0xffffffffu, w, lo);
+      const float own_iw = __shfl_sync(0xffffffffu, inv_w, lo);
+      const uint32_t own_tx0 = __shfl_sync(0xffffffffu, tx0, lo);
+      const uint32_t own_ty0 = __shfl_sync(0xffffffffu, ty0, lo);
+      const uint32_t own_p = __shfl_sync(0xffffffffu, p, lo);
+      const uint32_t l = k - own_rel;
+      uint32_t dy = (uint32_t)((float)l * own_iw);
+      uint32_t dx = l - dy * own_w;
+      if ((int)dx < 0) { dy -= 1; dx += own_w; } else if (dx >= own_w) { dy += 1; dx -= own_w; }
+      if (k < total) {
+        tkeys[own_off + l] = (own_ty0 + dy) * TX + own_tx0 + dx;
+        tvals[own_off + l] = own_p;
+      }
+    }
+  }
+}
+
+// one block per deferred large rectangle
+__global__ void __launch_bounds__(256)
+    k_emit_big(const uint32_t *__restrict__ ids, const uint32_t *__restrict__ offs,
+               const uint16_t *__restrict__ rect, const int64_t *counters, int TX,
+               const uint32_t *__restrict__ bigq, uint32_t *__restrict__ tkeys,
+               uint32_t *__restrict__ tvals) {
+  if (counters[2]) return;
+  const int64_t nbig = counters[3];
+  for (int64_t b = blockIdx.x; b < nbig; b += gridDim.x) {
+    const uint32_t j = bigq[b];
+    const uint32_t p = __ldg(ids + j), off = __ldg(offs + j);
+    const uint2 r = __ldg(reinterpret_cast<const uint2 *>(rect) + p);
+    const uint32_t tx0 = r.x & 0xffffu, ty0 = r.y & 0xffffu;
+    const uint32_t w = (r.x >> 16) - tx0 + 1;
+    const uint32_t cnt = w * ((r.y >> 16) - ty0 + 1);
+    for (uint32_t k = threadIdx.x; k < cnt; k += blockDim.x) {
+      const uint32_t dy = k / w, dx = k - dy * w;
+      tkeys[off + k] = (ty0 + dy) * TX + tx0 + dx;
+      tvals[off + k] = p;
     }
   }
 }
@@ -410,10 +509,15 @@ int launch_bin_sort(const BinArgs &a, const BinWorkspace &ws, cudaStream_t s) {
   uint32_t *vbuf[2];
   vbuf[0] = (passes % 2 == 0) ? a.vals : ws.tv;
   vbuf[1] = (passes % 2 == 0) ? ws.tv : a.vals;
-  k_emit<<<kSortBlocks, 256, 0, s>>>(ids, ws.offs, a.rect, ctr, a.TX, ws.tk[0], vbuf[0]);
+  // dk[0] is free once the depth sort is done: it holds the deferred queue
+  k_emit<<<kSortBlocks, 256, 0, s>>>(ids, ws.offs, a.rect, ctr, a.TX, ws.tk[0], vbuf[0], ws.dk[0]);
+  k_emit_big<<<kSortBlocks, 256, 0, s>>>(ids, ws.offs, a.rect, ctr, a.TX, ws.dk[0], ws.tk[0], vbuf[0]);
+  // tile digits split evenly over the passes (13 bits -> 7 + 6): fewer
+  // buckets per pass give longer runs in the scatter's coalesced write-out
+  const int per_pass = (a.tile_bits + passes - 1) / passes;
   for (int p = 0; p < passes; ++p) {
-    const int shift = 8 * p;
-    const int bits = min(8, a.tile_bits - shift);
+    const int shift = per_pass * p;
+    const int bits = min(per_pass, a.tile_bits - shift);
     radix_pass(ws.tk[p & 1], vbuf[p & 1], nullptr, &ctr[1], 0, &ctr[2], shift, bits, ws,
                ws.tk[(p + 1) & 1], vbuf[(p + 1) & 1], nullptr, s);
   }

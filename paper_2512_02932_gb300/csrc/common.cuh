@@ -13,7 +13,7 @@ constexpr int kTilePix = kTile * kTile;
 constexpr float kLog2e = 1.4426950408889634f;
 
 // ---------------------------------------------------------------------------
-// Render record: 4 x float4 (64 B) per primitive, written by preprocess and
+// Render record: 5 x float4 (80 B) per primitive, written by preprocess and
 // staged through shared memory by the render kernels.
 //   r0 = (x_c, y_c, z_c, alpha_s)   projected centre (pixels), camera depth,
 //        alpha_s = +alpha for a 3D Gaussian, -alpha for a 2D surfel
@@ -21,13 +21,17 @@ constexpr float kLog2e = 1.4426950408889634f;
 //        2D: (Q00, Q01, Q10, Q11)
 //   r2 = 3D: (0, 0, r, g)   2D: (Q20, Q21, r, g)
 //   r3 = (b, nx, ny, nz)    colour blue, camera-space normal
+//   r4 = (x0, x1, y0, y1)   padded pixel box outside which the pair never
+//        contributes (the box the tile rectangle is cut from); a warp skips a
+//        record whose box misses its pixel block
 // For a surfel, with (dx, dy) the pixel offset from the projected centre:
 //   p = (Q00 dx + Q01 dy, Q10 dx + Q11 dy, Q20 dx + Q21 dy + 1),
 //   (u, v) = (p0, p1) / p2, hit depth z = z_c / p2     (Eq. 14 re-centred)
 // ---------------------------------------------------------------------------
 struct Rec {
-  float4 r0, r1, r2, r3;
+  float4 r0, r1, r2, r3, r4;
 };
+constexpr int kRecF4 = 5;
 
 // Per-primitive gradient of the render record, accumulated by render_bwd
 // (16 floats):

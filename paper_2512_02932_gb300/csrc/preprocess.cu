@@ -29,6 +29,7 @@ struct Contract {
   float e0, e1, f0, f1;                // t=0: re-centred homography block
   uint32_t dbits;
   int tx0, tx1, ty0, ty1;
+  float bx0, bx1, by0, by1;  // padded pixel box of the alpha >= alpha_min region
 };
 
 __device__ __forceinline__ float pad_extent(float r) {
@@ -180,10 +181,14 @@ __device__ bool run_contract(const float mu[3], const float ls[3], const float q
   if (whole) {
     o.tx0 = 0; o.tx1 = (c.W - 1) / kTile;
     o.ty0 = 0; o.ty1 = (c.H - 1) / kTile;
+    o.bx0 = o.by0 = -1e30f;
+    o.bx1 = o.by1 = 1e30f;
   } else {
     const float px = pad_extent(hx), py = pad_extent(hy);
-    if (!pixel_tiles(csub(ctrx, px), cadd(ctrx, px), c.W, &o.tx0, &o.tx1)) return false;
-    if (!pixel_tiles(csub(ctry, py), cadd(ctry, py), c.H, &o.ty0, &o.ty1)) return false;
+    o.bx0 = csub(ctrx, px); o.bx1 = cadd(ctrx, px);
+    o.by0 = csub(ctry, py); o.by1 = cadd(ctry, py);
+    if (!pixel_tiles(o.bx0, o.bx1, c.W, &o.tx0, &o.tx1)) return false;
+    if (!pixel_tiles(o.by0, o.by1, c.H, &o.ty0, &o.ty1)) return false;
   }
   return true;
 }
@@ -300,10 +305,34 @@ __device__ __forceinline__ void load_sh(const float *sh, int64_t i, float *f) {
   }
 }
 
+// write one primitive's SH row (zeros if v is null); 16-byte stores where the
+// row is 16-byte aligned (degrees 1 and 3)
+template <int DEG>
+__device__ __forceinline__ void store_sh(float *dst, const float *v) {
+  constexpr int NB = (DEG + 1) * (DEG + 1);
+  if constexpr ((NB * 3) % 4 == 0) {
+    float4 *d4 = reinterpret_cast<float4 *>(dst);
+#pragma unroll
+    for (int k = 0; k < NB * 3 / 4; ++k)
+      d4[k] = v ? make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3])
+                : make_float4(0.f, 0.f, 0.f, 0.f);
+  } else {
+#pragma unroll
+    for (int k = 0; k < NB * 3; ++k) dst[k] = v ? v[k] : 0.0f;
+  }
+}
+
 __device__ __forceinline__ int normal_axis(int type, const float ls[3]) {
   if (type == 0) return 2;
   if (ls[2] <= ls[0] && ls[2] <= ls[1]) return 2;
   return ls[0] <= ls[1] ? 0 : 1;
+}
+
+// camera-space axis k of the primitive, selected without dynamic indexing
+__device__ __forceinline__ void axis_of(const Contract &o, int k, float &x, float &y, float &z) {
+  x = k == 0 ? o.a[0][0] : (k == 1 ? o.a[1][0] : o.a[2][0]);
+  y = k == 0 ? o.a[0][1] : (k == 1 ? o.a[1][1] : o.a[2][1]);
+  z = k == 0 ? o.a[0][2] : (k == 1 ? o.a[1][2] : o.a[2][2]);
 }
 
 __device__ __forceinline__ void load_params(const PrepArgs &a, int64_t i, float mu[3], float ls[3],
@@ -371,7 +400,8 @@ __global__ void __launch_bounds__(256) preprocess_fwd_kernel(PrepArgs a) {
   }
   // normal: smallest-scale axis (z for a surfel), facing the camera
   const int kn = normal_axis(type, ls);
-  float n0 = o.a[kn][0], n1 = o.a[kn][1], n2 = o.a[kn][2];
+  float n0, n1, n2;
+  axis_of(o, kn, n0, n1, n2);
   if (n0 * o.X + n1 * o.Y + n2 * o.Z > 0.0f) { n0 = -n0; n1 = -n1; n2 = -n2; }
   const float ctrx = fmaf(c.fx, o.xz, c.cx), ctry = fmaf(c.fy, o.yz, c.cy);
   Rec r;
@@ -405,8 +435,9 @@ __global__ void __launch_bounds__(256) preprocess_fwd_kernel(PrepArgs a) {
     r.r2 = make_float4(Q20, Q21, col[0], col[1]);
   }
   r.r3 = make_float4(col[2], n0, n1, n2);
-  float4 *dst = reinterpret_cast<float4 *>(a.rec) + 4 * i;
-  dst[0] = r.r0; dst[1] = r.r1; dst[2] = r.r2; dst[3] = r.r3;
+  r.r4 = make_float4(o.bx0, o.bx1, o.by0, o.by1);
+  float4 *dst = reinterpret_cast<float4 *>(a.rec) + kRecF4 * i;
+  dst[0] = r.r0; dst[1] = r.r1; dst[2] = r.r2; dst[3] = r.r3; dst[4] = r.r4;
 }
 
 // ---------------------------------------------------------------------------
@@ -423,7 +454,7 @@ __global__ void __launch_bounds__(256) preprocess_bwd_kernel(PrepArgs a, PrepGra
     for (int k = 0; k < 3; ++k) { g.means[3 * i + k] = 0.f; g.log_scales[3 * i + k] = 0.f; }
     reinterpret_cast<float4 *>(g.quats)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     g.logits[i] = 0.f;
-    for (int k = 0; k < NB * 3; ++k) gsh[k] = 0.f;
+    store_sh<DEG>(gsh, nullptr);
     return;
   }
   float mu[3], ls[3], q[4], logit;
@@ -451,10 +482,16 @@ __global__ void __launch_bounds__(256) preprocess_bwd_kernel(PrepArgs a, PrepGra
   // normal
   {
     const int kn = normal_axis(type, ls);
-    const float sg = (o.a[kn][0] * X + o.a[kn][1] * Y + o.a[kn][2] * Z > 0.0f) ? -1.f : 1.f;
-    dA[kn][0] += sg * G[13];
-    dA[kn][1] += sg * G[14];
-    dA[kn][2] += sg * G[15];
+    float ax, ay, az;
+    axis_of(o, kn, ax, ay, az);
+    const float sg = (ax * X + ay * Y + az * Z > 0.0f) ? -1.f : 1.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float w = (k == kn) ? sg : 0.0f;
+      dA[k][0] += w * G[13];
+      dA[k][1] += w * G[14];
+      dA[k][2] += w * G[15];
+    }
   }
   const float dxc = G[4], dyc = G[5];
   if (type == 1) {
@@ -611,10 +648,14 @@ __global__ void __launch_bounds__(256) preprocess_bwd_kernel(PrepArgs a, PrepGra
     for (int k = 0; k < NB; ++k) v = fmaf(f[3 * k + ch], Yb[k], v);
     dv[ch] = v > 0.0f ? G[1 + ch] : 0.0f;
   }
+  {
+    float out[NB * 3];
 #pragma unroll
-  for (int k = 0; k < NB; ++k)
+    for (int k = 0; k < NB; ++k)
 #pragma unroll
-    for (int ch = 0; ch < 3; ++ch) gsh[3 * k + ch] = dv[ch] * Yb[k];
+      for (int ch = 0; ch < 3; ++ch) out[3 * k + ch] = dv[ch] * Yb[k];
+    store_sh<DEG>(gsh, out);
+  }
   if (DEG > 0) {
     float wk[NB];
 #pragma unroll

@@ -75,16 +75,49 @@ __device__ __forceinline__ void pixel_of(int tile, int TX, int warp, int lane, i
 }
 
 // ---------------------------------------------------------------------------
+// staging helpers
+// ---------------------------------------------------------------------------
+// Copy the records of list entries [base, base + cnt) into this warp's buffer
+// (lane l copies entry base + l) and, for the backward, their ids.
+__device__ __forceinline__ void stage_chunk(const float4 *__restrict__ rec, const uint32_t *__restrict__ vals,
+                                            uint32_t base, uint32_t end, float4 *buf, uint32_t *ids, int lane) {
+  const uint32_t idx = base + lane;
+  if (idx < end) {
+    const uint32_t id = __ldg(vals + idx);
+    if (ids) ids[lane] = id;
+    const float4 *src = rec + kRecF4 * (size_t)id;
+    float4 *dst = buf + lane * kRecF4;
+#pragma unroll
+    for (int k = 0; k < kRecF4; ++k) cp_async16(dst + k, src + k);
+  }
+  cp_async_commit();
+}
+
+// Bit l of the result is set iff staged record l (l < cnt) has a pixel box
+// that meets this warp's 8x4 block of pixel centres [x0+0.5, x0+7.5] x
+// [y0+0.5, y0+3.5].
+__device__ __forceinline__ uint32_t chunk_mask(const float4 *buf, int cnt, int lane, float bx0, float by0) {
+  bool hit = false;
+  if (lane < cnt) {
+    const float4 b = buf[lane * kRecF4 + 4];
+    hit = b.x <= bx0 + 7.5f && b.y >= bx0 + 0.5f && b.z <= by0 + 3.5f && b.w >= by0 + 0.5f;
+  }
+  return __ballot_sync(0xffffffffu, hit);
+}
+
+// ---------------------------------------------------------------------------
 // forward
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kRW * 32) render_fwd_kernel(RenderArgs a) {
-  __shared__ __align__(16) float4 sm[kRW][2][kCh * 4];
+  __shared__ __align__(16) float4 sm[kRW][2][kCh * kRecF4];
   const int tile = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int pxi, pyi;
   pixel_of(tile, a.cam.TX, warp, lane, pxi, pyi);
   const bool inside = pxi < a.cam.W && pyi < a.cam.H;
   const float px = (float)pxi + 0.5f, py = (float)pyi + 0.5f;
+  const float wx0 = (float)((tile % a.cam.TX) * kTile + (warp & 1) * 8);
+  const float wy0 = (float)((tile / a.cam.TX) * kTile + (warp >> 1) * 4);
   const uint32_t start = a.ranges[2 * tile], end = a.ranges[2 * tile + 1];
   const float4 *rec = reinterpret_cast<const float4 *>(a.rec);
   float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f, N0 = 0.f, N1 = 0.f, N2 = 0.f;
@@ -92,57 +125,42 @@ __global__ void __launch_bounds__(kRW * 32) render_fwd_kernel(RenderArgs a) {
   bool done = !inside;
   if (__all_sync(0xffffffffu, done)) return;
 
-  if (start < end) {
-    const uint32_t idx = start + lane;
-    if (idx < end) {
-      const float4 *src = rec + 4 * (size_t)__ldg(a.vals + idx);
-      float4 *dst = &sm[warp][0][lane * 4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) cp_async16(dst + k, src + k);
-    }
-    cp_async_commit();
-  }
+  if (start < end) stage_chunk(rec, a.vals, start, end, &sm[warp][0][0], nullptr, lane);
   int buf = 0;
   for (uint32_t base = start; base < end; base += kCh) {
-    const bool has_next = base + kCh < end;
-    if (has_next) {
-      const uint32_t idx = base + kCh + lane;
-      if (idx < end) {
-        const float4 *src = rec + 4 * (size_t)__ldg(a.vals + idx);
-        float4 *dst = &sm[warp][buf ^ 1][lane * 4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) cp_async16(dst + k, src + k);
-      }
-      cp_async_commit();
+    if (base + kCh < end) {
+      stage_chunk(rec, a.vals, base + kCh, end, &sm[warp][buf ^ 1][0], nullptr, lane);
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
     }
     __syncwarp();
-    const int cnt = (int)min((uint32_t)kCh, end - base);
-    if (!done) {
-      const float4 *chunk = &sm[warp][buf][0];
-      for (int j = 0; j < cnt; ++j) {
-        const float4 r0 = chunk[4 * j], r1 = chunk[4 * j + 1], r2 = chunk[4 * j + 2];
-        PairEval e;
-        if (!eval_pair(r0, r1, r2, px, py, a.cfg, e)) continue;
-        const float Tn = T * (1.0f - e.at);
-        if (Tn < a.cfg.T_min) {
-          done = true;
-          break;
-        }
-        const float w = e.at * T;
-        const float4 r3 = chunk[4 * j + 3];
-        C0 = fmaf(w, r2.z, C0);
-        C1 = fmaf(w, r2.w, C1);
-        C2 = fmaf(w, r3.x, C2);
-        D = fmaf(w, e.z, D);
-        N0 = fmaf(w, r3.y, N0);
-        N1 = fmaf(w, r3.z, N1);
-        N2 = fmaf(w, r3.w, N2);
-        T = Tn;
-        last = base - start + (uint32_t)j + 1u;
+    const float4 *chunk = &sm[warp][buf][0];
+    uint32_t mask = chunk_mask(chunk, (int)min((uint32_t)kCh, end - base), lane, wx0, wy0);
+    while (mask) {
+      const int j = __ffs(mask) - 1;
+      mask &= mask - 1;
+      if (done) continue;
+      const float4 *r = chunk + j * kRecF4;
+      const float4 r0 = r[0], r1 = r[1], r2 = r[2];
+      PairEval e;
+      if (!eval_pair(r0, r1, r2, px, py, a.cfg, e)) continue;
+      const float Tn = T * (1.0f - e.at);
+      if (Tn < a.cfg.T_min) {
+        done = true;
+        continue;
       }
+      const float w = e.at * T;
+      const float4 r3 = r[3];
+      C0 = fmaf(w, r2.z, C0);
+      C1 = fmaf(w, r2.w, C1);
+      C2 = fmaf(w, r3.x, C2);
+      D = fmaf(w, e.z, D);
+      N0 = fmaf(w, r3.y, N0);
+      N1 = fmaf(w, r3.z, N1);
+      N2 = fmaf(w, r3.w, N2);
+      T = Tn;
+      last = base - start + (uint32_t)j + 1u;
     }
     if (__all_sync(0xffffffffu, done)) break;
     __syncwarp();
@@ -204,7 +222,7 @@ __device__ __forceinline__ float warp_sum16(float (&v)[16], int lane, int &comp)
 }
 
 __global__ void __launch_bounds__(kRW * 32) render_bwd_kernel(RenderBwdArgs a) {
-  __shared__ __align__(16) float4 sm[kRW][2][kCh * 4];
+  __shared__ __align__(16) float4 sm[kRW][2][kCh * kRecF4];
   __shared__ uint32_t sid[kRW][2][kCh];
   const int tile = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -212,6 +230,8 @@ __global__ void __launch_bounds__(kRW * 32) render_bwd_kernel(RenderBwdArgs a) {
   pixel_of(tile, a.cam.TX, warp, lane, pxi, pyi);
   const bool inside = pxi < a.cam.W && pyi < a.cam.H;
   const float px = (float)pxi + 0.5f, py = (float)pyi + 0.5f;
+  const float wx0 = (float)((tile % a.cam.TX) * kTile + (warp & 1) * 8);
+  const float wy0 = (float)((tile / a.cam.TX) * kTile + (warp >> 1) * 4);
   const uint32_t start = a.ranges[2 * tile];
   const size_t HW = (size_t)a.cam.W * a.cam.H;
   const size_t p = inside ? (size_t)pyi * a.cam.W + pxi : 0;
@@ -235,42 +255,26 @@ __global__ void __launch_bounds__(kRW * 32) render_bwd_kernel(RenderBwdArgs a) {
 
   uint32_t ce = start + wmax;
   uint32_t cs = ce - min((uint32_t)kCh, wmax);
-  {
-    const uint32_t idx = cs + lane;
-    if (idx < ce) {
-      const uint32_t id = __ldg(a.vals + idx);
-      sid[warp][0][lane] = id;
-      const float4 *src = rec + 4 * (size_t)id;
-      float4 *dst = &sm[warp][0][lane * 4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) cp_async16(dst + k, src + k);
-    }
-    cp_async_commit();
-  }
+  stage_chunk(rec, a.vals, cs, ce, &sm[warp][0][0], &sid[warp][0][0], lane);
   int buf = 0;
   while (true) {
     const bool has_next = cs > start;
     const uint32_t ncs = has_next ? cs - min((uint32_t)kCh, cs - start) : cs;
     if (has_next) {
-      const uint32_t idx = ncs + lane;
-      if (idx < cs) {
-        const uint32_t id = __ldg(a.vals + idx);
-        sid[warp][buf ^ 1][lane] = id;
-        const float4 *src = rec + 4 * (size_t)id;
-        float4 *dst = &sm[warp][buf ^ 1][lane * 4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) cp_async16(dst + k, src + k);
-      }
-      cp_async_commit();
+      stage_chunk(rec, a.vals, ncs, cs, &sm[warp][buf ^ 1][0], &sid[warp][buf ^ 1][0], lane);
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
     }
     __syncwarp();
     const float4 *chunk = &sm[warp][buf][0];
-    for (int jj = (int)(ce - cs) - 1; jj >= 0; --jj) {
+    uint32_t mask = chunk_mask(chunk, (int)(ce - cs), lane, wx0, wy0);
+    while (mask) {
+      const int jj = 31 - __clz(mask);
+      mask &= ~(1u << jj);
       const uint32_t j = cs + (uint32_t)jj;
-      const float4 r0 = chunk[4 * jj], r1 = chunk[4 * jj + 1], r2 = chunk[4 * jj + 2];
+      const float4 *r = chunk + jj * kRecF4;
+      const float4 r0 = r[0], r1 = r[1], r2 = r[2];
       PairEval e;
       const bool contrib = inside && (j - start) < last && eval_pair(r0, r1, r2, px, py, a.cfg, e);
       if (!__any_sync(0xffffffffu, contrib)) continue;
@@ -278,7 +282,7 @@ __global__ void __launch_bounds__(kRW * 32) render_bwd_kernel(RenderBwdArgs a) {
 #pragma unroll
       for (int k = 0; k < 16; ++k) g[k] = 0.f;
       if (contrib) {
-        const float4 r3 = chunk[4 * jj + 3];
+        const float4 r3 = r[3];
         const float c0 = r2.z, c1 = r2.w, c2 = r3.x, n0 = r3.y, n1 = r3.z, n2 = r3.w;
         const float om = 1.0f - e.at;
         const float Ti = __fdividef(T, om);
@@ -331,9 +335,17 @@ __global__ void __launch_bounds__(kRW * 32) render_bwd_kernel(RenderBwdArgs a) {
   cp_async_wait<0>();
 }
 
+// Prefer the largest shared-memory carve-out: the staging buffers decide how
+// many tile CTAs fit on an SM.
+static void prefer_shared(const void *fn) {
+  cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+}
+
 int launch_render_fwd(const RenderArgs &a, cudaStream_t s) {
   const int tiles = a.cam.TX * a.cam.TY;
   if (tiles <= 0) return 0;
+  static bool once = (prefer_shared((const void *)render_fwd_kernel), true);
+  (void)once;
   render_fwd_kernel<<<tiles, kRW * 32, 0, s>>>(a);
   return 0;
 }
@@ -341,6 +353,8 @@ int launch_render_fwd(const RenderArgs &a, cudaStream_t s) {
 int launch_render_bwd(const RenderBwdArgs &a, cudaStream_t s) {
   const int tiles = a.cam.TX * a.cam.TY;
   if (tiles <= 0) return 0;
+  static bool once = (prefer_shared((const void *)render_bwd_kernel), true);
+  (void)once;
   render_bwd_kernel<<<tiles, kRW * 32, 0, s>>>(a);
   return 0;
 }

@@ -15,7 +15,7 @@ import torch
 
 from . import abi
 
-REC_FLOATS = 16
+REC_FLOATS = 20
 GRAD_FLOATS = 16
 TILE = 16
 
