@@ -153,8 +153,12 @@ def render(scene, cam, cfg, pixels=None, params=None, chunk=1024):
     m2 = muc[i2]
     ok2 = (m2[:, 2] > cfg.near).detach()
     bxm = torch.cross(b2, -m2, dim=1)  # for tau
-    # global order: (contract binary32 depth bits, id)
-    db, _, _ = native.contract_bin(scene, cam, cfg)
+    # global order: (contract binary32 depth bits, id); visibility is the
+    # contract's binary32 decision (a primitive it does not bin is not drawn)
+    db, _, touched = native.contract_bin(scene, cam, cfg)
+    binned = torch.as_tensor(touched > 0)
+    ok3 = ok3 & binned[torch.as_tensor(i3)]
+    ok2 = ok2 & binned[torch.as_tensor(i2)]
     order = np.lexsort((np.arange(scene.n), db))
     pos = np.empty(scene.n, np.int64)
     pos[order] = np.arange(scene.n)
@@ -301,5 +305,7 @@ def pair_alpha(scene, cam, cfg, pixels):
             okk = torch.isfinite(u) & torch.isfinite(v) & (tau > cfg.near) & (m2[:, 2] > cfg.near)[None]
             d[:, i2] = torch.where(okk, u * u + v * v, torch.full_like(u, 1e30))
             ok[:, i2] = okk
+        _, _, touched = native.contract_bin(scene, cam, cfg)
+        ok = ok & torch.as_tensor(touched > 0)[None]
         araw = alpha[None] * torch.exp(-0.5 * d)
         return araw.numpy(), ok.numpy()

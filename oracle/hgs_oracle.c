@@ -57,6 +57,17 @@ enum {
 #define AMB_T_REL     1e-3   /* |T' - T_min| <= this * T_min               */
 #define AMB_NEAR_REL  1e-5   /* |z - near| <= this * max(1, near)          */
 #define AMB_FLIP      1e-5   /* |n . mu_c| / |mu_c| below this             */
+/* conditioning: in binary32, (u, v) evaluated from the pixel's offset to the
+ * projected centre carry an error of up to COND_ULPS ulps of the magnitude of
+ * the terms that cancel, |du/dx dx| + |du/dy dy| (likewise v): a few ulps for
+ * the record's coefficients and two for the evaluation.  A pixel is not
+ * comparable when that error can move one contribution by more than
+ * COND_ALPHA (twice that is still under the 1e-3 image tolerance).  Only
+ * extremely anisotropic footprints evaluated far from their centre (e.g. a
+ * 1e5:1 ribbon thousands of pixels along its length) reach it. */
+#define COND_ULPS     8.0
+#define COND_ALPHA    4e-4
+#define EPS32         5.960464477539063e-08
 
 /* ------------------------------------------------------------------------ */
 /* (3) real spherical harmonics, degree <= 3                                 */
@@ -353,7 +364,7 @@ typedef struct {
   double col[3], nrm[3];
   double X, Y, Z;                 /* camera-space centre */
   uint32_t key;                   /* contract FP32 depth bits: the order key */
-  double mx, my, ca, cb, cc;      /* 3D: projected centre and conic */
+  double mx, my, ca, cb, cc;      /* 3D: projected centre, Cholesky factor of the conic */
   double a[3], b[3];              /* 2D: s_x R_cw r0, s_y R_cw r1 */
   double ndot;                    /* |n . mu_c| / |mu_c| */
   double bx0, bx1, by0, by1;      /* padded continuous bbox in pixels */
@@ -373,8 +384,8 @@ typedef struct {
   int maxcell;
 } orc_ctx;
 
-static void prep_prim(orc_ctx *C, int64_t i, const double *mu64, const double *ls32,
-                      const double *q32, double logit32, const double *sh32, int type) {
+static void prep_prim(orc_ctx *C, int64_t i, const double *mu64, const double *ls64,
+                      const double *q64, double logit64, const double *sh64, int type) {
   prim_t *p = &C->P[i];
   memset(p, 0, sizeof(*p));
   p->type = type;
@@ -391,16 +402,29 @@ static void prep_prim(orc_ctx *C, int64_t i, const double *mu64, const double *l
     p->key = bits_from_f32(Z32);
   }
   const double nearz = C->cfg[CF_NEAR], amin = C->cfg[CF_ALPHA_MIN];
+  {
+    /* visibility is the binning contract's binary32 decision: a primitive the
+     * contract does not bin (behind the near plane, below alpha_min, a
+     * degenerate projection, or parameters that overflow binary32) is not
+     * rendered */
+    const float ls32[3] = {(float)ls64[0], (float)ls64[1], (float)ls64[2]};
+    const float q32[4] = {(float)q64[0], (float)q64[1], (float)q64[2], (float)q64[3]};
+    int rr[4];
+    uint32_t dbb;
+    if (!contract_one(mu32, ls32, q32, (float)logit64, type, C->cam32, C->W, C->H, 16,
+                      (float)nearz, (float)amin, (float)C->cfg[CF_DILATION], rr, &dbb))
+      return;
+  }
   if (fabs(p->Z - nearz) <= AMB_NEAR_REL * fmax(1.0, nearz)) p->amb_near = 1;
   if (!(p->Z > nearz) && !p->amb_near) return;
   /* activations (Sec. 3.1): scale = exp(log s), unit quaternion, sigmoid */
-  double s[3] = {exp((double)ls32[0]), exp((double)ls32[1]), exp((double)ls32[2])};
-  double q[4] = {q32[0], q32[1], q32[2], q32[3]};
+  double s[3] = {exp(ls64[0]), exp(ls64[1]), exp(ls64[2])};
+  double q[4] = {q64[0], q64[1], q64[2], q64[3]};
   double qn = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
   if (!(qn > 0)) return;
   double Rq[9];
   quat_to_rot(q, Rq);
-  double alpha = 1.0 / (1.0 + exp(-(double)logit32));
+  double alpha = 1.0 / (1.0 + exp(-logit64));
   double alpha_bb = alpha;
   if (type == 0) {
     /* scale modulation for 2D Gaussians (Eqs. 6-7) */
@@ -418,8 +442,8 @@ static void prep_prim(orc_ctx *C, int64_t i, const double *mu64, const double *l
   /* normal: axis of the smallest scale (2D: the z axis), facing the camera */
   int kn;
   if (type == 0) kn = 2;
-  else if (ls32[2] <= ls32[0] && ls32[2] <= ls32[1]) kn = 2;
-  else if (ls32[0] <= ls32[1]) kn = 0;
+  else if (ls64[2] <= ls64[0] && ls64[2] <= ls64[1]) kn = 2;
+  else if (ls64[0] <= ls64[1]) kn = 0;
   else kn = 1;
   double nd = ax[kn][0] * p->X + ax[kn][1] * p->Y + ax[kn][2] * p->Z;
   double sg = nd > 0 ? -1.0 : 1.0;
@@ -437,7 +461,7 @@ static void prep_prim(orc_ctx *C, int64_t i, const double *mu64, const double *l
     sh_basis(C->deg, dv[0] / dn, dv[1] / dn, dv[2] / dn, Yb);
     for (int ch = 0; ch < 3; ++ch) {
       double v = 0.5;
-      for (int k = 0; k < C->nb; ++k) v += (double)sh32[3 * k + ch] * Yb[k];
+      for (int k = 0; k < C->nb; ++k) v += sh64[3 * k + ch] * Yb[k];
       p->col[ch] = v > 0 ? v : 0;
     }
   }
@@ -447,30 +471,30 @@ static void prep_prim(orc_ctx *C, int64_t i, const double *mu64, const double *l
   const double fx = C->fx, fy = C->fy, cx = C->cx, cy = C->cy;
   double X = p->X, Y = p->Y, Z = p->Z;
   if (type == 1) {
-    /* EWA projection, App. C Eq. 13: Sigma' = J W Sigma W^T J^T */
-    double V[3][3];
-    for (int i2 = 0; i2 < 3; ++i2)
-      for (int j2 = 0; j2 < 3; ++j2) {
-        double v = 0;
-        for (int k = 0; k < 3; ++k) v += s[k] * s[k] * ax[k][i2] * ax[k][j2];
-        V[i2][j2] = v;
-      }
+    /* EWA projection, App. C Eq. 13: Sigma' = J W Sigma W^T J^T = T T^T with
+     * T = J W R S (2x3).  det Sigma' by Cauchy-Binet (sum of squared 2x2
+     * minors of T) and Eq. 1's quadratic form through the Cholesky factor of
+     * Sigma'^-1, so needle-like footprints keep full precision. */
     double J[2][3] = {{fx / Z, 0, -fx * X / (Z * Z)}, {0, fy / Z, -fy * Y / (Z * Z)}};
+    double T[2][3];
+    for (int r = 0; r < 2; ++r)
+      for (int k = 0; k < 3; ++k)
+        T[r][k] = s[k] * (J[r][0] * ax[k][0] + J[r][1] * ax[k][1] + J[r][2] * ax[k][2]);
     double S2[2][2];
     for (int r = 0; r < 2; ++r)
-      for (int c = 0; c < 2; ++c) {
-        double v = 0;
-        for (int i2 = 0; i2 < 3; ++i2)
-          for (int j2 = 0; j2 < 3; ++j2) v += J[r][i2] * V[i2][j2] * J[c][j2];
-        S2[r][c] = v;
-      }
-    S2[0][0] += C->cfg[CF_DILATION];
-    S2[1][1] += C->cfg[CF_DILATION];
-    double det = S2[0][0] * S2[1][1] - S2[0][1] * S2[1][0];
-    if (!(det > 0)) return;
-    p->ca = S2[1][1] / det;
-    p->cb = -S2[0][1] / det;
-    p->cc = S2[0][0] / det;
+      for (int c2 = 0; c2 < 2; ++c2)
+        S2[r][c2] = T[r][0] * T[c2][0] + T[r][1] * T[c2][1] + T[r][2] * T[c2][2];
+    const double dil = C->cfg[CF_DILATION];
+    double m01 = T[0][0] * T[1][1] - T[1][0] * T[0][1];
+    double m02 = T[0][0] * T[1][2] - T[1][0] * T[0][2];
+    double m12 = T[0][1] * T[1][2] - T[1][1] * T[0][2];
+    double det = m01 * m01 + m02 * m02 + m12 * m12 + dil * (S2[0][0] + S2[1][1]) + dil * dil;
+    S2[0][0] += dil;
+    S2[1][1] += dil;
+    if (!(det > 0) || !(S2[1][1] > 0)) return;
+    p->ca = sqrt(S2[1][1] / det);              /* W00 */
+    p->cb = -S2[0][1] / sqrt(S2[1][1] * det);   /* W01 */
+    p->cc = 1.0 / sqrt(S2[1][1]);               /* W11 */
     p->mx = fx * X / Z + cx;
     p->my = fy * Y / Z + cy;
     double hx = sqrt(dmax * S2[0][0]), hy = sqrt(dmax * S2[1][1]);
@@ -479,6 +503,8 @@ static void prep_prim(orc_ctx *C, int64_t i, const double *mu64, const double *l
     p->bx0 = p->mx - hx; p->bx1 = p->mx + hx;
     p->by0 = p->my - hy; p->by1 = p->my + hy;
   } else {
+    p->mx = fx * X / Z + cx;
+    p->my = fy * Y / Z + cy;
     for (int r = 0; r < 3; ++r) { p->a[r] = s[0] * ax[0][r]; p->b[r] = s[1] * ax[1][r]; }
     /* bbox of the image of the disc u^2+v^2 <= dmax: whole image unless the
      * disc lies entirely in front of the camera */
@@ -601,6 +627,42 @@ static int cmp_contrib(const void *A, const void *B) {
   return a->id < b->id ? -1 : (a->id > b->id);
 }
 
+/* ray-splat intersection (App. C): solve mu_c + u a + v b = tau ray(px, py)
+ * by Gaussian elimination with partial pivoting.  Returns 0 if the system is
+ * singular (the ray lies in the splat's plane). */
+static int surfel_hit(const orc_ctx *C, const prim_t *p, double px, double py, double sol[3]) {
+  double ray[3] = {(px - C->cx) / C->fx, (py - C->cy) / C->fy, 1.0};
+  double A[3][4] = {{p->a[0], p->b[0], -ray[0], -p->X},
+                    {p->a[1], p->b[1], -ray[1], -p->Y},
+                    {p->a[2], p->b[2], -ray[2], -p->Z}};
+  double scale = sqrt(p->a[0] * p->a[0] + p->a[1] * p->a[1] + p->a[2] * p->a[2]) *
+                 sqrt(p->b[0] * p->b[0] + p->b[1] * p->b[1] + p->b[2] * p->b[2]) *
+                 sqrt(ray[0] * ray[0] + ray[1] * ray[1] + 1.0);
+  double detv = 1.0;
+  for (int c = 0; c < 3; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < 3; ++r)
+      if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
+    if (piv != c) {
+      for (int k = 0; k < 4; ++k) { double tmp = A[c][k]; A[c][k] = A[piv][k]; A[piv][k] = tmp; }
+      detv = -detv;
+    }
+    detv *= A[c][c];
+    if (A[c][c] == 0.0) return 0;
+    for (int r = c + 1; r < 3; ++r) {
+      double f = A[r][c] / A[c][c];
+      for (int k = c; k < 4; ++k) A[r][k] -= f * A[c][k];
+    }
+  }
+  if (fabs(detv) <= 1e-12 * scale) return 0;
+  for (int r = 2; r >= 0; --r) {
+    double v = A[r][3];
+    for (int k = r + 1; k < 3; ++k) v -= A[r][k] * sol[k];
+    sol[r] = v / A[r][r];
+  }
+  return 1;
+}
+
 /* Unified distance (Eq. 1) and contribution (Sec. 3.1) of primitive p at the
  * pixel centre (px, py).  Returns 1 if the pair must be listed: it
  * contributes (*at_out > 0), or its contribution decision sits inside an
@@ -614,40 +676,12 @@ static int eval_pair(const orc_ctx *C, const prim_t *p, double px, double py,
   const double amin = C->cfg[CF_ALPHA_MIN], nearz = C->cfg[CF_NEAR];
   if (p->type == 1) {
     double dx = px - p->mx, dy = py - p->my;
-    d = p->ca * dx * dx + 2.0 * p->cb * dx * dy + p->cc * dy * dy;
+    double u = p->ca * dx + p->cb * dy, v = p->cc * dy;
+    d = u * u + v * v;
     z = p->Z;
   } else {
-    /* ray-splat intersection (App. C): solve mu_c + u a + v b = tau ray */
-    double ray[3] = {(px - C->cx) / C->fx, (py - C->cy) / C->fy, 1.0};
-    double A[3][4] = {{p->a[0], p->b[0], -ray[0], -p->X},
-                      {p->a[1], p->b[1], -ray[1], -p->Y},
-                      {p->a[2], p->b[2], -ray[2], -p->Z}};
-    double scale = sqrt(p->a[0] * p->a[0] + p->a[1] * p->a[1] + p->a[2] * p->a[2]) *
-                   sqrt(p->b[0] * p->b[0] + p->b[1] * p->b[1] + p->b[2] * p->b[2]) *
-                   sqrt(ray[0] * ray[0] + ray[1] * ray[1] + 1.0);
-    double detv = 1.0;
-    for (int c = 0; c < 3; ++c) {
-      int piv = c;
-      for (int r = c + 1; r < 3; ++r)
-        if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
-      if (piv != c) {
-        for (int k = 0; k < 4; ++k) { double tmp = A[c][k]; A[c][k] = A[piv][k]; A[piv][k] = tmp; }
-        detv = -detv;
-      }
-      detv *= A[c][c];
-      if (A[c][c] == 0.0) return 0;
-      for (int r = c + 1; r < 3; ++r) {
-        double f = A[r][c] / A[c][c];
-        for (int k = c; k < 4; ++k) A[r][k] -= f * A[c][k];
-      }
-    }
-    if (fabs(detv) <= 1e-12 * scale) return 0;
     double sol[3];
-    for (int r = 2; r >= 0; --r) {
-      double v = A[r][3];
-      for (int k = r + 1; k < 3; ++k) v -= A[r][k] * sol[k];
-      sol[r] = v / A[r][r];
-    }
+    if (!surfel_hit(C, p, px, py, sol)) return 0;
     double u = sol[0], v = sol[1];
     z = sol[2];
     d = u * u + v * v;
@@ -663,6 +697,29 @@ static int eval_pair(const orc_ctx *C, const prim_t *p, double px, double py,
   double ag = p->alpha * exp(-0.5 * d);
   if (fabs(ag - amin) <= AMB_ALPHA_REL * amin) a = 1;
   int contributes = ag >= amin;
+  if (contributes && !a) {
+    /* conditioning of (u, v) as functions of the offset to the centre */
+    double ex = px - p->mx, ey = py - p->my, u, v, dux, duy, dvx, dvy;
+    if (p->type == 1) {
+      u = p->ca * ex + p->cb * ey; v = p->cc * ey;
+      dux = p->ca; duy = p->cb; dvx = 0.0; dvy = p->cc;
+    } else {
+      double s0[3], s1[3], s2[3];
+      const double hh = 1e-3;
+      if (surfel_hit(C, p, px, py, s0) && surfel_hit(C, p, px + hh, py, s1) &&
+          surfel_hit(C, p, px, py + hh, s2)) {
+        u = s0[0]; v = s0[1];
+        dux = (s1[0] - s0[0]) / hh; dvx = (s1[1] - s0[1]) / hh;
+        duy = (s2[0] - s0[0]) / hh; dvy = (s2[1] - s0[1]) / hh;
+      } else {
+        u = v = dux = duy = dvx = dvy = 0.0;
+      }
+    }
+    double du = COND_ULPS * EPS32 * (fabs(dux * ex) + fabs(duy * ey));
+    double dv = COND_ULPS * EPS32 * (fabs(dvx * ex) + fabs(dvy * ey));
+    double dd = 2.0 * (fabs(u) * du + fabs(v) * dv) + du * du + dv * dv;
+    if (ag * 0.5 * dd > COND_ALPHA) a = 1;
+  }
   if (contributes && p->ndot < AMB_FLIP) a = 1;
   if (p->amb_near && (contributes || a)) {
     a = 1;

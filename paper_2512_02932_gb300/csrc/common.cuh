@@ -17,13 +17,17 @@ constexpr float kLog2e = 1.4426950408889634f;
 // staged through shared memory by the render kernels.
 //   r0 = (x_c, y_c, z_c, alpha_s)   projected centre (pixels), camera depth,
 //        alpha_s = +alpha for a 3D Gaussian, -alpha for a 2D surfel
-//   r1 = 3D: (a, b, c, 0)  conic: d = a dx^2 + 2 b dx dy + c dy^2  (Eq. 1)
+//   r1 = 3D: (W00, W01, W11, 0)  Cholesky factor of the conic (Eq. 1):
+//        d = (W00 dx + W01 dy)^2 + (W11 dy)^2
 //        2D: (Q00, Q01, Q10, Q11)
 //   r2 = 3D: (0, 0, r, g)   2D: (Q20, Q21, r, g)
 //   r3 = (b, nx, ny, nz)    colour blue, camera-space normal
-//   r4 = (x0, x1, y0, y1)   padded pixel box outside which the pair never
-//        contributes (the box the tile rectangle is cut from); a warp skips a
-//        record whose box misses its pixel block
+//   r4 = (x_lo, y_lo, box_x, box_y)  low parts of the projected centre (the
+//        centre is the double-float x_c + x_lo: binary32 alone cannot place
+//        it to the 1e-4 px a sub-pixel splat needs) and the padded pixel box
+//        outside which the pair never contributes, as two half2 (x0, x1) and
+//        (y0, y1) rounded outwards; a warp skips a record whose box misses
+//        its pixel block
 // For a surfel, with (dx, dy) the pixel offset from the projected centre:
 //   p = (Q00 dx + Q01 dy, Q10 dx + Q11 dy, Q20 dx + Q21 dy + 1),
 //   (u, v) = (p0, p1) / p2, hit depth z = z_c / p2     (Eq. 14 re-centred)
@@ -109,6 +113,17 @@ __device__ __forceinline__ float rcp_approx(float x) {
   float y;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
+}
+
+// error-free transforms for the double-float projected centre
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
+  p = __fmul_rn(a, b);
+  e = __fmaf_rn(a, b, -p);
 }
 
 __device__ __forceinline__ void set_error(int32_t *dev_err, int32_t code) {

@@ -10,6 +10,8 @@
 // Backward, one thread per primitive: the record gradient accumulated by
 //   render_bwd, chained through the same forward quantities to the raw
 //   parameters (means, log-scales, quaternion, opacity logit, SH).
+#include <cuda_fp16.h>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -305,6 +307,44 @@ __device__ __forceinline__ void load_sh(const float *sh, int64_t i, float *f) {
   }
 }
 
+// a d - b c with one rounding error (Kahan's FMA algorithm)
+__device__ __forceinline__ float det2(float a, float b, float c, float d) {
+  const float w = __fmul_rn(b, c);
+  const float e = __fmaf_rn(-b, c, w);
+  return __fadd_rn(__fmaf_rn(a, d, -w), e);
+}
+
+// Projected covariance of a 3D Gaussian from its factor T = J W R S (2x3):
+// Sigma' = T T^T + dilation I, with det(T T^T) by the Cauchy-Binet sum of the
+// squared 2x2 minors (a sum of squares: no cancellation, so the conic of a
+// needle-like footprint stays accurate in binary32).
+struct Cov2 {
+  float s00, s01, s11, det;
+};
+
+__device__ __forceinline__ Cov2 projected_cov(const Contract &o, const CamK &c, float dil) {
+  const float iz = o.iz;
+  const float j00 = c.fx * iz, j02 = -c.fx * o.X * iz * iz;
+  const float j11 = c.fy * iz, j12 = -c.fy * o.Y * iz * iz;
+  float tx[3], ty[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    tx[k] = o.s[k] * fmaf(j00, o.a[k][0], j02 * o.a[k][2]);
+    ty[k] = o.s[k] * fmaf(j11, o.a[k][1], j12 * o.a[k][2]);
+  }
+  Cov2 v;
+  const float x2 = tx[0] * tx[0] + tx[1] * tx[1] + tx[2] * tx[2];
+  const float y2 = ty[0] * ty[0] + ty[1] * ty[1] + ty[2] * ty[2];
+  v.s01 = tx[0] * ty[0] + tx[1] * ty[1] + tx[2] * ty[2];
+  const float m01 = tx[0] * ty[1] - ty[0] * tx[1];
+  const float m02 = tx[0] * ty[2] - ty[0] * tx[2];
+  const float m12 = tx[1] * ty[2] - ty[1] * tx[2];
+  v.s00 = x2 + dil;
+  v.s11 = y2 + dil;
+  v.det = (m01 * m01 + m02 * m02 + m12 * m12) + dil * (x2 + y2) + dil * dil;
+  return v;
+}
+
 // write one primitive's SH row (zeros if v is null); 16-byte stores where the
 // row is 16-byte aligned (degrees 1 and 3)
 template <int DEG>
@@ -358,6 +398,58 @@ __device__ __forceinline__ float modulate(float alpha, float sz, const CfgK &f, 
   return alpha * e;
 }
 
+// Projected centre fx X/Z + cx, fy Y/Z + cy as double-floats (hi + lo), from
+// the binary32 inputs with error-free products and sums (~44 bits).
+__device__ __forceinline__ void df_dot(const float r[3], const float mu[3], float t, float &hi, float &lo) {
+  float h = t, l = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    float p, pe, s, se;
+    two_prod(r[k], mu[k], p, pe);
+    two_sum(h, p, s, se);
+    h = s;
+    l = __fadd_rn(l, __fadd_rn(pe, se));
+  }
+  two_sum(h, l, hi, lo);
+}
+
+__device__ __forceinline__ void df_centre(const CamK &c, const float mu[3], float &xh, float &xl,
+                                          float &yh, float &yl) {
+  float Xh, Xl, Yh, Yl, Zh, Zl;
+  df_dot(c.R + 0, mu, c.t[0], Xh, Xl);
+  df_dot(c.R + 3, mu, c.t[1], Yh, Yl);
+  df_dot(c.R + 6, mu, c.t[2], Zh, Zl);
+  // x/z: q1 + q2 with q2 = (X - q1 Z) / Z
+  auto ddiv = [&](float nh, float nl, float &qh, float &ql) {
+    const float q1 = __fdiv_rn(nh, Zh);
+    float p, pe;
+    two_prod(q1, Zh, p, pe);
+    const float r = __fsub_rn(__fsub_rn(__fsub_rn(nh, p), pe), __fmul_rn(q1, Zl));
+    const float q2 = __fdiv_rn(__fadd_rn(r, nl), Zh);
+    two_sum(q1, q2, qh, ql);
+  };
+  auto dscale = [&](float f, float off, float qh, float ql, float &oh, float &ol) {
+    float p, pe, s, se;
+    two_prod(f, qh, p, pe);
+    two_sum(p, off, s, se);
+    two_sum(s, __fadd_rn(__fadd_rn(se, pe), __fmul_rn(f, ql)), oh, ol);
+  };
+  float qxh, qxl, qyh, qyl;
+  ddiv(Xh, Xl, qxh, qxl);
+  ddiv(Yh, Yl, qyh, qyl);
+  dscale(c.fx, c.cx, qxh, qxl, xh, xl);
+  dscale(c.fy, c.cy, qyh, qyl, yh, yl);
+}
+
+// two halves rounded outwards (lo down, hi up), packed in a float's bits
+__device__ __forceinline__ float pack_box(float lo, float hi) {
+  lo = fmaxf(lo, -65504.0f);
+  hi = fminf(hi, 65504.0f);
+  const __half a = __float2half_rd(lo), b = __float2half_ru(hi);
+  const uint32_t u = (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
+  return __uint_as_float(u);
+}
+
 // ---------------------------------------------------------------------------
 // forward kernel
 // ---------------------------------------------------------------------------
@@ -403,19 +495,25 @@ __global__ void __launch_bounds__(256) preprocess_fwd_kernel(PrepArgs a) {
   float n0, n1, n2;
   axis_of(o, kn, n0, n1, n2);
   if (n0 * o.X + n1 * o.Y + n2 * o.Z > 0.0f) { n0 = -n0; n1 = -n1; n2 = -n2; }
-  const float ctrx = fmaf(c.fx, o.xz, c.cx), ctry = fmaf(c.fy, o.yz, c.cy);
+  float ctrx, ctrx_lo, ctry, ctry_lo;
+  df_centre(c, mu, ctrx, ctrx_lo, ctry, ctry_lo);
   Rec r;
   if (type == 1) {
-    const float det = o.s00 * o.s11 - o.s01 * o.s01;
-    const float id = 1.0f / det;
-    r.r0 = make_float4(ctrx, ctry, o.Z, o.alpha);
-    r.r1 = make_float4(o.s11 * id, -o.s01 * id, o.s00 * id, 0.0f);
+    // Eq. 1 as d = |W (dx, dy)|^2 with W the Cholesky factor of the conic:
+    // W = [[sqrt(s11/det), -s01/sqrt(s11 det)], [0, 1/sqrt(s11)]]
+    const Cov2 cv = projected_cov(o, c, a.cfg.dilation);
+    const float w00 = sqrtf(cv.s11 / cv.det);
+    const float w01 = -cv.s01 * rsqrtf(cv.s11 * cv.det);
+    const float w11 = rsqrtf(cv.s11);
+    const bool ok = cv.det > 0.0f && cv.s11 > 0.0f && isfinite(w00) && isfinite(w01) && isfinite(w11);
+    r.r0 = make_float4(ctrx, ctry, o.Z, ok ? o.alpha : 0.0f);
+    r.r1 = ok ? make_float4(w00, w01, w11, 0.0f) : make_float4(0.f, 0.f, 0.f, 0.f);
     r.r2 = make_float4(0.0f, 0.0f, col[0], col[1]);
   } else {
     float gate, fac;
     const float am = modulate(o.alpha, o.s[2], a.cfg, &gate, &fac);
     const float m0z = o.s[0] * o.a[0][2], m1z = o.s[1] * o.a[1][2];
-    const float detE = o.e0 * o.f1 - o.e1 * o.f0;
+    const float detE = det2(o.e0, o.e1, o.f0, o.f1);
     const float ie = 1.0f / detE;
     const float E00 = o.f1 * ie, E01 = -o.e1 * ie, E10 = -o.f0 * ie, E11 = o.e0 * ie;
     const float ifx = 1.0f / c.fx, ify = 1.0f / c.fy;
@@ -435,7 +533,7 @@ __global__ void __launch_bounds__(256) preprocess_fwd_kernel(PrepArgs a) {
     r.r2 = make_float4(Q20, Q21, col[0], col[1]);
   }
   r.r3 = make_float4(col[2], n0, n1, n2);
-  r.r4 = make_float4(o.bx0, o.bx1, o.by0, o.by1);
+  r.r4 = make_float4(ctrx_lo, ctry_lo, pack_box(o.bx0, o.bx1), pack_box(o.by0, o.by1));
   float4 *dst = reinterpret_cast<float4 *>(a.rec) + kRecF4 * i;
   dst[0] = r.r0; dst[1] = r.r1; dst[2] = r.r2; dst[3] = r.r3; dst[4] = r.r4;
 }
@@ -497,9 +595,9 @@ __global__ void __launch_bounds__(256) preprocess_bwd_kernel(PrepArgs a, PrepGra
   if (type == 1) {
     dalpha = G[0];
     // conic (a, b, c) = inverse of (s00, s01; s01, s11)
-    const float det = o.s00 * o.s11 - o.s01 * o.s01;
-    const float id = 1.0f / det;
-    const float ca = o.s11 * id, cb = -o.s01 * id, cc = o.s00 * id;
+    const Cov2 cv = projected_cov(o, c, a.cfg.dilation);
+    const float id = 1.0f / cv.det;
+    const float ca = cv.s11 * id, cb = -cv.s01 * id, cc = cv.s00 * id;
     const float ga = G[7], gb = G[8], gc = G[9];
     const float ds00 = -(ga * ca * ca + gb * ca * cb + gc * cb * cb);
     const float ds11 = -(ga * cb * cb + gb * cb * cc + gc * cc * cc);
@@ -557,7 +655,7 @@ __global__ void __launch_bounds__(256) preprocess_bwd_kernel(PrepArgs a, PrepGra
   } else {
     // re-centred homography block and its inverse
     const float m0z = o.s[0] * o.a[0][2], m1z = o.s[1] * o.a[1][2];
-    const float detE = o.e0 * o.f1 - o.e1 * o.f0;
+    const float detE = det2(o.e0, o.e1, o.f0, o.f1);
     const float ie = 1.0f / detE;
     const float E00 = o.f1 * ie, E01 = -o.e1 * ie, E10 = -o.f0 * ie, E11 = o.e0 * ie;
     const float ifx = 1.0f / fx, ify = 1.0f / fy;

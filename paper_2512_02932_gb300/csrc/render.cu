@@ -11,6 +11,8 @@
 // The per-pair evaluation (eval_pair) is written with explicitly rounded
 // operations so the backward kernel reproduces the forward's contribution
 // decisions bit for bit.
+#include <cuda_fp16.h>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -36,14 +38,18 @@ struct PairEval {
 // Unified distance (Eq. 1) and contribution (Sec. 3.1) of one record at the
 // pixel centre (px, py).  Returns true iff the pair contributes.
 __device__ __forceinline__ bool eval_pair(const float4 &r0, const float4 &r1, const float4 &r2,
-                                          float px, float py, const CfgK &f, PairEval &e) {
-  e.dx = __fsub_rn(px, r0.x);
-  e.dy = __fsub_rn(py, r0.y);
+                                          const float4 &r4, float px, float py, const CfgK &f,
+                                          PairEval &e) {
+  // offset from the double-float projected centre (x_c + x_lo, y_c + y_lo)
+  e.dx = __fsub_rn(__fsub_rn(px, r0.x), r4.x);
+  e.dy = __fsub_rn(__fsub_rn(py, r0.y), r4.y);
   float q;
   if (r0.w > 0.0f) {
-    // 3D: d = a dx^2 + 2 b dx dy + c dy^2 with the conic of Eq. 13
-    const float h = __fmaf_rn(r1.x, e.dx, __fmul_rn(__fadd_rn(r1.y, r1.y), e.dy));
-    q = __fmaf_rn(__fmul_rn(r1.z, e.dy), e.dy, __fmul_rn(h, e.dx));
+    // 3D: d = (x-mu')^T Sigma'^-1 (x-mu') of Eq. 1, evaluated as |W d|^2 with
+    // W the Cholesky factor of the conic (u = W00 dx + W01 dy, v = W11 dy)
+    e.u = __fmaf_rn(r1.x, e.dx, __fmul_rn(r1.y, e.dy));
+    e.v = __fmul_rn(r1.z, e.dy);
+    q = __fmaf_rn(e.u, e.u, __fmul_rn(e.v, e.v));
     e.alpha = r0.w;
     e.z = r0.z;
   } else {
@@ -96,11 +102,18 @@ __device__ __forceinline__ void stage_chunk(const float4 *__restrict__ rec, cons
 // Bit l of the result is set iff staged record l (l < cnt) has a pixel box
 // that meets this warp's 8x4 block of pixel centres [x0+0.5, x0+7.5] x
 // [y0+0.5, y0+3.5].
+__device__ __forceinline__ float2 unpack_box(float v) {
+  const uint32_t u = __float_as_uint(v);
+  return make_float2(__half2float(__ushort_as_half((unsigned short)(u & 0xffffu))),
+                     __half2float(__ushort_as_half((unsigned short)(u >> 16))));
+}
+
 __device__ __forceinline__ uint32_t chunk_mask(const float4 *buf, int cnt, int lane, float bx0, float by0) {
   bool hit = false;
   if (lane < cnt) {
     const float4 b = buf[lane * kRecF4 + 4];
-    hit = b.x <= bx0 + 7.5f && b.y >= bx0 + 0.5f && b.z <= by0 + 3.5f && b.w >= by0 + 0.5f;
+    const float2 bx = unpack_box(b.z), by = unpack_box(b.w);
+    hit = bx.x <= bx0 + 7.5f && bx.y >= bx0 + 0.5f && by.x <= by0 + 3.5f && by.y >= by0 + 0.5f;
   }
   return __ballot_sync(0xffffffffu, hit);
 }
@@ -142,9 +155,9 @@ __global__ void __launch_bounds__(kRW * 32) render_fwd_kernel(RenderArgs a) {
       mask &= mask - 1;
       if (done) continue;
       const float4 *r = chunk + j * kRecF4;
-      const float4 r0 = r[0], r1 = r[1], r2 = r[2];
+      const float4 r0 = r[0], r1 = r[1], r2 = r[2], r4 = r[4];
       PairEval e;
-      if (!eval_pair(r0, r1, r2, px, py, a.cfg, e)) continue;
+      if (!eval_pair(r0, r1, r2, r4, px, py, a.cfg, e)) continue;
       const float Tn = T * (1.0f - e.at);
       if (Tn < a.cfg.T_min) {
         done = true;
@@ -274,9 +287,9 @@ __global__ void __launch_bounds__(kRW * 32) render_bwd_kernel(RenderBwdArgs a) {
       mask &= ~(1u << jj);
       const uint32_t j = cs + (uint32_t)jj;
       const float4 *r = chunk + jj * kRecF4;
-      const float4 r0 = r[0], r1 = r[1], r2 = r[2];
+      const float4 r0 = r[0], r1 = r[1], r2 = r[2], r4 = r[4];
       PairEval e;
-      const bool contrib = inside && (j - start) < last && eval_pair(r0, r1, r2, px, py, a.cfg, e);
+      const bool contrib = inside && (j - start) < last && eval_pair(r0, r1, r2, r4, px, py, a.cfg, e);
       if (!__any_sync(0xffffffffu, contrib)) continue;
       float g[16];
 #pragma unroll
@@ -304,11 +317,12 @@ __global__ void __launch_bounds__(kRW * 32) render_bwd_kernel(RenderBwdArgs a) {
           dd = dat * (-0.5f * e.at);
         }
         if (r0.w > 0.0f) {
+          // conic-space gradient: d = a dx^2 + 2 b dx dy + c dy^2
           g[7] = dd * e.dx * e.dx;
           g[8] = dd * 2.0f * e.dx * e.dy;
           g[9] = dd * e.dy * e.dy;
-          const float ddx = dd * 2.0f * (r1.x * e.dx + r1.y * e.dy);
-          const float ddy = dd * 2.0f * (r1.y * e.dx + r1.z * e.dy);
+          const float ddx = dd * 2.0f * e.u * r1.x;
+          const float ddy = dd * 2.0f * (e.u * r1.y + e.v * r1.z);
           g[4] = -ddx; g[5] = -ddy; g[6] = dzp;
         } else {
           const float du = 2.0f * e.u * dd, dv = 2.0f * e.v * dd;

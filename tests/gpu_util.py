@@ -60,6 +60,8 @@ def assert_images_match(gpu, orc, amb, max_abs=IMG_MAX_ABS, mean_abs=IMG_MEAN_AB
             g, o = g[None], o[None]
         for c in range(g.shape[0]):
             d = np.abs(g[c].astype(np.float64) - o[c])[ok]
+            if key == "depth":  # unnormalised depth: bounds relative to max(1, |depth|)
+                d = d / np.maximum(1.0, np.abs(o[c][ok]))
             report[f"{key}{c}"] = (float(d.max()) if d.size else 0.0, float(d.mean()) if d.size else 0.0)
             assert d.size == 0 or d.max() <= max_abs, (key, c, d.max(), np.unravel_index(
                 np.argmax(np.where(ok, np.abs(g[c] - o[c]), 0)), ok.shape))
