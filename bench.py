@@ -46,6 +46,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-pixels", type=int, default=20000)
     p.add_argument("--profile-phases", action="store_true", default=True)
+    p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--serving-seconds", type=float, default=5.0)
+    p.add_argument("--serving-rate", type=float, default=200.0)
     return p.parse_args()
 
 
@@ -182,11 +185,44 @@ def reference_arm(args, world, rank):
 
 
 # ---------------------------------------------------------------------------
+def run_serving(args, dev, cfg):
+    """Serving workload: 4 resident scenes (200k, 500k, 1M, 3M primitives,
+    3D shares 50-80%, SH degree 3), Poisson arrivals with random orbit poses
+    and resolutions from {512^2, 800x600, 1280x720, 1920x1080}; the batched
+    server against the one-request-per-launch renderer, in real time, then
+    both saturated (all requests waiting at t = 0)."""
+    import synthetic as S
+    from paper_2512_02932_gb300 import SceneTensors
+    from paper_2512_02932_gb300.serving import Server, ServingConfig
+    scenes = [SceneTensors.from_numpy(sc, dev) for sc in S.serving_scenes()]
+    reqs = S.serving_requests(seed=3, rate_hz=args.serving_rate, duration_s=args.serving_seconds)
+    out = {"workload": f"4 resident scenes (200k/500k/1M/3M prims), Poisson {args.serving_rate:g} req/s "
+                       f"for {args.serving_seconds:g} s, mixed resolutions", "requests": len(reqs)}
+    warm = reqs[:16]
+    for name, plain in (("batched", False), ("plain", True)):
+        srv = Server(scenes, cfg, ServingConfig(), device=dev, plain=plain)
+        srv.run(warm, realtime=False)
+        _, st = srv.run(reqs, realtime=True)
+        _, sat = srv.run([(0.0, sid, cam) for (_, sid, cam) in reqs[:400]], realtime=False)
+        out[name] = {"frames_per_s": round(st["frames_per_s"], 2), "p50_ms": round(st["p50_ms"], 3),
+                     "p99_ms": round(st["p99_ms"], 3), "mean_ms": round(st["mean_ms"], 3),
+                     "saturated_frames_per_s": round(sat["frames_per_s"], 2),
+                     "saturated_p50_ms": round(sat["p50_ms"], 3), "failed": st["failed"]}
+        del srv
+        torch_sync(dev)
+    return out
+
+
+def torch_sync(dev):
+    import torch
+    torch.cuda.synchronize(dev)
+
+
 def launches_per_step(rast, exchange_steps, steps):
     tiles = rast.ranges.shape[0]
     tile_bits = max(1, math.ceil(math.log2(tiles))) if tiles > 1 else 1
     passes = (tile_bits + 7) // 8
-    bin_sort = 3 * (4 + passes) + 3 + 1 + 1 + (1 if rast.keys is not None else 0)
+    bin_sort = 3 * (4 + passes) + 3 + 2 + 1 + (1 if rast.keys is not None else 0)
     per = 1 + bin_sort + 1 + 2
     return per * steps + exchange_steps
 
@@ -270,18 +306,19 @@ def main():
     K = int(rast.d_count.item())
     n_last_sum = int(rast.n_last.to(torch.int64).sum().item())
 
-    # per-phase timing on the launching stream (same workload, separate loop)
+    # per-phase timing on the launching stream (same workload, separate loop):
+    # CUDA events around each ABI call; the backward's two stages separately
     phases = {}
     if args.profile_phases:
         s = torch.cuda.current_stream()
         dsc = SceneTensors(st.means.detach(), st.log_scales.detach(), st.quats.detach(),
                            st.opacity_logits.detach(), st.sh.detach(), st.types, 3)
         g = torch.sign(torch.randn((3, args.height, args.width), device=dev)) / target.numel()
-        names = ["preprocess", "bin_sort", "render_fwd", "render_bwd+preprocess_bwd"]
+        names = ["preprocess", "bin_sort", "render_fwd", "render_bwd", "preprocess_bwd"]
         acc = {n: 0.0 for n in names}
         reps = max(3, min(10, args.steps))
         for _ in range(reps):
-            evs = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+            evs = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
             evs[0].record(s)
             rast.preprocess(dsc, cam, cfg)
             evs[1].record(s)
@@ -289,12 +326,17 @@ def main():
             evs[2].record(s)
             rast.render()
             evs[3].record(s)
-            rast.backward(g, None, None, None)
+            _, f_rec, f_prep = rast.backward(g, None, None, None, stages=True)
+            f_rec()
             evs[4].record(s)
+            f_prep()
+            evs[5].record(s)
             torch.cuda.synchronize()
             for i, n in enumerate(names):
                 acc[n] += evs[i].elapsed_time(evs[i + 1])
         phases = {n: round(v / reps, 4) for n, v in acc.items()}
+        n_contrib_sum = int(rast.n_contrib.to(torch.int64).sum().item())
+        n_last_sum = int(rast.n_last.to(torch.int64).sum().item())
 
     # end to end through the public API with host buffers: H2D of the step's
     # inputs (scene parameters + target) from pinned memory, D2H of the loss
@@ -341,6 +383,24 @@ def main():
         e2e = {"value": round(e2e_ms, 4), "unit": "ms", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": 4, "steps": ksteps}
 
+    roofline = None
+    if phases:
+        # dominant kernel: the blend backward (FP32 issue bound).  Algorithmic
+        # FP32 work (FMA = 2 flops): 16 flops per (pixel, list entry) the pixel
+        # consumed (70/30 mix of the 13-flop 3D and 22-flop surfel evaluation)
+        # + 70 flops of gradient per contributing pair.  Peak: 152 SMs x 128
+        # FP32 lanes x 2 flops x the max SM clock.
+        sm_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
+        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        flops = 16.0 * n_last_sum + 70.0 * n_contrib_sum
+        achieved = flops / (phases["render_bwd"] * 1e-3) / 1e12
+        roofline = {"kernel": "render_bwd_kernel", "bound": "alu", "achieved": round(achieved, 3),
+                    "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                    "traffic": None, "peak_source": "FP32 lanes x max SM clock (no measured FP32 peak)",
+                    "units": {"pixel_list_entries": n_last_sum, "contributing_pairs": n_contrib_sum}}
+    serving = None
+    if not args.no_serving and world == 1:
+        serving = run_serving(args, dev, cfg)
     line = {
         "metric": METRIC, "value": round(ms_per_step, 4), "unit": "ms", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
@@ -348,11 +408,13 @@ def main():
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_prims": args.n, "width": args.width, "height": args.height,
                    "sh_degree": 3, "instances_K": K, "pixel_list_entries": n_last_sum,
-                   "l2": "inputs larger than L2 (scene 708 MB, records 192 MB, lists > 100 MB)",
+                   "l2": "inputs larger than L2 (scene 708 MB, records 240 MB, lists > 100 MB)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "phases_ms": phases,
         "step_ms": {"min": round(min(step_ms), 4), "median": round(statistics.median(step_ms), 4),
                     "max": round(max(step_ms), 4), "first": round(step_ms[0], 4)},
+        "roofline": roofline,
+        "serving": serving,
         "gpu_launches": launches_per_step(rast, n_exchange[0], args.steps),
         "clocks": clk,
         "e2e": e2e,

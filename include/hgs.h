@@ -139,6 +139,7 @@ typedef struct {
   float *alpha;     /* [H,W] 1 - T_final */
   float *T_final;   /* [H,W] final transmittance (needed by the backward) */
   uint32_t *n_last; /* [H,W] list entries consumed (needed by the backward) */
+  uint32_t *n_contrib; /* [H,W] optional (may be NULL): contributing pairs */
 } hgs_image;
 
 /* Upstream gradients dL/d(outputs), same shapes as hgs_image; any may be NULL
@@ -256,6 +257,54 @@ int hgs_render_bwd(const hgs_scene *scene, const hgs_projected *proj,
                    const hgs_binning *bins, const hgs_camera *cam, const hgs_config *cfg,
                    const hgs_image *fwd, const hgs_image_grad *dL, float *grad_ws,
                    hgs_scene_grad *out, int32_t *dev_err, hgs_stream_t stream);
+
+/* One request of a batched render: a resident scene, a camera and the
+ * request's own output planes (rgb, depth, normal, alpha, T_final, n_last as
+ * in hgs_image, sized for this camera). */
+typedef struct {
+  hgs_scene scene;
+  hgs_camera cam;
+  hgs_image out;
+} hgs_request;
+
+#define HGS_MAX_BATCH 16
+
+/* Bytes of device workspace hgs_render_batch needs for these requests and
+ * `capacity` tile instances in total.  Host only. */
+int hgs_render_batch_workspace(int nreq, const hgs_request *reqs, int64_t capacity, size_t *bytes);
+
+/* hgs_render_batch -- the forward rasterizer (hgs_preprocess + hgs_bin_sort +
+ * hgs_render_fwd) for up to HGS_MAX_BATCH requests of different scenes and
+ * resolutions, each stage one launch for the whole batch (the serving form).
+ * The requests' primitives are concatenated and their 16x16 tile grids are
+ * stacked vertically into one grid (width = widest request), so one sort and
+ * one render launch cover every request; each request's image is exactly the
+ * one hgs_render_fwd would produce alone (a tile never mixes requests).
+ * ws: device workspace of hgs_render_batch_workspace() bytes, A16; it holds
+ * the combined records, the instance list and the sort scratch.
+ * d_count (device int64) receives the batch's instance count K; if K >
+ * capacity, HGS_ERR_CAPACITY is stored in *dev_err and the images hold only
+ * the background (nothing out of bounds): grow and retry.
+ * Errors: INVALID_ARG for nreq outside 1..HGS_MAX_BATCH, a bad scene, camera
+ * or output pointer, a too small workspace; UNSUPPORTED for tile != 16 or a
+ * stacked grid over 65535 tile rows. */
+int hgs_render_batch(int nreq, const hgs_request *reqs, const hgs_config *cfg, void *ws, size_t ws_bytes,
+                     int64_t capacity, int64_t *d_count, int32_t *dev_err, hgs_stream_t stream);
+
+/* The two stages of hgs_render_bwd, for callers that want the per-primitive
+ * gradient of the render record or time the stages separately:
+ * hgs_render_bwd_records -- zero grad_ws, then replay every tile's list in
+ *   reverse and accumulate dL/d(record) (centre, conic or surfel homography,
+ *   opacity, colour, depth, normal: 16 floats per primitive) into grad_ws.
+ * hgs_preprocess_bwd -- chain grad_ws through the projection, the SH decode,
+ *   the activations and the scale modulation to the raw parameters.
+ * Arguments and errors as in hgs_render_bwd. */
+int hgs_render_bwd_records(const hgs_scene *scene, const hgs_projected *proj, const hgs_binning *bins,
+                           const hgs_camera *cam, const hgs_config *cfg, const hgs_image *fwd,
+                           const hgs_image_grad *dL, float *grad_ws, int32_t *dev_err, hgs_stream_t stream);
+int hgs_preprocess_bwd(const hgs_scene *scene, const hgs_projected *proj, const hgs_camera *cam,
+                       const hgs_config *cfg, const float *grad_ws, hgs_scene_grad *out, int32_t *dev_err,
+                       hgs_stream_t stream);
 
 /* hgs_exchange_types -- Adaptive Type Exchange (Sec. 3.2) in place.
  * ERANK mode: erank = exp(-sum p_i log p_i), p = q / |q|_1, q = (s_x^2,

@@ -19,6 +19,7 @@ HGS_ERR_UNSUPPORTED = -5
 HGS_EXCHANGE_ERANK = 0
 HGS_EXCHANGE_MASK = 1
 HGS_BIN_SORT_STATIC_BYTES = 64 << 20
+HGS_MAX_BATCH = 16
 
 P = C.c_void_p
 
@@ -53,7 +54,8 @@ class hgs_binning(C.Structure):
 
 
 class hgs_image(C.Structure):
-    _fields_ = [("rgb", P), ("depth", P), ("normal", P), ("alpha", P), ("T_final", P), ("n_last", P)]
+    _fields_ = [("rgb", P), ("depth", P), ("normal", P), ("alpha", P), ("T_final", P), ("n_last", P),
+                ("n_contrib", P)]
 
 
 class hgs_image_grad(C.Structure):
@@ -62,6 +64,10 @@ class hgs_image_grad(C.Structure):
 
 class hgs_scene_grad(C.Structure):
     _fields_ = [("means", P), ("log_scales", P), ("quats", P), ("opacity_logits", P), ("sh", P)]
+
+
+class hgs_request(C.Structure):
+    _fields_ = [("scene", hgs_scene), ("cam", hgs_camera), ("out", hgs_image)]
 
 
 class hgs_exchange_cfg(C.Structure):
@@ -85,6 +91,14 @@ SYMBOLS = {
     "hgs_render_bwd": (C.c_int, [C.POINTER(hgs_scene), C.POINTER(hgs_projected), C.POINTER(hgs_binning),
                                  C.POINTER(hgs_camera), C.POINTER(hgs_config), C.POINTER(hgs_image),
                                  C.POINTER(hgs_image_grad), P, C.POINTER(hgs_scene_grad), P, P]),
+    "hgs_render_batch_workspace": (C.c_int, [C.c_int, C.POINTER(hgs_request), C.c_int64, C.POINTER(C.c_size_t)]),
+    "hgs_render_batch": (C.c_int, [C.c_int, C.POINTER(hgs_request), C.POINTER(hgs_config), P, C.c_size_t,
+                                   C.c_int64, P, P, P]),
+    "hgs_render_bwd_records": (C.c_int, [C.POINTER(hgs_scene), C.POINTER(hgs_projected), C.POINTER(hgs_binning),
+                                         C.POINTER(hgs_camera), C.POINTER(hgs_config), C.POINTER(hgs_image),
+                                         C.POINTER(hgs_image_grad), P, P, P]),
+    "hgs_preprocess_bwd": (C.c_int, [C.POINTER(hgs_scene), C.POINTER(hgs_projected), C.POINTER(hgs_camera),
+                                     C.POINTER(hgs_config), P, C.POINTER(hgs_scene_grad), P, P]),
     "hgs_exchange_types": (C.c_int, [C.POINTER(hgs_scene_mut), C.POINTER(hgs_exchange_cfg), P, P, P]),
 }
 
@@ -145,4 +159,8 @@ hgs_bin_sort = _fwd("hgs_bin_sort")
 hgs_bin_sort_static = _fwd("hgs_bin_sort_static")
 hgs_render_fwd = _fwd("hgs_render_fwd")
 hgs_render_bwd = _fwd("hgs_render_bwd")
+hgs_render_bwd_records = _fwd("hgs_render_bwd_records")
+hgs_preprocess_bwd = _fwd("hgs_preprocess_bwd")
 hgs_exchange_types = _fwd("hgs_exchange_types")
+hgs_render_batch_workspace = _fwd("hgs_render_batch_workspace")
+hgs_render_batch = _fwd("hgs_render_batch")

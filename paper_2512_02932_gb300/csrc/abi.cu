@@ -2,6 +2,7 @@
 // Host-side validation, conversion of the ABI structs to kernel argument
 // blocks, and launches on the caller's stream.  Nothing here allocates,
 // synchronises (except hgs_check) or prints.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -200,15 +201,14 @@ int hgs_render_fwd(int64_t n, const hgs_projected *proj, const hgs_binning *bins
   a.cam = ck;
   a.cfg = fk;
   a.rgb = out->rgb; a.depth = out->depth; a.normal = out->normal; a.alpha = out->alpha;
-  a.T_final = out->T_final; a.n_last = out->n_last;
+  a.T_final = out->T_final; a.n_last = out->n_last; a.n_contrib = out->n_contrib;
   launch_render_fwd(a, reinterpret_cast<cudaStream_t>(stream));
   return launched();
 }
 
-int hgs_render_bwd(const hgs_scene *scene, const hgs_projected *proj, const hgs_binning *bins,
-                   const hgs_camera *cam, const hgs_config *cfg, const hgs_image *fwd,
-                   const hgs_image_grad *dL, float *grad_ws, hgs_scene_grad *out, int32_t *dev_err,
-                   hgs_stream_t stream) {
+int hgs_render_bwd_records(const hgs_scene *scene, const hgs_projected *proj, const hgs_binning *bins,
+                           const hgs_camera *cam, const hgs_config *cfg, const hgs_image *fwd,
+                           const hgs_image_grad *dL, float *grad_ws, int32_t *dev_err, hgs_stream_t stream) {
   (void)dev_err;
   int st;
   if ((st = scene_ok(scene)) != HGS_OK) return st;
@@ -219,11 +219,7 @@ int hgs_render_bwd(const hgs_scene *scene, const hgs_projected *proj, const hgs_
   if ((st = proj_ok(proj, scene->n)) != HGS_OK) return st;
   if (!bins || !bins->ranges || (scene->n > 0 && !bins->vals)) return HGS_ERR_INVALID_ARG;
   if (!fwd || !fwd->T_final || !fwd->n_last || !dL) return HGS_ERR_INVALID_ARG;
-  if (!out || (scene->n > 0 && (!out->means || !out->log_scales || !out->quats ||
-                                !out->opacity_logits || !out->sh)))
-    return HGS_ERR_INVALID_ARG;
-  if (scene->n > 0 && (!grad_ws || !aligned16(grad_ws) || !aligned16(out->quats)))
-    return HGS_ERR_INVALID_ARG;
+  if (scene->n > 0 && (!grad_ws || !aligned16(grad_ws))) return HGS_ERR_INVALID_ARG;
   if (scene->n == 0) return HGS_OK;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   cudaMemsetAsync(grad_ws, 0, sizeof(float) * kGradW * (size_t)scene->n, s);
@@ -238,12 +234,176 @@ int hgs_render_bwd(const hgs_scene *scene, const hgs_projected *proj, const hgs_
   r.g_rgb = dL->rgb; r.g_depth = dL->depth; r.g_normal = dL->normal; r.g_alpha = dL->alpha;
   r.rec_grad = grad_ws;
   launch_render_bwd(r, s);
+  return launched();
+}
+
+int hgs_preprocess_bwd(const hgs_scene *scene, const hgs_projected *proj, const hgs_camera *cam,
+                       const hgs_config *cfg, const float *grad_ws, hgs_scene_grad *out, int32_t *dev_err,
+                       hgs_stream_t stream) {
+  (void)dev_err;
+  int st;
+  if ((st = scene_ok(scene)) != HGS_OK) return st;
+  CamK ck;
+  CfgK fk;
+  if ((st = cam_to_kernel(cam, &ck)) != HGS_OK) return st;
+  if ((st = cfg_to_kernel(cfg, &fk)) != HGS_OK) return st;
+  if ((st = proj_ok(proj, scene->n)) != HGS_OK) return st;
+  if (!out || (scene->n > 0 && (!out->means || !out->log_scales || !out->quats ||
+                                !out->opacity_logits || !out->sh)))
+    return HGS_ERR_INVALID_ARG;
+  if (scene->n > 0 && (!grad_ws || !aligned16(grad_ws) || !aligned16(out->quats)))
+    return HGS_ERR_INVALID_ARG;
+  if ((scene->sh_degree == 1 || scene->sh_degree == 3) && scene->n > 0 && !aligned16(out->sh))
+    return HGS_ERR_INVALID_ARG;
+  if (scene->n == 0) return HGS_OK;
   PrepGradArgs g;
   g.rec_grad = grad_ws;
   g.means = out->means; g.log_scales = out->log_scales; g.quats = out->quats;
   g.logits = out->opacity_logits; g.sh = out->sh;
   hgs_projected pcopy = *proj;
-  launch_preprocess_bwd(prep_args(scene, ck, fk, &pcopy), g, scene->sh_degree, s);
+  launch_preprocess_bwd(prep_args(scene, ck, fk, &pcopy), g, scene->sh_degree,
+                        reinterpret_cast<cudaStream_t>(stream));
+  return launched();
+}
+
+int hgs_render_bwd(const hgs_scene *scene, const hgs_projected *proj, const hgs_binning *bins,
+                   const hgs_camera *cam, const hgs_config *cfg, const hgs_image *fwd,
+                   const hgs_image_grad *dL, float *grad_ws, hgs_scene_grad *out, int32_t *dev_err,
+                   hgs_stream_t stream) {
+  if (!out) return HGS_ERR_INVALID_ARG;
+  int st = hgs_render_bwd_records(scene, proj, bins, cam, cfg, fwd, dL, grad_ws, dev_err, stream);
+  if (st != HGS_OK) return st;
+  return hgs_preprocess_bwd(scene, proj, cam, cfg, grad_ws, out, dev_err, stream);
+}
+
+}  // extern "C"
+
+namespace {
+
+struct BatchLayout {
+  int64_t total_n;
+  int TXmax, rows;
+  size_t off_rec, off_key, off_rect, off_touched, off_vals, off_ranges, off_sort, bytes;
+};
+
+size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
+int batch_layout(int nreq, const hgs_request *reqs, int64_t capacity, BatchLayout *L) {
+  if (nreq < 1 || nreq > HGS_MAX_BATCH || !reqs || capacity < 0) return HGS_ERR_INVALID_ARG;
+  int64_t n = 0;
+  int TXmax = 0, rows = 0;
+  for (int r = 0; r < nreq; ++r) {
+    const hgs_camera &c = reqs[r].cam;
+    if (c.width <= 0 || c.height <= 0 || c.width > 16384 || c.height > 16384) return HGS_ERR_INVALID_ARG;
+    if (reqs[r].scene.n < 0) return HGS_ERR_INVALID_ARG;
+    n += reqs[r].scene.n;
+    TXmax = std::max(TXmax, (c.width + kTile - 1) / kTile);
+    rows += (c.height + kTile - 1) / kTile;
+  }
+  if (n >= (int64_t(1) << 31)) return HGS_ERR_INVALID_ARG;
+  if (rows > 65535) return HGS_ERR_UNSUPPORTED;
+  L->total_n = n;
+  L->TXmax = TXmax;
+  L->rows = rows;
+  const size_t nn = (size_t)std::max<int64_t>(n, 1), cc = (size_t)std::max<int64_t>(capacity, 1);
+  size_t off = 0;
+  L->off_rec = off; off += al256(nn * kRecF4 * 16);
+  L->off_key = off; off += al256(nn * 4);
+  L->off_rect = off; off += al256(nn * 8);
+  L->off_touched = off; off += al256(nn * 4);
+  L->off_vals = off; off += al256(cc * 4);
+  L->off_ranges = off; off += al256((size_t)TXmax * rows * 8);
+  L->off_sort = off;
+  BinWorkspace w;
+  off += al256(bin_layout(nullptr, n, capacity, &w));
+  L->bytes = off;
+  return HGS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hgs_render_batch_workspace(int nreq, const hgs_request *reqs, int64_t capacity, size_t *bytes) {
+  if (!bytes) return HGS_ERR_INVALID_ARG;
+  BatchLayout L;
+  const int st = batch_layout(nreq, reqs, capacity, &L);
+  if (st != HGS_OK) return st;
+  *bytes = L.bytes;
+  return HGS_OK;
+}
+
+int hgs_render_batch(int nreq, const hgs_request *reqs, const hgs_config *cfg, void *ws, size_t ws_bytes,
+                     int64_t capacity, int64_t *d_count, int32_t *dev_err, hgs_stream_t stream) {
+  int st;
+  BatchLayout L;
+  if ((st = batch_layout(nreq, reqs, capacity, &L)) != HGS_OK) return st;
+  CfgK fk;
+  if ((st = cfg_to_kernel(cfg, &fk)) != HGS_OK) return st;
+  if (!ws || !aligned16(ws) || ws_bytes < L.bytes || !d_count) return HGS_ERR_INVALID_ARG;
+  char *base = static_cast<char *>(ws);
+  float *rec = reinterpret_cast<float *>(base + L.off_rec);
+  uint32_t *key = reinterpret_cast<uint32_t *>(base + L.off_key);
+  uint16_t *rect = reinterpret_cast<uint16_t *>(base + L.off_rect);
+  uint32_t *touched = reinterpret_cast<uint32_t *>(base + L.off_touched);
+  uint32_t *vals = reinterpret_cast<uint32_t *>(base + L.off_vals);
+  uint32_t *ranges = reinterpret_cast<uint32_t *>(base + L.off_ranges);
+  BatchPrepArgs bp;
+  BatchRenderArgs br;
+  bp.nreq = br.nreq = nreq;
+  br.TXmax = L.TXmax;
+  int64_t prim = 0;
+  int row = 0;
+  for (int r = 0; r < nreq; ++r) {
+    const hgs_request &q = reqs[r];
+    if ((st = scene_ok(&q.scene)) != HGS_OK) return st;
+    CamK ck;
+    if ((st = cam_to_kernel(&q.cam, &ck)) != HGS_OK) return st;
+    const hgs_image &o = q.out;
+    if (!o.rgb || !o.depth || !o.normal || !o.alpha || !o.T_final || !o.n_last) return HGS_ERR_INVALID_ARG;
+    hgs_projected p;
+    p.rec = rec + (size_t)prim * kRecF4 * 4;
+    p.depth_key = key + prim;
+    p.rect = rect + (size_t)prim * 4;
+    p.touched = touched + prim;
+    bp.req[r] = prep_args(&q.scene, ck, fk, &p);
+    bp.deg[r] = q.scene.sh_degree;
+    bp.row_off[r] = row;
+    bp.base[r] = prim;
+    RenderArgs &a = br.req[r];
+    a.rec = rec;  // records are addressed by their combined row
+    a.vals = vals;
+    a.ranges = ranges;
+    a.cam = ck;
+    a.cfg = fk;
+    a.rgb = o.rgb; a.depth = o.depth; a.normal = o.normal; a.alpha = o.alpha;
+    a.T_final = o.T_final; a.n_last = o.n_last; a.n_contrib = o.n_contrib;
+    br.row_off[r] = row;
+    prim += q.scene.n;
+    row += ck.TY;
+  }
+  bp.base[nreq] = prim;
+  br.row_off[nreq] = row;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  launch_preprocess_batch(bp, s);
+  BinWorkspace w;
+  bin_layout(base + L.off_sort, L.total_n, capacity, &w);
+  BinArgs b;
+  b.n = L.total_n;
+  b.capacity = capacity;
+  b.tiles = L.TXmax * L.rows;
+  b.tile_bits = tile_bits_for(b.tiles);
+  b.TX = L.TXmax;
+  b.depth_key = key;
+  b.touched = touched;
+  b.rect = rect;
+  b.vals = vals;
+  b.keys = nullptr;
+  b.ranges = ranges;
+  b.d_count = d_count;
+  b.dev_err = dev_err;
+  launch_bin_sort(b, w, s);
+  launch_render_batch(br, L.rows, s);
   return launched();
 }
 

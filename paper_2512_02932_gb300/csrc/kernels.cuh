@@ -23,6 +23,17 @@ struct PrepGradArgs {
 };
 
 int launch_preprocess_fwd(const PrepArgs &a, int deg, cudaStream_t s);
+
+constexpr int kMaxBatch = 16;
+
+struct BatchPrepArgs {
+  int nreq;
+  PrepArgs req[kMaxBatch];  // outputs already offset to the request's rows
+  int deg[kMaxBatch];
+  int row_off[kMaxBatch];   // first tile row of the request in the stacked grid
+  int64_t base[kMaxBatch + 1];
+};
+int launch_preprocess_batch(const BatchPrepArgs &b, cudaStream_t s);
 int launch_preprocess_bwd(const PrepArgs &a, const PrepGradArgs &g, int deg, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
@@ -70,6 +81,7 @@ struct RenderArgs {
   CfgK cfg;
   float *rgb, *depth, *normal, *alpha, *T_final;
   uint32_t *n_last;
+  uint32_t *n_contrib;  // optional
 };
 
 struct RenderBwdArgs {
@@ -84,6 +96,16 @@ struct RenderBwdArgs {
 };
 
 int launch_render_fwd(const RenderArgs &a, cudaStream_t s);
+
+// Batched render over a stacked tile grid: request r owns grid rows
+// [row_off[r], row_off[r+1]) and columns [0, req[r].cam.TX); its ranges are
+// indexed by the global tile id row * TXmax + column.
+struct BatchRenderArgs {
+  int nreq, TXmax;
+  RenderArgs req[kMaxBatch];
+  int row_off[kMaxBatch + 1];
+};
+int launch_render_batch(const BatchRenderArgs &b, int rows, cudaStream_t s);
 int launch_render_bwd(const RenderBwdArgs &a, cudaStream_t s);
 
 // ---------------------------------------------------------------------------

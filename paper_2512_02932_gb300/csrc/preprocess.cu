@@ -453,10 +453,11 @@ __device__ __forceinline__ float pack_box(float lo, float hi) {
 // ---------------------------------------------------------------------------
 // forward kernel
 // ---------------------------------------------------------------------------
+// One primitive: scene row i of `a`, written to row i of a's outputs; the tile
+// rectangle's rows are shifted by row_off (the batched render stacks the
+// requests' tile grids vertically).
 template <int DEG>
-__global__ void __launch_bounds__(256) preprocess_fwd_kernel(PrepArgs a) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n) return;
+__device__ __forceinline__ void preprocess_one(const PrepArgs &a, int64_t i, int row_off) {
   float mu[3], ls[3], q[4], logit;
   int type;
   load_params(a, i, mu, ls, q, logit, type);
@@ -470,7 +471,8 @@ __global__ void __launch_bounds__(256) preprocess_fwd_kernel(PrepArgs a) {
   }
   a.touched[i] = (uint32_t)((o.tx1 - o.tx0 + 1) * (o.ty1 - o.ty0 + 1));
   reinterpret_cast<uint2 *>(a.rect)[i] =
-      make_uint2((uint32_t)o.tx0 | ((uint32_t)o.tx1 << 16), (uint32_t)o.ty0 | ((uint32_t)o.ty1 << 16));
+      make_uint2((uint32_t)o.tx0 | ((uint32_t)o.tx1 << 16),
+                 (uint32_t)(o.ty0 + row_off) | ((uint32_t)(o.ty1 + row_off) << 16));
 
   const CamK &c = a.cam;
   // colour (Sec. 3.1): SH decoded along the view direction
@@ -536,6 +538,29 @@ __global__ void __launch_bounds__(256) preprocess_fwd_kernel(PrepArgs a) {
   r.r4 = make_float4(ctrx_lo, ctry_lo, pack_box(o.bx0, o.bx1), pack_box(o.by0, o.by1));
   float4 *dst = reinterpret_cast<float4 *>(a.rec) + kRecF4 * i;
   dst[0] = r.r0; dst[1] = r.r1; dst[2] = r.r2; dst[3] = r.r3; dst[4] = r.r4;
+}
+
+template <int DEG>
+__global__ void __launch_bounds__(256) preprocess_fwd_kernel(PrepArgs a) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  preprocess_one<DEG>(a, i, 0);
+}
+
+// Batched: the requests' primitives are concatenated; request r covers global
+// rows [base[r], base[r+1]) and its outputs start at row base[r].
+__global__ void __launch_bounds__(256) preprocess_batch_kernel(BatchPrepArgs b) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= b.base[b.nreq]) return;
+  int r = 0;
+  while (r + 1 < b.nreq && g >= b.base[r + 1]) ++r;
+  const int64_t i = g - b.base[r];
+  switch (b.deg[r]) {
+    case 0: preprocess_one<0>(b.req[r], i, b.row_off[r]); break;
+    case 1: preprocess_one<1>(b.req[r], i, b.row_off[r]); break;
+    case 2: preprocess_one<2>(b.req[r], i, b.row_off[r]); break;
+    default: preprocess_one<3>(b.req[r], i, b.row_off[r]); break;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -787,6 +812,13 @@ int launch_preprocess_fwd(const PrepArgs &a, int deg, cudaStream_t s) {
     case 2: preprocess_fwd_kernel<2><<<grid, 256, 0, s>>>(a); break;
     default: preprocess_fwd_kernel<3><<<grid, 256, 0, s>>>(a); break;
   }
+  return 0;
+}
+
+int launch_preprocess_batch(const BatchPrepArgs &b, cudaStream_t s) {
+  const int64_t total = b.base[b.nreq];
+  if (total == 0) return 0;
+  preprocess_batch_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(b);
   return 0;
 }
 

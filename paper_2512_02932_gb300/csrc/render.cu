@@ -121,20 +121,21 @@ __device__ __forceinline__ uint32_t chunk_mask(const float4 *buf, int cnt, int l
 // ---------------------------------------------------------------------------
 // forward
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kRW * 32) render_fwd_kernel(RenderArgs a) {
-  __shared__ __align__(16) float4 sm[kRW][2][kCh * kRecF4];
-  const int tile = blockIdx.x;
+// One 16x16 tile: `tile` indexes the ranges, `local` is the tile within the
+// request's own grid (a.cam.TX columns).
+__device__ __forceinline__ void render_tile_fwd(const RenderArgs &a, int tile, int local,
+                                                float4 (*sm)[2][kCh * kRecF4]) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int pxi, pyi;
-  pixel_of(tile, a.cam.TX, warp, lane, pxi, pyi);
+  pixel_of(local, a.cam.TX, warp, lane, pxi, pyi);
   const bool inside = pxi < a.cam.W && pyi < a.cam.H;
   const float px = (float)pxi + 0.5f, py = (float)pyi + 0.5f;
-  const float wx0 = (float)((tile % a.cam.TX) * kTile + (warp & 1) * 8);
-  const float wy0 = (float)((tile / a.cam.TX) * kTile + (warp >> 1) * 4);
+  const float wx0 = (float)((local % a.cam.TX) * kTile + (warp & 1) * 8);
+  const float wy0 = (float)((local / a.cam.TX) * kTile + (warp >> 1) * 4);
   const uint32_t start = a.ranges[2 * tile], end = a.ranges[2 * tile + 1];
   const float4 *rec = reinterpret_cast<const float4 *>(a.rec);
   float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f, N0 = 0.f, N1 = 0.f, N2 = 0.f;
-  uint32_t last = 0;
+  uint32_t last = 0, ncontrib = 0;
   bool done = !inside;
   if (__all_sync(0xffffffffu, done)) return;
 
@@ -174,6 +175,7 @@ __global__ void __launch_bounds__(kRW * 32) render_fwd_kernel(RenderArgs a) {
       N2 = fmaf(w, r3.w, N2);
       T = Tn;
       last = base - start + (uint32_t)j + 1u;
+      ++ncontrib;
     }
     if (__all_sync(0xffffffffu, done)) break;
     __syncwarp();
@@ -193,6 +195,22 @@ __global__ void __launch_bounds__(kRW * 32) render_fwd_kernel(RenderArgs a) {
   a.alpha[p] = 1.0f - T;
   a.T_final[p] = T;
   a.n_last[p] = last;
+  if (a.n_contrib) a.n_contrib[p] = ncontrib;
+}
+
+__global__ void __launch_bounds__(kRW * 32) render_fwd_kernel(RenderArgs a) {
+  __shared__ __align__(16) float4 sm[kRW][2][kCh * kRecF4];
+  render_tile_fwd(a, blockIdx.x, blockIdx.x, sm);
+}
+
+__global__ void __launch_bounds__(kRW * 32) render_batch_kernel(BatchRenderArgs b) {
+  __shared__ __align__(16) float4 sm[kRW][2][kCh * kRecF4];
+  const int gy = blockIdx.x / b.TXmax, tx = blockIdx.x % b.TXmax;
+  int r = 0;
+  while (r + 1 < b.nreq && gy >= b.row_off[r + 1]) ++r;
+  const RenderArgs &a = b.req[r];
+  if (tx >= a.cam.TX) return;
+  render_tile_fwd(a, blockIdx.x, (gy - b.row_off[r]) * a.cam.TX + tx, sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -361,6 +379,15 @@ int launch_render_fwd(const RenderArgs &a, cudaStream_t s) {
   static bool once = (prefer_shared((const void *)render_fwd_kernel), true);
   (void)once;
   render_fwd_kernel<<<tiles, kRW * 32, 0, s>>>(a);
+  return 0;
+}
+
+int launch_render_batch(const BatchRenderArgs &b, int rows, cudaStream_t s) {
+  const int blocks = rows * b.TXmax;
+  if (blocks <= 0) return 0;
+  static bool once = (prefer_shared((const void *)render_batch_kernel), true);
+  (void)once;
+  render_batch_kernel<<<blocks, kRW * 32, 0, s>>>(b);
   return 0;
 }
 

@@ -142,6 +142,7 @@ class Rasterizer:
         d = self.device
         self.T_final = torch.empty((H, W), dtype=torch.float32, device=d)
         self.n_last = torch.empty((H, W), dtype=torch.int32, device=d)
+        self.n_contrib = torch.empty((H, W), dtype=torch.int32, device=d)
         TX, TY = (W + TILE - 1) // TILE, (H + TILE - 1) // TILE
         self.ranges = torch.empty((TX * TY, 2), dtype=torch.int32, device=d)
         self.hw = (W, H)
@@ -210,7 +211,8 @@ class Rasterizer:
             "alpha": torch.empty((H, W), dtype=torch.float32, device=d),
         }
         img = abi.hgs_image(out["rgb"].data_ptr(), out["depth"].data_ptr(), out["normal"].data_ptr(),
-                            out["alpha"].data_ptr(), self.T_final.data_ptr(), self.n_last.data_ptr())
+                            out["alpha"].data_ptr(), self.T_final.data_ptr(), self.n_last.data_ptr(),
+                            self.n_contrib.data_ptr())
         self._img_s = img
         bins = self.bin_struct()
         abi.check(abi.hgs_render_fwd(self.n, C.byref(self._proj_s), C.byref(bins), C.byref(self._cam_s),
@@ -225,10 +227,17 @@ class Rasterizer:
         out = self.render()
         out["T_final"] = self.T_final
         out["n_last"] = self.n_last
+        out["n_contrib"] = self.n_contrib
         return out
 
     # -- backward ------------------------------------------------------------
-    def backward(self, g_rgb=None, g_depth=None, g_normal=None, g_alpha=None, grads=None):
+    def backward(self, g_rgb=None, g_depth=None, g_normal=None, g_alpha=None, grads=None, stages=False):
+        """Gradients of the raw parameters.  stages=True issues the two ABI
+        stages (record gradients, then preprocess backward) separately and
+        returns (grads, fn_records, fn_preprocess) callables for timing."""
+        return self._backward(g_rgb, g_depth, g_normal, g_alpha, grads, stages)
+
+    def _backward(self, g_rgb, g_depth, g_normal, g_alpha, grads, stages):
         n = self.n
         deg = self._scene_s.sh_degree
         nb = (deg + 1) ** 2
@@ -247,11 +256,23 @@ class Rasterizer:
                                  grads["quats"].data_ptr(), grads["opacity_logits"].data_ptr(),
                                  grads["sh"].data_ptr())
         bins = self.bin_struct()
+        self._keep_grads = (keep, dl, out, bins)
+        if stages:
+            def records():
+                abi.check(abi.hgs_render_bwd_records(C.byref(self._scene_s), C.byref(self._proj_s), C.byref(bins),
+                                                     C.byref(self._cam_s), C.byref(self._cfg_s),
+                                                     C.byref(self._img_s), C.byref(dl), _ptr(self.grad_ws),
+                                                     _ptr(self.dev_err), _stream()), "hgs_render_bwd_records")
+
+            def prep():
+                abi.check(abi.hgs_preprocess_bwd(C.byref(self._scene_s), C.byref(self._proj_s),
+                                                 C.byref(self._cam_s), C.byref(self._cfg_s), _ptr(self.grad_ws),
+                                                 C.byref(out), _ptr(self.dev_err), _stream()), "hgs_preprocess_bwd")
+            return grads, records, prep
         abi.check(abi.hgs_render_bwd(C.byref(self._scene_s), C.byref(self._proj_s), C.byref(bins),
                                      C.byref(self._cam_s), C.byref(self._cfg_s), C.byref(self._img_s),
                                      C.byref(dl), _ptr(self.grad_ws), C.byref(out), _ptr(self.dev_err),
                                      _stream()), "hgs_render_bwd")
-        self._keep_grads = keep
         return grads
 
     def check(self):

@@ -33,6 +33,9 @@ def test_tiny_lists_and_images(seed):
     assert_images_match(g, m, m["amb"])
     # transmittance and alpha are consistent
     np.testing.assert_allclose(g["alpha"], 1 - g["T_final"], atol=1e-7)
+    # contributor counts are integers: exact wherever the oracle is unambiguous
+    ok = ~m["amb"]
+    np.testing.assert_array_equal(g["n_contrib"][ok], m["n_contrib"][ok].astype(np.int64))
 
 
 def _gpu_vjp(scene, cam, cot, cfg=CFG):
