@@ -1,12 +1,13 @@
 // render.cu -- per-tile blending of the hybrid rasterizer (EGGS Sec. 3.1,
 // Eq. 1, Eq. 2) and its backward.
 //
-// One CTA per 16x16 tile, 8 warps; each warp owns an 8x4 pixel block and
-// walks the tile's sorted list on its own: it stages the list 32 records at a
-// time into a private double buffer in shared memory with cp.async, and
-// leaves as soon as a ballot says every one of its pixels has terminated
-// (transmittance below T_min).  No CTA-wide barrier is ever taken, so warps
-// of a tile never wait for each other.
+// One CTA per 16x16 tile, 4 warps; each warp owns an 8x8 pixel block, two
+// pixels per lane (rows y and y + 4), and walks the tile's sorted list on its
+// own: it stages the list 32 records at a time into a private double buffer
+// in shared memory with cp.async, skips records whose pixel box misses its
+// block, and leaves as soon as a ballot says every one of its pixels has
+// terminated (transmittance below T_min).  No CTA-wide barrier is ever
+// taken, so warps of a tile never wait for each other.
 //
 // The per-pair evaluation (eval_pair) is written with explicitly rounded
 // operations so the backward kernel reproduces the forward's contribution
@@ -18,7 +19,7 @@
 
 namespace hgs {
 
-constexpr int kRW = 8;   // warps per CTA
+constexpr int kRW = 4;   // warps per CTA (one 16x16 tile, 8x8 pixels per warp)
 constexpr int kCh = 32;  // records per staged chunk
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
@@ -74,10 +75,11 @@ __device__ __forceinline__ bool eval_pair(const float4 &r0, const float4 &r1, co
   return true;
 }
 
-__device__ __forceinline__ void pixel_of(int tile, int TX, int warp, int lane, int &px, int &py) {
-  const int tx = tile % TX, ty = tile / TX;
-  px = tx * kTile + (warp & 1) * 8 + (lane & 7);
-  py = ty * kTile + (warp >> 1) * 4 + (lane >> 3);
+// warp block origin (pixel coordinates of its top-left pixel) and the two
+// pixels of this lane: (x, y) and (x, y + 4)
+__device__ __forceinline__ void block_of(int local, int TX, int warp, int &bx, int &by) {
+  bx = (local % TX) * kTile + (warp & 1) * 8;
+  by = (local / TX) * kTile + (warp >> 1) * 8;
 }
 
 // ---------------------------------------------------------------------------
@@ -99,21 +101,21 @@ __device__ __forceinline__ void stage_chunk(const float4 *__restrict__ rec, cons
   cp_async_commit();
 }
 
-// Bit l of the result is set iff staged record l (l < cnt) has a pixel box
-// that meets this warp's 8x4 block of pixel centres [x0+0.5, x0+7.5] x
-// [y0+0.5, y0+3.5].
 __device__ __forceinline__ float2 unpack_box(float v) {
   const uint32_t u = __float_as_uint(v);
   return make_float2(__half2float(__ushort_as_half((unsigned short)(u & 0xffffu))),
                      __half2float(__ushort_as_half((unsigned short)(u >> 16))));
 }
 
-__device__ __forceinline__ uint32_t chunk_mask(const float4 *buf, int cnt, int lane, float bx0, float by0) {
+// Bit l of the result is set iff staged record l (l < cnt) has a pixel box
+// that meets this warp's 8x8 block of pixel centres [bx+0.5, bx+7.5] x
+// [by+0.5, by+7.5].
+__device__ __forceinline__ uint32_t chunk_mask(const float4 *buf, int cnt, int lane, float bx, float by) {
   bool hit = false;
   if (lane < cnt) {
     const float4 b = buf[lane * kRecF4 + 4];
-    const float2 bx = unpack_box(b.z), by = unpack_box(b.w);
-    hit = bx.x <= bx0 + 7.5f && bx.y >= bx0 + 0.5f && by.x <= by0 + 3.5f && by.y >= by0 + 0.5f;
+    const float2 x = unpack_box(b.z), y = unpack_box(b.w);
+    hit = x.x <= bx + 7.5f && x.y >= bx + 0.5f && y.x <= by + 7.5f && y.y >= by + 0.5f;
   }
   return __ballot_sync(0xffffffffu, hit);
 }
@@ -121,23 +123,78 @@ __device__ __forceinline__ uint32_t chunk_mask(const float4 *buf, int cnt, int l
 // ---------------------------------------------------------------------------
 // forward
 // ---------------------------------------------------------------------------
+struct FwdPix {
+  float px, py, T, C0, C1, C2, D, N0, N1, N2;
+  uint32_t last, nc;
+  bool inside, done;
+};
+
+// front-to-back blending of one contributor (Eq. 2), stopping before the
+// first one that would take T below T_min
+__device__ __forceinline__ void blend(FwdPix &s, const float4 *r, const float4 &r0, const float4 &r1,
+                                      const float4 &r2, const float4 &r4, const CfgK &cfg, uint32_t idx) {
+  if (s.done) return;
+  PairEval e;
+  if (!eval_pair(r0, r1, r2, r4, s.px, s.py, cfg, e)) return;
+  const float Tn = s.T * (1.0f - e.at);
+  if (Tn < cfg.T_min) {
+    s.done = true;
+    return;
+  }
+  const float w = e.at * s.T;
+  const float4 r3 = r[3];
+  s.C0 = fmaf(w, r2.z, s.C0);
+  s.C1 = fmaf(w, r2.w, s.C1);
+  s.C2 = fmaf(w, r3.x, s.C2);
+  s.D = fmaf(w, e.z, s.D);
+  s.N0 = fmaf(w, r3.y, s.N0);
+  s.N1 = fmaf(w, r3.z, s.N1);
+  s.N2 = fmaf(w, r3.w, s.N2);
+  s.T = Tn;
+  s.last = idx;
+  s.nc += 1u;
+}
+
+__device__ __forceinline__ void write_pix(const RenderArgs &a, const FwdPix &s) {
+  if (!s.inside) return;
+  const size_t HW = (size_t)a.cam.W * a.cam.H;
+  const size_t p = (size_t)(s.py - 0.5f) * a.cam.W + (size_t)(s.px - 0.5f);
+  a.rgb[p] = s.C0 + s.T * a.cfg.bg[0];
+  a.rgb[p + HW] = s.C1 + s.T * a.cfg.bg[1];
+  a.rgb[p + 2 * HW] = s.C2 + s.T * a.cfg.bg[2];
+  a.depth[p] = s.D;
+  a.normal[p] = s.N0;
+  a.normal[p + HW] = s.N1;
+  a.normal[p + 2 * HW] = s.N2;
+  a.alpha[p] = 1.0f - s.T;
+  a.T_final[p] = s.T;
+  a.n_last[p] = s.last;
+  if (a.n_contrib) a.n_contrib[p] = s.nc;
+}
+
 // One 16x16 tile: `tile` indexes the ranges, `local` is the tile within the
 // request's own grid (a.cam.TX columns).
 __device__ __forceinline__ void render_tile_fwd(const RenderArgs &a, int tile, int local,
                                                 float4 (*sm)[2][kCh * kRecF4]) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int pxi, pyi;
-  pixel_of(local, a.cam.TX, warp, lane, pxi, pyi);
-  const bool inside = pxi < a.cam.W && pyi < a.cam.H;
-  const float px = (float)pxi + 0.5f, py = (float)pyi + 0.5f;
-  const float wx0 = (float)((local % a.cam.TX) * kTile + (warp & 1) * 8);
-  const float wy0 = (float)((local / a.cam.TX) * kTile + (warp >> 1) * 4);
+  int bx, by;
+  block_of(local, a.cam.TX, warp, bx, by);
+  FwdPix s[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int x = bx + (lane & 7), y = by + (lane >> 3) + 4 * k;
+    s[k].px = (float)x + 0.5f;
+    s[k].py = (float)y + 0.5f;
+    s[k].inside = x < a.cam.W && y < a.cam.H;
+    s[k].done = !s[k].inside;
+    s[k].T = 1.0f;
+    s[k].C0 = s[k].C1 = s[k].C2 = s[k].D = s[k].N0 = s[k].N1 = s[k].N2 = 0.0f;
+    s[k].last = s[k].nc = 0u;
+  }
+  if (__all_sync(0xffffffffu, s[0].done && s[1].done)) return;
   const uint32_t start = a.ranges[2 * tile], end = a.ranges[2 * tile + 1];
   const float4 *rec = reinterpret_cast<const float4 *>(a.rec);
-  float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f, N0 = 0.f, N1 = 0.f, N2 = 0.f;
-  uint32_t last = 0, ncontrib = 0;
-  bool done = !inside;
-  if (__all_sync(0xffffffffu, done)) return;
+  const float fbx = (float)bx, fby = (float)by;
 
   if (start < end) stage_chunk(rec, a.vals, start, end, &sm[warp][0][0], nullptr, lane);
   int buf = 0;
@@ -150,52 +207,24 @@ __device__ __forceinline__ void render_tile_fwd(const RenderArgs &a, int tile, i
     }
     __syncwarp();
     const float4 *chunk = &sm[warp][buf][0];
-    uint32_t mask = chunk_mask(chunk, (int)min((uint32_t)kCh, end - base), lane, wx0, wy0);
+    uint32_t mask = chunk_mask(chunk, (int)min((uint32_t)kCh, end - base), lane, fbx, fby);
     while (mask) {
       const int j = __ffs(mask) - 1;
       mask &= mask - 1;
-      if (done) continue;
+      if (s[0].done && s[1].done) continue;
       const float4 *r = chunk + j * kRecF4;
       const float4 r0 = r[0], r1 = r[1], r2 = r[2], r4 = r[4];
-      PairEval e;
-      if (!eval_pair(r0, r1, r2, r4, px, py, a.cfg, e)) continue;
-      const float Tn = T * (1.0f - e.at);
-      if (Tn < a.cfg.T_min) {
-        done = true;
-        continue;
-      }
-      const float w = e.at * T;
-      const float4 r3 = r[3];
-      C0 = fmaf(w, r2.z, C0);
-      C1 = fmaf(w, r2.w, C1);
-      C2 = fmaf(w, r3.x, C2);
-      D = fmaf(w, e.z, D);
-      N0 = fmaf(w, r3.y, N0);
-      N1 = fmaf(w, r3.z, N1);
-      N2 = fmaf(w, r3.w, N2);
-      T = Tn;
-      last = base - start + (uint32_t)j + 1u;
-      ++ncontrib;
+      const uint32_t idx = base - start + (uint32_t)j + 1u;
+      blend(s[0], r, r0, r1, r2, r4, a.cfg, idx);
+      blend(s[1], r, r0, r1, r2, r4, a.cfg, idx);
     }
-    if (__all_sync(0xffffffffu, done)) break;
+    if (__all_sync(0xffffffffu, s[0].done && s[1].done)) break;
     __syncwarp();
     buf ^= 1;
   }
   cp_async_wait<0>();
-  if (!inside) return;
-  const size_t HW = (size_t)a.cam.W * a.cam.H;
-  const size_t p = (size_t)pyi * a.cam.W + pxi;
-  a.rgb[p] = C0 + T * a.cfg.bg[0];
-  a.rgb[p + HW] = C1 + T * a.cfg.bg[1];
-  a.rgb[p + 2 * HW] = C2 + T * a.cfg.bg[2];
-  a.depth[p] = D;
-  a.normal[p] = N0;
-  a.normal[p + HW] = N1;
-  a.normal[p + 2 * HW] = N2;
-  a.alpha[p] = 1.0f - T;
-  a.T_final[p] = T;
-  a.n_last[p] = last;
-  if (a.n_contrib) a.n_contrib[p] = ncontrib;
+  write_pix(a, s[0]);
+  write_pix(a, s[1]);
 }
 
 __global__ void __launch_bounds__(kRW * 32) render_fwd_kernel(RenderArgs a) {
@@ -252,37 +281,96 @@ __device__ __forceinline__ float warp_sum16(float (&v)[16], int lane, int &comp)
   return v[0];
 }
 
-__global__ void __launch_bounds__(kRW * 32) render_bwd_kernel(RenderBwdArgs a) {
+struct BwdPix {
+  float px, py, T;
+  uint32_t last;
+  float dC0, dC1, dC2, dD, dN0, dN1, dN2, dA;       // upstream gradient of the pixel
+  float ac0, ac1, ac2, az, an0, an1, an2, aa;       // everything behind, blended
+  bool inside;
+};
+
+__device__ __forceinline__ void load_bwd_pix(BwdPix &s, const RenderBwdArgs &a, int x, int y) {
+  s.px = (float)x + 0.5f;
+  s.py = (float)y + 0.5f;
+  s.inside = x < a.cam.W && y < a.cam.H;
+  s.T = 1.0f;
+  s.last = 0;
+  s.dC0 = s.dC1 = s.dC2 = s.dD = s.dN0 = s.dN1 = s.dN2 = s.dA = 0.f;
+  s.ac0 = a.cfg.bg[0]; s.ac1 = a.cfg.bg[1]; s.ac2 = a.cfg.bg[2];
+  s.az = s.an0 = s.an1 = s.an2 = s.aa = 0.f;
+  if (!s.inside) return;
+  const size_t HW = (size_t)a.cam.W * a.cam.H;
+  const size_t p = (size_t)y * a.cam.W + x;
+  s.T = a.T_final[p];
+  s.last = a.n_last[p];
+  if (a.g_rgb) { s.dC0 = a.g_rgb[p]; s.dC1 = a.g_rgb[p + HW]; s.dC2 = a.g_rgb[p + 2 * HW]; }
+  if (a.g_depth) s.dD = a.g_depth[p];
+  if (a.g_normal) { s.dN0 = a.g_normal[p]; s.dN1 = a.g_normal[p + HW]; s.dN2 = a.g_normal[p + 2 * HW]; }
+  if (a.g_alpha) s.dA = a.g_alpha[p];
+}
+
+// Add one contributing pair's gradient of the record (layout: common.cuh)
+// into g, recovering the transmittance in front of it by division and
+// updating the blended "behind" accumulators (reverse replay of Eq. 2).
+__device__ __forceinline__ void pair_grad(float (&g)[16], BwdPix &s, const PairEval &e, const float4 &r0,
+                                          const float4 &r1, const float4 &r2, const float4 &r3,
+                                          const CfgK &cfg) {
+  const float c0 = r2.z, c1 = r2.w, c2 = r3.x, n0 = r3.y, n1 = r3.z, n2 = r3.w;
+  const float Ti = __fdividef(s.T, 1.0f - e.at);
+  const float w = e.at * Ti;
+  const float fsum = (c0 - s.ac0) * s.dC0 + (c1 - s.ac1) * s.dC1 + (c2 - s.ac2) * s.dC2 +
+                     (e.z - s.az) * s.dD + (n0 - s.an0) * s.dN0 + (n1 - s.an1) * s.dN1 +
+                     (n2 - s.an2) * s.dN2 + (1.0f - s.aa) * s.dA;
+  const float dat = Ti * fsum;
+  s.ac0 += e.at * (c0 - s.ac0); s.ac1 += e.at * (c1 - s.ac1); s.ac2 += e.at * (c2 - s.ac2);
+  s.az += e.at * (e.z - s.az);
+  s.an0 += e.at * (n0 - s.an0); s.an1 += e.at * (n1 - s.an1); s.an2 += e.at * (n2 - s.an2);
+  s.aa += e.at * (1.0f - s.aa);
+  s.T = Ti;
+  g[1] += w * s.dC0; g[2] += w * s.dC1; g[3] += w * s.dC2;
+  g[13] += w * s.dN0; g[14] += w * s.dN1; g[15] += w * s.dN2;
+  const float dzp = w * s.dD;
+  float dd = 0.f;
+  if (e.araw <= cfg.alpha_max) {
+    g[0] += dat * e.g;
+    dd = dat * (-0.5f * e.at);
+  }
+  if (r0.w > 0.0f) {
+    // conic-space gradient: d = a dx^2 + 2 b dx dy + c dy^2
+    g[7] += dd * e.dx * e.dx;
+    g[8] += dd * 2.0f * e.dx * e.dy;
+    g[9] += dd * e.dy * e.dy;
+    g[4] -= dd * 2.0f * e.u * r1.x;
+    g[5] -= dd * 2.0f * (e.u * r1.y + e.v * r1.z);
+    g[6] += dzp;
+  } else {
+    const float du = 2.0f * e.u * dd, dv = 2.0f * e.v * dd;
+    const float dp0 = du * e.inv, dp1 = dv * e.inv;
+    const float dp2 = -(du * e.u + dv * e.v + dzp * e.z) * e.inv;
+    g[7] += dp0 * e.dx; g[8] += dp0 * e.dy;
+    g[9] += dp1 * e.dx; g[10] += dp1 * e.dy;
+    g[11] += dp2 * e.dx; g[12] += dp2 * e.dy;
+    g[4] -= dp0 * r1.x + dp1 * r1.z + dp2 * r2.x;
+    g[5] -= dp0 * r1.y + dp1 * r1.w + dp2 * r2.y;
+    g[6] += dzp * e.inv;
+  }
+}
+
+__global__ void __launch_bounds__(kRW * 32, 5) render_bwd_kernel(RenderBwdArgs a) {
   __shared__ __align__(16) float4 sm[kRW][2][kCh * kRecF4];
   __shared__ uint32_t sid[kRW][2][kCh];
   const int tile = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int pxi, pyi;
-  pixel_of(tile, a.cam.TX, warp, lane, pxi, pyi);
-  const bool inside = pxi < a.cam.W && pyi < a.cam.H;
-  const float px = (float)pxi + 0.5f, py = (float)pyi + 0.5f;
-  const float wx0 = (float)((tile % a.cam.TX) * kTile + (warp & 1) * 8);
-  const float wy0 = (float)((tile / a.cam.TX) * kTile + (warp >> 1) * 4);
+  int bx, by;
+  block_of(tile, a.cam.TX, warp, bx, by);
+  BwdPix s[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) load_bwd_pix(s[k], a, bx + (lane & 7), by + (lane >> 3) + 4 * k);
   const uint32_t start = a.ranges[2 * tile];
-  const size_t HW = (size_t)a.cam.W * a.cam.H;
-  const size_t p = inside ? (size_t)pyi * a.cam.W + pxi : 0;
-  float T = 1.0f;
-  uint32_t last = 0;
-  float dC0 = 0.f, dC1 = 0.f, dC2 = 0.f, dD = 0.f, dN0 = 0.f, dN1 = 0.f, dN2 = 0.f, dA = 0.f;
-  if (inside) {
-    T = a.T_final[p];
-    last = a.n_last[p];
-    if (a.g_rgb) { dC0 = a.g_rgb[p]; dC1 = a.g_rgb[p + HW]; dC2 = a.g_rgb[p + 2 * HW]; }
-    if (a.g_depth) dD = a.g_depth[p];
-    if (a.g_normal) { dN0 = a.g_normal[p]; dN1 = a.g_normal[p + HW]; dN2 = a.g_normal[p + 2 * HW]; }
-    if (a.g_alpha) dA = a.g_alpha[p];
-  }
-  // accumulated colour / depth / normal / alpha of everything behind
-  float ac0 = a.cfg.bg[0], ac1 = a.cfg.bg[1], ac2 = a.cfg.bg[2];
-  float az = 0.f, an0 = 0.f, an1 = 0.f, an2 = 0.f, aa = 0.f;
-  const uint32_t wmax = __reduce_max_sync(0xffffffffu, last);
+  const uint32_t wmax = __reduce_max_sync(0xffffffffu, max(s[0].last, s[1].last));
   if (wmax == 0) return;
   const float4 *rec = reinterpret_cast<const float4 *>(a.rec);
+  const float fbx = (float)bx, fby = (float)by;
 
   uint32_t ce = start + wmax;
   uint32_t cs = ce - min((uint32_t)kCh, wmax);
@@ -299,64 +387,26 @@ __global__ void __launch_bounds__(kRW * 32) render_bwd_kernel(RenderBwdArgs a) {
     }
     __syncwarp();
     const float4 *chunk = &sm[warp][buf][0];
-    uint32_t mask = chunk_mask(chunk, (int)(ce - cs), lane, wx0, wy0);
+    uint32_t mask = chunk_mask(chunk, (int)(ce - cs), lane, fbx, fby);
     while (mask) {
       const int jj = 31 - __clz(mask);
       mask &= ~(1u << jj);
-      const uint32_t j = cs + (uint32_t)jj;
+      const uint32_t jrel = cs + (uint32_t)jj - start;
       const float4 *r = chunk + jj * kRecF4;
       const float4 r0 = r[0], r1 = r[1], r2 = r[2], r4 = r[4];
-      PairEval e;
-      const bool contrib = inside && (j - start) < last && eval_pair(r0, r1, r2, r4, px, py, a.cfg, e);
-      if (!__any_sync(0xffffffffu, contrib)) continue;
+      PairEval e0, e1;
+      const bool c0 = s[0].inside && jrel < s[0].last && eval_pair(r0, r1, r2, r4, s[0].px, s[0].py, a.cfg, e0);
+      const bool c1 = s[1].inside && jrel < s[1].last && eval_pair(r0, r1, r2, r4, s[1].px, s[1].py, a.cfg, e1);
+      if (!__any_sync(0xffffffffu, c0 || c1)) continue;
       float g[16];
 #pragma unroll
       for (int k = 0; k < 16; ++k) g[k] = 0.f;
-      if (contrib) {
-        const float4 r3 = r[3];
-        const float c0 = r2.z, c1 = r2.w, c2 = r3.x, n0 = r3.y, n1 = r3.z, n2 = r3.w;
-        const float om = 1.0f - e.at;
-        const float Ti = __fdividef(T, om);
-        const float w = e.at * Ti;
-        const float fsum = (c0 - ac0) * dC0 + (c1 - ac1) * dC1 + (c2 - ac2) * dC2 + (e.z - az) * dD +
-                           (n0 - an0) * dN0 + (n1 - an1) * dN1 + (n2 - an2) * dN2 + (1.0f - aa) * dA;
-        const float dat = Ti * fsum;
-        ac0 += e.at * (c0 - ac0); ac1 += e.at * (c1 - ac1); ac2 += e.at * (c2 - ac2);
-        az += e.at * (e.z - az);
-        an0 += e.at * (n0 - an0); an1 += e.at * (n1 - an1); an2 += e.at * (n2 - an2);
-        aa += e.at * (1.0f - aa);
-        T = Ti;
-        g[1] = w * dC0; g[2] = w * dC1; g[3] = w * dC2;
-        g[13] = w * dN0; g[14] = w * dN1; g[15] = w * dN2;
-        const float dzp = w * dD;
-        float dd = 0.f;
-        if (e.araw <= a.cfg.alpha_max) {
-          g[0] = dat * e.g;
-          dd = dat * (-0.5f * e.at);
-        }
-        if (r0.w > 0.0f) {
-          // conic-space gradient: d = a dx^2 + 2 b dx dy + c dy^2
-          g[7] = dd * e.dx * e.dx;
-          g[8] = dd * 2.0f * e.dx * e.dy;
-          g[9] = dd * e.dy * e.dy;
-          const float ddx = dd * 2.0f * e.u * r1.x;
-          const float ddy = dd * 2.0f * (e.u * r1.y + e.v * r1.z);
-          g[4] = -ddx; g[5] = -ddy; g[6] = dzp;
-        } else {
-          const float du = 2.0f * e.u * dd, dv = 2.0f * e.v * dd;
-          const float dp0 = du * e.inv, dp1 = dv * e.inv;
-          const float dp2 = -(du * e.u + dv * e.v + dzp * e.z) * e.inv;
-          g[7] = dp0 * e.dx; g[8] = dp0 * e.dy;
-          g[9] = dp1 * e.dx; g[10] = dp1 * e.dy;
-          g[11] = dp2 * e.dx; g[12] = dp2 * e.dy;
-          const float ddx = dp0 * r1.x + dp1 * r1.z + dp2 * r2.x;
-          const float ddy = dp0 * r1.y + dp1 * r1.w + dp2 * r2.y;
-          g[4] = -ddx; g[5] = -ddy; g[6] = dzp * e.inv;
-        }
-      }
+      const float4 r3 = r[3];
+      if (c0) pair_grad(g, s[0], e0, r0, r1, r2, r3, a.cfg);
+      if (c1) pair_grad(g, s[1], e1, r0, r1, r2, r3, a.cfg);
       int comp;
-      const float s = warp_sum16(g, lane, comp);
-      if ((lane & 1) == 0) atomicAdd(a.rec_grad + (size_t)sid[warp][buf][jj] * kGradW + comp, s);
+      const float v = warp_sum16(g, lane, comp);
+      if ((lane & 1) == 0) atomicAdd(a.rec_grad + (size_t)sid[warp][buf][jj] * kGradW + comp, v);
     }
     if (!has_next) break;
     __syncwarp();
