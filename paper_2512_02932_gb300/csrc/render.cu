@@ -107,15 +107,100 @@ __device__ __forceinline__ float2 unpack_box(float v) {
                      __half2float(__ushort_as_half((unsigned short)(u >> 16))));
 }
 
+// Squared distance from the origin to the segment P -> P + E (FP32; used
+// only with a margin, see block_may_hit).
+__device__ __forceinline__ float seg_dist2(float px, float py, float ex, float ey) {
+  const float l2 = fmaf(ex, ex, ey * ey);
+  const float t = fminf(fmaxf(-fmaf(px, ex, py * ey) * rcp_approx(l2), 0.0f), 1.0f);
+  const float qx = fmaf(t, ex, px), qy = fmaf(t, ey, py);
+  return fmaf(qx, qx, qy * qy);
+}
+
+// Can the record contribute to any pixel centre of the 8x8 block whose first
+// centre is (bx + 0.5, by + 0.5)?  A pair contributes only if its distance d
+// (Eq. 1) satisfies alpha * exp(-d/2) >= alpha_min, i.e. d <= 2 ln(alpha /
+// alpha_min).  The test bounds d from below over the whole rectangle of the
+// block's centres and keeps the record unless that bound exceeds the limit
+// by a margin far above the FP32 error of either side, so it never drops a
+// pair that eval_pair would accept and the rendered result is unchanged.
+//  * 3D: d = u^2 + v^2 with u = W00 X + W01 Y, v = W11 Y (X, Y offsets from
+//    the centre).  For fixed Y the minimum of u^2 over X in [x0, x1] is
+//    max(a, -b, 0)^2 with a = W01 Y + W00 x0, b = W01 Y + W00 x1; the
+//    resulting function of Y is convex, so its minimum over [y0, y1] is at
+//    the clamp of whichever of its three piecewise minimisers (Y = 0 and the
+//    two affine pieces' vertices) is global, and the least of the three
+//    clamped values is exact.
+//  * 2D: (u, v) = (p0, p1) / p2 with p = Q (X, Y, 1) (Eq. 14).  Where p2 > 0
+//    over the rectangle the map is projective, so the rectangle goes to the
+//    convex quadrilateral of its corners' images and the pixels' (u, v) lie
+//    inside it; the block can be hit only if that quadrilateral meets the
+//    disc u^2 + v^2 <= limit.  Corners behind the camera, or mapped too far
+//    for FP32 to place the edges precisely, keep the record.
+__device__ __forceinline__ bool block_may_hit(const float4 &r0, const float4 &r1, const float4 &r2,
+                                              const float4 &r4, float bx, float by, const CfgK &f) {
+  const float x0 = ((bx + 0.5f) - r0.x) - r4.x, y0 = ((by + 0.5f) - r0.y) - r4.y;
+  const float x1 = x0 + 7.0f, y1 = y0 + 7.0f;
+  const float ratio = __fdividef(fabsf(r0.w), f.alpha_min);
+  if (!(ratio > 1.0f)) return false;  // alpha below alpha_min: never contributes
+  const float lim = fmaf(2.0f * __logf(ratio), 1.001f, 0.05f);
+  if (r0.w > 0.0f) {
+    const float W00 = r1.x, W01 = r1.y, W11 = r1.z;
+    const float C = fmaf(W01, W01, W11 * W11);
+    const float k = -W01 * W00 * rcp_approx(C);
+    const float c0 = fminf(fmaxf(0.0f, y0), y1);
+    const float ca = fminf(fmaxf(k * x0, y0), y1);
+    const float cb = fminf(fmaxf(k * x1, y0), y1);
+    float dmin = 3.0e38f;
+    const float ys[3] = {c0, ca, cb};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const float Y = ys[i];
+      const float a = fmaf(W01, Y, W00 * x0), b = fmaf(W01, Y, W00 * x1);
+      const float m = fmaxf(fmaxf(a, -b), 0.0f);
+      const float v = W11 * Y;
+      dmin = fminf(dmin, fmaf(m, m, v * v));
+    }
+    return !(dmin > lim);
+  }
+  float u[4], v[4];
+  const float xs[4] = {x0, x1, x1, x0}, yy[4] = {y0, y0, y1, y1};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float p0 = fmaf(r1.x, xs[i], r1.y * yy[i]);
+    const float p1 = fmaf(r1.z, xs[i], r1.w * yy[i]);
+    const float p2 = fmaf(r2.x, xs[i], fmaf(r2.y, yy[i], 1.0f));
+    if (!(p2 > 0.0f)) return true;
+    const float inv = rcp_approx(p2);
+    u[i] = p0 * inv;
+    v[i] = p1 * inv;
+    if (!(fabsf(u[i]) < 1024.0f && fabsf(v[i]) < 1024.0f)) return true;
+  }
+  bool pos = true, neg = true;
+  float dmin = 3.0e38f;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int j = (i + 1) & 3;
+    const float ex = u[j] - u[i], ey = v[j] - v[i];
+    const float c = fmaf(ey, u[i], -ex * v[i]);
+    pos = pos && c >= 0.0f;
+    neg = neg && c <= 0.0f;
+    dmin = fminf(dmin, seg_dist2(u[i], v[i], ex, ey));
+  }
+  return pos || neg || !(dmin > lim);
+}
+
 // Bit l of the result is set iff staged record l (l < cnt) has a pixel box
 // that meets this warp's 8x8 block of pixel centres [bx+0.5, bx+7.5] x
-// [by+0.5, by+7.5].
-__device__ __forceinline__ uint32_t chunk_mask(const float4 *buf, int cnt, int lane, float bx, float by) {
+// [by+0.5, by+7.5] and passes block_may_hit.
+__device__ __forceinline__ uint32_t chunk_mask(const float4 *buf, int cnt, int lane, float bx, float by,
+                                               const CfgK &f) {
   bool hit = false;
   if (lane < cnt) {
-    const float4 b = buf[lane * kRecF4 + 4];
+    const float4 *r = buf + lane * kRecF4;
+    const float4 b = r[4];
     const float2 x = unpack_box(b.z), y = unpack_box(b.w);
     hit = x.x <= bx + 7.5f && x.y >= bx + 0.5f && y.x <= by + 7.5f && y.y >= by + 0.5f;
+    if (hit) hit = block_may_hit(r[0], r[1], r[2], b, bx, by, f);
   }
   return __ballot_sync(0xffffffffu, hit);
 }
@@ -207,7 +292,7 @@ __device__ __forceinline__ void render_tile_fwd(const RenderArgs &a, int tile, i
     }
     __syncwarp();
     const float4 *chunk = &sm[warp][buf][0];
-    uint32_t mask = chunk_mask(chunk, (int)min((uint32_t)kCh, end - base), lane, fbx, fby);
+    uint32_t mask = chunk_mask(chunk, (int)min((uint32_t)kCh, end - base), lane, fbx, fby, a.cfg);
     while (mask) {
       const int j = __ffs(mask) - 1;
       mask &= mask - 1;
@@ -387,7 +472,7 @@ __global__ void __launch_bounds__(kRW * 32, 5) render_bwd_kernel(RenderBwdArgs a
     }
     __syncwarp();
     const float4 *chunk = &sm[warp][buf][0];
-    uint32_t mask = chunk_mask(chunk, (int)(ce - cs), lane, fbx, fby);
+    uint32_t mask = chunk_mask(chunk, (int)(ce - cs), lane, fbx, fby, a.cfg);
     while (mask) {
       const int jj = 31 - __clz(mask);
       mask &= ~(1u << jj);
