@@ -227,7 +227,9 @@ def launches_per_step(rast, exchange_steps, steps):
     tiles = rast.ranges.shape[0]
     tile_bits = max(1, math.ceil(math.log2(tiles))) if tiles > 1 else 1
     passes = (tile_bits + 7) // 8
-    bin_sort = 3 * (4 + passes) + 3 + 2 + 1 + (1 if rast.keys is not None else 0)
+    # depth histogram + 4 depth passes, offsets scan (3), emit (2), tile
+    # histogram + tile passes, range fix-up, optional 64-bit keys
+    bin_sort = 1 + 4 + 3 + 2 + 1 + passes + 1 + (1 if rast.keys is not None else 0)
     per = 1 + bin_sort + 1 + 2
     return per * steps + exchange_steps
 

@@ -41,13 +41,16 @@ int launch_preprocess_bwd(const PrepArgs &a, const PrepGradArgs &g, int deg, cud
 // ---------------------------------------------------------------------------
 struct BinWorkspace {
   // carved from the caller's workspace by bin_layout()
-  uint32_t *hist;        // [256 * kSortBlocks]
+  int64_t *counters;     // [16]: 0 = n_visible, 1 = K, 2 = overflow flag, 3 = deferred rects
+  uint32_t *tile_ctr;    // [16] tile counters of the look-back passes
+  uint32_t *hist;        // [8][256] global digit histograms (4 depth + up to 4 tile passes)
+  size_t head_bytes;     // counters .. hist, cleared at the start of every sort
   uint64_t *blk;         // [kSortBlocks] scan partials
-  int64_t *counters;     // [8]: 0 = n_visible, 1 = K, 2 = overflow flag
   uint32_t *dk[2], *dv[2];  // depth sort ping-pong, [n] each
   uint32_t *offs;        // [n] instance offsets in depth order
   uint32_t *tk[2];       // tile keys ping-pong, [capacity]
   uint32_t *tv;          // tile vals scratch, [capacity]
+  uint64_t *status[2];   // look-back status words, ping-pong between passes
   size_t bytes;
 };
 
