@@ -47,9 +47,7 @@ size_t bin_layout(void *base, int64_t n, int64_t capacity, BinWorkspace *ws) {
   ws->tk[0] = (uint32_t *)take(sizeof(uint32_t) * cc);
   ws->tk[1] = (uint32_t *)take(sizeof(uint32_t) * cc);
   ws->tv = (uint32_t *)take(sizeof(uint32_t) * cc);
-  // look-back status words: one per (2048-key tile, digit) of the larger sort
-  const size_t tiles = (std::max(nn, cc) + kTileElems - 1) / kTileElems;
-  for (int k = 0; k < 2; ++k) ws->status[k] = (uint64_t *)take(sizeof(uint64_t) * 256 * tiles);
+  ws->chist = (uint32_t *)take(sizeof(uint32_t) * 256 * kSortBlocks);
   ws->bytes = off;
   return off;
 }
@@ -73,298 +71,331 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 }
 
 // ---------------------------------------------------------------------------
-// global digit histograms of up to four passes in one read of the keys
+// histogram helpers
 // ---------------------------------------------------------------------------
-struct DigitSpec {
-  int npass;
-  int shift[4], bits[4];
-};
-
-struct HistArgs {
-  const uint32_t *keys, *valid;  // valid: optional 0/1 filter
-  const int64_t *d_n;            // element count on the device, or null: n_host
-  int64_t n_host;
-  const int64_t *d_abort;        // optional: nonzero -> no elements
-  DigitSpec sp;
-  uint32_t *hist;                // [npass][256], zero on entry
-  uint64_t *status0;             // status words of the first pass, zeroed here
-  int radix0;
-  uint32_t *ranges;              // optional: set to (0xffffffff, 0) for `tiles`
-  int tiles;
-};
-
-__device__ __forceinline__ int64_t hist_n(const HistArgs &a) {
-  if (a.d_abort && *a.d_abort) return 0;
-  return a.d_n ? *a.d_n : a.n_host;
-}
-
-// Counts runs of equal digits in a thread's four consecutive keys with one
-// shared atomic per run.
-__global__ void __launch_bounds__(256) k_digit_hist(HistArgs a) {
-  __shared__ uint32_t h[4][256];
-  const int tid = threadIdx.x;
-  for (int k = tid; k < 4 * 256; k += 256) (&h[0][0])[k] = 0u;
-  const int64_t n = hist_n(a);
-  const int64_t gthreads = (int64_t)gridDim.x * blockDim.x, gid = (int64_t)blockIdx.x * blockDim.x + tid;
-  {
-    const int64_t zs = (n + kTileElems - 1) / kTileElems * a.radix0;
-    for (int64_t k = gid; k < zs; k += gthreads) a.status0[k] = 0ull;
-    if (a.ranges)
-      for (int64_t k = gid; k < a.tiles; k += gthreads)
-        reinterpret_cast<uint2 *>(a.ranges)[k] = make_uint2(0xffffffffu, 0u);
-  }
-  __syncthreads();
-  const bool vec = ((reinterpret_cast<uintptr_t>(a.keys) | reinterpret_cast<uintptr_t>(a.valid)) & 15u) == 0;
-  for (int64_t e = gid * 4; e < n; e += gthreads * 4) {
-    uint32_t k[4], v[4];
-    if (vec && e + 4 <= n) {
-      const uint4 kk = __ldg(reinterpret_cast<const uint4 *>(a.keys + e));
-      k[0] = kk.x; k[1] = kk.y; k[2] = kk.z; k[3] = kk.w;
-      if (a.valid) {
-        const uint4 vv = __ldg(reinterpret_cast<const uint4 *>(a.valid + e));
-        v[0] = vv.x != 0u; v[1] = vv.y != 0u; v[2] = vv.z != 0u; v[3] = vv.w != 0u;
-      } else {
-        v[0] = v[1] = v[2] = v[3] = 1u;
-      }
+// Four consecutive keys (and 0/1 validity) starting at e; elements at or past
+// `end` are invalid.  `vec`: keys and valid are 16-byte aligned.
+__device__ __forceinline__ void load4(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ valid,
+                                      int64_t e, int64_t end, bool vec, uint32_t (&k)[4], uint32_t (&v)[4]) {
+  if (vec && e + 4 <= end) {
+    const uint4 kk = __ldg(reinterpret_cast<const uint4 *>(keys + e));
+    k[0] = kk.x; k[1] = kk.y; k[2] = kk.z; k[3] = kk.w;
+    if (valid) {
+      const uint4 vv = __ldg(reinterpret_cast<const uint4 *>(valid + e));
+      v[0] = vv.x != 0u; v[1] = vv.y != 0u; v[2] = vv.z != 0u; v[3] = vv.w != 0u;
     } else {
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const bool in = e + i < n;
-        k[i] = in ? __ldg(a.keys + e + i) : 0u;
-        v[i] = in && (!a.valid || __ldg(a.valid + e + i) != 0u) ? 1u : 0u;
-      }
+      v[0] = v[1] = v[2] = v[3] = 1u;
     }
+  } else {
 #pragma unroll
-    for (int p = 0; p < 4; ++p) {
-      if (p >= a.sp.npass) break;
-      const int sh = a.sp.shift[p];
-      const uint32_t m = (1u << a.sp.bits[p]) - 1u;
-      uint32_t dp = (k[0] >> sh) & m, c = v[0];
-#pragma unroll
-      for (int i = 1; i < 4; ++i) {
-        const uint32_t d = (k[i] >> sh) & m;
-        if (d != dp) {
-          if (c) atomicAdd(&h[p][dp], c);
-          dp = d;
-          c = 0u;
-        }
-        c += v[i];
-      }
-      if (c) atomicAdd(&h[p][dp], c);
+    for (int i = 0; i < 4; ++i) {
+      const bool in = e + i < end;
+      k[i] = in ? __ldg(keys + e + i) : 0u;
+      v[i] = in && (!valid || __ldg(valid + e + i) != 0u) ? 1u : 0u;
     }
   }
-  __syncthreads();
+}
+
+// Add four keys' digits to a shared histogram, one atomic per run of equal
+// digits (runs are common: a primitive's instances share tile rows).
+__device__ __forceinline__ void count_runs(uint32_t *h, const uint32_t (&k)[4], const uint32_t (&v)[4],
+                                           int shift, uint32_t mask) {
+  uint32_t dp = (k[0] >> shift) & mask, c = v[0];
 #pragma unroll
-  for (int p = 0; p < 4; ++p)
-    if (p < a.sp.npass && tid < (1 << a.sp.bits[p]) && h[p][tid]) atomicAdd(&a.hist[p * 256 + tid], h[p][tid]);
+  for (int i = 1; i < 4; ++i) {
+    const uint32_t d = (k[i] >> shift) & mask;
+    if (d != dp) {
+      if (c) atomicAdd(&h[dp], c);
+      dp = d;
+      c = 0u;
+    }
+    c += v[i];
+  }
+  if (c) atomicAdd(&h[dp], c);
 }
 
 // ---------------------------------------------------------------------------
-// one stable radix pass with decoupled look-back (single sweep over the data)
+// one stable radix pass: chunk histograms, their scan, and the scatter
 // ---------------------------------------------------------------------------
-// Tiles of 2048 keys are claimed in order through an atomic counter.  A tile
-// ranks its keys (warp-local match + per-warp digit counters), publishes its
-// per-digit counts, then walks back over earlier tiles' published words,
-// adding counts until it meets a tile that already published its inclusive
-// prefix; it then publishes its own.  Status word: flag in the top two bits
-// (1 = this tile's count, 2 = inclusive prefix), value below.  A tile never
-// waits for anything before publishing its count, and every earlier tile was
-// claimed by a running block, so the walk always ends; it is nevertheless
-// bounded, and a wait that runs out reports HGS_ERR_TIMEOUT and carries on
-// with what it has (writes stay in bounds).
-constexpr uint64_t kFlagCount = 1ull << 62, kFlagPrefix = 2ull << 62, kValueMask = (1ull << 62) - 1ull;
-constexpr int kSpinLimit = 1 << 22;
-
-__device__ __forceinline__ uint64_t ld_relaxed(const uint64_t *p) {
-  uint64_t v;
-  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_relaxed(uint64_t *p, uint64_t v) {
-  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
-struct SweepArgs {
+// The keys are cut into G contiguous chunks of whole 2048-key tiles, one per
+// block of a grid that fits on the device at once.  k_chunk_hist counts each
+// chunk's digits (and adds them to the pass's global histogram),
+// k_chunk_scan turns the counts into each chunk's first output position per
+// digit (digit base from the global histogram plus the counts of earlier
+// chunks), and k_scatter walks its chunk tile by tile in order, so no block
+// ever waits for another.
+struct PassArgs {
   const uint32_t *keys_in, *vals_in;  // vals_in null: the value is the index
   const uint32_t *valid;              // optional 0/1 filter (compacting pass)
   const int64_t *d_n;                 // input count on the device, or null: n_host
   int64_t n_host;
   const int64_t *d_abort;
   int shift, bits;
-  const uint32_t *ghist;              // this pass's global digit histogram [256]
-  uint64_t *status;                   // [tiles << bits], zero on entry
-  uint64_t *status_next;              // optional: zeroed for the next pass
-  int next_radix;
-  uint32_t *tile_ctr;                 // zero on entry
+  uint32_t *ghist;                    // [256] this pass's global digit histogram, zero on entry
+  uint32_t *chist;                    // [256][kMaxChunks] chunk counts -> chunk offsets
+  uint32_t *ranges_init;              // optional: set to (0xffffffff, 0) for `tiles` tiles
+  int tiles;
   uint32_t *keys_out, *vals_out;      // keys_out optional
   uint32_t *ranges;                   // optional (last tile pass): [start, end) per key
   int64_t *count_out;                 // optional: number of elements written
-  int32_t *dev_err;
+};
+constexpr int kMaxChunks = kSortBlocks;
+
+__device__ __forceinline__ int64_t pass_n(const PassArgs &a) {
+  if (a.d_abort && *a.d_abort) return 0;
+  return a.d_n ? *a.d_n : a.n_host;
+}
+
+// tiles [t0, t1) of this block's chunk
+__device__ __forceinline__ void chunk_tiles(int64_t n, int64_t &t0, int64_t &t1) {
+  const int64_t ntiles = (n + kTileElems - 1) / kTileElems;
+  const int64_t per = (ntiles + gridDim.x - 1) / gridDim.x;
+  t0 = min(ntiles, (int64_t)blockIdx.x * per);
+  t1 = min(ntiles, t0 + per);
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_chunk_hist(PassArgs a) {
+  constexpr int W = kSortThreads / 32;
+  __shared__ uint32_t h[W][256];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int k = tid; k < W * 256; k += kSortThreads) (&h[0][0])[k] = 0u;
+  __syncthreads();
+  const int64_t n = pass_n(a);
+  if (a.ranges_init)
+    for (int t = blockIdx.x * blockDim.x + tid; t < a.tiles; t += gridDim.x * blockDim.x)
+      reinterpret_cast<uint2 *>(a.ranges_init)[t] = make_uint2(0xffffffffu, 0u);
+  int64_t t0, t1;
+  chunk_tiles(n, t0, t1);
+  const int64_t e0 = t0 * kTileElems, e1 = min(n, t1 * kTileElems);
+  const uint32_t mask = (1u << a.bits) - 1u;
+  const bool vec = ((reinterpret_cast<uintptr_t>(a.keys_in) | reinterpret_cast<uintptr_t>(a.valid)) & 15u) == 0;
+  for (int64_t e = e0 + tid * 4; e < e1; e += kSortThreads * 16) {
+    uint32_t k[4][4], v[4][4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) load4(a.keys_in, a.valid, e + j * kSortThreads * 4, e1, vec, k[j], v[j]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) count_runs(h[warp], k[j], v[j], a.shift, mask);
+  }
+  __syncthreads();
+  if (tid < (1 << a.bits)) {
+    uint32_t c = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) c += h[w][tid];
+    a.chist[(size_t)tid * kMaxChunks + blockIdx.x] = c;
+    if (c) atomicAdd(a.ghist + tid, c);
+  }
+}
+
+// one block per digit: chunk offsets = digit base + counts of earlier chunks
+__global__ void __launch_bounds__(256) k_chunk_scan(PassArgs a, int nchunks) {
+  __shared__ uint32_t wsum[8];
+  __shared__ uint32_t s_base;
+  const int d = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  {
+    uint32_t v = tid < d ? __ldg(a.ghist + tid) : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) wsum[warp] = v;
+    __syncthreads();
+    if (tid == 0) {
+      uint32_t t = 0;
+      for (int w = 0; w < 8; ++w) t += wsum[w];
+      s_base = t;
+    }
+    __syncthreads();
+  }
+  uint32_t *row = a.chist + (size_t)d * kMaxChunks;
+  const int per = (nchunks + 255) / 256;
+  uint32_t loc[kMaxChunks / 256];
+  uint32_t sum = 0;
+#pragma unroll
+  for (int k = 0; k < kMaxChunks / 256; ++k) {
+    const int idx = tid * per + k;
+    loc[k] = (k < per && idx < nchunks) ? row[idx] : 0u;
+    sum += loc[k];
+  }
+  uint32_t incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  __syncthreads();
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  uint32_t run = s_base;
+  for (int w = 0; w < warp; ++w) run += wsum[w];
+  run += incl - sum;
+#pragma unroll
+  for (int k = 0; k < kMaxChunks / 256; ++k) {
+    const int idx = tid * per + k;
+    if (k < per && idx < nchunks) row[idx] = run;
+    run += loc[k];
+  }
+}
+
+// Raw tiles are prefetched one ahead into shared memory with cp.async; the
+// buffer of the tile being ranked is reused to stage it in digit order.
+struct alignas(16) ScatterSmem {
+  uint32_t raw_k[2][kTileElems], raw_v[2][kTileElems];
+  uint32_t wcnt[kSortThreads / 32][256];
+  uint32_t tdig[256];
+  uint32_t base[2][256];
+  uint32_t scan_tmp[kSortThreads / 32];
+  uint32_t tile_count;
 };
 
-__global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(SweepArgs a) {
+__device__ __forceinline__ void cp_async16g(void *smem, const void *gmem) {
+  const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Copy tile `t` (elements [t*2048, min(n, t*2048+2048))) into buffer b.
+__device__ __forceinline__ void fetch_tile(const PassArgs &a, ScatterSmem &sm, int b, int64_t t, int64_t n,
+                                           bool vec, int tid) {
+  const int64_t e0 = t * kTileElems;
+  const int cnt = (int)min((int64_t)kTileElems, n - e0);
+  if (vec && cnt == kTileElems) {
+#pragma unroll
+    for (int k = 0; k < kTileElems / 4 / kSortThreads; ++k) {
+      const int q = (k * kSortThreads + tid) * 4;
+      cp_async16g(&sm.raw_k[b][q], a.keys_in + e0 + q);
+      if (a.vals_in) cp_async16g(&sm.raw_v[b][q], a.vals_in + e0 + q);
+    }
+  } else {
+    for (int q = tid; q < cnt; q += kSortThreads) {
+      sm.raw_k[b][q] = __ldg(a.keys_in + e0 + q);
+      if (a.vals_in) sm.raw_v[b][q] = __ldg(a.vals_in + e0 + q);
+    }
+  }
+  cp_commit();
+}
+
+template <int BITS>
+__global__ void __launch_bounds__(kSortThreads) k_scatter(PassArgs a) {
   constexpr int W = kSortThreads / 32;
-  __shared__ uint32_t wcnt[W][256];
-  __shared__ uint32_t tdig[256];       // tile-local exclusive start of each digit
-  __shared__ uint64_t gbase[256];      // global start of each digit in the output
-  __shared__ uint64_t gpos[256];       // global start of this tile's run of each digit
-  __shared__ uint32_t scan_tmp[W];
-  __shared__ uint32_t stage_k[kTileElems], stage_v[kTileElems];
-  __shared__ uint32_t s_tile, s_count;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ScatterSmem &sm = *reinterpret_cast<ScatterSmem *>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const bool aborted = a.d_abort && *a.d_abort;
-  const int64_t n = aborted ? 0 : (a.d_n ? *a.d_n : a.n_host);
-  const int64_t ntiles = (n + kTileElems - 1) / kTileElems;
-  const int R = 1 << a.bits;
-  const uint32_t mask = (uint32_t)R - 1u;
-  if (a.status_next) {
-    const int64_t zs = ntiles * a.next_radix;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + tid; k < zs; k += (int64_t)gridDim.x * blockDim.x)
-      a.status_next[k] = 0ull;
+  const int64_t n = pass_n(a);
+  int64_t t0, t1;
+  chunk_tiles(n, t0, t1);
+  constexpr int R = 1 << BITS;
+  constexpr uint32_t mask = (uint32_t)R - 1u;
+  if (a.count_out && blockIdx.x == 0 && tid == 0) {
+    uint64_t all = 0;
+    for (int d = 0; d < R; ++d) all += a.ghist[d];
+    *a.count_out = (a.d_abort && *a.d_abort) ? 0 : (int64_t)all;
   }
-  // exclusive scan of the global histogram: where each digit starts
-  uint64_t n_out;
-  {
-    const uint32_t t = tid < R ? __ldg(a.ghist + tid) : 0u;
-    uint32_t incl = t;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += v;
-    }
-    if (lane == 31) scan_tmp[warp] = incl;
-    __syncthreads();
-    uint64_t wb = 0, all = 0;
-#pragma unroll
-    for (int w = 0; w < W; ++w) {
-      if (w < warp) wb += scan_tmp[w];
-      all += scan_tmp[w];
-    }
-    gbase[tid] = wb + incl - t;
-    n_out = aborted ? 0 : all;
-    if (a.count_out && blockIdx.x == 0 && tid == 0) *a.count_out = (int64_t)n_out;
-  }
+  if (t0 >= t1) return;
+  const bool vec = ((reinterpret_cast<uintptr_t>(a.keys_in) | reinterpret_cast<uintptr_t>(a.vals_in)) & 15u) == 0;
+  sm.base[0][tid] = tid < R ? a.chist[(size_t)tid * kMaxChunks + blockIdx.x] : 0u;
+  fetch_tile(a, sm, 0, t0, n, vec, tid);
   const uint32_t lt = lanemask_lt();
-  while (true) {
-    if (tid == 0) s_tile = atomicAdd(a.tile_ctr, 1u);
+  int cb = 0;
+  for (int64_t t = t0; t < t1; ++t) {
+    const int b = (int)((t - t0) & 1);
+    cp_wait_all();
     __syncthreads();
-    const int64_t tile = s_tile;
-    if (tile >= ntiles) break;
-    const int64_t tb = tile * kTileElems;
+    if (t + 1 < t1) fetch_tile(a, sm, b ^ 1, t + 1, n, vec, tid);
+    const int64_t e0 = t * kTileElems;
     uint32_t key[kSortItems], val[kSortItems], dig[kSortItems];
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
-      const int64_t e = tb + warp * (32 * kSortItems) + r * 32 + lane;
+      const int q = warp * (32 * kSortItems) + r * 32 + lane;
+      const int64_t e = e0 + q;
       dig[r] = kNoDigit;
-      key[r] = 0u;
-      val[r] = 0u;
-      if (e < n) {
-        key[r] = __ldg(a.keys_in + e);
-        val[r] = a.vals_in ? __ldg(a.vals_in + e) : (uint32_t)e;
-        if (!a.valid || __ldg(a.valid + e) != 0u) dig[r] = (key[r] >> a.shift) & mask;
-      }
+      key[r] = sm.raw_k[b][q];
+      val[r] = a.vals_in ? sm.raw_v[b][q] : (uint32_t)e;
+      if (e < n && (!a.valid || __ldg(a.valid + e) != 0u)) dig[r] = (key[r] >> a.shift) & mask;
     }
 #pragma unroll
-    for (int k = 0; k < 256 / 32; ++k) wcnt[warp][lane * 8 + k] = 0u;
+    for (int k = 0; k < 256 / 32; ++k) sm.wcnt[warp][lane * 8 + k] = 0u;
     __syncwarp();
-    // 1) warp-local stable ranks
+    // 1) warp-local stable ranks; the lanes holding the same digit are found
+    //    with one ballot per digit bit (plus one for validity)
     uint32_t loc[kSortItems];
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
       const uint32_t d = dig[r];
-      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      const bool ok = d != kNoDigit;
+      uint32_t peers = __ballot_sync(0xffffffffu, ok);
+      if (!ok) peers = ~peers;
+#pragma unroll
+      for (int bb = 0; bb < BITS; ++bb) {
+        const bool bit = (d >> bb) & 1u;
+        const uint32_t m = __ballot_sync(0xffffffffu, bit);
+        peers &= bit ? m : ~m;
+      }
       const int leader = __ffs(peers) - 1;
       uint32_t old = 0;
-      if (lane == leader && d != kNoDigit) {
-        old = wcnt[warp][d];
-        wcnt[warp][d] = old + __popc(peers);
+      if (lane == leader && ok) {
+        old = sm.wcnt[warp][d];
+        sm.wcnt[warp][d] = old + __popc(peers);
       }
       old = __shfl_sync(0xffffffffu, old, leader);
       loc[r] = old + __popc(peers & lt);
       __syncwarp();
     }
     __syncthreads();
-    // 2) per digit: prefix over warps and the tile's count; publish it
+    // 2) per digit: prefix over warps, the tile's count, and the tile-wide
+    //    exclusive scan over digits (staging order)
     uint32_t tot = 0;
 #pragma unroll
     for (int w = 0; w < W; ++w) {
-      const uint32_t c = wcnt[w][tid];
-      wcnt[w][tid] = tot;
+      const uint32_t c = sm.wcnt[w][tid];
+      sm.wcnt[w][tid] = tot;
       tot += c;
     }
-    if (tid < R) st_relaxed(a.status + (((size_t)tile) << a.bits) + tid, (tile == 0 ? kFlagPrefix : kFlagCount) | tot);
-    //    tile-wide exclusive scan over digits (staging order)
     uint32_t incl = tot;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
       if (lane >= o) incl += v;
     }
-    if (lane == 31) scan_tmp[warp] = incl;
-    // 3) look back for the exclusive prefix of each digit over earlier tiles
-    if (tid < R) {
-      uint64_t excl = 0;
-      if (tile > 0) {
-        int64_t j = tile - 1;
-        int spins = 0;
-        while (true) {
-          const uint64_t w = ld_relaxed(a.status + (((size_t)j) << a.bits) + tid);
-          const uint64_t f = w & ~kValueMask;
-          if (f == 0ull) {
-            if (++spins > kSpinLimit) {
-              set_error(a.dev_err, HGS_ERR_TIMEOUT);
-              break;
-            }
-            __nanosleep(64);
-            continue;
-          }
-          excl += w & kValueMask;
-          if (f == kFlagPrefix || j == 0) break;
-          --j;
-        }
-        st_relaxed(a.status + (((size_t)tile) << a.bits) + tid, kFlagPrefix | (excl + tot));
-      }
-      gpos[tid] = gbase[tid] + excl;
-    }
+    if (lane == 31) sm.scan_tmp[warp] = incl;
     __syncthreads();
     {
       uint32_t wb = 0;
 #pragma unroll
       for (int w = 0; w < W; ++w)
-        if (w < warp) wb += scan_tmp[w];
-      tdig[tid] = wb + incl - tot;
-      if (tid == 255) s_count = wb + incl;
+        if (w < warp) wb += sm.scan_tmp[w];
+      sm.tdig[tid] = wb + incl - tot;
+      sm.base[cb ^ 1][tid] = sm.base[cb][tid] + tot;
+      if (tid == 255) sm.tile_count = wb + incl;
     }
     __syncthreads();
-    // 4) stage the tile in digit order
+    // 3) stage the tile in digit order over its own raw buffer
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
       const uint32_t d = dig[r];
       if (d != kNoDigit) {
-        const uint32_t lpos = tdig[d] + wcnt[warp][d] + loc[r];
-        stage_k[lpos] = key[r];
-        stage_v[lpos] = val[r];
+        const uint32_t lpos = sm.tdig[d] + sm.wcnt[warp][d] + loc[r];
+        sm.raw_k[b][lpos] = key[r];
+        sm.raw_v[b][lpos] = val[r];
       }
     }
     __syncthreads();
-    // 5) write the digit runs out: consecutive threads, consecutive addresses.
+    // 4) write the digit runs out: consecutive threads, consecutive addresses.
     //    In the last pass of the tile sort equal keys are adjacent here, so
     //    each run's first and last element bound that tile's range.
-    const uint32_t cnt = s_count;
+    const uint32_t cnt = sm.tile_count;
     for (uint32_t i = tid; i < cnt; i += kSortThreads) {
-      const uint32_t k = stage_k[i];
+      const uint32_t k = sm.raw_k[b][i];
       const uint32_t d = (k >> a.shift) & mask;
-      const uint64_t pos = gpos[d] + (i - tdig[d]);
-      if (pos >= n_out) continue;
+      const uint32_t pos = sm.base[cb][d] + (i - sm.tdig[d]);
       if (a.keys_out) a.keys_out[pos] = k;
-      a.vals_out[pos] = stage_v[i];
+      a.vals_out[pos] = sm.raw_v[b][i];
       if (a.ranges) {
-        if (i == 0 || stage_k[i - 1] != k) atomicMin(a.ranges + 2 * (size_t)k, (uint32_t)pos);
-        if (i + 1 == cnt || stage_k[i + 1] != k) atomicMax(a.ranges + 2 * (size_t)k + 1, (uint32_t)(pos + 1));
+        if (i == 0 || sm.raw_k[b][i - 1] != k) atomicMin(a.ranges + 2 * (size_t)k, pos);
+        if (i + 1 == cnt || sm.raw_k[b][i + 1] != k) atomicMax(a.ranges + 2 * (size_t)k + 1, pos + 1);
       }
     }
-    __syncthreads();
+    cb ^= 1;
   }
+  cp_wait_all();
 }
 
 // ---------------------------------------------------------------------------
@@ -568,38 +599,43 @@ __global__ void __launch_bounds__(256)
 }
 
 // ---------------------------------------------------------------------------
-// Blocks of the look-back passes: as many as fit on the device at once.
-static int sweep_grid() {
+// Chunks (blocks) of the radix passes: as many scatter blocks as fit on the
+// device at once, so every chunk is in flight from the start.
+static int pass_grid() {
   static int cached[64] = {0};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
   if (cached[dev] == 0) {
     int sms = 0, per = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_onesweep, kSortThreads, 0);
-    cached[dev] = std::max(1, sms) * std::max(1, per);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_scatter<8>, kSortThreads, sizeof(ScatterSmem));
+    cached[dev] = std::min(kMaxChunks, std::max(1, sms) * std::max(1, per));
   }
   return cached[dev];
+}
+
+template <int B>
+static void scatter_bits(const PassArgs &p, int G, cudaStream_t s) {
+  if (p.bits == B)
+    k_scatter<B><<<G, kSortThreads, sizeof(ScatterSmem), s>>>(p);
+  else if constexpr (B > 1)
+    scatter_bits<B - 1>(p, G, s);
+}
+
+static void radix_pass(const PassArgs &p, int G, cudaStream_t s) {
+  k_chunk_hist<<<G, kSortThreads, 0, s>>>(p);
+  k_chunk_scan<<<1 << p.bits, 256, 0, s>>>(p, G);
+  scatter_bits<8>(p, G, s);
 }
 
 int launch_bin_sort(const BinArgs &a, const BinWorkspace &ws, cudaStream_t s) {
   int64_t *ctr = ws.counters;  // 0 = n_visible, 1 = K, 2 = overflow, 3 = deferred rects
   cudaMemsetAsync(ctr, 0, ws.head_bytes, s);
-  const int G = sweep_grid();
+  const int G = pass_grid();
   // 1) depth digits over the binned primitives (the first pass compacts)
-  HistArgs h{};
-  h.keys = a.depth_key;
-  h.valid = a.touched;
-  h.n_host = a.n;
-  h.sp.npass = 4;
-  for (int p = 0; p < 4; ++p) { h.sp.shift[p] = 8 * p; h.sp.bits[p] = 8; }
-  h.hist = ws.hist;
-  h.status0 = ws.status[0];
-  h.radix0 = 256;
-  k_digit_hist<<<G, 256, 0, s>>>(h);
   const uint32_t *dk_in = a.depth_key, *dv_in = nullptr;
   for (int p = 0; p < 4; ++p) {
-    SweepArgs w{};
+    PassArgs w{};
     w.keys_in = dk_in;
     w.vals_in = dv_in;
     w.valid = p == 0 ? a.touched : nullptr;
@@ -608,15 +644,11 @@ int launch_bin_sort(const BinArgs &a, const BinWorkspace &ws, cudaStream_t s) {
     w.shift = 8 * p;
     w.bits = 8;
     w.ghist = ws.hist + 256 * p;
-    w.status = ws.status[p & 1];
-    w.status_next = p < 3 ? ws.status[(p + 1) & 1] : nullptr;
-    w.next_radix = 256;
-    w.tile_ctr = ws.tile_ctr + p;
+    w.chist = ws.chist;
     w.keys_out = ws.dk[p & 1];
     w.vals_out = ws.dv[p & 1];
     w.count_out = p == 0 ? &ctr[0] : nullptr;
-    w.dev_err = a.dev_err;
-    k_onesweep<<<G, kSortThreads, 0, s>>>(w);
+    radix_pass(w, G, s);
     dk_in = ws.dk[p & 1];
     dv_in = ws.dv[p & 1];
   }
@@ -635,40 +667,28 @@ int launch_bin_sort(const BinArgs &a, const BinWorkspace &ws, cudaStream_t s) {
   // dk[0] is free once the depth sort is done: it holds the deferred queue
   k_emit<<<kSortBlocks, 256, 0, s>>>(ids, ws.offs, a.rect, ctr, a.TX, ws.tk[0], vbuf[0], ws.dk[0]);
   k_emit_big<<<kSortBlocks, 256, 0, s>>>(ids, ws.offs, a.rect, ctr, a.TX, ws.dk[0], ws.tk[0], vbuf[0]);
-  HistArgs t{};
-  t.keys = ws.tk[0];
-  t.d_n = &ctr[1];
-  t.d_abort = &ctr[2];
-  t.sp.npass = passes;
+  int tshift[4], tbits[4];
   for (int p = 0; p < passes; ++p) {
-    t.sp.shift[p] = per_pass * p;
-    t.sp.bits[p] = std::min(per_pass, a.tile_bits - per_pass * p);
+    tshift[p] = per_pass * p;
+    tbits[p] = std::min(per_pass, a.tile_bits - per_pass * p);
   }
-  t.hist = ws.hist + 256 * 4;
-  t.status0 = ws.status[0];
-  t.radix0 = 1 << t.sp.bits[0];
-  t.ranges = a.ranges;
-  t.tiles = a.tiles;
-  k_digit_hist<<<G, 256, 0, s>>>(t);
   for (int p = 0; p < passes; ++p) {
     const bool last = p + 1 == passes;
-    SweepArgs w{};
+    PassArgs w{};
     w.keys_in = ws.tk[p & 1];
     w.vals_in = vbuf[p & 1];
     w.d_n = &ctr[1];
     w.d_abort = &ctr[2];
-    w.shift = t.sp.shift[p];
-    w.bits = t.sp.bits[p];
-    w.ghist = t.hist + 256 * p;
-    w.status = ws.status[p & 1];
-    w.status_next = last ? nullptr : ws.status[(p + 1) & 1];
-    w.next_radix = last ? 0 : 1 << t.sp.bits[p + 1];
-    w.tile_ctr = ws.tile_ctr + 4 + p;
+    w.shift = tshift[p];
+    w.bits = tbits[p];
+    w.ghist = ws.hist + 256 * (4 + p);
+    w.chist = ws.chist;
+    w.ranges_init = p == 0 ? a.ranges : nullptr;
+    w.tiles = a.tiles;
     w.keys_out = (!last || a.keys) ? ws.tk[(p + 1) & 1] : nullptr;
     w.vals_out = vbuf[(p + 1) & 1];
     w.ranges = last ? a.ranges : nullptr;
-    w.dev_err = a.dev_err;
-    k_onesweep<<<G, kSortThreads, 0, s>>>(w);
+    radix_pass(w, G, s);
   }
   k_ranges_fix<<<(a.tiles + 255) / 256, 256, 0, s>>>(a.ranges, a.tiles);
   if (a.keys) k_keys64<<<kSortBlocks, 256, 0, s>>>(ws.tk[passes & 1], a.vals, a.depth_key, ctr, a.keys);

@@ -50,7 +50,7 @@ struct BinWorkspace {
   uint32_t *offs;        // [n] instance offsets in depth order
   uint32_t *tk[2];       // tile keys ping-pong, [capacity]
   uint32_t *tv;          // tile vals scratch, [capacity]
-  uint64_t *status[2];   // look-back status words, ping-pong between passes
+  uint32_t *chist;       // [256][kSortBlocks] per-chunk digit counts / offsets of a pass
   size_t bytes;
 };
 
