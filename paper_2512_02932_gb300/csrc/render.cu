@@ -370,7 +370,12 @@ struct BwdPix {
   float px, py, T;
   uint32_t last;
   float dC0, dC1, dC2, dD, dN0, dN1, dN2, dA;       // upstream gradient of the pixel
-  float ac0, ac1, ac2, az, an0, an1, an2, aa;       // everything behind, blended
+  // Everything behind the current pair, blended, only enters the gradient
+  // through its dot product with the pixel's upstream gradient, so that dot
+  // product is kept instead of the eight blended channels:
+  // S = sum_k acc_k dC_k over rgb, depth, normal and alpha (acc_alpha
+  // blends the constant 1), starting from the background colour.
+  float S;
   bool inside;
 };
 
@@ -381,8 +386,7 @@ __device__ __forceinline__ void load_bwd_pix(BwdPix &s, const RenderBwdArgs &a, 
   s.T = 1.0f;
   s.last = 0;
   s.dC0 = s.dC1 = s.dC2 = s.dD = s.dN0 = s.dN1 = s.dN2 = s.dA = 0.f;
-  s.ac0 = a.cfg.bg[0]; s.ac1 = a.cfg.bg[1]; s.ac2 = a.cfg.bg[2];
-  s.az = s.an0 = s.an1 = s.an2 = s.aa = 0.f;
+  s.S = 0.f;
   if (!s.inside) return;
   const size_t HW = (size_t)a.cam.W * a.cam.H;
   const size_t p = (size_t)y * a.cam.W + x;
@@ -392,25 +396,25 @@ __device__ __forceinline__ void load_bwd_pix(BwdPix &s, const RenderBwdArgs &a, 
   if (a.g_depth) s.dD = a.g_depth[p];
   if (a.g_normal) { s.dN0 = a.g_normal[p]; s.dN1 = a.g_normal[p + HW]; s.dN2 = a.g_normal[p + 2 * HW]; }
   if (a.g_alpha) s.dA = a.g_alpha[p];
+  s.S = a.cfg.bg[0] * s.dC0 + a.cfg.bg[1] * s.dC1 + a.cfg.bg[2] * s.dC2;
 }
 
 // Add one contributing pair's gradient of the record (layout: common.cuh)
 // into g, recovering the transmittance in front of it by division and
-// updating the blended "behind" accumulators (reverse replay of Eq. 2).
+// updating the blended "behind" term (reverse replay of Eq. 2).  With
+// cd = sum_k c_k dC_k over the record's channels, dL/dalpha is
+// T_i (cd - S), and blending the pair in moves S by alpha (cd - S).
 __device__ __forceinline__ void pair_grad(float (&g)[16], BwdPix &s, const PairEval &e, const float4 &r0,
                                           const float4 &r1, const float4 &r2, const float4 &r3,
                                           const CfgK &cfg) {
   const float c0 = r2.z, c1 = r2.w, c2 = r3.x, n0 = r3.y, n1 = r3.z, n2 = r3.w;
   const float Ti = __fdividef(s.T, 1.0f - e.at);
   const float w = e.at * Ti;
-  const float fsum = (c0 - s.ac0) * s.dC0 + (c1 - s.ac1) * s.dC1 + (c2 - s.ac2) * s.dC2 +
-                     (e.z - s.az) * s.dD + (n0 - s.an0) * s.dN0 + (n1 - s.an1) * s.dN1 +
-                     (n2 - s.an2) * s.dN2 + (1.0f - s.aa) * s.dA;
+  const float cd = fmaf(c0, s.dC0, fmaf(c1, s.dC1, fmaf(c2, s.dC2, fmaf(e.z, s.dD,
+                   fmaf(n0, s.dN0, fmaf(n1, s.dN1, fmaf(n2, s.dN2, s.dA)))))));
+  const float fsum = cd - s.S;
   const float dat = Ti * fsum;
-  s.ac0 += e.at * (c0 - s.ac0); s.ac1 += e.at * (c1 - s.ac1); s.ac2 += e.at * (c2 - s.ac2);
-  s.az += e.at * (e.z - s.az);
-  s.an0 += e.at * (n0 - s.an0); s.an1 += e.at * (n1 - s.an1); s.an2 += e.at * (n2 - s.an2);
-  s.aa += e.at * (1.0f - s.aa);
+  s.S = fmaf(e.at, fsum, s.S);
   s.T = Ti;
   g[1] += w * s.dC0; g[2] += w * s.dC1; g[3] += w * s.dC2;
   g[13] += w * s.dN0; g[14] += w * s.dN1; g[15] += w * s.dN2;
@@ -422,9 +426,10 @@ __device__ __forceinline__ void pair_grad(float (&g)[16], BwdPix &s, const PairE
   }
   if (r0.w > 0.0f) {
     // conic-space gradient: d = a dx^2 + 2 b dx dy + c dy^2
-    g[7] += dd * e.dx * e.dx;
-    g[8] += dd * 2.0f * e.dx * e.dy;
-    g[9] += dd * e.dy * e.dy;
+    const float ddx = dd * e.dx, ddy = dd * e.dy;
+    g[7] += ddx * e.dx;
+    g[8] += 2.0f * ddx * e.dy;
+    g[9] += ddy * e.dy;
     g[4] -= dd * 2.0f * e.u * r1.x;
     g[5] -= dd * 2.0f * (e.u * r1.y + e.v * r1.z);
     g[6] += dzp;
