@@ -30,7 +30,16 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "fwd+bwd ms/iter @3M prims 1600x1064; served frames/s + p50/p99 latency"
-WORKLOAD = "scene-scale training step: 3M prims (70% 3D / 30% 2D, SH deg 3), 1600x1064, fwd+bwd, L1 loss"
+
+
+def workload(args):
+    return (f"scene-scale training step: {args.n} prims (70% 3D / 30% 2D, SH deg 3), "
+            f"{args.width}x{args.height}, fwd+bwd, L1 loss")
+
+
+def base_config(args, world):
+    return {"workload": workload(args), "n_prims": args.n, "width": args.width, "height": args.height,
+            "sh_degree": 3, "parallelism": "replicas" if world > 1 else "single"}
 
 
 def parse():
@@ -39,7 +48,7 @@ def parse():
     p.add_argument("--steps", type=int, default=100)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--n", type=int, default=3_000_000)
+    p.add_argument("--prims", dest="n", type=int, default=3_000_000)
     p.add_argument("--width", type=int, default=1600)
     p.add_argument("--height", type=int, default=1064)
     p.add_argument("--no-e2e", action="store_true")
@@ -114,10 +123,10 @@ def dist_init(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
+    if world > 1 and args.impl == "ours":
+        # the reference arm runs on rank 0 alone and needs no process group
         import torch.distributed as dist
-        backend = "nccl" if args.impl == "ours" else "gloo"
-        dist.init_process_group(backend=backend)
+        dist.init_process_group(backend="nccl")
     return world, rank, local
 
 
@@ -182,7 +191,7 @@ def reference_arm(args, world, rank):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD + " (CPU oracle, forward, sampled pixels extrapolated)"},
+            "config": base_config(args, world),
             "cpu_baseline": {"value": v, "unit": "ms", "cores": res["cores"], "kind": "oracle",
                              "sample": res["sample"]},
             "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -413,10 +422,8 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_prims": args.n, "width": args.width, "height": args.height,
-                   "sh_degree": 3, "instances_K": K, "pixel_list_entries": n_last_sum,
-                   "l2": "inputs larger than L2 (scene 708 MB, records 240 MB, lists > 100 MB)",
-                   "parallelism": "replicas" if world > 1 else "single"},
+        "config": {**base_config(args, world), "instances_K": K, "pixel_list_entries": n_last_sum,
+                   "l2": "inputs larger than L2 (scene 708 MB, records 240 MB, lists > 100 MB)"},
         "phases_ms": phases,
         "step_ms": {"min": round(min(step_ms), 4), "median": round(statistics.median(step_ms), 4),
                     "max": round(max(step_ms), 4), "first": round(step_ms[0], 4)},
