@@ -404,21 +404,25 @@ __device__ __forceinline__ void load_bwd_pix(BwdPix &s, const RenderBwdArgs &a, 
 // updating the blended "behind" term (reverse replay of Eq. 2).  With
 // cd = sum_k c_k dC_k over the record's channels, dL/dalpha is
 // T_i (cd - S), and blending the pair in moves S by alpha (cd - S).
+// FULL = false: only the rgb cotangent is nonzero (depth, normal and alpha
+// gradients absent), so their terms and gradient slots (6, 13-15) vanish.
+template <bool FULL>
 __device__ __forceinline__ void pair_grad(float (&g)[16], BwdPix &s, const PairEval &e, const float4 &r0,
                                           const float4 &r1, const float4 &r2, const float4 &r3,
                                           const CfgK &cfg) {
   const float c0 = r2.z, c1 = r2.w, c2 = r3.x, n0 = r3.y, n1 = r3.z, n2 = r3.w;
   const float Ti = __fdividef(s.T, 1.0f - e.at);
   const float w = e.at * Ti;
-  const float cd = fmaf(c0, s.dC0, fmaf(c1, s.dC1, fmaf(c2, s.dC2, fmaf(e.z, s.dD,
-                   fmaf(n0, s.dN0, fmaf(n1, s.dN1, fmaf(n2, s.dN2, s.dA)))))));
+  const float cd = FULL ? fmaf(c0, s.dC0, fmaf(c1, s.dC1, fmaf(c2, s.dC2, fmaf(e.z, s.dD,
+                          fmaf(n0, s.dN0, fmaf(n1, s.dN1, fmaf(n2, s.dN2, s.dA)))))))
+                        : fmaf(c0, s.dC0, fmaf(c1, s.dC1, c2 * s.dC2));
   const float fsum = cd - s.S;
   const float dat = Ti * fsum;
   s.S = fmaf(e.at, fsum, s.S);
   s.T = Ti;
   g[1] += w * s.dC0; g[2] += w * s.dC1; g[3] += w * s.dC2;
-  g[13] += w * s.dN0; g[14] += w * s.dN1; g[15] += w * s.dN2;
-  const float dzp = w * s.dD;
+  if (FULL) { g[13] += w * s.dN0; g[14] += w * s.dN1; g[15] += w * s.dN2; }
+  const float dzp = FULL ? w * s.dD : 0.0f;
   float dd = 0.f;
   if (e.araw <= cfg.alpha_max) {
     g[0] += dat * e.g;
@@ -432,7 +436,7 @@ __device__ __forceinline__ void pair_grad(float (&g)[16], BwdPix &s, const PairE
     g[9] += ddy * e.dy;
     g[4] -= dd * 2.0f * e.u * r1.x;
     g[5] -= dd * 2.0f * (e.u * r1.y + e.v * r1.z);
-    g[6] += dzp;
+    if (FULL) g[6] += dzp;
   } else {
     const float du = 2.0f * e.u * dd, dv = 2.0f * e.v * dd;
     const float dp0 = du * e.inv, dp1 = dv * e.inv;
@@ -442,10 +446,84 @@ __device__ __forceinline__ void pair_grad(float (&g)[16], BwdPix &s, const PairE
     g[11] += dp2 * e.dx; g[12] += dp2 * e.dy;
     g[4] -= dp0 * r1.x + dp1 * r1.z + dp2 * r2.x;
     g[5] -= dp0 * r1.y + dp1 * r1.w + dp2 * r2.y;
-    g[6] += dzp * e.inv;
+    if (FULL) g[6] += dzp * e.inv;
   }
 }
 
+// Butterfly sums for the rgb-only backward, which reduces 9 (3D) or 12 (2D)
+// of the 16 slots.  sum8: slots v[0..7] transposed over lanes 16, 8, 4 and
+// finished over lanes 2, 1; lane l ends with slot ((l >> 2) & 7)'s total.
+// sum4: slots v[0..3] over lanes 16, 8, finished over 4, 2, 1; lane l ends
+// with slot ((l >> 3) & 3).  sum1: plain butterfly.
+__device__ __forceinline__ float sum8(float (&v)[8], int lane) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const bool hi = lane & 16;
+    const float send = hi ? v[i] : v[i + 4];
+    v[i] = (hi ? v[i + 4] : v[i]) + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const bool hi = lane & 8;
+    const float send = hi ? v[i] : v[i + 2];
+    v[i] = (hi ? v[i + 2] : v[i]) + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  {
+    const bool hi = lane & 4;
+    const float send = hi ? v[0] : v[1];
+    v[0] = (hi ? v[1] : v[0]) + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+  return v[0];
+}
+__device__ __forceinline__ float sum4(float (&v)[4], int lane) {
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const bool hi = lane & 16;
+    const float send = hi ? v[i] : v[i + 2];
+    v[i] = (hi ? v[i + 2] : v[i]) + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+  {
+    const bool hi = lane & 8;
+    const float send = hi ? v[0] : v[1];
+    v[0] = (hi ? v[1] : v[0]) + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+  return v[0];
+}
+__device__ __forceinline__ float sum1(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Warp-reduce one record's gradient and add it to the record's row.
+template <bool FULL>
+__device__ __forceinline__ void reduce_record(float (&g)[16], bool is3d, int lane, float *row) {
+  if (FULL) {
+    int comp;
+    const float v = warp_sum16(g, lane, comp);
+    if ((lane & 1) == 0) atomicAdd(row + comp, v);
+    return;
+  }
+  // slots 0-5, 7, 8 in one transpose; then 9 (3D) or 9-12 (2D)
+  float a[8] = {g[0], g[1], g[2], g[3], g[4], g[5], g[7], g[8]};
+  const int s8 = (lane >> 2) & 7;
+  const float v8 = sum8(a, lane);
+  if ((lane & 3) == 0) atomicAdd(row + (s8 < 6 ? s8 : s8 + 1), v8);
+  if (is3d) {
+    const float v = sum1(g[9]);
+    if (lane == 0) atomicAdd(row + 9, v);
+  } else {
+    float b[4] = {g[9], g[10], g[11], g[12]};
+    const float v4 = sum4(b, lane);
+    if ((lane & 7) == 0) atomicAdd(row + 9 + ((lane >> 3) & 3), v4);
+  }
+}
+
+template <bool FULL>
 __global__ void __launch_bounds__(kRW * 32, 5) render_bwd_kernel(RenderBwdArgs a) {
   __shared__ __align__(16) float4 sm[kRW][2][kCh * kRecF4];
   __shared__ uint32_t sid[kRW][2][kCh];
@@ -492,11 +570,9 @@ __global__ void __launch_bounds__(kRW * 32, 5) render_bwd_kernel(RenderBwdArgs a
 #pragma unroll
       for (int k = 0; k < 16; ++k) g[k] = 0.f;
       const float4 r3 = r[3];
-      if (c0) pair_grad(g, s[0], e0, r0, r1, r2, r3, a.cfg);
-      if (c1) pair_grad(g, s[1], e1, r0, r1, r2, r3, a.cfg);
-      int comp;
-      const float v = warp_sum16(g, lane, comp);
-      if ((lane & 1) == 0) atomicAdd(a.rec_grad + (size_t)sid[warp][buf][jj] * kGradW + comp, v);
+      if (c0) pair_grad<FULL>(g, s[0], e0, r0, r1, r2, r3, a.cfg);
+      if (c1) pair_grad<FULL>(g, s[1], e1, r0, r1, r2, r3, a.cfg);
+      reduce_record<FULL>(g, r0.w > 0.0f, lane, a.rec_grad + (size_t)sid[warp][buf][jj] * kGradW);
     }
     if (!has_next) break;
     __syncwarp();
@@ -534,9 +610,14 @@ int launch_render_batch(const BatchRenderArgs &b, int rows, cudaStream_t s) {
 int launch_render_bwd(const RenderBwdArgs &a, cudaStream_t s) {
   const int tiles = a.cam.TX * a.cam.TY;
   if (tiles <= 0) return 0;
-  static bool once = (prefer_shared((const void *)render_bwd_kernel), true);
+  static bool once = (prefer_shared((const void *)render_bwd_kernel<true>),
+                      prefer_shared((const void *)render_bwd_kernel<false>), true);
   (void)once;
-  render_bwd_kernel<<<tiles, kRW * 32, 0, s>>>(a);
+  // with only an rgb cotangent the depth/normal/alpha terms are identically 0
+  if (a.g_depth || a.g_normal || a.g_alpha)
+    render_bwd_kernel<true><<<tiles, kRW * 32, 0, s>>>(a);
+  else
+    render_bwd_kernel<false><<<tiles, kRW * 32, 0, s>>>(a);
   return 0;
 }
 

@@ -302,6 +302,9 @@ class RasterizeFunction(torch.autograd.Function):
         scene = SceneTensors(means.detach(), log_scales.detach(), quats.detach(),
                              opacity_logits.detach(), sh.detach(), types, sh_degree)
         out = rast.forward(scene, cam, cfg)
+        # maps the loss does not use arrive as None (not zero images), so an
+        # image-only loss runs the backward specialised for it
+        ctx.set_materialize_grads(False)
         ctx.rast = rast
         ctx.gen = rast.generation
         ctx.scene = scene

@@ -38,10 +38,15 @@ def test_tiny_lists_and_images(seed):
     np.testing.assert_array_equal(g["n_contrib"][ok], m["n_contrib"][ok].astype(np.int64))
 
 
-def _gpu_vjp(scene, cam, cot, cfg=CFG):
+def _gpu_vjp(scene, cam, cot, cfg=CFG, rgb_only=False):
+    """rgb_only: pass only the rgb cotangent (the others as absent), which
+    selects the backward specialised for an image loss."""
     r, st, g = gpu_forward(scene, cam, cfg, keep_keys=False)
     t = {k: torch.from_numpy(v).cuda() for k, v in cot.items()}
-    grads = r.backward(t["rgb"], t["depth"], t["normal"], t["alpha"])
+    if rgb_only:
+        grads = r.backward(t["rgb"], None, None, None)
+    else:
+        grads = r.backward(t["rgb"], t["depth"], t["normal"], t["alpha"])
     torch.cuda.synchronize()
     r.check()
     return g, {k: v.cpu().numpy() for k, v in grads.items()}
@@ -61,6 +66,30 @@ def test_tiny_gradients(seed):
     cot = _masked_cot(10 + seed, cam, m["amb"])
     _, ref = AR.vjp(scene, cam, CFG, cot)
     _, got = _gpu_vjp(scene, cam, cot)
+    assert_grads_match(got, ref)
+
+
+@pytest.mark.parametrize("seed", [1, 4])
+def test_tiny_gradients_rgb_cotangent_only(seed):
+    scene, cam = S.tiny_scene(seed)
+    m = _oracle_maps(scene, cam)
+    cot = _masked_cot(30 + seed, cam, m["amb"])
+    for k in ("depth", "normal", "alpha"):
+        cot[k] = np.zeros_like(cot[k])
+    _, ref = AR.vjp(scene, cam, CFG, cot)
+    _, got = _gpu_vjp(scene, cam, cot, rgb_only=True)
+    assert_grads_match(got, ref)
+
+
+def test_sh_degree3_surface_gradients_rgb_only():
+    scene = S.surface_scene(400, seed=8, frac3d=0.5, ls_loc=-2.6, ls_scale=0.4)
+    cam = S.orbit_camera(40.0, 10.0, 3.0, 96, 72, 50.0)
+    m = _oracle_maps(scene, cam)
+    cot = _masked_cot(22, cam, m["amb"])
+    for k in ("depth", "normal", "alpha"):
+        cot[k] = np.zeros_like(cot[k])
+    _, ref = AR.vjp(scene, cam, CFG, cot)
+    _, got = _gpu_vjp(scene, cam, cot, rgb_only=True)
     assert_grads_match(got, ref)
 
 
@@ -244,4 +273,43 @@ def test_surfels_reaching_the_near_plane():
     cot = _masked_cot(4, cam, m["amb"])
     _, ref = AR.vjp(scene, cam, CFG, cot)
     _, got = _gpu_vjp(scene, cam, cot)
+    assert_grads_match(got, ref)
+
+
+# ---------------------------------------------------------------------------
+# the autograd Function
+# ---------------------------------------------------------------------------
+def _autograd_grads(scene, cam, loss_fn):
+    from paper_2512_02932_gb300 import rasterize
+    st = SceneTensors.from_numpy(scene)
+    params = [st.means, st.log_scales, st.quats, st.opacity_logits, st.sh]
+    for p in params:
+        p.requires_grad_(True)
+    rgb, depth, normal, alpha = rasterize(st, cam, CFG)
+    loss_fn(rgb, depth, normal, alpha).backward()
+    torch.cuda.synchronize()
+    names = ["means", "log_scales", "quats", "opacity_logits", "sh"]
+    return {k: p.grad.detach().cpu().numpy() for k, p in zip(names, params)}
+
+
+@pytest.mark.parametrize("with_depth", [False, True])
+def test_autograd_function_matches_oracle(with_depth):
+    """Loss through torch.autograd: an rgb-only loss (unused maps arrive as
+    None and select the image-loss backward) and one that also uses depth."""
+    scene, cam = S.tiny_scene(2)
+    m = _oracle_maps(scene, cam)
+    cot = _masked_cot(40, cam, m["amb"])
+    if not with_depth:
+        cot["depth"] = np.zeros_like(cot["depth"])
+    cot["normal"] = np.zeros_like(cot["normal"])
+    cot["alpha"] = np.zeros_like(cot["alpha"])
+    c_rgb = torch.from_numpy(cot["rgb"]).cuda()
+    c_depth = torch.from_numpy(cot["depth"]).cuda()
+
+    def loss(rgb, depth, normal, alpha):
+        L = (rgb * c_rgb).sum()
+        return L + (depth * c_depth).sum() if with_depth else L
+
+    got = _autograd_grads(scene, cam, loss)
+    _, ref = AR.vjp(scene, cam, CFG, cot)
     assert_grads_match(got, ref)

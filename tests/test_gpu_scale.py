@@ -97,9 +97,10 @@ def _check_pixels(out, scene, cam, npix, seed, orc=None, max_amb=0.05):
     return orc
 
 
-def _fd_check(scene, cam, r, st, orc, rect, touched, n_prims, seed, max_tiles=6):
+def _fd_check(scene, cam, r, st, orc, rect, touched, n_prims, seed, max_tiles=6, rgb_only=False):
     """GPU gradients of L = sum(cot * outputs) against FP64 central
-    differences of the oracle, for sampled primitives and parameters."""
+    differences of the oracle, for sampled primitives and parameters.
+    rgb_only: the loss sees the rgb map only (the image-loss backward)."""
     rng = np.random.default_rng(seed)
     TX = (cam.width + 15) // 16
     cand = np.nonzero((touched > 0) & (touched <= max_tiles))[0]
@@ -113,6 +114,9 @@ def _fd_check(scene, cam, r, st, orc, rect, touched, n_prims, seed, max_tiles=6)
     allpix = np.unique(np.concatenate(list(pix_of.values())), axis=0)
     _, amb = orc.render(allpix)
     cot = S.random_cotangents(seed + 1, cam.height, cam.width)
+    if rgb_only:
+        for k in ("depth", "normal", "alpha"):
+            cot[k] = np.zeros_like(cot[k])
     for k in cot:
         m = cot[k] if cot[k].ndim == 2 else cot[k]
         if m.ndim == 2:
@@ -120,7 +124,10 @@ def _fd_check(scene, cam, r, st, orc, rect, touched, n_prims, seed, max_tiles=6)
         else:
             m[:, allpix[amb, 1], allpix[amb, 0]] = 0.0
     t = {k: torch.from_numpy(v).cuda() for k, v in cot.items()}
-    grads = r.backward(t["rgb"], t["depth"], t["normal"], t["alpha"])
+    if rgb_only:
+        grads = r.backward(t["rgb"], None, None, None)
+    else:
+        grads = r.backward(t["rgb"], t["depth"], t["normal"], t["alpha"])
     torch.cuda.synchronize()
     r.check()
     G = {k: v.cpu().numpy() for k, v in grads.items()}
@@ -192,6 +199,7 @@ def test_scene_scale_3m_fwd_bwd():
     assert K > 20_000_000
     orc = _check_pixels(out, scene, cam, npix=3000, seed=1)
     _fd_check(scene, cam, r, st, orc, rect, touched, n_prims=60, seed=2)
+    _fd_check(scene, cam, r, st, orc, rect, touched, n_prims=30, seed=3, rgb_only=True)
 
 
 def test_stress_6m_4k_fwd_bwd():
