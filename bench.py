@@ -236,11 +236,46 @@ def launches_per_step(rast, exchange_steps, steps):
     tiles = rast.ranges.shape[0]
     tile_bits = max(1, math.ceil(math.log2(tiles))) if tiles > 1 else 1
     passes = (tile_bits + 7) // 8
-    # depth histogram + 4 depth passes, offsets scan (3), emit (2), tile
-    # histogram + tile passes, range fix-up, optional 64-bit keys
-    bin_sort = 1 + 4 + 3 + 2 + 1 + passes + 1 + (1 if rast.keys is not None else 0)
+    # 4 depth passes and the tile passes (chunk histogram, chunk scan,
+    # scatter each), offsets scan (3), emit (2), range fix-up, optional
+    # 64-bit keys
+    bin_sort = 3 * (4 + passes) + 3 + 2 + 1 + (1 if rast.keys is not None else 0)
     per = 1 + bin_sort + 1 + 2
     return per * steps + exchange_steps
+
+
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "render_bwd_traffic_3M_1600x1064.md")
+TRAFFIC_SOURCES = [os.path.join(ROOT, "paper_2512_02932_gb300", "csrc", f) for f in ("render.cu", "common.cuh")]
+
+
+def source_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def profiled_traffic(args):
+    """DRAM bytes per render_bwd launch from the committed ncu capture, used
+    only when the kernel sources hash to what was captured and the workload is
+    the captured one; otherwise None."""
+    if (args.n, args.width, args.height) != (3_000_000, 1600, 1064):
+        return None
+    try:
+        with open(TRAFFIC_PROFILE) as fh:
+            text = fh.read()
+    except OSError:
+        return None
+    fields = {}
+    for ln in text.splitlines():
+        if ln.startswith(("source_sha256:", "dram_bytes_per_launch:")):
+            k, v = ln.split(":", 1)
+            fields[k] = v.strip()
+    if fields.get("source_sha256") != source_sha256():
+        return None
+    return int(fields["dram_bytes_per_launch"])
 
 
 def main():
@@ -401,19 +436,22 @@ def main():
 
     roofline = None
     if phases:
-        # dominant kernel: the blend backward (FP32 issue bound).  Algorithmic
-        # FP32 work (FMA = 2 flops): 16 flops per (pixel, list entry) the pixel
-        # consumed (70/30 mix of the 13-flop 3D and 22-flop surfel evaluation)
-        # + 70 flops of gradient per contributing pair.  Peak: 152 SMs x 128
-        # FP32 lanes x 2 flops x the max SM clock.
+        # dominant kernel: the blend backward (FP32 issue bound), rgb-only
+        # cotangent (L1 image loss).  Algorithmic FP32 work (FMA = 2 flops):
+        # 16 flops per (pixel, list entry) the pixel consumed (70/30 mix of the
+        # 12-flop 3D and 24-flop surfel evaluation) + 56 per contributing pair
+        # (46 of gradient, ~10 of the per-record sum over pixels).  Peak: 152
+        # SMs x 128 FP32 lanes x 2 flops x the max SM clock.
         sm_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
         peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-        flops = 16.0 * n_last_sum + 70.0 * n_contrib_sum
+        flops = 16.0 * n_last_sum + 56.0 * n_contrib_sum
         achieved = flops / (phases["render_bwd"] * 1e-3) / 1e12
         roofline = {"kernel": "render_bwd_kernel", "bound": "alu", "achieved": round(achieved, 3),
                     "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                    "traffic": None, "peak_source": "FP32 lanes x max SM clock (no measured FP32 peak)",
-                    "units": {"pixel_list_entries": n_last_sum, "contributing_pairs": n_contrib_sum}}
+                    "traffic": profiled_traffic(args),
+                    "peak_source": "derived: FP32 lanes x max SM clock (no measured FP32 peak)",
+                    "units": {"pixel_list_entries": n_last_sum, "contributing_pairs": n_contrib_sum,
+                              "flops_per_entry": 16, "flops_per_contributing_pair": 56}}
     serving = None
     if not args.no_serving and world == 1:
         serving = run_serving(args, dev, cfg)
