@@ -306,6 +306,50 @@ int hgs_preprocess_bwd(const hgs_scene *scene, const hgs_projected *proj, const 
                        const hgs_config *cfg, const float *grad_ws, hgs_scene_grad *out, int32_t *dev_err,
                        hgs_stream_t stream);
 
+/* ---------------------------------------------------------------------------
+ * Frequency-decoupled optimisation (Sec. 3.3, Eq. 8, Algorithm 1; App. E)
+ * ------------------------------------------------------------------------- */
+
+/* hgs_image_losses -- the image losses of Eq. 8 other than D-SSIM, with their
+ * gradient images.  Level-1 Haar DWT (App. E) with l = (1,1)/sqrt2,
+ * h = (1,-1)/sqrt2 on the 2x2 blocks (a b; c d) at rows 2i, 2i+1, columns
+ * 2j, 2j+1: LL = (a+b+c+d)/2, LH = (a+b-c-d)/2, HL = (a-b+c-d)/2,
+ * HH = (a-b-c+d)/2, applied to image - target.
+ *   L1     = mean over C*H*W pixels of |image - target|
+ *   L_low  = mean over the C*(H/2)*(W/2) LL coefficients of dLL^2
+ *   L_high = mean over the 3*C*(H/2)*(W/2) LH, HL and HH coefficients of their squares
+ * An odd last row or column lies outside every block and enters L1 only.
+ * image, target: [C,H,W] float32 device arrays (caller-owned).
+ * d_losses: device double[3] <- (L1, L_low, L_high); zeroed by this call.
+ * g_l1, g_low, g_high: [C,H,W] float32 device outputs, each optional (NULL
+ *   skips it): w_l1 dL1/dimage (sign(0) = 0), w_low dL_low/dimage,
+ *   w_high dL_high/dimage.  Every pixel of a requested output is written.
+ * Errors: INVALID_ARG for NULL image, target or d_losses, or C, H, W < 1. */
+int hgs_image_losses(const float *image, const float *target, int32_t channels, int32_t height,
+                     int32_t width, double w_l1, double w_low, double w_high, double *d_losses,
+                     float *g_l1, float *g_low, float *g_high, hgs_stream_t stream);
+
+/* hgs_render_bwd_fdo -- the backward of frequency-decoupled optimisation
+ * (Algorithm 1).  g_color, g_low and g_high are the rgb cotangents ([3,H,W]
+ * float32, device) of the appearance loss and of the (weighted) low- and
+ * high-frequency losses.  Each is replayed through the rasterizer as in
+ * hgs_render_bwd_records, giving per primitive three raw-parameter gradients
+ * g^color, g^low, g^high (each the concatenation of the primitive's means,
+ * log-scale, quaternion, opacity-logit and SH gradients).  Where
+ * g^low . g^high < 0 a surfel (type 0) replaces g^high by g^high -
+ * (g^high . g^low)/|g^low|^2 g^low (Eq. 9) and a 3D Gaussian replaces g^low
+ * by g^low - (g^high . g^low)/|g^high|^2 g^high (Eq. 10).  *out receives
+ * g^color + g^low + g^high.
+ * grad_ws: [3,n,16] float device scratch, A16, zeroed by this call.
+ * d_conflicts: device uint64 counter incremented once per conflicting
+ *   primitive (may be NULL; not zeroed by this call).
+ * Other arguments and errors as in hgs_render_bwd. */
+int hgs_render_bwd_fdo(const hgs_scene *scene, const hgs_projected *proj, const hgs_binning *bins,
+                       const hgs_camera *cam, const hgs_config *cfg, const hgs_image *fwd,
+                       const float *g_color, const float *g_low, const float *g_high, float *grad_ws,
+                       hgs_scene_grad *out, unsigned long long *d_conflicts, int32_t *dev_err,
+                       hgs_stream_t stream);
+
 /* hgs_exchange_types -- Adaptive Type Exchange (Sec. 3.2) in place.
  * ERANK mode: erank = exp(-sum p_i log p_i), p = q / |q|_1, q = (s_x^2,
  * s_y^2, s_z^2) (Eq. 3); a 3D Gaussian with erank < theta_e becomes 2D, a 2D

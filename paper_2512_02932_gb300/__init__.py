@@ -6,6 +6,8 @@ hand-written CUDA behind a C ABI (include/hgs.h).
   rasterizer  device buffers, Rasterizer, RasterizeFunction (autograd),
               exchange_types
   serving     continuous-batching render loop over resident scenes
+  fdo         frequency-decoupled optimisation: Haar DWT image losses and
+              the Algorithm 1 backward
   build       nvcc build of libhgs.so
 """
 from .abi import HgsError, load  # noqa: F401

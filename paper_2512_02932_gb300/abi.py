@@ -100,6 +100,11 @@ SYMBOLS = {
     "hgs_preprocess_bwd": (C.c_int, [C.POINTER(hgs_scene), C.POINTER(hgs_projected), C.POINTER(hgs_camera),
                                      C.POINTER(hgs_config), P, C.POINTER(hgs_scene_grad), P, P]),
     "hgs_exchange_types": (C.c_int, [C.POINTER(hgs_scene_mut), C.POINTER(hgs_exchange_cfg), P, P, P]),
+    "hgs_image_losses": (C.c_int, [P, P, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double,
+                                   P, P, P, P, P]),
+    "hgs_render_bwd_fdo": (C.c_int, [C.POINTER(hgs_scene), C.POINTER(hgs_projected), C.POINTER(hgs_binning),
+                                     C.POINTER(hgs_camera), C.POINTER(hgs_config), C.POINTER(hgs_image),
+                                     P, P, P, P, C.POINTER(hgs_scene_grad), P, P, P]),
 }
 
 _lib = None
@@ -164,3 +169,5 @@ hgs_preprocess_bwd = _fwd("hgs_preprocess_bwd")
 hgs_exchange_types = _fwd("hgs_exchange_types")
 hgs_render_batch_workspace = _fwd("hgs_render_batch_workspace")
 hgs_render_batch = _fwd("hgs_render_batch")
+hgs_image_losses = _fwd("hgs_image_losses")
+hgs_render_bwd_fdo = _fwd("hgs_render_bwd_fdo")

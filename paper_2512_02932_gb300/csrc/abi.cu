@@ -276,6 +276,60 @@ int hgs_render_bwd(const hgs_scene *scene, const hgs_projected *proj, const hgs_
   return hgs_preprocess_bwd(scene, proj, cam, cfg, grad_ws, out, dev_err, stream);
 }
 
+
+int hgs_image_losses(const float *image, const float *target, int32_t channels, int32_t height,
+                     int32_t width, double w_l1, double w_low, double w_high, double *d_losses,
+                     float *g_l1, float *g_low, float *g_high, hgs_stream_t stream) {
+  if (!image || !target || !d_losses || channels < 1 || height < 1 || width < 1) return HGS_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaMemsetAsync(d_losses, 0, 3 * sizeof(double), s);
+  LossArgs a;
+  a.img = image; a.tgt = target;
+  a.C = channels; a.H = height; a.W = width;
+  a.loss = d_losses;
+  a.g_l1 = g_l1; a.g_low = g_low; a.g_high = g_high;
+  a.w_l1 = w_l1; a.w_low = w_low; a.w_high = w_high;
+  launch_image_losses(a, s);
+  return launched();
+}
+
+int hgs_render_bwd_fdo(const hgs_scene *scene, const hgs_projected *proj, const hgs_binning *bins,
+                       const hgs_camera *cam, const hgs_config *cfg, const hgs_image *fwd,
+                       const float *g_color, const float *g_low, const float *g_high, float *grad_ws,
+                       hgs_scene_grad *out, unsigned long long *d_conflicts, int32_t *dev_err,
+                       hgs_stream_t stream) {
+  if (!g_color || !g_low || !g_high || !out) return HGS_ERR_INVALID_ARG;
+  int st;
+  if ((st = scene_ok(scene)) != HGS_OK) return st;
+  const size_t stride = (size_t)kGradW * (size_t)scene->n;
+  const float *cots[3] = {g_color, g_low, g_high};
+  for (int k = 0; k < 3; ++k) {
+    hgs_image_grad dl = {cots[k], nullptr, nullptr, nullptr};
+    st = hgs_render_bwd_records(scene, proj, bins, cam, cfg, fwd, &dl, grad_ws ? grad_ws + k * stride : nullptr,
+                                dev_err, stream);
+    if (st != HGS_OK) return st;
+  }
+  CamK ck;
+  CfgK fk;
+  if ((st = cam_to_kernel(cam, &ck)) != HGS_OK) return st;
+  if ((st = cfg_to_kernel(cfg, &fk)) != HGS_OK) return st;
+  if (scene->n > 0 && (!out->means || !out->log_scales || !out->quats || !out->opacity_logits || !out->sh ||
+                       !aligned16(out->quats)))
+    return HGS_ERR_INVALID_ARG;
+  if ((scene->sh_degree == 1 || scene->sh_degree == 3) && scene->n > 0 && !aligned16(out->sh))
+    return HGS_ERR_INVALID_ARG;
+  if (scene->n == 0) return HGS_OK;
+  PrepGradFdoArgs g;
+  g.rec_color = grad_ws; g.rec_low = grad_ws + stride; g.rec_high = grad_ws + 2 * stride;
+  g.means = out->means; g.log_scales = out->log_scales; g.quats = out->quats;
+  g.logits = out->opacity_logits; g.sh = out->sh;
+  g.n_conflicts = d_conflicts;
+  hgs_projected pcopy = *proj;
+  launch_preprocess_bwd_fdo(prep_args(scene, ck, fk, &pcopy), g, scene->sh_degree,
+                            reinterpret_cast<cudaStream_t>(stream));
+  return launched();
+}
+
 }  // extern "C"
 
 namespace {

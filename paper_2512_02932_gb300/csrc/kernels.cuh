@@ -36,6 +36,15 @@ struct BatchPrepArgs {
 int launch_preprocess_batch(const BatchPrepArgs &b, cudaStream_t s);
 int launch_preprocess_bwd(const PrepArgs &a, const PrepGradArgs &g, int deg, cudaStream_t s);
 
+// Frequency-decoupled optimisation (Algorithm 1): three record gradients in
+// (appearance, low-frequency, high-frequency losses), one projected sum out.
+struct PrepGradFdoArgs {
+  const float *rec_color, *rec_low, *rec_high;  // [n,16] each
+  float *means, *log_scales, *quats, *logits, *sh;
+  unsigned long long *n_conflicts;              // optional counter
+};
+int launch_preprocess_bwd_fdo(const PrepArgs &a, const PrepGradFdoArgs &g, int deg, cudaStream_t s);
+
 // ---------------------------------------------------------------------------
 // binning
 // ---------------------------------------------------------------------------
@@ -110,6 +119,18 @@ struct BatchRenderArgs {
 };
 int launch_render_batch(const BatchRenderArgs &b, int rows, cudaStream_t s);
 int launch_render_bwd(const RenderBwdArgs &a, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// image losses (frequency-decoupled optimisation)
+// ---------------------------------------------------------------------------
+struct LossArgs {
+  const float *img, *tgt;        // [C,H,W]
+  int C, H, W;
+  double *loss;                  // [3]: L1, L_low, L_high, accumulated (zeroed by the caller)
+  float *g_l1, *g_low, *g_high;  // optional gradient images [C,H,W]
+  double w_l1, w_low, w_high;    // weights applied to the gradient images
+};
+int launch_image_losses(const LossArgs &a, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // exchange

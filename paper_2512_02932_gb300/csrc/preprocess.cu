@@ -566,35 +566,57 @@ __global__ void __launch_bounds__(256) preprocess_batch_kernel(BatchPrepArgs b) 
 // ---------------------------------------------------------------------------
 // backward kernel
 // ---------------------------------------------------------------------------
+// Raw-parameter gradient of one primitive.  The SH part is dv (x) Y: the
+// colour gradient per channel, zero where the colour was clamped, times the
+// basis at the view direction.
+struct PGrad {
+  float mu[3], ls[3], logit, dv[3];
+  float4 q;
+};
+
+// What the backward needs of one primitive besides its record gradient.
 template <int DEG>
-__global__ void __launch_bounds__(256) preprocess_bwd_kernel(PrepArgs a, PrepGradArgs g) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n) return;
-  constexpr int NB = (DEG + 1) * (DEG + 1);
-  float *gsh = g.sh + (int64_t)i * NB * 3;
-  if (__ldg(a.touched + i) == 0u) {
-#pragma unroll
-    for (int k = 0; k < 3; ++k) { g.means[3 * i + k] = 0.f; g.log_scales[3 * i + k] = 0.f; }
-    reinterpret_cast<float4 *>(g.quats)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    g.logits[i] = 0.f;
-    store_sh<DEG>(gsh, nullptr);
-    return;
-  }
-  float mu[3], ls[3], q[4], logit;
+struct BwdCtx {
+  static constexpr int NB = (DEG + 1) * (DEG + 1);
+  float mu[3], ls[3];
   int type;
-  load_params(a, i, mu, ls, q, logit, type);
   Contract o;
-  run_contract(mu, ls, q, logit, type, a.cam, a.cfg, o);
+  float f[NB * 3], Yb[NB];
+  float ux, uy, uz, il;
+  bool cpos[3];  // colour channel not clamped at 0
+};
+
+template <int DEG>
+__device__ __forceinline__ void bwd_ctx(const PrepArgs &a, int64_t i, BwdCtx<DEG> &x) {
+  constexpr int NB = BwdCtx<DEG>::NB;
+  float q[4], logit;
+  load_params(a, i, x.mu, x.ls, q, logit, x.type);
+  run_contract(x.mu, x.ls, q, logit, x.type, a.cam, a.cfg, x.o);
+  load_sh<DEG>(a.sh, i, x.f);
   const CamK &c = a.cam;
-  float G[kGradW];
-  {
-    const float4 *src = reinterpret_cast<const float4 *>(g.rec_grad) + 4 * i;
+  const float vx = x.mu[0] - c.campos[0], vy = x.mu[1] - c.campos[1], vz = x.mu[2] - c.campos[2];
+  x.il = rsqrtf(vx * vx + vy * vy + vz * vz);
+  x.ux = vx * x.il; x.uy = vy * x.il; x.uz = vz * x.il;
+  sh_eval<DEG>(x.ux, x.uy, x.uz, x.Yb);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const float4 v = src[k];
-      G[4 * k] = v.x; G[4 * k + 1] = v.y; G[4 * k + 2] = v.z; G[4 * k + 3] = v.w;
-    }
+  for (int ch = 0; ch < 3; ++ch) {
+    float v = 0.5f;
+#pragma unroll
+    for (int k = 0; k < NB; ++k) v = fmaf(x.f[3 * k + ch], x.Yb[k], v);
+    x.cpos[ch] = v > 0.0f;
   }
+}
+
+// The chain from a record gradient G (layout: common.cuh) to the raw
+// parameters: projection (App. C), camera, rotation, activations and the SH
+// colour.  Linear in G.
+template <int DEG>
+__device__ __forceinline__ PGrad chain_grad(const PrepArgs &a, const BwdCtx<DEG> &ctx, const float (&G)[kGradW]) {
+  constexpr int NB = BwdCtx<DEG>::NB;
+  const CamK &c = a.cam;
+  const Contract &o = ctx.o;
+  const int type = ctx.type;
+  const float(&ls)[3] = ctx.ls;
   float dX = 0.f, dY = 0.f, dZ = G[6];
   float dA[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
   float dls[3] = {0.f, 0.f, 0.f};
@@ -755,49 +777,148 @@ __global__ void __launch_bounds__(256) preprocess_bwd_kernel(PrepArgs a, PrepGra
   gq.y = (dq[1] - x * qd) * o.qinv;
   gq.z = (dq[2] - y * qd) * o.qinv;
   gq.w = (dq[3] - z * qd) * o.qinv;
-  // colour
-  float f[NB * 3];
-  load_sh<DEG>(a.sh, i, f);
-  float vx = mu[0] - c.campos[0], vy = mu[1] - c.campos[1], vz = mu[2] - c.campos[2];
-  const float il = rsqrtf(vx * vx + vy * vy + vz * vz);
-  const float ux = vx * il, uy = vy * il, uz = vz * il;
-  float Yb[NB];
-  sh_eval<DEG>(ux, uy, uz, Yb);
-  float dv[3];
+  PGrad r;
+  r.q = gq;
 #pragma unroll
-  for (int ch = 0; ch < 3; ++ch) {
-    float v = 0.5f;
-#pragma unroll
-    for (int k = 0; k < NB; ++k) v = fmaf(f[3 * k + ch], Yb[k], v);
-    dv[ch] = v > 0.0f ? G[1 + ch] : 0.0f;
-  }
-  {
-    float out[NB * 3];
-#pragma unroll
-    for (int k = 0; k < NB; ++k)
-#pragma unroll
-      for (int ch = 0; ch < 3; ++ch) out[3 * k + ch] = dv[ch] * Yb[k];
-    store_sh<DEG>(gsh, out);
-  }
+  for (int ch = 0; ch < 3; ++ch) r.dv[ch] = ctx.cpos[ch] ? G[1 + ch] : 0.0f;
   if (DEG > 0) {
     float wk[NB];
 #pragma unroll
-    for (int k = 0; k < NB; ++k) wk[k] = dv[0] * f[3 * k] + dv[1] * f[3 * k + 1] + dv[2] * f[3 * k + 2];
+    for (int k = 0; k < NB; ++k) wk[k] = r.dv[0] * ctx.f[3 * k] + r.dv[1] * ctx.f[3 * k + 1] + r.dv[2] * ctx.f[3 * k + 2];
     float gd[3];
-    sh_grad<DEG>(ux, uy, uz, wk, gd);
-    const float dotp = gd[0] * ux + gd[1] * uy + gd[2] * uz;
-    dmu[0] += (gd[0] - ux * dotp) * il;
-    dmu[1] += (gd[1] - uy * dotp) * il;
-    dmu[2] += (gd[2] - uz * dotp) * il;
+    sh_grad<DEG>(ctx.ux, ctx.uy, ctx.uz, wk, gd);
+    const float dotp = gd[0] * ctx.ux + gd[1] * ctx.uy + gd[2] * ctx.uz;
+    dmu[0] += (gd[0] - ctx.ux * dotp) * ctx.il;
+    dmu[1] += (gd[1] - ctx.uy * dotp) * ctx.il;
+    dmu[2] += (gd[2] - ctx.uz * dotp) * ctx.il;
   }
-  const float dlogit = dalpha * o.alpha * (1.f - o.alpha);
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    g.means[3 * i + k] = dmu[k];
-    g.log_scales[3 * i + k] = dls[k];
+    r.mu[k] = dmu[k];
+    r.ls[k] = dls[k];
   }
-  reinterpret_cast<float4 *>(g.quats)[i] = gq;
-  g.logits[i] = dlogit;
+  r.logit = dalpha * o.alpha * (1.f - o.alpha);
+  return r;
+}
+
+__device__ __forceinline__ void load_rec_grad(const float *rec_grad, int64_t i, float (&G)[kGradW]) {
+  const float4 *src = reinterpret_cast<const float4 *>(rec_grad) + 4 * i;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float4 v = src[k];
+    G[4 * k] = v.x; G[4 * k + 1] = v.y; G[4 * k + 2] = v.z; G[4 * k + 3] = v.w;
+  }
+}
+
+template <int DEG>
+__device__ __forceinline__ void store_pgrad(const PrepGradArgs &g, int64_t i, const PGrad &r, const float *Yb) {
+  constexpr int NB = (DEG + 1) * (DEG + 1);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    g.means[3 * i + k] = r.mu[k];
+    g.log_scales[3 * i + k] = r.ls[k];
+  }
+  reinterpret_cast<float4 *>(g.quats)[i] = r.q;
+  g.logits[i] = r.logit;
+  float out[NB * 3];
+#pragma unroll
+  for (int k = 0; k < NB; ++k)
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) out[3 * k + ch] = Yb ? r.dv[ch] * Yb[k] : 0.0f;
+  store_sh<DEG>(g.sh + (int64_t)i * NB * 3, Yb ? out : nullptr);
+}
+
+template <int DEG>
+__device__ __forceinline__ void store_zero_grad(const PrepGradArgs &g, int64_t i) {
+  PGrad z;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) { z.mu[k] = 0.f; z.ls[k] = 0.f; z.dv[k] = 0.f; }
+  z.logit = 0.f;
+  z.q = make_float4(0.f, 0.f, 0.f, 0.f);
+  store_pgrad<DEG>(g, i, z, nullptr);
+}
+
+template <int DEG>
+__global__ void __launch_bounds__(256) preprocess_bwd_kernel(PrepArgs a, PrepGradArgs g) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  if (__ldg(a.touched + i) == 0u) {
+    store_zero_grad<DEG>(g, i);
+    return;
+  }
+  BwdCtx<DEG> x;
+  bwd_ctx<DEG>(a, i, x);
+  float G[kGradW];
+  load_rec_grad(g.rec_grad, i, G);
+  const PGrad r = chain_grad<DEG>(a, x, G);
+  store_pgrad<DEG>(g, i, r, x.Yb);
+}
+
+
+// Frequency-decoupled optimisation, Algorithm 1 (§3.3): with g_low and
+// g_high the primitive's full raw-parameter gradients (means, log-scales,
+// quaternion, opacity logit and all SH coefficients, concatenated) from the
+// low- and high-frequency losses, a conflict is g_low . g_high < 0.  Then a
+// surfel (t = 0) keeps g_low and replaces g_high by its component normal to
+// g_low (Eq. 9); a 3D Gaussian keeps g_high and projects g_low (Eq. 10).  The
+// update is g_color + g_low + g_high.  Each gradient is the linear chain of
+// its record gradient, so the three are formed in registers and only the
+// sum is written.  The SH block of each gradient is dv (x) Y, so its dot
+// products are (dv . dv') |Y|^2.
+__device__ __forceinline__ float pgrad_dot(const PGrad &p, const PGrad &q, float yy) {
+  float d = p.logit * q.logit + p.q.x * q.q.x + p.q.y * q.q.y + p.q.z * q.q.z + p.q.w * q.q.w;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) d += p.mu[k] * q.mu[k] + p.ls[k] * q.ls[k] + yy * p.dv[k] * q.dv[k];
+  return d;
+}
+
+__device__ __forceinline__ void pgrad_axpy(PGrad &y, float s, const PGrad &x) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    y.mu[k] = fmaf(s, x.mu[k], y.mu[k]);
+    y.ls[k] = fmaf(s, x.ls[k], y.ls[k]);
+    y.dv[k] = fmaf(s, x.dv[k], y.dv[k]);
+  }
+  y.logit = fmaf(s, x.logit, y.logit);
+  y.q.x = fmaf(s, x.q.x, y.q.x); y.q.y = fmaf(s, x.q.y, y.q.y);
+  y.q.z = fmaf(s, x.q.z, y.q.z); y.q.w = fmaf(s, x.q.w, y.q.w);
+}
+
+template <int DEG>
+__global__ void __launch_bounds__(256) preprocess_bwd_fdo_kernel(PrepArgs a, PrepGradFdoArgs g3) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  PrepGradArgs g;
+  g.rec_grad = nullptr;
+  g.means = g3.means; g.log_scales = g3.log_scales; g.quats = g3.quats; g.logits = g3.logits; g.sh = g3.sh;
+  if (__ldg(a.touched + i) == 0u) {
+    store_zero_grad<DEG>(g, i);
+    return;
+  }
+  BwdCtx<DEG> x;
+  bwd_ctx<DEG>(a, i, x);
+  float yy = 0.0f;
+#pragma unroll
+  for (int k = 0; k < BwdCtx<DEG>::NB; ++k) yy = fmaf(x.Yb[k], x.Yb[k], yy);
+  float G[kGradW];
+  load_rec_grad(g3.rec_low, i, G);
+  PGrad pl = chain_grad<DEG>(a, x, G);
+  load_rec_grad(g3.rec_high, i, G);
+  PGrad ph = chain_grad<DEG>(a, x, G);
+  const float lh = pgrad_dot(pl, ph, yy);
+  if (lh < 0.0f) {
+    if (x.type == 0) {
+      pgrad_axpy(ph, -lh / pgrad_dot(pl, pl, yy), pl);  // Eq. 9
+    } else {
+      pgrad_axpy(pl, -lh / pgrad_dot(ph, ph, yy), ph);  // Eq. 10
+    }
+    if (g3.n_conflicts) atomicAdd(g3.n_conflicts, 1ull);
+  }
+  load_rec_grad(g3.rec_color, i, G);
+  PGrad r = chain_grad<DEG>(a, x, G);
+  pgrad_axpy(r, 1.0f, pl);
+  pgrad_axpy(r, 1.0f, ph);
+  store_pgrad<DEG>(g, i, r, x.Yb);
 }
 
 // ---------------------------------------------------------------------------
@@ -830,6 +951,18 @@ int launch_preprocess_bwd(const PrepArgs &a, const PrepGradArgs &g, int deg, cud
     case 1: preprocess_bwd_kernel<1><<<grid, 256, 0, s>>>(a, g); break;
     case 2: preprocess_bwd_kernel<2><<<grid, 256, 0, s>>>(a, g); break;
     default: preprocess_bwd_kernel<3><<<grid, 256, 0, s>>>(a, g); break;
+  }
+  return 0;
+}
+
+int launch_preprocess_bwd_fdo(const PrepArgs &a, const PrepGradFdoArgs &g, int deg, cudaStream_t s) {
+  if (a.n == 0) return 0;
+  const unsigned grid = (unsigned)((a.n + 255) / 256);
+  switch (deg) {
+    case 0: preprocess_bwd_fdo_kernel<0><<<grid, 256, 0, s>>>(a, g); break;
+    case 1: preprocess_bwd_fdo_kernel<1><<<grid, 256, 0, s>>>(a, g); break;
+    case 2: preprocess_bwd_fdo_kernel<2><<<grid, 256, 0, s>>>(a, g); break;
+    default: preprocess_bwd_fdo_kernel<3><<<grid, 256, 0, s>>>(a, g); break;
   }
   return 0;
 }
