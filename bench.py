@@ -56,6 +56,7 @@ def parse():
     p.add_argument("--cpu-sample-pixels", type=int, default=20000)
     p.add_argument("--profile-phases", action="store_true", default=True)
     p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--no-fdo", action="store_true")
     p.add_argument("--serving-seconds", type=float, default=5.0)
     p.add_argument("--serving-rate", type=float, default=200.0)
     return p.parse_args()
@@ -242,6 +243,62 @@ def launches_per_step(rast, exchange_steps, steps):
     bin_sort = 3 * (4 + passes) + 3 + 2 + 1 + (1 if rast.keys is not None else 0)
     per = 1 + bin_sort + 1 + 2
     return per * steps + exchange_steps
+
+
+def hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def run_fdo(args, dev, st, cam, cfg, target):
+    """Frequency-decoupled training step on the same workload: forward, the
+    Eq. 8 image losses (L1 + Haar L_low/L_high, one kernel) and the Algorithm 1
+    backward (three rgb replays + fused projection)."""
+    import torch
+    from paper_2512_02932_gb300 import Rasterizer, fdo
+    rast = Rasterizer(dev, sync_check=True)
+    ctr = torch.zeros(1, dtype=torch.int64, device=dev)
+    for _ in range(3):
+        fdo.fdo_step(st, cam, cfg, target, rast)
+    torch.cuda.synchronize()
+    reps = max(3, min(20, args.steps))
+    names = ["forward", "losses", "bwd_fdo"]
+    acc = {n: 0.0 for n in names}
+    s = torch.cuda.current_stream()
+    e_all0, e_all1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e_all0.record(s)
+    for k in range(reps):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(s)
+        maps = rast.forward(st, cam, cfg)
+        ev[1].record(s)
+        ls = fdo.image_losses(maps["rgb"], target, 1.0, fdo.LAMBDA_LOW, fdo.LAMBDA_HIGH)
+        ev[2].record(s)
+        if k == reps - 1:
+            ctr.zero_()
+        fdo.fdo_backward(rast, ls["g_l1"], ls["g_low"], ls["g_high"], d_conflicts=ctr if k == reps - 1 else None)
+        ev[3].record(s)
+        torch.cuda.synchronize()
+        for i, n in enumerate(names):
+            acc[n] += ev[i].elapsed_time(ev[i + 1])
+    e_all1.record(s)
+    torch.cuda.synchronize()
+    rast.check()
+    ph = {n: round(v / reps, 4) for n, v in acc.items()}
+    C_, H_, W_ = target.shape
+    loss_bytes = 4 * C_ * H_ * W_ * (2 + 3)  # image + target read, three gradient images written
+    gbs = loss_bytes / (ph["losses"] * 1e-3) / 1e9
+    peak, src = hbm_peak()
+    touched = int((rast.touched[: st.n] > 0).sum().item())
+    return {"workload": "same scene and view; loss = L1 + 0.2 L_low + 0.4 L_high (Haar level 1), Algorithm 1 backward",
+            "ms_per_step": round(sum(ph.values()), 4), "phases_ms": ph,
+            "image_losses": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+                             "frac": round(gbs / peak, 4), "bytes": loss_bytes, "peak_source": src},
+            "conflicting_fraction": round(int(ctr.item()) / max(touched, 1), 4),
+            "losses": [round(float(v), 6) for v in ls["loss"].cpu().tolist()]}
 
 
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "render_bwd_traffic_3M_1600x1064.md")
@@ -455,6 +512,11 @@ def main():
     serving = None
     if not args.no_serving and world == 1:
         serving = run_serving(args, dev, cfg)
+    fdo_line = None
+    if not args.no_fdo and world == 1:
+        dsc = SceneTensors(st.means.detach(), st.log_scales.detach(), st.quats.detach(),
+                           st.opacity_logits.detach(), st.sh.detach(), st.types, 3)
+        fdo_line = run_fdo(args, dev, dsc, cam, cfg, target)
     line = {
         "metric": METRIC, "value": round(ms_per_step, 4), "unit": "ms", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
@@ -467,6 +529,7 @@ def main():
                     "max": round(max(step_ms), 4), "first": round(step_ms[0], 4)},
         "roofline": roofline,
         "serving": serving,
+        "fdo": fdo_line,
         "gpu_launches": launches_per_step(rast, n_exchange[0], args.steps),
         "clocks": clk,
         "e2e": e2e,

@@ -223,7 +223,7 @@ int hgs_render_bwd_records(const hgs_scene *scene, const hgs_projected *proj, co
   if (scene->n == 0) return HGS_OK;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   cudaMemsetAsync(grad_ws, 0, sizeof(float) * kGradW * (size_t)scene->n, s);
-  RenderBwdArgs r;
+  RenderBwdArgs r{};
   r.rec = proj->rec;
   r.vals = bins->vals;
   r.ranges = bins->ranges;
@@ -298,35 +298,48 @@ int hgs_render_bwd_fdo(const hgs_scene *scene, const hgs_projected *proj, const 
                        const float *g_color, const float *g_low, const float *g_high, float *grad_ws,
                        hgs_scene_grad *out, unsigned long long *d_conflicts, int32_t *dev_err,
                        hgs_stream_t stream) {
-  if (!g_color || !g_low || !g_high || !out) return HGS_ERR_INVALID_ARG;
+  (void)dev_err;
   int st;
+  if (!g_color || !g_low || !g_high || !out) return HGS_ERR_INVALID_ARG;
   if ((st = scene_ok(scene)) != HGS_OK) return st;
-  const size_t stride = (size_t)kGradW * (size_t)scene->n;
-  const float *cots[3] = {g_color, g_low, g_high};
-  for (int k = 0; k < 3; ++k) {
-    hgs_image_grad dl = {cots[k], nullptr, nullptr, nullptr};
-    st = hgs_render_bwd_records(scene, proj, bins, cam, cfg, fwd, &dl, grad_ws ? grad_ws + k * stride : nullptr,
-                                dev_err, stream);
-    if (st != HGS_OK) return st;
-  }
   CamK ck;
   CfgK fk;
   if ((st = cam_to_kernel(cam, &ck)) != HGS_OK) return st;
   if ((st = cfg_to_kernel(cfg, &fk)) != HGS_OK) return st;
+  if ((st = proj_ok(proj, scene->n)) != HGS_OK) return st;
+  if (!bins || !bins->ranges || (scene->n > 0 && !bins->vals)) return HGS_ERR_INVALID_ARG;
+  if (!fwd || !fwd->T_final || !fwd->n_last) return HGS_ERR_INVALID_ARG;
+  if (scene->n > 0 && (!grad_ws || !aligned16(grad_ws))) return HGS_ERR_INVALID_ARG;
   if (scene->n > 0 && (!out->means || !out->log_scales || !out->quats || !out->opacity_logits || !out->sh ||
                        !aligned16(out->quats)))
     return HGS_ERR_INVALID_ARG;
   if ((scene->sh_degree == 1 || scene->sh_degree == 3) && scene->n > 0 && !aligned16(out->sh))
     return HGS_ERR_INVALID_ARG;
   if (scene->n == 0) return HGS_OK;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const size_t stride = (size_t)kGradW * (size_t)scene->n;
+  // the three cotangents in one replay: one evaluation and transmittance step
+  // per pair, three record-gradient sets
+  cudaMemsetAsync(grad_ws, 0, 3 * sizeof(float) * stride, s);
+  RenderBwdArgs r{};
+  r.rec = proj->rec;
+  r.vals = bins->vals;
+  r.ranges = bins->ranges;
+  r.cam = ck;
+  r.cfg = fk;
+  r.T_final = fwd->T_final;
+  r.n_last = fwd->n_last;
+  r.nc = 3;
+  r.g_rgbs[0] = g_color; r.g_rgbs[1] = g_low; r.g_rgbs[2] = g_high;
+  for (int k = 0; k < 3; ++k) r.rec_grads[k] = grad_ws + k * stride;
+  launch_render_bwd(r, s);
   PrepGradFdoArgs g;
   g.rec_color = grad_ws; g.rec_low = grad_ws + stride; g.rec_high = grad_ws + 2 * stride;
   g.means = out->means; g.log_scales = out->log_scales; g.quats = out->quats;
   g.logits = out->opacity_logits; g.sh = out->sh;
   g.n_conflicts = d_conflicts;
   hgs_projected pcopy = *proj;
-  launch_preprocess_bwd_fdo(prep_args(scene, ck, fk, &pcopy), g, scene->sh_degree,
-                            reinterpret_cast<cudaStream_t>(stream));
+  launch_preprocess_bwd_fdo(prep_args(scene, ck, fk, &pcopy), g, scene->sh_degree, s);
   return launched();
 }
 

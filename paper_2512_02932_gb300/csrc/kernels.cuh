@@ -105,6 +105,12 @@ struct RenderBwdArgs {
   const uint32_t *n_last;
   const float *g_rgb, *g_depth, *g_normal, *g_alpha;
   float *rec_grad;  // [n,16], zeroed before launch
+  // rgb-only cotangents replayed together (frequency-decoupled optimisation):
+  // nc sets, set k read from g_rgbs[k] and accumulated into rec_grads[k]
+  // ([n,16] each, zeroed).  nc = 0: the single set g_rgb / rec_grad above.
+  int nc;
+  const float *g_rgbs[3];
+  float *rec_grads[3];
 };
 
 int launch_render_fwd(const RenderArgs &a, cudaStream_t s);

@@ -15,9 +15,10 @@
 // odd last row or column lies outside every block and enters L1 only.  L1
 // is the mean |image - target| over all C H W pixels (sign(0) = 0).
 //
-// One thread per 2x2 block and channel; the block's two row pairs are read
-// as float2 when the width is even.  Sums go from registers through a warp
-// and block reduction to one double atomic per block and loss.
+// A block takes whole block-rows (a channel's row pair), its threads the 2x2
+// blocks along it, reading each block's two row pairs as float2 when the
+// width is even.  Sums go from registers through a warp and block reduction
+// to one double atomic per block and loss.
 #include <algorithm>
 
 #include "common.cuh"
@@ -48,9 +49,56 @@ __device__ __forceinline__ void block_add3(float s1, float sl, float sh, double 
   }
 }
 
+// The 2x2 block (bx) of block-row r (channel c, rows 2i, 2i+1): losses and
+// gradient images.
+__device__ __forceinline__ void haar_block(const LossArgs &a, size_t p0, bool vec, float g1, float gl, float gh,
+                                           float &s1, float &sl, float &sh) {
+  const size_t p1 = p0 + (size_t)a.W;
+  float d00, d01, d10, d11;
+  if (vec) {
+    const float2 x0 = __ldg(reinterpret_cast<const float2 *>(a.img + p0));
+    const float2 x1 = __ldg(reinterpret_cast<const float2 *>(a.img + p1));
+    const float2 y0 = __ldg(reinterpret_cast<const float2 *>(a.tgt + p0));
+    const float2 y1 = __ldg(reinterpret_cast<const float2 *>(a.tgt + p1));
+    d00 = x0.x - y0.x; d01 = x0.y - y0.y; d10 = x1.x - y1.x; d11 = x1.y - y1.y;
+  } else {
+    d00 = a.img[p0] - a.tgt[p0]; d01 = a.img[p0 + 1] - a.tgt[p0 + 1];
+    d10 = a.img[p1] - a.tgt[p1]; d11 = a.img[p1 + 1] - a.tgt[p1 + 1];
+  }
+  const float LL = 0.5f * (d00 + d01 + d10 + d11), LH = 0.5f * (d00 + d01 - d10 - d11);
+  const float HL = 0.5f * (d00 - d01 + d10 - d11), HH = 0.5f * (d00 - d01 - d10 + d11);
+  s1 += fabsf(d00) + fabsf(d01) + fabsf(d10) + fabsf(d11);
+  sl += LL * LL;
+  sh += LH * LH + HL * HL + HH * HH;
+  // d/dx of mean(band^2): 2 band / n times the pixel's coefficient (+-1/2)
+  if (a.g_l1) {
+    const float2 u0 = make_float2(g1 * sgnf(d00), g1 * sgnf(d01)), u1 = make_float2(g1 * sgnf(d10), g1 * sgnf(d11));
+    if (vec) { *reinterpret_cast<float2 *>(a.g_l1 + p0) = u0; *reinterpret_cast<float2 *>(a.g_l1 + p1) = u1; }
+    else { a.g_l1[p0] = u0.x; a.g_l1[p0 + 1] = u0.y; a.g_l1[p1] = u1.x; a.g_l1[p1 + 1] = u1.y; }
+  }
+  if (a.g_low) {
+    const float v = gl * LL;
+    if (vec) {
+      *reinterpret_cast<float2 *>(a.g_low + p0) = make_float2(v, v);
+      *reinterpret_cast<float2 *>(a.g_low + p1) = make_float2(v, v);
+    } else {
+      a.g_low[p0] = v; a.g_low[p0 + 1] = v; a.g_low[p1] = v; a.g_low[p1 + 1] = v;
+    }
+  }
+  if (a.g_high) {
+    const float2 u0 = make_float2(gh * (LH + HL + HH), gh * (LH - HL - HH));
+    const float2 u1 = make_float2(gh * (-LH + HL - HH), gh * (-LH - HL + HH));
+    if (vec) { *reinterpret_cast<float2 *>(a.g_high + p0) = u0; *reinterpret_cast<float2 *>(a.g_high + p1) = u1; }
+    else { a.g_high[p0] = u0.x; a.g_high[p0 + 1] = u0.y; a.g_high[p1] = u1.x; a.g_high[p1 + 1] = u1.y; }
+  }
+}
+
+// Blocks stride over block-rows (channel, row pair); threads over the 2x2
+// blocks of a row, so no index needs a division.
 __global__ void __launch_bounds__(256) image_losses_kernel(LossArgs a) {
   const int H2 = a.H / 2, W2 = a.W / 2;
-  const int64_t per_c = (int64_t)H2 * W2, nblk = (int64_t)a.C * per_c;
+  const int rows = a.C * H2;
+  const int64_t nblk = (int64_t)rows * W2;
   const double n_all = (double)a.C * a.H * a.W;
   const double n_low = (double)nblk, n_high = 3.0 * (double)nblk;
   const float g1 = (float)(a.w_l1 / n_all);
@@ -61,52 +109,15 @@ __global__ void __launch_bounds__(256) image_losses_kernel(LossArgs a) {
                      reinterpret_cast<uintptr_t>(a.g_l1) | reinterpret_cast<uintptr_t>(a.g_low) |
                      reinterpret_cast<uintptr_t>(a.g_high)) & 7u) == 0;
   float s1 = 0.f, sl = 0.f, sh = 0.f;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += stride) {
-    const int64_t c = b / per_c, r = b - c * per_c;
-    const int64_t i = r / W2, j = r - i * W2;
-    const size_t p0 = (size_t)((c * a.H + 2 * i) * a.W + 2 * j), p1 = p0 + (size_t)a.W;
-    float d00, d01, d10, d11;
-    if (vec) {
-      const float2 x0 = *reinterpret_cast<const float2 *>(a.img + p0);
-      const float2 x1 = *reinterpret_cast<const float2 *>(a.img + p1);
-      const float2 y0 = *reinterpret_cast<const float2 *>(a.tgt + p0);
-      const float2 y1 = *reinterpret_cast<const float2 *>(a.tgt + p1);
-      d00 = x0.x - y0.x; d01 = x0.y - y0.y; d10 = x1.x - y1.x; d11 = x1.y - y1.y;
-    } else {
-      d00 = a.img[p0] - a.tgt[p0]; d01 = a.img[p0 + 1] - a.tgt[p0 + 1];
-      d10 = a.img[p1] - a.tgt[p1]; d11 = a.img[p1 + 1] - a.tgt[p1 + 1];
-    }
-    const float LL = 0.5f * (d00 + d01 + d10 + d11), LH = 0.5f * (d00 + d01 - d10 - d11);
-    const float HL = 0.5f * (d00 - d01 + d10 - d11), HH = 0.5f * (d00 - d01 - d10 + d11);
-    s1 += fabsf(d00) + fabsf(d01) + fabsf(d10) + fabsf(d11);
-    sl += LL * LL;
-    sh += LH * LH + HL * HL + HH * HH;
-    // d/dx of mean(band^2): 2 band / n times the pixel's coefficient (+-1/2)
-    if (a.g_l1) {
-      const float2 u0 = make_float2(g1 * sgnf(d00), g1 * sgnf(d01)), u1 = make_float2(g1 * sgnf(d10), g1 * sgnf(d11));
-      if (vec) { *reinterpret_cast<float2 *>(a.g_l1 + p0) = u0; *reinterpret_cast<float2 *>(a.g_l1 + p1) = u1; }
-      else { a.g_l1[p0] = u0.x; a.g_l1[p0 + 1] = u0.y; a.g_l1[p1] = u1.x; a.g_l1[p1 + 1] = u1.y; }
-    }
-    if (a.g_low) {
-      const float v = gl * LL;
-      if (vec) {
-        *reinterpret_cast<float2 *>(a.g_low + p0) = make_float2(v, v);
-        *reinterpret_cast<float2 *>(a.g_low + p1) = make_float2(v, v);
-      } else {
-        a.g_low[p0] = v; a.g_low[p0 + 1] = v; a.g_low[p1] = v; a.g_low[p1 + 1] = v;
-      }
-    }
-    if (a.g_high) {
-      const float2 u0 = make_float2(gh * (LH + HL + HH), gh * (LH - HL - HH));
-      const float2 u1 = make_float2(gh * (-LH + HL - HH), gh * (-LH - HL + HH));
-      if (vec) { *reinterpret_cast<float2 *>(a.g_high + p0) = u0; *reinterpret_cast<float2 *>(a.g_high + p1) = u1; }
-      else { a.g_high[p0] = u0.x; a.g_high[p0 + 1] = u0.y; a.g_high[p1] = u1.x; a.g_high[p1 + 1] = u1.y; }
-    }
+  for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+    const int c = r / H2, i = r - c * H2;
+    const size_t row0 = ((size_t)c * a.H + 2 * (size_t)i) * a.W;
+    for (int j = threadIdx.x; j < W2; j += blockDim.x) haar_block(a, row0 + 2 * (size_t)j, vec, g1, gl, gh, s1, sl, sh);
   }
   // an odd last column (rows 0 .. 2 H2 - 1) and an odd last row (all columns)
-  const int64_t col_n = (a.W & 1) ? 2 * (int64_t)H2 : 0, row_n = (a.H & 1) ? (int64_t)a.W : 0;
+  const int col_n = (a.W & 1) ? 2 * H2 : 0, row_n = (a.H & 1) ? a.W : 0;
   const int64_t tail = (int64_t)a.C * (col_n + row_n);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tail; t += stride) {
     const int64_t c = t / (col_n + row_n), k = t - c * (col_n + row_n);
     const int64_t y = k < col_n ? k : a.H - 1, x = k < col_n ? a.W - 1 : k - col_n;
@@ -121,11 +132,12 @@ __global__ void __launch_bounds__(256) image_losses_kernel(LossArgs a) {
 }
 
 int launch_image_losses(const LossArgs &a, cudaStream_t s) {
-  const int64_t work = (int64_t)a.C * ((int64_t)(a.H / 2) * (a.W / 2) + a.H + a.W);
+  // one block per block-row up to a few resident waves (each block ends in
+  // three double atomics on the same three words, so not too many blocks)
+  const int64_t rows = (int64_t)a.C * (a.H / 2);
   int sms = 152, dev = 0;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t want = (work + 255) / 256;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * 8));
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(rows, (int64_t)sms * 4));
   image_losses_kernel<<<grid, 256, 0, s>>>(a);
   return 0;
 }

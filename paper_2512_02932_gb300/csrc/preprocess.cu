@@ -885,7 +885,7 @@ __device__ __forceinline__ void pgrad_axpy(PGrad &y, float s, const PGrad &x) {
 }
 
 template <int DEG>
-__global__ void __launch_bounds__(256) preprocess_bwd_fdo_kernel(PrepArgs a, PrepGradFdoArgs g3) {
+__global__ void __launch_bounds__(128) preprocess_bwd_fdo_kernel(PrepArgs a, PrepGradFdoArgs g3) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
   PrepGradArgs g;
@@ -957,12 +957,12 @@ int launch_preprocess_bwd(const PrepArgs &a, const PrepGradArgs &g, int deg, cud
 
 int launch_preprocess_bwd_fdo(const PrepArgs &a, const PrepGradFdoArgs &g, int deg, cudaStream_t s) {
   if (a.n == 0) return 0;
-  const unsigned grid = (unsigned)((a.n + 255) / 256);
+  const unsigned grid = (unsigned)((a.n + 127) / 128);
   switch (deg) {
-    case 0: preprocess_bwd_fdo_kernel<0><<<grid, 256, 0, s>>>(a, g); break;
-    case 1: preprocess_bwd_fdo_kernel<1><<<grid, 256, 0, s>>>(a, g); break;
-    case 2: preprocess_bwd_fdo_kernel<2><<<grid, 256, 0, s>>>(a, g); break;
-    default: preprocess_bwd_fdo_kernel<3><<<grid, 256, 0, s>>>(a, g); break;
+    case 0: preprocess_bwd_fdo_kernel<0><<<grid, 128, 0, s>>>(a, g); break;
+    case 1: preprocess_bwd_fdo_kernel<1><<<grid, 128, 0, s>>>(a, g); break;
+    case 2: preprocess_bwd_fdo_kernel<2><<<grid, 128, 0, s>>>(a, g); break;
+    default: preprocess_bwd_fdo_kernel<3><<<grid, 128, 0, s>>>(a, g); break;
   }
   return 0;
 }

@@ -523,23 +523,94 @@ __device__ __forceinline__ void reduce_record(float (&g)[16], bool is3d, int lan
   }
 }
 
-template <bool FULL>
-__global__ void __launch_bounds__(kRW * 32, 5) render_bwd_kernel(RenderBwdArgs a) {
-  __shared__ __align__(16) float4 sm[kRW][2][kCh * kRecF4];
-  __shared__ uint32_t sid[kRW][2][kCh];
-  const int tile = blockIdx.x;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int bx, by;
-  block_of(tile, a.cam.TX, warp, bx, by);
-  BwdPix s[2];
+// Pixel state of the rgb-only backward with NC cotangent sets replayed at
+// once: the transmittance is shared, each set keeps its cotangent and its
+// blended dot product S (as in BwdPix).
+template <int NC>
+struct RgbPix {
+  float px, py, T;
+  uint32_t last;
+  float dC[NC][3];
+  float S[NC];
+  bool inside;
+};
+
+template <int NC>
+__device__ __forceinline__ void load_rgb_pix(RgbPix<NC> &s, const RenderBwdArgs &a, const float *const (&g)[3], int x,
+                                             int y) {
+  s.px = (float)x + 0.5f;
+  s.py = (float)y + 0.5f;
+  s.inside = x < a.cam.W && y < a.cam.H;
+  s.T = 1.0f;
+  s.last = 0;
 #pragma unroll
-  for (int k = 0; k < 2; ++k) load_bwd_pix(s[k], a, bx + (lane & 7), by + (lane >> 3) + 4 * k);
+  for (int c = 0; c < NC; ++c) { s.dC[c][0] = s.dC[c][1] = s.dC[c][2] = 0.f; s.S[c] = 0.f; }
+  if (!s.inside) return;
+  const size_t HW = (size_t)a.cam.W * a.cam.H;
+  const size_t p = (size_t)y * a.cam.W + x;
+  s.T = a.T_final[p];
+  s.last = a.n_last[p];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    if (g[c]) { s.dC[c][0] = g[c][p]; s.dC[c][1] = g[c][p + HW]; s.dC[c][2] = g[c][p + 2 * HW]; }
+    s.S[c] = a.cfg.bg[0] * s.dC[c][0] + a.cfg.bg[1] * s.dC[c][1] + a.cfg.bg[2] * s.dC[c][2];
+  }
+}
+
+// pair_grad<false> for NC cotangent sets sharing one evaluation and one
+// transmittance step
+template <int NC>
+__device__ __forceinline__ void pair_grad_rgb(float (&g)[NC][16], RgbPix<NC> &s, const PairEval &e, const float4 &r0,
+                                              const float4 &r1, const float4 &r2, const float4 &r3,
+                                              const CfgK &cfg) {
+  const float c0 = r2.z, c1 = r2.w, c2 = r3.x;
+  const float Ti = __fdividef(s.T, 1.0f - e.at);
+  const float w = e.at * Ti;
+  s.T = Ti;
+  const bool open = e.araw <= cfg.alpha_max;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const float cd = fmaf(c0, s.dC[c][0], fmaf(c1, s.dC[c][1], c2 * s.dC[c][2]));
+    const float fsum = cd - s.S[c];
+    const float dat = Ti * fsum;
+    s.S[c] = fmaf(e.at, fsum, s.S[c]);
+    g[c][1] += w * s.dC[c][0]; g[c][2] += w * s.dC[c][1]; g[c][3] += w * s.dC[c][2];
+    float dd = 0.f;
+    if (open) {
+      g[c][0] += dat * e.g;
+      dd = dat * (-0.5f * e.at);
+    }
+    if (r0.w > 0.0f) {
+      const float ddx = dd * e.dx, ddy = dd * e.dy;
+      g[c][7] += ddx * e.dx;
+      g[c][8] += 2.0f * ddx * e.dy;
+      g[c][9] += ddy * e.dy;
+      g[c][4] -= dd * 2.0f * e.u * r1.x;
+      g[c][5] -= dd * 2.0f * (e.u * r1.y + e.v * r1.z);
+    } else {
+      const float du = 2.0f * e.u * dd, dv = 2.0f * e.v * dd;
+      const float dp0 = du * e.inv, dp1 = dv * e.inv;
+      const float dp2 = -(du * e.u + dv * e.v) * e.inv;
+      g[c][7] += dp0 * e.dx; g[c][8] += dp0 * e.dy;
+      g[c][9] += dp1 * e.dx; g[c][10] += dp1 * e.dy;
+      g[c][11] += dp2 * e.dx; g[c][12] += dp2 * e.dy;
+      g[c][4] -= dp0 * r1.x + dp1 * r1.z + dp2 * r2.x;
+      g[c][5] -= dp0 * r1.y + dp1 * r1.w + dp2 * r2.y;
+    }
+  }
+}
+
+// Reverse walk over a warp's part of one tile list (shared by both backward
+// kernels): stage chunks of 32 records from the back with cp.async, test
+// them against the warp's block, and call body(record, id, jrel) for each
+// record that passes, newest first.
+template <class Body>
+__device__ __forceinline__ void bwd_walk(const RenderBwdArgs &a, int tile, int warp, int lane, int bx, int by,
+                                         uint32_t wmax, float4 (*sm)[2][kCh * kRecF4],
+                                         uint32_t (*sid)[2][kCh], Body &&body) {
   const uint32_t start = a.ranges[2 * tile];
-  const uint32_t wmax = __reduce_max_sync(0xffffffffu, max(s[0].last, s[1].last));
-  if (wmax == 0) return;
   const float4 *rec = reinterpret_cast<const float4 *>(a.rec);
   const float fbx = (float)bx, fby = (float)by;
-
   uint32_t ce = start + wmax;
   uint32_t cs = ce - min((uint32_t)kCh, wmax);
   stage_chunk(rec, a.vals, cs, ce, &sm[warp][0][0], &sid[warp][0][0], lane);
@@ -559,20 +630,7 @@ __global__ void __launch_bounds__(kRW * 32, 5) render_bwd_kernel(RenderBwdArgs a
     while (mask) {
       const int jj = 31 - __clz(mask);
       mask &= ~(1u << jj);
-      const uint32_t jrel = cs + (uint32_t)jj - start;
-      const float4 *r = chunk + jj * kRecF4;
-      const float4 r0 = r[0], r1 = r[1], r2 = r[2], r4 = r[4];
-      PairEval e0, e1;
-      const bool c0 = s[0].inside && jrel < s[0].last && eval_pair(r0, r1, r2, r4, s[0].px, s[0].py, a.cfg, e0);
-      const bool c1 = s[1].inside && jrel < s[1].last && eval_pair(r0, r1, r2, r4, s[1].px, s[1].py, a.cfg, e1);
-      if (!__any_sync(0xffffffffu, c0 || c1)) continue;
-      float g[16];
-#pragma unroll
-      for (int k = 0; k < 16; ++k) g[k] = 0.f;
-      const float4 r3 = r[3];
-      if (c0) pair_grad<FULL>(g, s[0], e0, r0, r1, r2, r3, a.cfg);
-      if (c1) pair_grad<FULL>(g, s[1], e1, r0, r1, r2, r3, a.cfg);
-      reduce_record<FULL>(g, r0.w > 0.0f, lane, a.rec_grad + (size_t)sid[warp][buf][jj] * kGradW);
+      body(chunk + jj * kRecF4, sid[warp][buf][jj], cs + (uint32_t)jj - start);
     }
     if (!has_next) break;
     __syncwarp();
@@ -581,6 +639,68 @@ __global__ void __launch_bounds__(kRW * 32, 5) render_bwd_kernel(RenderBwdArgs a
     cs = ncs;
   }
   cp_async_wait<0>();
+}
+
+// rgb-only backward (image losses): NC cotangent sets replayed together
+template <int NC>
+__global__ void __launch_bounds__(kRW * 32, NC == 1 ? 5 : 4) render_bwd_rgb_kernel(RenderBwdArgs a) {
+  __shared__ __align__(16) float4 sm[kRW][2][kCh * kRecF4];
+  __shared__ uint32_t sid[kRW][2][kCh];
+  const int tile = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int bx, by;
+  block_of(tile, a.cam.TX, warp, bx, by);
+  RgbPix<NC> s[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) load_rgb_pix<NC>(s[k], a, a.g_rgbs, bx + (lane & 7), by + (lane >> 3) + 4 * k);
+  const uint32_t wmax = __reduce_max_sync(0xffffffffu, max(s[0].last, s[1].last));
+  if (wmax == 0) return;
+  bwd_walk(a, tile, warp, lane, bx, by, wmax, sm, sid, [&](const float4 *r, uint32_t id, uint32_t jrel) {
+    const float4 r0 = r[0], r1 = r[1], r2 = r[2], r4 = r[4];
+    PairEval e0, e1;
+    const bool c0 = s[0].inside && jrel < s[0].last && eval_pair(r0, r1, r2, r4, s[0].px, s[0].py, a.cfg, e0);
+    const bool c1 = s[1].inside && jrel < s[1].last && eval_pair(r0, r1, r2, r4, s[1].px, s[1].py, a.cfg, e1);
+    if (!__any_sync(0xffffffffu, c0 || c1)) return;
+    float g[NC][16];
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+      for (int k = 0; k < 16; ++k) g[c][k] = 0.f;
+    const float4 r3 = r[3];
+    if (c0) pair_grad_rgb<NC>(g, s[0], e0, r0, r1, r2, r3, a.cfg);
+    if (c1) pair_grad_rgb<NC>(g, s[1], e1, r0, r1, r2, r3, a.cfg);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) reduce_record<false>(g[c], r0.w > 0.0f, lane, a.rec_grads[c] + (size_t)id * kGradW);
+  });
+}
+
+// general backward: any of the rgb, depth, normal and alpha cotangents
+__global__ void __launch_bounds__(kRW * 32, 5) render_bwd_kernel(RenderBwdArgs a) {
+  __shared__ __align__(16) float4 sm[kRW][2][kCh * kRecF4];
+  __shared__ uint32_t sid[kRW][2][kCh];
+  const int tile = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int bx, by;
+  block_of(tile, a.cam.TX, warp, bx, by);
+  BwdPix s[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) load_bwd_pix(s[k], a, bx + (lane & 7), by + (lane >> 3) + 4 * k);
+  const uint32_t wmax = __reduce_max_sync(0xffffffffu, max(s[0].last, s[1].last));
+  if (wmax == 0) return;
+  bwd_walk(a, tile, warp, lane, bx, by, wmax, sm, sid, [&](const float4 *r, uint32_t id, uint32_t jrel) {
+    const float4 r0 = r[0], r1 = r[1], r2 = r[2], r4 = r[4];
+    PairEval e0, e1;
+    const bool c0 = s[0].inside && jrel < s[0].last && eval_pair(r0, r1, r2, r4, s[0].px, s[0].py, a.cfg, e0);
+    const bool c1 = s[1].inside && jrel < s[1].last && eval_pair(r0, r1, r2, r4, s[1].px, s[1].py, a.cfg, e1);
+    if (!__any_sync(0xffffffffu, c0 || c1)) return;
+    float g[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) g[k] = 0.f;
+    const float4 r3 = r[3];
+    if (c0) pair_grad<true>(g, s[0], e0, r0, r1, r2, r3, a.cfg);
+    if (c1) pair_grad<true>(g, s[1], e1, r0, r1, r2, r3, a.cfg);
+    reduce_record<true>(g, r0.w > 0.0f, lane, a.rec_grad + (size_t)id * kGradW);
+  });
 }
 
 // Prefer the largest shared-memory carve-out: the staging buffers decide how
@@ -610,14 +730,30 @@ int launch_render_batch(const BatchRenderArgs &b, int rows, cudaStream_t s) {
 int launch_render_bwd(const RenderBwdArgs &a, cudaStream_t s) {
   const int tiles = a.cam.TX * a.cam.TY;
   if (tiles <= 0) return 0;
-  static bool once = (prefer_shared((const void *)render_bwd_kernel<true>),
-                      prefer_shared((const void *)render_bwd_kernel<false>), true);
+  static bool once = (prefer_shared((const void *)render_bwd_kernel),
+                      prefer_shared((const void *)render_bwd_rgb_kernel<1>),
+                      prefer_shared((const void *)render_bwd_rgb_kernel<3>), true);
   (void)once;
-  // with only an rgb cotangent the depth/normal/alpha terms are identically 0
-  if (a.g_depth || a.g_normal || a.g_alpha)
-    render_bwd_kernel<true><<<tiles, kRW * 32, 0, s>>>(a);
+  if (a.nc == 0 && (a.g_depth || a.g_normal || a.g_alpha)) {
+    render_bwd_kernel<<<tiles, kRW * 32, 0, s>>>(a);
+    return 0;
+  }
+  // rgb cotangents only: their depth/normal/alpha terms are identically 0
+  RenderBwdArgs b = a;
+  if (b.nc == 0) {
+    b.nc = 1;
+    b.g_rgbs[0] = a.g_rgb;
+    b.rec_grads[0] = a.rec_grad;
+  }
+  if (b.nc == 3)
+    render_bwd_rgb_kernel<3><<<tiles, kRW * 32, 0, s>>>(b);
   else
-    render_bwd_kernel<false><<<tiles, kRW * 32, 0, s>>>(a);
+    for (int c = 0; c < b.nc; ++c) {
+      RenderBwdArgs one = b;
+      one.g_rgbs[0] = b.g_rgbs[c];
+      one.rec_grads[0] = b.rec_grads[c];
+      render_bwd_rgb_kernel<1><<<tiles, kRW * 32, 0, s>>>(one);
+    }
   return 0;
 }
 
