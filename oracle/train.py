@@ -50,27 +50,36 @@ def quat_to_rot(q):
                      [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
 
 
+def thresholds(size_thresh, min_opacity):
+    """The size and opacity thresholds mapped onto the stored parameters:
+    binary32 log(size_thresh) for the log-scales and logit(min_opacity) for
+    the opacity logits (both maps are monotonic, so the decisions are the
+    definitions' decisions, taken on the stored values)."""
+    return F32(np.log(size_thresh)), F32(np.log(min_opacity / (1.0 - min_opacity)))
+
+
 def densify_actions(grad_accum, vis_count, log_scales, opacity_logits, types, grad_thresh, size_thresh,
                     min_opacity):
     """Per primitive: 0 = remove, 1 = keep, 2 = keep + clone, 3 = split (two
-    new primitives replace it).  Decided in binary32."""
+    new primitives replace it).  Decided in binary32: the mean gradient as
+    one rounded division, size and opacity compared on the stored log-scale
+    and logit (`thresholds`)."""
     acc = np.asarray(grad_accum, F32)
     cnt = np.asarray(vis_count, F32)
     with np.errstate(divide="ignore", invalid="ignore"):
         mean_g = np.where(cnt > 0, acc / np.where(cnt > 0, cnt, F32(1)), F32(0)).astype(F32)
     ls = np.asarray(log_scales, F32)
     types = np.asarray(types)
-    # largest active scale: exp(max log-scale over the active axes)
-    act = np.where(types[:, None] == 1, ls, np.concatenate([ls[:, :2], np.full((len(ls), 1), -np.inf, F32)], 1))
-    size = np.exp(act.max(1).astype(np.float64)).astype(F32)
+    # largest active log-scale (a surfel's two in-plane axes)
+    lmax = np.where(types == 1, ls.max(1), ls[:, :2].max(1)).astype(F32)
     logits = np.asarray(opacity_logits, F32)
-    alpha = (1.0 / (1.0 + np.exp(-logits.astype(np.float64)))).astype(F32)
+    ls_t, lg_t = thresholds(size_thresh, min_opacity)
     hot = mean_g >= F32(grad_thresh)
-    big = size > F32(size_thresh)
+    big = lmax > ls_t
     act_code = np.ones(len(ls), np.int64)
     act_code[hot & ~big] = 2
     act_code[hot & big] = 3
-    act_code[(alpha < F32(min_opacity)) & (act_code == 1)] = 0
+    act_code[(logits < lg_t) & (act_code == 1)] = 0
     return act_code
 
 
