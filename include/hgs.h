@@ -350,6 +350,91 @@ int hgs_render_bwd_fdo(const hgs_scene *scene, const hgs_projected *proj, const 
                        hgs_scene_grad *out, unsigned long long *d_conflicts, int32_t *dev_err,
                        hgs_stream_t stream);
 
+/* ---------------------------------------------------------------------------
+ * Training loop (App. A: the 3DGS schedule with Adaptive Type Exchange every
+ * 500 iterations and densification every 100 iterations from 500 to 15K)
+ * ------------------------------------------------------------------------- */
+
+/* One parameter array and its Adam state: count float32 values each, device,
+ * caller-owned (16-byte aligned arrays take the float4 path).  period > 0
+ * splits the learning rate along rows: element k uses lr if k % period <
+ * head and lr_tail otherwise (e.g. an SH row's DC and higher-order
+ * coefficients); period = 0 uses lr throughout, otherwise period >= 4 and
+ * head <= period. */
+typedef struct {
+  float *param;
+  const float *grad;
+  float *m, *v;
+  int64_t count;
+  float lr;
+  int32_t period, head;
+  float lr_tail;
+} hgs_adam_group;
+
+/* hgs_adam_step -- one Adam update (step t >= 1, bias-corrected):
+ * m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+ * p -= (lr / (1 - b1^t)) m / (sqrt(v) / sqrt(1 - b2^t) + eps), per group.
+ * The coefficients 1 - b1, 1 - b2 and the bias corrections are formed in
+ * binary64 from the arguments and rounded once; the update is binary32.
+ * Errors: INVALID_ARG for ngroups < 0, NULL groups or arrays, or t < 1. */
+int hgs_adam_step(int32_t ngroups, const hgs_adam_group *groups, int32_t step, double beta1, double beta2,
+                  double eps, hgs_stream_t stream);
+
+/* hgs_grad_stats -- the statistic densification decides on: for every
+ * primitive binned in the last hgs_bin_sort (touched > 0), accum += the norm
+ * of its loss gradient with respect to the projected centre (pixels; record
+ * gradient slots 4 and 5 left in grad_ws by hgs_render_bwd) and count += 1.
+ * grad_ws: [n,16]; accum, count: [n] float32 device. */
+int hgs_grad_stats(int64_t n, const float *grad_ws, const hgs_projected *proj, float *accum, float *count,
+                   hgs_stream_t stream);
+
+/* Densification thresholds, on the stored parameters: mean gradient
+ * statistic (pixels), largest active log-scale, opacity logit. */
+typedef struct {
+  float grad_thresh;
+  float log_size_thresh;
+  float logit_min_opacity;
+} hgs_densify_cfg;
+
+/* Bytes of device workspace hgs_densify_plan needs for n primitives. */
+int hgs_densify_workspace(int64_t n, size_t *bytes);
+
+/* hgs_densify_plan -- the 3DGS densification decision per primitive, in
+ * binary32: with g = accum / count (0 if never binned), size = the largest
+ * active log-scale (a surfel's two in-plane axes):
+ *   g >= grad_thresh and size <= log_size_thresh -> 2 (keep and clone)
+ *   g >= grad_thresh and size >  log_size_thresh -> 3 (split into two)
+ *   otherwise, logit < logit_min_opacity         -> 0 (remove), else 1 (keep).
+ * actions: [n] int32; offsets: [n+1] int64, the first output row of each
+ * primitive (exclusive scan of its 0/1/2 rows), offsets[n] = the new count,
+ * also written to *d_new_n.  All device. */
+int hgs_densify_plan(const hgs_scene *scene, const float *accum, const float *count, const hgs_densify_cfg *cfg,
+                     int32_t *actions, int64_t *offsets, void *ws, size_t ws_bytes, int64_t *d_new_n,
+                     hgs_stream_t stream);
+
+/* Parameter arrays and Adam moments of a training scene (rows as in
+ * hgs_scene; moments[k] and moments[5+k] are m and v of the k-th of means,
+ * log-scales, quaternions, opacity logits, SH; any moment may be NULL). */
+typedef struct {
+  float *means, *log_scales, *quats, *opacity_logits, *sh;
+  uint8_t *types;
+  float *moments[10];
+} hgs_train_arrays;
+
+/* hgs_densify_apply -- write the densified scene into `out` (offsets[n]
+ * rows): a kept primitive's row and moments are copied; a clone adds an
+ * exact copy with zero moments; a split writes two rows centred at
+ * mu + R (s * z) (z from normals_z [n,2,3], a surfel's third scale taken as
+ * 0), with log-scales reduced by log 1.6 (a surfel's third kept), the other
+ * parameters copied and zero moments.  in and out must not overlap. */
+int hgs_densify_apply(int64_t n, int32_t sh_degree, const hgs_train_arrays *in, hgs_train_arrays *out,
+                      const float *normals_z, const int32_t *actions, const int64_t *offsets,
+                      hgs_stream_t stream);
+
+/* hgs_reset_opacity -- alpha <- min(alpha, ceiling) on the logits; the
+ * logits' Adam moments m, v (may be NULL) are zeroed. */
+int hgs_reset_opacity(int64_t n, float *opacity_logits, float ceiling, float *m, float *v, hgs_stream_t stream);
+
 /* hgs_exchange_types -- Adaptive Type Exchange (Sec. 3.2) in place.
  * ERANK mode: erank = exp(-sum p_i log p_i), p = q / |q|_1, q = (s_x^2,
  * s_y^2, s_z^2) (Eq. 3); a 3D Gaussian with erank < theta_e becomes 2D, a 2D

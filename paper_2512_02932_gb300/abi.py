@@ -74,6 +74,20 @@ class hgs_exchange_cfg(C.Structure):
     _fields_ = [("mode", C.c_int32), ("theta_e", C.c_float), ("mask", P)]
 
 
+class hgs_adam_group(C.Structure):
+    _fields_ = [("param", P), ("grad", P), ("m", P), ("v", P), ("count", C.c_int64), ("lr", C.c_float),
+                ("period", C.c_int32), ("head", C.c_int32), ("lr_tail", C.c_float)]
+
+
+class hgs_densify_cfg(C.Structure):
+    _fields_ = [("grad_thresh", C.c_float), ("log_size_thresh", C.c_float), ("logit_min_opacity", C.c_float)]
+
+
+class hgs_train_arrays(C.Structure):
+    _fields_ = [("means", P), ("log_scales", P), ("quats", P), ("opacity_logits", P), ("sh", P),
+                ("types", P), ("moments", P * 10)]
+
+
 SYMBOLS = {
     "hgs_default_config": (None, [C.POINTER(hgs_config)]),
     "hgs_status_string": (C.c_char_p, [C.c_int]),
@@ -105,6 +119,15 @@ SYMBOLS = {
     "hgs_render_bwd_fdo": (C.c_int, [C.POINTER(hgs_scene), C.POINTER(hgs_projected), C.POINTER(hgs_binning),
                                      C.POINTER(hgs_camera), C.POINTER(hgs_config), C.POINTER(hgs_image),
                                      P, P, P, P, C.POINTER(hgs_scene_grad), P, P, P]),
+    "hgs_adam_step": (C.c_int, [C.c_int32, C.POINTER(hgs_adam_group), C.c_int32, C.c_double, C.c_double,
+                                C.c_double, P]),
+    "hgs_grad_stats": (C.c_int, [C.c_int64, P, C.POINTER(hgs_projected), P, P, P]),
+    "hgs_densify_workspace": (C.c_int, [C.c_int64, C.POINTER(C.c_size_t)]),
+    "hgs_densify_plan": (C.c_int, [C.POINTER(hgs_scene), P, P, C.POINTER(hgs_densify_cfg), P, P, P, C.c_size_t,
+                                   P, P]),
+    "hgs_densify_apply": (C.c_int, [C.c_int64, C.c_int32, C.POINTER(hgs_train_arrays),
+                                    C.POINTER(hgs_train_arrays), P, P, P, P]),
+    "hgs_reset_opacity": (C.c_int, [C.c_int64, P, C.c_float, P, P, P]),
 }
 
 _lib = None
@@ -171,3 +194,9 @@ hgs_render_batch_workspace = _fwd("hgs_render_batch_workspace")
 hgs_render_batch = _fwd("hgs_render_batch")
 hgs_image_losses = _fwd("hgs_image_losses")
 hgs_render_bwd_fdo = _fwd("hgs_render_bwd_fdo")
+hgs_adam_step = _fwd("hgs_adam_step")
+hgs_grad_stats = _fwd("hgs_grad_stats")
+hgs_densify_workspace = _fwd("hgs_densify_workspace")
+hgs_densify_plan = _fwd("hgs_densify_plan")
+hgs_densify_apply = _fwd("hgs_densify_apply")
+hgs_reset_opacity = _fwd("hgs_reset_opacity")

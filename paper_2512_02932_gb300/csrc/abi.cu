@@ -343,6 +343,106 @@ int hgs_render_bwd_fdo(const hgs_scene *scene, const hgs_projected *proj, const 
   return launched();
 }
 
+int hgs_adam_step(int32_t ngroups, const hgs_adam_group *groups, int32_t step, double beta1, double beta2,
+                  double eps, hgs_stream_t stream) {
+  if (ngroups < 0 || (ngroups > 0 && !groups) || step < 1) return HGS_ERR_INVALID_ARG;
+  for (int k = 0; k < ngroups; ++k)
+    if (groups[k].count < 0 || groups[k].head < 0 || (groups[k].period != 0 && groups[k].period < 4) ||
+        groups[k].head > std::max(groups[k].period, 0) ||
+        (groups[k].count > 0 && (!groups[k].param || !groups[k].grad || !groups[k].m || !groups[k].v)))
+      return HGS_ERR_INVALID_ARG;
+  AdamArgs a;
+  a.beta1 = (float)beta1; a.beta2 = (float)beta2; a.eps = (float)eps;
+  a.omb1 = (float)(1.0 - beta1);
+  a.omb2 = (float)(1.0 - beta2);
+  a.bc1 = (float)(1.0 - std::pow(beta1, (double)step));
+  a.sqrt_bc2 = (float)std::sqrt(1.0 - std::pow(beta2, (double)step));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  for (int k = 0; k < ngroups; ++k) {
+    AdamGroup g;
+    g.param = groups[k].param; g.grad = groups[k].grad; g.m = groups[k].m; g.v = groups[k].v;
+    g.count = groups[k].count; g.lr = groups[k].lr;
+    g.period = groups[k].period; g.head = groups[k].head; g.lr_tail = groups[k].lr_tail;
+    launch_adam(a, g, s);
+  }
+  return launched();
+}
+
+int hgs_grad_stats(int64_t n, const float *grad_ws, const hgs_projected *proj, float *accum, float *count,
+                   hgs_stream_t stream) {
+  if (n < 0 || (n > 0 && (!grad_ws || !proj || !proj->touched || !accum || !count))) return HGS_ERR_INVALID_ARG;
+  launch_grad_stats(n, grad_ws, proj->touched, accum, count, reinterpret_cast<cudaStream_t>(stream));
+  return launched();
+}
+
+int hgs_densify_workspace(int64_t n, size_t *bytes) {
+  if (n < 0 || !bytes) return HGS_ERR_INVALID_ARG;
+  *bytes = 256 + sizeof(int64_t) * 1024 + sizeof(int32_t) * (size_t)(n > 0 ? n : 1);
+  return HGS_OK;
+}
+
+int hgs_densify_plan(const hgs_scene *scene, const float *accum, const float *count, const hgs_densify_cfg *cfg,
+                     int32_t *actions, int64_t *offsets, void *ws, size_t ws_bytes, int64_t *d_new_n,
+                     hgs_stream_t stream) {
+  int st;
+  if ((st = scene_ok(scene)) != HGS_OK) return st;
+  if (!cfg || !offsets || !d_new_n) return HGS_ERR_INVALID_ARG;
+  if (scene->n > 0 && (!accum || !count || !actions || !ws)) return HGS_ERR_INVALID_ARG;
+  size_t need = 0;
+  hgs_densify_workspace(scene->n, &need);
+  if (scene->n > 0 && (ws_bytes < need || !aligned16(ws))) return HGS_ERR_INVALID_ARG;
+  DensifyPlanArgs a;
+  a.n = scene->n;
+  a.grad_accum = accum; a.vis_count = count;
+  a.log_scales = scene->log_scales; a.logits = scene->opacity_logits; a.types = scene->types;
+  a.grad_thresh = cfg->grad_thresh; a.log_size_thresh = cfg->log_size_thresh;
+  a.logit_min_opacity = cfg->logit_min_opacity;
+  a.actions = actions;
+  a.offsets = offsets;
+  a.partial = reinterpret_cast<int64_t *>(static_cast<char *>(ws));
+  a.counts = reinterpret_cast<int32_t *>(static_cast<char *>(ws) + 256 + sizeof(int64_t) * 1024);
+  a.d_new_n = d_new_n;
+  launch_densify_plan(a, reinterpret_cast<cudaStream_t>(stream));
+  return launched();
+}
+
+static void train_arrays_k(const hgs_train_arrays *t, TrainArraysK *k) {
+  k->means = t->means; k->log_scales = t->log_scales; k->quats = t->quats;
+  k->logits = t->opacity_logits; k->sh = t->sh; k->types = t->types;
+  for (int i = 0; i < 10; ++i) k->moments[i] = t->moments[i];
+}
+
+int hgs_densify_apply(int64_t n, int32_t sh_degree, const hgs_train_arrays *in, hgs_train_arrays *out,
+                      const float *normals_z, const int32_t *actions, const int64_t *offsets,
+                      hgs_stream_t stream) {
+  if (n < 0 || sh_degree < 0 || sh_degree > 3 || !in || !out) return HGS_ERR_INVALID_ARG;
+  if (n == 0) return HGS_OK;
+  if (!normals_z || !actions || !offsets) return HGS_ERR_INVALID_ARG;
+  const float *req_in[6] = {in->means, in->log_scales, in->quats, in->opacity_logits, in->sh,
+                            reinterpret_cast<const float *>(in->types)};
+  const float *req_out[6] = {out->means, out->log_scales, out->quats, out->opacity_logits, out->sh,
+                             reinterpret_cast<const float *>(out->types)};
+  for (int k = 0; k < 6; ++k)
+    if (!req_in[k] || !req_out[k]) return HGS_ERR_INVALID_ARG;
+  DensifyApplyArgs a;
+  a.n = n;
+  a.sh_floats = (sh_degree + 1) * (sh_degree + 1) * 3;
+  train_arrays_k(in, &a.in);
+  train_arrays_k(out, &a.out);
+  a.normals_z = normals_z;
+  a.actions = actions;
+  a.offsets = offsets;
+  launch_densify_apply(a, reinterpret_cast<cudaStream_t>(stream));
+  return launched();
+}
+
+int hgs_reset_opacity(int64_t n, float *opacity_logits, float ceiling, float *m, float *v, hgs_stream_t stream) {
+  if (n < 0 || (n > 0 && !opacity_logits) || !(ceiling > 0.0f && ceiling < 1.0f)) return HGS_ERR_INVALID_ARG;
+  const float cap = (float)std::log((double)ceiling / (1.0 - (double)ceiling));
+  launch_reset_opacity(n, opacity_logits, cap, m, v, reinterpret_cast<cudaStream_t>(stream));
+  return launched();
+}
+
 }  // extern "C"
 
 namespace {

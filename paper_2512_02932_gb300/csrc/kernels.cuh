@@ -139,6 +139,55 @@ struct LossArgs {
 int launch_image_losses(const LossArgs &a, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
+// training loop
+// ---------------------------------------------------------------------------
+struct AdamArgs {
+  float beta1, beta2, eps;
+  float omb1, omb2;     // 1 - beta1, 1 - beta2 (formed in binary64, then rounded)
+  float bc1, sqrt_bc2;  // 1 - beta1^t, sqrt(1 - beta2^t)
+};
+struct AdamGroup {
+  float *param;
+  const float *grad;
+  float *m, *v;
+  int64_t count;
+  float lr;
+  int period, head;  // period > 0: element k uses lr if k % period < head, else lr_tail
+  float lr_tail;
+};
+int launch_adam(const AdamArgs &a, const AdamGroup &g, cudaStream_t s);
+int launch_grad_stats(int64_t n, const float *rec_grad, const uint32_t *touched, float *accum, float *count,
+                      cudaStream_t s);
+
+struct DensifyPlanArgs {
+  int64_t n;
+  const float *grad_accum, *vis_count, *log_scales, *logits;
+  const uint8_t *types;
+  float grad_thresh, log_size_thresh, logit_min_opacity;
+  int32_t *actions, *counts;  // [n]
+  int64_t *offsets;           // [n+1]
+  int64_t *partial;           // [1024] scan scratch
+  int64_t *d_new_n;
+};
+int launch_densify_plan(const DensifyPlanArgs &a, cudaStream_t s);
+
+struct TrainArraysK {
+  float *means, *log_scales, *quats, *logits, *sh;
+  uint8_t *types;
+  float *moments[10];  // Adam m of the five arrays, then v of the five
+};
+struct DensifyApplyArgs {
+  int64_t n;
+  int sh_floats;       // (l+1)^2 * 3
+  TrainArraysK in, out;
+  const float *normals_z;  // [n,2,3]
+  const int32_t *actions;
+  const int64_t *offsets;
+};
+int launch_densify_apply(const DensifyApplyArgs &a, cudaStream_t s);
+int launch_reset_opacity(int64_t n, float *logits, float cap, float *m, float *v, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
 // exchange
 // ---------------------------------------------------------------------------
 struct ExchangeArgs {
