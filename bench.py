@@ -57,6 +57,7 @@ def parse():
     p.add_argument("--profile-phases", action="store_true", default=True)
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--no-fdo", action="store_true")
+    p.add_argument("--no-train", action="store_true")
     p.add_argument("--serving-seconds", type=float, default=5.0)
     p.add_argument("--serving-rate", type=float, default=200.0)
     return p.parse_args()
@@ -301,6 +302,48 @@ def run_fdo(args, dev, st, cam, cfg, target):
             "losses": [round(float(v), 6) for v in ls["loss"].cpu().tolist()]}
 
 
+def run_train(args, dev, scene_np, cam, cfg, target):
+    """Full training iteration on the same workload through Trainer: forward,
+    L1 loss, backward, densification statistic and the fused Adam update of
+    all 59 floats per primitive (densify / reset / exchange disabled so the
+    primitive count stays fixed)."""
+    import torch
+    from paper_2512_02932_gb300 import SceneTensors
+    from paper_2512_02932_gb300.train import TrainConfig, Trainer
+    tc = TrainConfig(densify_from=10 ** 9, opacity_reset_every=0, exchange_from=10 ** 9)
+    tr = Trainer(SceneTensors.from_numpy(scene_np, dev), cfg, tc, device=dev)
+    for _ in range(3):
+        tr.step(cam, target)
+    torch.cuda.synchronize()
+    reps = max(3, min(20, args.steps))
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(reps):
+        tr.step(cam, target)
+    e1.record(s)
+    torch.cuda.synchronize()
+    it_ms = e0.elapsed_time(e1) / reps
+    # the optimizer alone, on the last gradients
+    grads = tr._keep_groups[1]
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(s)
+    for _ in range(reps):
+        tr.adam(grads)
+    a1.record(s)
+    torch.cuda.synchronize()
+    tr.rast.check()
+    adam_ms = a0.elapsed_time(a1) / reps
+    floats = sum(p.numel() for p in tr.params().values())
+    adam_bytes = 28 * floats  # read p, g, m, v; write p, m, v
+    gbs = adam_bytes / (adam_ms * 1e-3) / 1e9
+    peak, src = hbm_peak()
+    return {"workload": "same scene and view; Trainer.step: forward, L1, backward, statistic, Adam (59 floats/prim)",
+            "ms_per_iteration": round(it_ms, 4), "adam_ms": round(adam_ms, 4),
+            "adam": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(gbs / peak, 4), "bytes": adam_bytes, "peak_source": src}}
+
+
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "render_bwd_traffic_3M_1600x1064.md")
 TRAFFIC_SOURCES = [os.path.join(ROOT, "paper_2512_02932_gb300", "csrc", f) for f in ("render.cu", "common.cuh")]
 
@@ -517,6 +560,9 @@ def main():
         dsc = SceneTensors(st.means.detach(), st.log_scales.detach(), st.quats.detach(),
                            st.opacity_logits.detach(), st.sh.detach(), st.types, 3)
         fdo_line = run_fdo(args, dev, dsc, cam, cfg, target)
+    train_line = None
+    if not args.no_train and world == 1:
+        train_line = run_train(args, dev, scene, cam, cfg, target)
     line = {
         "metric": METRIC, "value": round(ms_per_step, 4), "unit": "ms", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
@@ -530,6 +576,7 @@ def main():
         "roofline": roofline,
         "serving": serving,
         "fdo": fdo_line,
+        "train": train_line,
         "gpu_launches": launches_per_step(rast, n_exchange[0], args.steps),
         "clocks": clk,
         "e2e": e2e,
