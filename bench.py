@@ -58,6 +58,7 @@ def parse():
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--no-fdo", action="store_true")
     p.add_argument("--no-train", action="store_true")
+    p.add_argument("--no-stress", action="store_true")
     p.add_argument("--serving-seconds", type=float, default=5.0)
     p.add_argument("--serving-rate", type=float, default=200.0)
     return p.parse_args()
@@ -344,6 +345,52 @@ def run_train(args, dev, scene_np, cam, cfg, target):
                      "frac": round(gbs / peak, 4), "bytes": adam_bytes, "peak_source": src}}
 
 
+def run_stress(args, dev, cfg):
+    """The stress workload: 6M primitives (90% surfels, heavy-tailed scales),
+    3840x2160, forward + backward through the ABI stages, with per-phase CUDA
+    events and the instance count."""
+    import torch
+    import synthetic as S
+    from paper_2512_02932_gb300 import Rasterizer, SceneTensors
+    scene, cam = S.stress_scene()
+    st = SceneTensors.from_numpy(scene, dev)
+    probe = Rasterizer(dev, sync_check=True)
+    probe.forward(st, cam, cfg)
+    K = probe.last_K
+    del probe
+    rast = Rasterizer(dev, capacity=int(K * 1.05) + (1 << 20), sync_check=False)
+    g = torch.sign(torch.randn((3, cam.height, cam.width), device=dev)) / (3 * cam.height * cam.width)
+    names = ["preprocess", "bin_sort", "render_fwd", "render_bwd", "preprocess_bwd"]
+    acc = {n: 0.0 for n in names}
+    s = torch.cuda.current_stream()
+    reps = 3
+    for k in range(reps + 1):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        ev[0].record(s)
+        rast.preprocess(st, cam, cfg)
+        ev[1].record(s)
+        rast.bin_sort(sync_check=False)
+        ev[2].record(s)
+        rast.render()
+        ev[3].record(s)
+        _, f_rec, f_prep = rast.backward(g, None, None, None, stages=True)
+        f_rec()
+        ev[4].record(s)
+        f_prep()
+        ev[5].record(s)
+        torch.cuda.synchronize()
+        if k > 0:
+            for i, n in enumerate(names):
+                acc[n] += ev[i].elapsed_time(ev[i + 1])
+    rast.check()
+    ph = {n: round(v / reps, 3) for n, v in acc.items()}
+    out = {"workload": "stress: 6M prims (90% 2D, log-scales -4.5 + 0.8 t_3), 3840x2160, fwd+bwd (rgb cotangent)",
+           "ms_per_step": round(sum(ph.values()), 3), "phases_ms": ph, "instances_K": K}
+    del rast, st
+    torch.cuda.empty_cache()
+    return out
+
+
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "render_bwd_traffic_3M_1600x1064.md")
 TRAFFIC_SOURCES = [os.path.join(ROOT, "paper_2512_02932_gb300", "csrc", f) for f in ("render.cu", "common.cuh")]
 
@@ -585,6 +632,9 @@ def main():
     train_line = None
     if not args.no_train and world == 1:
         train_line = run_train(args, dev, scene, cam, cfg, target)
+    stress_line = None
+    if not args.no_stress and world == 1:
+        stress_line = run_stress(args, dev, cfg)
     line = {
         "metric": METRIC, "value": round(ms_per_step, 4), "unit": "ms", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
@@ -599,6 +649,7 @@ def main():
         "serving": serving,
         "fdo": fdo_line,
         "train": train_line,
+        "stress": stress_line,
         "gpu_launches": launches_per_step(rast, n_exchange[0], args.steps),
         "clocks": clk,
         "e2e": e2e,

@@ -173,6 +173,9 @@ class Rasterizer:
     def preprocess(self, scene: SceneTensors, cam, cfg=None):
         self._ensure_prims(scene.n)
         self._ensure_image(cam.width, cam.height)
+        # the backward reads the same parameter arrays: keep them alive with
+        # the raw pointers the ABI structs hold
+        self._scene_ref = scene
         self._scene_s = scene.struct()
         self._cam_s = camera_struct(cam)
         self._cfg_s = config_struct(cfg)

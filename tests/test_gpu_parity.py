@@ -313,3 +313,17 @@ def test_autograd_function_matches_oracle(with_depth):
     got = _autograd_grads(scene, cam, loss)
     _, ref = AR.vjp(scene, cam, CFG, cot)
     assert_grads_match(got, ref)
+
+
+def test_backward_after_the_caller_dropped_its_scene_tensors():
+    """The Rasterizer keeps the arrays of its last forward alive for the
+    backward, so a temporary SceneTensors is safe."""
+    scene, cam = S.tiny_scene(6)
+    r = Rasterizer("cuda")
+    r.forward(SceneTensors.from_numpy(scene), cam, CFG)   # temporary, no reference kept
+    junk = [torch.full((1 << 20,), float("nan"), device="cuda") for _ in range(8)]  # reuse freed memory
+    g = r.backward(torch.ones((3, cam.height, cam.width), device="cuda"), None, None, None)
+    torch.cuda.synchronize()
+    del junk
+    for k, v in g.items():
+        assert torch.isfinite(v).all(), k
