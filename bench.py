@@ -241,8 +241,9 @@ def launches_per_step(rast, exchange_steps, steps):
     passes = (tile_bits + 7) // 8
     # 4 depth passes and the tile passes (chunk histogram, chunk scan,
     # scatter each), offsets scan (3), emit (2), range fix-up, optional
-    # 64-bit keys
-    bin_sort = 3 * (4 + passes) + 3 + 2 + 1 + (1 if rast.keys is not None else 0)
+    # 64-bit keys, the wide-rectangle path (5, launched every frame; they
+    # return at once when the frame takes the radix path)
+    bin_sort = 3 * (4 + passes) + 3 + 2 + 1 + (1 if rast.keys is not None else 0) + 5
     per = 1 + bin_sort + 1 + 2
     return per * steps + exchange_steps
 

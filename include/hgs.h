@@ -98,6 +98,10 @@ typedef struct {
   float dilation;  /* added to the diagonal of the projected 3D covariance */
   float bg[3];     /* background colour */
   int32_t tile;    /* tile edge in pixels; this build supports 16 only */
+  int32_t wide_rects; /* binning of rectangles over 256 tiles: 0 = the device picks,
+                         per frame, the counting path when they carry most of the
+                         instances; 1 = always the counting path; 2 = always the
+                         radix sort.  The lists are the same either way. */
 } hgs_config;
 
 /* Per-primitive output of hgs_preprocess (caller-allocated, n rows each):

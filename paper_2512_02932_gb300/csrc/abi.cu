@@ -38,6 +38,7 @@ int cam_to_kernel(const hgs_camera *c, CamK *k) {
 int cfg_to_kernel(const hgs_config *c, CfgK *k) {
   if (!c) return HGS_ERR_INVALID_ARG;
   if (c->tile != kTile) return HGS_ERR_UNSUPPORTED;
+  if (c->wide_rects < 0 || c->wide_rects > 2) return HGS_ERR_INVALID_ARG;
   if (!(c->alpha_min > 0.f) || !(c->alpha_max >= c->alpha_min) || !(c->alpha_max < 1.f) ||
       !(c->T_min > 0.f) || !(c->T_z > 0.f) || !(c->near_z > 0.f) || !(c->dilation >= 0.f) ||
       !std::isfinite(c->lambda_z) || !std::isfinite(c->theta_z))
@@ -101,6 +102,7 @@ void hgs_default_config(hgs_config *c) {
   c->dilation = 0.0f;
   c->bg[0] = c->bg[1] = c->bg[2] = 0.0f;
   c->tile = kTile;
+  c->wide_rects = 0;
 }
 
 const char *hgs_status_string(int s) {
@@ -144,7 +146,7 @@ int hgs_preprocess(const hgs_scene *scene, const hgs_camera *cam, const hgs_conf
 int hgs_bin_sort_workspace(int64_t n, int64_t capacity, int32_t tiles, size_t *bytes) {
   if (!bytes || n < 0 || capacity < 0 || tiles <= 0) return HGS_ERR_INVALID_ARG;
   BinWorkspace ws;
-  *bytes = bin_layout(nullptr, n, capacity, &ws);
+  *bytes = bin_layout(nullptr, n, capacity, tiles, &ws);
   return HGS_OK;
 }
 
@@ -162,11 +164,12 @@ int hgs_bin_sort(int64_t n, const hgs_projected *proj, const hgs_camera *cam, co
   if ((st = proj_ok(proj, n)) != HGS_OK) return st;
   if (!ws || !aligned16(ws)) return HGS_ERR_INVALID_ARG;
   BinWorkspace w;
-  const size_t need = bin_layout(ws, n, capacity, &w);
+  const size_t need = bin_layout(ws, n, capacity, ck.TX * ck.TY, &w);
   if (ws_bytes < need) return HGS_ERR_INVALID_ARG;
   BinArgs a;
   a.n = n;
   a.capacity = capacity;
+  a.wide_cfg = cfg->wide_rects;
   a.tiles = ck.TX * ck.TY;
   a.tile_bits = tile_bits_for(a.tiles);
   a.TX = ck.TX;
@@ -482,7 +485,7 @@ int batch_layout(int nreq, const hgs_request *reqs, int64_t capacity, BatchLayou
   L->off_ranges = off; off += al256((size_t)TXmax * rows * 8);
   L->off_sort = off;
   BinWorkspace w;
-  off += al256(bin_layout(nullptr, n, capacity, &w));
+  off += al256(bin_layout(nullptr, n, capacity, TXmax * rows, &w));
   L->bytes = off;
   return HGS_OK;
 }
@@ -554,10 +557,11 @@ int hgs_render_batch(int nreq, const hgs_request *reqs, const hgs_config *cfg, v
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   launch_preprocess_batch(bp, s);
   BinWorkspace w;
-  bin_layout(base + L.off_sort, L.total_n, capacity, &w);
+  bin_layout(base + L.off_sort, L.total_n, capacity, L.TXmax * L.rows, &w);
   BinArgs b;
   b.n = L.total_n;
   b.capacity = capacity;
+  b.wide_cfg = cfg->wide_rects;
   b.tiles = L.TXmax * L.rows;
   b.tile_bits = tile_bits_for(b.tiles);
   b.TX = L.TXmax;

@@ -21,10 +21,14 @@ namespace hgs {
 
 constexpr int kTileElems = kSortThreads * kSortItems;  // 2048
 constexpr uint32_t kNoDigit = 0xffffffffu;
+constexpr uint32_t kBigRect = 256;     // tiles: wider rectangles are deferred (k_emit_big) or take the wide path
+constexpr int64_t kWideMax = 1 << 21;  // most wide primitives the mask path takes
+constexpr size_t kMaskWordsMax = size_t(1) << 24;  // coverage-mask words (64 MiB)
+constexpr int kWideRangesMax = 16;                 // word ranges per strip of the mask path
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-size_t bin_layout(void *base, int64_t n, int64_t capacity, BinWorkspace *ws) {
+size_t bin_layout(void *base, int64_t n, int64_t capacity, int tiles, BinWorkspace *ws) {
   size_t off = 0;
   char *b = static_cast<char *>(base);
   auto take = [&](size_t bytes) -> void * {
@@ -33,12 +37,13 @@ size_t bin_layout(void *base, int64_t n, int64_t capacity, BinWorkspace *ws) {
     return p;
   };
   const size_t nn = (size_t)(n > 0 ? n : 1), cc = (size_t)(capacity > 0 ? capacity : 1);
+  const size_t tt = (size_t)(tiles > 0 ? tiles : 1);
   // the small head (counters, pass counters, histograms) is cleared with one memset
   ws->counters = (int64_t *)take(sizeof(int64_t) * 16 + sizeof(uint32_t) * 16 + sizeof(uint32_t) * 8 * 256);
   ws->tile_ctr = b ? reinterpret_cast<uint32_t *>(ws->counters + 16) : nullptr;
   ws->hist = b ? ws->tile_ctr + 16 : nullptr;
   ws->head_bytes = sizeof(int64_t) * 16 + sizeof(uint32_t) * 16 + sizeof(uint32_t) * 8 * 256;
-  ws->blk = (uint64_t *)take(sizeof(uint64_t) * kSortBlocks);
+  ws->blk = (uint64_t *)take(sizeof(uint64_t) * 3 * kSortBlocks);
   for (int k = 0; k < 2; ++k) {
     ws->dk[k] = (uint32_t *)take(sizeof(uint32_t) * nn);
     ws->dv[k] = (uint32_t *)take(sizeof(uint32_t) * nn);
@@ -48,6 +53,19 @@ size_t bin_layout(void *base, int64_t n, int64_t capacity, BinWorkspace *ws) {
   ws->tk[1] = (uint32_t *)take(sizeof(uint32_t) * cc);
   ws->tv = (uint32_t *)take(sizeof(uint32_t) * cc);
   ws->chist = (uint32_t *)take(sizeof(uint32_t) * 256 * kSortBlocks);
+  // wide path: the wide primitives' depth-order positions and ids, their
+  // coverage masks (TX + TY words per 32 wide primitives, a budget that
+  // scales with the tiles: TX + TY <= tiles + 1), the per-(range, tile)
+  // counts, the list lengths, the small instances' ranges.
+  const int64_t wmax = std::min<int64_t>((int64_t)nn, kWideMax);
+  ws->wide_max = wmax;
+  ws->wide_j = (uint32_t *)take(sizeof(uint32_t) * (size_t)wmax);
+  ws->wide_id = (uint32_t *)take(sizeof(uint32_t) * (size_t)wmax);
+  ws->mask_words = std::min(std::min(kMaskWordsMax, tt << 10), (tt + 1) * (((size_t)wmax + 31) / 32));
+  ws->masks = (uint32_t *)take(sizeof(uint32_t) * ws->mask_words);
+  ws->wide_cnt = (uint32_t *)take(sizeof(uint32_t) * tt * kWideRangesMax);
+  ws->wide_len = (uint32_t *)take(sizeof(uint32_t) * tt);
+  ws->small_ranges = (uint32_t *)take(sizeof(uint32_t) * 2 * tt);
   ws->bytes = off;
   return off;
 }
@@ -135,6 +153,12 @@ struct PassArgs {
   uint32_t *chist;                    // [256][kMaxChunks] chunk counts -> chunk offsets
   uint32_t *ranges_init;              // optional: set to (0xffffffff, 0) for `tiles` tiles
   int tiles;
+  // tile passes: *wide != 0 on the wide path.  The first pass then also sets
+  // wide_ranges_init like ranges_init; the last one sends the values to
+  // vals_out_wide and the ranges to ranges_wide and writes no keys.
+  const int64_t *wide;
+  uint32_t *wide_ranges_init;
+  uint32_t *vals_out_wide, *ranges_wide;
   uint32_t *keys_out, *vals_out;      // keys_out optional
   uint32_t *ranges;                   // optional (last tile pass): [start, end) per key
   int64_t *count_out;                 // optional: number of elements written
@@ -157,13 +181,16 @@ __device__ __forceinline__ void chunk_tiles(int64_t n, int64_t &t0, int64_t &t1)
 __global__ void __launch_bounds__(kSortThreads) k_chunk_hist(PassArgs a) {
   constexpr int W = kSortThreads / 32;
   __shared__ uint32_t h[W][256];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5;
   for (int k = tid; k < W * 256; k += kSortThreads) (&h[0][0])[k] = 0u;
   __syncthreads();
   const int64_t n = pass_n(a);
   if (a.ranges_init)
     for (int t = blockIdx.x * blockDim.x + tid; t < a.tiles; t += gridDim.x * blockDim.x)
       reinterpret_cast<uint2 *>(a.ranges_init)[t] = make_uint2(0xffffffffu, 0u);
+  if (a.wide_ranges_init && *a.wide)
+    for (int t = blockIdx.x * blockDim.x + tid; t < a.tiles; t += gridDim.x * blockDim.x)
+      reinterpret_cast<uint2 *>(a.wide_ranges_init)[t] = make_uint2(0xffffffffu, 0u);
   int64_t t0, t1;
   chunk_tiles(n, t0, t1);
   const int64_t e0 = t0 * kTileElems, e1 = min(n, t1 * kTileElems);
@@ -276,6 +303,11 @@ __device__ __forceinline__ void fetch_tile(const PassArgs &a, ScatterSmem &sm, i
 template <int BITS>
 __global__ void __launch_bounds__(kSortThreads) k_scatter(PassArgs a) {
   constexpr int W = kSortThreads / 32;
+  if (a.vals_out_wide && *a.wide) {
+    a.vals_out = a.vals_out_wide;
+    a.ranges = a.ranges_wide;
+    a.keys_out = nullptr;
+  }
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ScatterSmem &sm = *reinterpret_cast<ScatterSmem *>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -399,90 +431,174 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter(PassArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// instance offsets: exclusive scan of touched[] in depth order
+// instance offsets: exclusive scans of touched[] in depth order
 // ---------------------------------------------------------------------------
+// Three sums per primitive of the depth order: all its instances, the
+// instances of a rectangle of at most kBigRect tiles ("small"), and 1 for a
+// wider rectangle.  When wide rectangles carry most of the instances (or the
+// caller asks for it) they skip the radix sort: their per-tile lists are
+// written by counting (k_wide_*) and merged with the sorted small instances.
+
+__device__ __forceinline__ void split_counts(uint32_t t, uint64_t &all, uint64_t &small, uint64_t &wide) {
+  all = t;
+  small = t <= kBigRect ? t : 0u;
+  wide = t > kBigRect ? 1u : 0u;
+}
+
 __global__ void __launch_bounds__(kSortThreads)
     k_scan_partial(const uint32_t *__restrict__ ids, const uint32_t *__restrict__ touched,
                    const int64_t *d_n, uint64_t *__restrict__ blk) {
-  __shared__ uint64_t ws[kSortThreads / 32];
+  __shared__ uint64_t ws[3][kSortThreads / 32];
   const int tid = threadIdx.x;
   int64_t b0, b1;
   block_range(*d_n, b0, b1);
-  uint64_t s = 0;
-  for (int64_t j = b0 + tid; j < b1; j += kSortThreads) s += __ldg(touched + __ldg(ids + j));
+  uint64_t s[3] = {0, 0, 0};
+  for (int64_t j = b0 + tid; j < b1; j += kSortThreads) {
+    uint64_t x, y, z;
+    split_counts(__ldg(touched + __ldg(ids + j)), x, y, z);
+    s[0] += x; s[1] += y; s[2] += z;
+  }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  if ((tid & 31) == 0) ws[tid >> 5] = s;
+  for (int k = 0; k < 3; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_down_sync(0xffffffffu, s[k], o);
+    if ((tid & 31) == 0) ws[k][tid >> 5] = s[k];
+  }
   __syncthreads();
-  if (tid == 0) {
+  if (tid < 3) {
     uint64_t t = 0;
-    for (int w = 0; w < kSortThreads / 32; ++w) t += ws[w];
-    blk[blockIdx.x] = t;
+    for (int w = 0; w < kSortThreads / 32; ++w) t += ws[tid][w];
+    blk[(size_t)tid * kSortBlocks + blockIdx.x] = t;
   }
 }
 
-// single block: exclusive scan of the block partials, K, capacity check
+// single block: exclusive scans of the block partials; K, the path, and the
+// capacity check.  counters: 1 = K, 2 = overflow, 4 = wide path, 5 = small
+// instances, 6 = wide primitives B, 7 = instances the radix sort takes.
+// The wide path is taken when it is allowed (B within wide_cap) and asked
+// for (wide_cfg 1), or, under wide_cfg 0, when the wide instances outnumber
+// both 8x the (32 tiles, 32 wide primitives) mask visits it costs and half
+// the small instances it re-reads in the merge.
 __global__ void __launch_bounds__(1024)
-    k_scan_top(uint64_t *__restrict__ blk, int nblocks, int64_t capacity, int64_t *counters,
-               int64_t *d_count, int32_t *dev_err) {
-  __shared__ uint64_t wsum[32];
+    k_scan_top(uint64_t *__restrict__ blk, int nblocks, int64_t capacity, int wide_cfg, int64_t wide_cap,
+               int tiles, int64_t *counters, int64_t *d_count, int32_t *dev_err) {
+  __shared__ uint64_t wsum[3][32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint64_t v = tid < nblocks ? blk[tid] : 0ull;
-  uint64_t incl = v;
+  uint64_t v[3], incl[3];
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint64_t u = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += u;
+  for (int k = 0; k < 3; ++k) {
+    v[k] = tid < nblocks ? blk[(size_t)k * kSortBlocks + tid] : 0ull;
+    incl[k] = v[k];
   }
-  if (lane == 31) wsum[warp] = incl;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const uint64_t u = __shfl_up_sync(0xffffffffu, incl[k], o);
+      if (lane >= o) incl[k] += u;
+    }
+  if (lane == 31)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) wsum[k][warp] = incl[k];
   __syncthreads();
-  uint64_t wb = 0;
-  for (int w = 0; w < warp; ++w) wb += wsum[w];
-  if (tid < nblocks) blk[tid] = wb + incl - v;
-  if (tid == 1023) {
-    const uint64_t K = wb + incl;
+  uint64_t tot[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    uint64_t wb = 0, all = 0;
+    for (int w = 0; w < 32; ++w) {
+      if (w < warp) wb += wsum[k][w];
+      all += wsum[k][w];
+    }
+    if (tid < nblocks) blk[(size_t)k * kSortBlocks + tid] = wb + incl[k] - v[k];
+    tot[k] = all;
+  }
+  if (tid == 0) {
+    const uint64_t K = tot[0], Ks = tot[1], B = tot[2], Kw = K - Ks;
     counters[1] = (int64_t)K;
     if (d_count) *d_count = (int64_t)K;
     const bool over = (int64_t)K > capacity || K > 0xffffffffull;
     counters[2] = over ? 1 : 0;
     if (over) set_error(dev_err, HGS_ERR_CAPACITY);
+    const uint64_t visits = (uint64_t)tiles * ((B + 31) / 32) / 32;
+    const bool fits = B > 0 && (int64_t)B <= wide_cap;
+    const bool wide = fits && (wide_cfg == 1 || (wide_cfg == 0 && Kw > 8 * visits && 2 * Kw > Ks));
+    counters[4] = wide ? 1 : 0;
+    counters[5] = (int64_t)Ks;
+    counters[6] = (int64_t)B;
+    counters[7] = wide ? (int64_t)Ks : (int64_t)K;
+  }
+}
+
+// Offsets of each primitive's instances in the radix sort's input: all its
+// instances, or on the wide path only those of small rectangles, where the
+// wide primitives' depth-order positions are listed too (wide_j), and every
+// position j gets the number of wide primitives ahead of it (kpos).
+template <bool WIDE>
+__device__ __forceinline__ void scan_final_body(const uint32_t *__restrict__ ids,
+                                                const uint32_t *__restrict__ touched, const int64_t *counters,
+                                                const uint64_t *__restrict__ blk, uint32_t *__restrict__ offs,
+                                                uint32_t *__restrict__ wide_j, uint32_t *__restrict__ kpos) {
+  constexpr int NS = WIDE ? 2 : 1;
+  __shared__ uint32_t wsum[NS][kSortThreads / 32];
+  __shared__ uint32_t carry[NS];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int64_t b0, b1;
+  block_range(counters[0], b0, b1);
+  if (tid == 0) {
+    carry[0] = (uint32_t)blk[(size_t)(WIDE ? 1 : 0) * kSortBlocks + blockIdx.x];
+    if (WIDE) carry[NS - 1] = (uint32_t)blk[(size_t)2 * kSortBlocks + blockIdx.x];
+  }
+  __syncthreads();
+  for (int64_t tb = b0; tb < b1; tb += kSortThreads) {
+    const int64_t j = tb + tid;
+    const uint32_t t = j < b1 ? __ldg(touched + __ldg(ids + j)) : 0u;
+    uint32_t v[NS];
+    v[0] = WIDE ? (t <= kBigRect ? t : 0u) : t;
+    if (WIDE) v[NS - 1] = t > kBigRect ? 1u : 0u;
+    uint32_t incl[NS];
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      incl[k] = v[k];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, incl[k], o);
+        if (lane >= o) incl[k] += u;
+      }
+      if (lane == 31) wsum[k][warp] = incl[k];
+    }
+    __syncthreads();
+    uint32_t wb[NS], all[NS];
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      wb[k] = 0;
+      all[k] = 0;
+#pragma unroll
+      for (int w = 0; w < kSortThreads / 32; ++w) {
+        if (w < warp) wb[k] += wsum[k][w];
+        all[k] += wsum[k][w];
+      }
+    }
+    if (j < b1) {
+      offs[j] = carry[0] + wb[0] + incl[0] - v[0];
+      if (WIDE) {
+        const uint32_t before = carry[NS - 1] + wb[NS - 1] + incl[NS - 1] - v[NS - 1];
+        kpos[j] = before;  // wide primitives ahead of j in depth order
+        if (v[NS - 1]) wide_j[before] = (uint32_t)j;
+      }
+    }
+    __syncthreads();
+    if (tid < NS) carry[tid] += all[tid];
+    __syncthreads();
   }
 }
 
 __global__ void __launch_bounds__(kSortThreads)
     k_scan_final(const uint32_t *__restrict__ ids, const uint32_t *__restrict__ touched,
                  const int64_t *counters, const uint64_t *__restrict__ blk,
-                 uint32_t *__restrict__ offs) {
-  __shared__ uint32_t wsum[kSortThreads / 32];
-  __shared__ uint32_t carry;
+                 uint32_t *__restrict__ offs, uint32_t *__restrict__ wide_j, uint32_t *__restrict__ kpos) {
   if (counters[2]) return;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  int64_t b0, b1;
-  block_range(counters[0], b0, b1);
-  if (tid == 0) carry = (uint32_t)blk[blockIdx.x];
-  __syncthreads();
-  for (int64_t tb = b0; tb < b1; tb += kSortThreads) {
-    const int64_t j = tb + tid;
-    const uint32_t t = j < b1 ? __ldg(touched + __ldg(ids + j)) : 0u;
-    uint32_t incl = t;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += u;
-    }
-    if (lane == 31) wsum[warp] = incl;
-    __syncthreads();
-    uint32_t wb = 0, all = 0;
-#pragma unroll
-    for (int w = 0; w < kSortThreads / 32; ++w) {
-      if (w < warp) wb += wsum[w];
-      all += wsum[w];
-    }
-    if (j < b1) offs[j] = carry + wb + incl - t;
-    __syncthreads();
-    if (tid == 0) carry += all;
-    __syncthreads();
-  }
+  if (counters[4]) scan_final_body<true>(ids, touched, counters, blk, offs, wide_j, kpos);
+  else scan_final_body<false>(ids, touched, counters, blk, offs, wide_j, kpos);
 }
 
 // ---------------------------------------------------------------------------
@@ -490,15 +606,16 @@ __global__ void __launch_bounds__(kSortThreads)
 // primitives in depth order.  A warp takes 32 consecutive primitives, whose
 // instances form one contiguous output range; lanes write that range in
 // order (coalesced), each output slot finding its owner lane by a binary
-// search over the lanes' exclusive prefix.
+// search over the lanes' exclusive prefix.  Rectangles over kBigRect tiles
+// are deferred to k_emit_big; on the wide path they are skipped (the mask
+// path lists them) and the value is the depth-order position, which the
+// merge compares.
 // ---------------------------------------------------------------------------
-constexpr uint32_t kBigRect = 256;  // tiles; larger rectangles go to k_emit_big
-
-__global__ void __launch_bounds__(256)
-    k_emit(const uint32_t *__restrict__ ids, const uint32_t *__restrict__ offs,
-           const uint16_t *__restrict__ rect, int64_t *counters, int TX,
-           uint32_t *__restrict__ tkeys, uint32_t *__restrict__ tvals, uint32_t *__restrict__ bigq) {
-  if (counters[2]) return;
+template <bool WIDE>
+__device__ __forceinline__ void emit_body(const uint32_t *__restrict__ ids, const uint32_t *__restrict__ offs,
+                                          const uint16_t *__restrict__ rect, int64_t *counters, int TX,
+                                          uint32_t *__restrict__ tkeys, uint32_t *__restrict__ tvals,
+                                          uint32_t *__restrict__ bigq) {
   const int64_t M = counters[0];
   const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -513,11 +630,14 @@ __global__ void __launch_bounds__(256)
       ty0 = r.y & 0xffffu;
       w = (r.x >> 16) - tx0 + 1;
       cnt = w * ((r.y >> 16) - ty0 + 1);
-      if (cnt > kBigRect) {  // deferred: written by one block in k_emit_big
-        const unsigned long long slot = atomicAdd(reinterpret_cast<unsigned long long *>(&counters[3]), 1ull);
-        bigq[slot] = (uint32_t)j;
+      if (cnt > kBigRect) {
+        if (!WIDE) {
+          const unsigned long long slot = atomicAdd(reinterpret_cast<unsigned long long *>(&counters[3]), 1ull);
+          bigq[slot] = (uint32_t)j;
+        }
         cnt = 0;
       }
+      if (WIDE) p = (uint32_t)j;
     }
     // exclusive prefix of the small counts within the warp
     uint32_t incl = cnt;
@@ -557,13 +677,22 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+__global__ void __launch_bounds__(256)
+    k_emit(const uint32_t *__restrict__ ids, const uint32_t *__restrict__ offs,
+           const uint16_t *__restrict__ rect, int64_t *counters, int TX,
+           uint32_t *__restrict__ tkeys, uint32_t *__restrict__ tvals, uint32_t *__restrict__ bigq) {
+  if (counters[2]) return;
+  if (counters[4]) emit_body<true>(ids, offs, rect, counters, TX, tkeys, tvals, bigq);
+  else emit_body<false>(ids, offs, rect, counters, TX, tkeys, tvals, bigq);
+}
+
 // one block per deferred large rectangle
 __global__ void __launch_bounds__(256)
     k_emit_big(const uint32_t *__restrict__ ids, const uint32_t *__restrict__ offs,
                const uint16_t *__restrict__ rect, const int64_t *counters, int TX,
                const uint32_t *__restrict__ bigq, uint32_t *__restrict__ tkeys,
                uint32_t *__restrict__ tvals) {
-  if (counters[2]) return;
+  if (counters[2] || counters[4]) return;
   const int64_t nbig = counters[3];
   for (int64_t b = blockIdx.x; b < nbig; b += gridDim.x) {
     const uint32_t j = bigq[b];
@@ -591,7 +720,7 @@ __global__ void __launch_bounds__(256) k_ranges_fix(uint32_t *__restrict__ range
 __global__ void __launch_bounds__(256)
     k_keys64(const uint32_t *__restrict__ tkeys, const uint32_t *__restrict__ vals,
              const uint32_t *__restrict__ depth_key, const int64_t *counters, uint64_t *__restrict__ keys) {
-  if (counters[2]) return;
+  if (counters[2] || counters[4]) return;
   const int64_t K = counters[1];
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < K;
        k += (int64_t)gridDim.x * blockDim.x)
@@ -599,6 +728,384 @@ __global__ void __launch_bounds__(256)
 }
 
 // ---------------------------------------------------------------------------
+// wide path: the wide rectangles' tile lists from coverage masks
+// ---------------------------------------------------------------------------
+// The wide primitives (rectangles over kBigRect tiles) are numbered
+// k = 0..B-1 in depth order and grouped in words of 32.  For every word
+// there is one 32-bit mask per tile column, saying which of its rectangles
+// span that column, and one per tile row; the word's primitives that cover
+// tile (tx, ty) are the bits of colmask[tx] & rowmask[ty], in depth order.
+// A warp takes a strip of 32 tiles of one row (a lane per tile) and a range
+// of words; walking the words in order, each lane appends its tile's
+// covering primitives to a shared-memory buffer, with the tile's small
+// instances (as the radix sort ordered them) slotted in by kappa, the number
+// of wide primitives ahead of them in depth order.  Full buffers are copied
+// out with coalesced stores.  A counting pass over the same (strip, range)
+// items gives every range its output offset within the tile's list.
+// Masks are stored word-major ([word][tx], then [word][ty]), so one warp's
+// column masks are 32 consecutive words and its row mask one broadcast word.
+constexpr int kWB = 8;              // words per prefetched batch
+constexpr int kWBuf = 96;           // entries per lane buffer
+constexpr int kWBufStride = kWBuf + 1;
+constexpr int kWideWarps = 2;
+
+struct WideArgs {
+  const uint32_t *ids;       // depth order -> primitive id
+  const uint32_t *wide_j;    // [B] depth-order positions of the wide primitives, ascending
+  uint32_t *wide_id;         // [B] their primitive ids
+  const uint32_t *kpos;      // [M] wide primitives ahead of each depth-order position
+  const uint16_t *rect;
+  int64_t *counters;         // 4 = wide path, 5 = small instances, 6 = B, 8 = next write item
+  int TX, TY, tiles, strips, R;
+  uint32_t *masks;           // [NW][TX] column masks, then [NW][TY] row masks
+  uint32_t *cnt;             // [R][tiles] wide instances per (range, tile) -> exclusive over ranges
+  uint32_t *len;             // [tiles] list lengths
+  uint32_t *small;           // small instances by tile: depth-order positions -> primitive ids
+  uint32_t *kappa;           // [Ks] their kappa
+  const uint32_t *small_ranges;  // [tiles][2], (0xffffffff, 0) when empty
+  uint32_t *vals;            // [K] output: primitive ids
+  uint64_t *keys;            // optional [K] output
+  const uint32_t *depth_key;
+  uint32_t *ranges;          // [tiles][2] output
+};
+
+__device__ __forceinline__ int wide_words(const int64_t *counters) { return (int)((counters[6] + 31) / 32); }
+// words per range: a multiple of the batch
+__device__ __forceinline__ int wide_wpr(int NW, int R) { return ((NW + R - 1) / R + kWB - 1) / kWB * kWB; }
+
+// One block per 1024 wide primitives (32 words): ids and masks.
+__global__ void __launch_bounds__(256) k_wide_build(WideArgs a) {
+  __shared__ uint32_t xr[32 * 33], yr[32 * 33];  // packed (lo | hi << 16) spans, a padded row per word
+  if (a.counters[2] || !a.counters[4]) return;
+  const int64_t B = a.counters[6];
+  const int NW = wide_words(a.counters);
+  const int64_t groups = (B + 1023) / 1024;
+  const int tid = threadIdx.x;
+  uint32_t *colT = a.masks, *rowT = a.masks + (size_t)NW * a.TX;
+  for (int64_t c = blockIdx.x; c < groups; c += gridDim.x) {
+    for (int i = tid; i < 1024; i += 256) {
+      const int64_t k = c * 1024 + i;
+      uint32_t rx = 0x0000ffffu, ry = 0x0000ffffu;  // lo 0xffff > hi 0: spans nothing
+      if (k < B) {
+        const uint32_t p = __ldg(a.ids + __ldg(a.wide_j + k));
+        a.wide_id[k] = p;
+        const uint2 r = __ldg(reinterpret_cast<const uint2 *>(a.rect) + p);
+        rx = r.x;
+        ry = r.y;
+      }
+      xr[(i >> 5) * 33 + (i & 31)] = rx;
+      yr[(i >> 5) * 33 + (i & 31)] = ry;
+    }
+    __syncthreads();
+    const int nw = (int)(NW - c * 32 < 32 ? NW - c * 32 : 32);
+    for (int wl = 0; wl < nw; ++wl) {
+      const size_t w = (size_t)c * 32 + wl;
+      const uint32_t *xs = xr + wl * 33, *ys = yr + wl * 33;
+      for (int e = tid; e < a.TX + a.TY; e += 256) {
+        const bool col = e < a.TX;
+        const uint32_t v = col ? (uint32_t)e : (uint32_t)(e - a.TX);
+        const uint32_t *sp = col ? xs : ys;
+        uint32_t m = 0;
+#pragma unroll 8
+        for (int b = 0; b < 32; ++b) {
+          const uint32_t q = sp[b];
+          m |= (uint32_t)((q & 0xffffu) <= v && v <= (q >> 16)) << b;
+        }
+        if (col) colT[w * a.TX + v] = m;
+        else rowT[w * a.TY + v] = m;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ void strip_of(const WideArgs &a, int item, int &r, int &ty, int &tx) {
+  const int spr = (a.TX + 31) / 32;  // strips per row
+  const int st = item / a.R;
+  r = item - st * a.R;
+  ty = st / spr;
+  tx = (st - ty * spr) * 32 + (int)(threadIdx.x & 31);
+}
+
+// Counting pass, a warp per (strip, range): cnt[r][t] = covering wide
+// primitives of the range's words.
+__global__ void __launch_bounds__(256) k_wide_count(WideArgs a) {
+  if (a.counters[2] || !a.counters[4]) return;
+  const int NW = wide_words(a.counters), wpr = wide_wpr(NW, a.R);
+  const uint32_t *colT = a.masks, *rowT = a.masks + (size_t)NW * a.TX;
+  const int items = a.strips * a.R;
+  const int nwarps = gridDim.x * (blockDim.x >> 5);
+  for (int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); item < items; item += nwarps) {
+    int r, ty, tx;
+    strip_of(a, item, r, ty, tx);
+    const int w0 = r * wpr, w1 = min(NW, w0 + wpr);
+    const bool ok = tx < a.TX;
+    uint32_t c = 0;
+    for (int w = w0; w < w1; w += kWB) {
+      uint32_t cm[kWB], rm[kWB];
+#pragma unroll
+      for (int i = 0; i < kWB; ++i) {
+        const bool in = ok && w + i < w1;
+        cm[i] = in ? __ldg(colT + (size_t)(w + i) * a.TX + tx) : 0u;
+        rm[i] = in ? __ldg(rowT + (size_t)(w + i) * a.TY + ty) : 0u;
+      }
+#pragma unroll
+      for (int i = 0; i < kWB; ++i) c += __popc(cm[i] & rm[i]);
+    }
+    if (ok) a.cnt[(size_t)r * a.tiles + (size_t)ty * a.TX + tx] = c;
+  }
+}
+
+// Per tile: the ranges' counts -> exclusive offsets, and the list length
+// (wide + small).  Per small instance: its kappa, and the depth-order
+// position replaced by the primitive id.
+__global__ void __launch_bounds__(256) k_wide_tiles(WideArgs a) {
+  if (a.counters[2] || !a.counters[4]) return;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.tiles; t += stride) {
+    uint32_t run = 0;
+    for (int r = 0; r < a.R; ++r) {
+      uint32_t *p = a.cnt + (size_t)r * a.tiles + t;
+      const uint32_t v = *p;
+      *p = run;
+      run += v;
+    }
+    const uint2 sr = reinterpret_cast<const uint2 *>(a.small_ranges)[t];
+    a.len[t] = run + (sr.x == 0xffffffffu ? 0u : sr.y - sr.x);
+  }
+  const int64_t Ks = a.counters[5];
+  uint32_t *__restrict__ small = a.small;
+  uint32_t *__restrict__ kappa = a.kappa;
+  for (int64_t q0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; q0 < Ks; q0 += stride * 4) {
+    uint32_t j[4], k[4], p[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) j[i] = q0 + i < Ks ? small[q0 + i] : 0u;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      k[i] = __ldg(a.kpos + j[i]);
+      p[i] = __ldg(a.ids + j[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (q0 + i < Ks) {
+        kappa[q0 + i] = k[i];
+        small[q0 + i] = p[i];
+      }
+  }
+}
+
+// One block: exclusive scan of the list lengths over the tiles -> ranges.
+__global__ void __launch_bounds__(1024) k_wide_prefix(WideArgs a) {
+  __shared__ uint32_t wsum[32];
+  __shared__ uint32_t carry;
+  if (a.counters[2] || !a.counters[4]) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < a.tiles; base += 4096) {
+    uint32_t v[4], s = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int t = base + tid * 4 + i;
+      v[i] = t < a.tiles ? a.len[t] : 0u;
+      s += v[i];
+    }
+    uint32_t incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += u;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    uint32_t wb = 0, all = 0;
+    for (int w = 0; w < 32; ++w) {
+      if (w < warp) wb += wsum[w];
+      all += wsum[w];
+    }
+    uint32_t run = carry + wb + incl - s;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int t = base + tid * 4 + i;
+      if (t < a.tiles) reinterpret_cast<uint2 *>(a.ranges)[t] = v[i] ? make_uint2(run, run + v[i]) : make_uint2(0u, 0u);
+      run += v[i];
+    }
+    __syncthreads();
+    if (tid == 0) carry += all;
+    __syncthreads();
+  }
+}
+
+// Write pass, a warp per (strip, range), taken from a counter.
+__global__ void __launch_bounds__(kWideWarps * 32) k_wide_write(WideArgs a) {
+  __shared__ uint32_t sbuf[kWideWarps][32 * kWBufStride];
+  __shared__ uint32_t smask[kWideWarps][kWB * 32];  // the batch's colmask & rowmask, per lane
+  __shared__ uint32_t sid[kWideWarps][kWB * 32];    // the batch's wide primitive ids
+  if (a.counters[2] || !a.counters[4]) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t *buf = sbuf[warp] + lane * kWBufStride;
+  uint32_t *mk = smask[warp];
+  uint32_t *wid = sid[warp];
+  const int NW = wide_words(a.counters), wpr = wide_wpr(NW, a.R);
+  const int64_t B = a.counters[6];
+  const uint32_t *colT = a.masks, *rowT = a.masks + (size_t)NW * a.TX;
+  const int items = a.strips * a.R;
+  unsigned long long *next = reinterpret_cast<unsigned long long *>(a.counters + 8);
+  constexpr uint32_t kNone = 0xffffffffu;
+  for (;;) {
+    unsigned long long it = 0;
+    if (lane == 0) it = atomicAdd(next, 1ull);
+    const int item = (int)__shfl_sync(0xffffffffu, it, 0);
+    if (item >= items) break;
+    int r, ty, tx;
+    strip_of(a, item, r, ty, tx);
+    const int w0 = r * wpr, w1 = min(NW, w0 + wpr);
+    const uint32_t K0 = (uint32_t)w0 * 32u;  // this range's small instances: kappa in [K0, K1)
+    const uint32_t K1 = r + 1 < a.R ? (uint32_t)(w0 + wpr) * 32u : kNone;
+    const int64_t t = (int64_t)ty * a.TX + tx;
+    bool ok = tx < a.TX;
+    uint32_t out = 0, end = 0, sp = 0, se = 0;
+    if (ok) {
+      const uint2 rg = reinterpret_cast<const uint2 *>(a.ranges)[t];
+      ok = rg.x != rg.y;
+      if (ok) {
+        const uint2 sr = reinterpret_cast<const uint2 *>(a.small_ranges)[t];
+        uint32_t lo = 0, hi = 0;
+        if (sr.x != 0xffffffffu) { lo = sr.x; hi = sr.y; }
+        // [sp, se): the small instances with kappa in [K0, K1)
+        uint32_t l = lo, h = hi;
+        while (l < h) {
+          const uint32_t mid = (l + h) >> 1;
+          if (__ldg(a.kappa + mid) < K0) l = mid + 1; else h = mid;
+        }
+        sp = l;
+        h = hi;
+        if (K1 != kNone)
+          while (l < h) {
+            const uint32_t mid = (l + h) >> 1;
+            if (__ldg(a.kappa + mid) < K1) l = mid + 1; else h = mid;
+          }
+        se = h;
+        out = rg.x + a.cnt[(size_t)r * a.tiles + t] + (sp - lo);
+        end = rg.y;
+      }
+    }
+    const uint64_t tkey = (uint64_t)t << 32;
+    // ring of the next four small instances (kappa, id); kNone past the end
+    uint32_t rk[4], ri[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const bool in = ok && sp + i < se;
+      rk[i] = in ? __ldg(a.kappa + sp + i) : kNone;
+      ri[i] = in ? __ldg(a.small + sp + i) : 0u;
+    }
+    uint32_t nleft = ok ? se - sp : 0u;  // small instances not yet taken
+    uint32_t cnt = 0;
+    // copies every lane's buffered run to its list (coalesced per run),
+    // never past the tile's range
+    auto flush = [&]() {
+      __syncwarp();
+      for (int l = 0; l < 32; ++l) {
+        const uint32_t n = __shfl_sync(0xffffffffu, cnt, l);
+        if (n == 0) continue;
+        const uint32_t dst = __shfl_sync(0xffffffffu, out, l);
+        const uint32_t lim = __shfl_sync(0xffffffffu, end, l);
+        const uint64_t tk = __shfl_sync(0xffffffffu, tkey, l);
+        const uint32_t *src = sbuf[warp] + l * kWBufStride;
+        for (uint32_t q = lane; q < n; q += 32) {
+          const uint32_t p = src[q];
+          if (dst + q < lim) {
+            a.vals[dst + q] = p;
+            if (a.keys) a.keys[dst + q] = tk | __ldg(a.depth_key + p);
+          }
+        }
+      }
+      out += cnt;
+      cnt = 0;
+      __syncwarp();
+    };
+    auto pop_small = [&]() -> uint32_t {
+      const uint32_t v = ri[0];
+      rk[0] = rk[1]; ri[0] = ri[1];
+      rk[1] = rk[2]; ri[1] = ri[2];
+      rk[2] = rk[3]; ri[2] = ri[3];
+      --nleft;
+      if (nleft >= 4) {
+        rk[3] = __ldg(a.kappa + se - nleft + 3);
+        ri[3] = __ldg(a.small + se - nleft + 3);
+      } else {
+        rk[3] = kNone;
+      }
+      return v;
+    };
+    uint32_t cmn[kWB], rmn[kWB], idn[kWB];
+    auto fetch = [&](int wb) {
+#pragma unroll
+      for (int i = 0; i < kWB; ++i) {
+        const int w = wb + i;
+        const bool in = w < w1;
+        cmn[i] = in && ok ? __ldg(colT + (size_t)w * a.TX + tx) : 0u;
+        rmn[i] = in && ok ? __ldg(rowT + (size_t)w * a.TY + ty) : 0u;
+        idn[i] = in && (int64_t)w * 32 + lane < B ? __ldg(a.wide_id + (size_t)w * 32 + lane) : 0u;
+      }
+    };
+    if (w0 < w1) fetch(w0);
+    for (int wb = w0; wb < w1; wb += kWB) {
+      __syncwarp();
+#pragma unroll
+      for (int i = 0; i < kWB; ++i) {
+        mk[i * 32 + lane] = cmn[i] & rmn[i];
+        wid[i * 32 + lane] = idn[i];
+      }
+      __syncwarp();
+      if (wb + kWB < w1) fetch(wb + kWB);
+      const int nb = min(kWB, w1 - wb);
+#pragma unroll 1
+      for (int i = 0; i < nb; ++i) {
+        const uint32_t kb = (uint32_t)(wb + i) * 32u;
+        uint32_t mw = mk[i * 32 + lane];
+        const bool sdue = rk[0] < kb + 32u;
+        if (!__any_sync(0xffffffffu, mw != 0u || sdue)) continue;
+        if (__any_sync(0xffffffffu, cnt > (uint32_t)(kWBuf - 33))) flush();
+        const uint32_t *ids = wid + i * 32;
+        if (!__any_sync(0xffffffffu, sdue)) {
+          // the word's wide bits in order
+          while (mw) {
+            const uint32_t b = (uint32_t)(__ffs(mw) - 1);
+            mw &= mw - 1u;
+            buf[cnt++] = ids[b];
+          }
+          continue;
+        }
+        // with the small instances whose kappa falls before each wide bit
+        for (;;) {
+          int guard = 0;
+          while (guard < 32) {
+            const bool due = rk[0] < kb + 32u;
+            if (!mw && !due) break;
+            const uint32_t b = mw ? (uint32_t)(__ffs(mw) - 1) : 32u;
+            if (due && rk[0] <= kb + b) {
+              buf[cnt++] = pop_small();
+            } else {
+              buf[cnt++] = ids[b];
+              mw &= mw - 1u;
+            }
+            ++guard;
+          }
+          if (!__any_sync(0xffffffffu, mw != 0u || rk[0] < kb + 32u)) break;
+          if (__any_sync(0xffffffffu, cnt > (uint32_t)(kWBuf - 33))) flush();
+        }
+      }
+    }
+    // small instances after the range's last word
+    while (__any_sync(0xffffffffu, nleft != 0u)) {
+      if (__any_sync(0xffffffffu, cnt > (uint32_t)(kWBuf - 33))) flush();
+      for (int guard = 0; guard < 32 && nleft; ++guard) buf[cnt++] = pop_small();
+    }
+    flush();
+  }
+}
+
 // Chunks (blocks) of the radix passes: as many scatter blocks as fit on the
 // device at once, so every chunk is in flight from the start.
 static int pass_grid() {
@@ -612,6 +1119,25 @@ static int pass_grid() {
     cached[dev] = std::min(kMaxChunks, std::max(1, sms) * std::max(1, per));
   }
   return cached[dev];
+}
+
+// grids of the wide path, per device: k_wide_build and its companions, and
+// k_wide_write (every block resident); the SM count
+static void wide_grids(int &build, int &write, int &sms_out) {
+  static int cached[64][3] = {{0}};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+  if (cached[dev][0] == 0) {
+    int sms = 0, per = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_wide_write, kWideWarps * 32, 0);
+    cached[dev][0] = std::max(1, sms) * 8;
+    cached[dev][1] = std::max(1, sms) * std::max(1, per);
+    cached[dev][2] = std::max(1, sms);
+  }
+  build = cached[dev][0];
+  write = cached[dev][1];
+  sms_out = cached[dev][2];
 }
 
 template <int B>
@@ -655,8 +1181,16 @@ int launch_bin_sort(const BinArgs &a, const BinWorkspace &ws, cudaStream_t s) {
   const uint32_t *ids = ws.dv[1];
   // 2) instance offsets and K (capacity check on the device)
   k_scan_partial<<<kSortBlocks, kSortThreads, 0, s>>>(ids, a.touched, &ctr[0], ws.blk);
-  k_scan_top<<<1, 1024, 0, s>>>(ws.blk, kSortBlocks, a.capacity, ctr, a.d_count, a.dev_err);
-  k_scan_final<<<kSortBlocks, kSortThreads, 0, s>>>(ids, a.touched, ctr, ws.blk, ws.offs);
+  // the wide path takes at most wide_cap primitives: its id arrays and the
+  // mask budget (TX + TY words per 32 of them)
+  const int TY = a.tiles / a.TX;
+  const int64_t wide_cap =
+      std::min<int64_t>(ws.wide_max, (int64_t)(ws.mask_words / (size_t)(a.TX + TY)) * 32);
+  k_scan_top<<<1, 1024, 0, s>>>(ws.blk, kSortBlocks, a.capacity, a.wide_cfg, wide_cap, a.tiles, ctr, a.d_count,
+                                a.dev_err);
+  // dk[0] is free once the depth sort is done: it holds the deferred queue,
+  // or, on the wide path, kpos
+  k_scan_final<<<kSortBlocks, kSortThreads, 0, s>>>(ids, a.touched, ctr, ws.blk, ws.offs, ws.wide_j, ws.dk[0]);
   // 3) emit, then the tile digits, split evenly over the passes (13 bits ->
   //    7 + 6): fewer buckets per pass give longer runs in the write-out
   const int passes = (a.tile_bits + 7) / 8;
@@ -664,7 +1198,6 @@ int launch_bin_sort(const BinArgs &a, const BinWorkspace &ws, cudaStream_t s) {
   uint32_t *vbuf[2];
   vbuf[0] = (passes % 2 == 0) ? a.vals : ws.tv;
   vbuf[1] = (passes % 2 == 0) ? ws.tv : a.vals;
-  // dk[0] is free once the depth sort is done: it holds the deferred queue
   k_emit<<<kSortBlocks, 256, 0, s>>>(ids, ws.offs, a.rect, ctr, a.TX, ws.tk[0], vbuf[0], ws.dk[0]);
   k_emit_big<<<kSortBlocks, 256, 0, s>>>(ids, ws.offs, a.rect, ctr, a.TX, ws.dk[0], ws.tk[0], vbuf[0]);
   int tshift[4], tbits[4];
@@ -677,7 +1210,7 @@ int launch_bin_sort(const BinArgs &a, const BinWorkspace &ws, cudaStream_t s) {
     PassArgs w{};
     w.keys_in = ws.tk[p & 1];
     w.vals_in = vbuf[p & 1];
-    w.d_n = &ctr[1];
+    w.d_n = &ctr[7];
     w.d_abort = &ctr[2];
     w.shift = tshift[p];
     w.bits = tbits[p];
@@ -688,10 +1221,52 @@ int launch_bin_sort(const BinArgs &a, const BinWorkspace &ws, cudaStream_t s) {
     w.keys_out = (!last || a.keys) ? ws.tk[(p + 1) & 1] : nullptr;
     w.vals_out = vbuf[(p + 1) & 1];
     w.ranges = last ? a.ranges : nullptr;
+    w.wide = &ctr[4];
+    if (p == 0) w.wide_ranges_init = ws.small_ranges;
+    if (last) {
+      // wide path: the sorted small instances go to the key buffer this pass
+      // would otherwise fill, their ranges to small_ranges
+      w.vals_out_wide = ws.tk[(p + 1) & 1];
+      w.ranges_wide = ws.small_ranges;
+    }
     radix_pass(w, G, s);
   }
   k_ranges_fix<<<(a.tiles + 255) / 256, 256, 0, s>>>(a.ranges, a.tiles);
   if (a.keys) k_keys64<<<kSortBlocks, 256, 0, s>>>(ws.tk[passes & 1], a.vals, a.depth_key, ctr, a.keys);
+  // 4) wide path (every kernel returns at once on the radix path).  The
+  //    sorted small instances are in tk[passes & 1]; tk[(passes + 1) & 1]
+  //    is free and takes their kappa.
+  {
+    int gb = 1, gw = 1, sms = 1;
+    wide_grids(gb, gw, sms);
+    WideArgs wa{};
+    wa.ids = ids;
+    wa.wide_j = ws.wide_j;
+    wa.wide_id = ws.wide_id;
+    wa.kpos = ws.dk[0];
+    wa.rect = a.rect;
+    wa.counters = ctr;
+    wa.TX = a.TX;
+    wa.TY = TY;
+    wa.tiles = a.tiles;
+    wa.strips = TY * ((a.TX + 31) / 32);
+    wa.R = std::max(1, std::min(kWideRangesMax, (sms * 32 + wa.strips - 1) / wa.strips));
+    wa.masks = ws.masks;
+    wa.cnt = ws.wide_cnt;
+    wa.len = ws.wide_len;
+    wa.small = ws.tk[passes & 1];
+    wa.kappa = ws.tk[(passes + 1) & 1];
+    wa.small_ranges = ws.small_ranges;
+    wa.vals = a.vals;
+    wa.keys = a.keys;
+    wa.depth_key = a.depth_key;
+    wa.ranges = a.ranges;
+    k_wide_build<<<gb, 256, 0, s>>>(wa);
+    k_wide_count<<<gb, 256, 0, s>>>(wa);
+    k_wide_tiles<<<gb, 256, 0, s>>>(wa);
+    k_wide_prefix<<<1, 1024, 0, s>>>(wa);
+    k_wide_write<<<gw, kWideWarps * 32, 0, s>>>(wa);
+  }
   return 0;
 }
 

@@ -50,7 +50,7 @@ int launch_preprocess_bwd_fdo(const PrepArgs &a, const PrepGradFdoArgs &g, int d
 // ---------------------------------------------------------------------------
 struct BinWorkspace {
   // carved from the caller's workspace by bin_layout()
-  int64_t *counters;     // [16]: 0 = n_visible, 1 = K, 2 = overflow flag, 3 = deferred rects
+  int64_t *counters;     // [16]: 0 = n_visible, 1 = K, 2 = overflow flag, 3 = deferred rects, 4..8 wide path
   uint32_t *tile_ctr;    // [16] tile counters of the look-back passes
   uint32_t *hist;        // [8][256] global digit histograms (4 depth + up to 4 tile passes)
   size_t head_bytes;     // counters .. hist, cleared at the start of every sort
@@ -60,6 +60,15 @@ struct BinWorkspace {
   uint32_t *tk[2];       // tile keys ping-pong, [capacity]
   uint32_t *tv;          // tile vals scratch, [capacity]
   uint32_t *chist;       // [256][kSortBlocks] per-chunk digit counts / offsets of a pass
+  // wide-rectangle path
+  int64_t wide_max;      // most wide primitives it takes
+  uint32_t *wide_j;      // [wide_max] their depth-order positions
+  uint32_t *wide_id;     // [wide_max] their primitive ids
+  size_t mask_words;
+  uint32_t *masks;       // [mask_words] coverage masks
+  uint32_t *wide_cnt;    // [16][tiles] per (word range, tile) counts
+  uint32_t *wide_len;    // [tiles] list lengths
+  uint32_t *small_ranges;  // [tiles][2]
   size_t bytes;
 };
 
@@ -67,11 +76,12 @@ constexpr int kSortBlocks = 1024;  // fixed grid of every sort/scan pass
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 8;      // per thread per tile (tile = 2048 keys)
 
-size_t bin_layout(void *base, int64_t n, int64_t capacity, BinWorkspace *ws);
+size_t bin_layout(void *base, int64_t n, int64_t capacity, int tiles, BinWorkspace *ws);
 
 struct BinArgs {
   int64_t n, capacity;
   int tiles, tile_bits, TX;
+  int wide_cfg;  // rectangles over 256 tiles: 0 = path chosen per frame, 1 = counting path, 2 = radix sort
   const uint32_t *depth_key, *touched;
   const uint16_t *rect;
   uint32_t *vals;

@@ -55,6 +55,7 @@ def config_struct(cfg=None) -> abi.hgs_config:
     c.theta_z = cfg.theta_z
     c.T_z = cfg.T_z
     c.dilation = cfg.dilation
+    c.wide_rects = int(getattr(cfg, "wide_rects", 0))
     for i in range(3):
         c.bg[i] = float(cfg.bg[i])
     c.tile = int(cfg.tile)
