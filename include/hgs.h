@@ -209,11 +209,15 @@ int hgs_bin_sort_workspace(int64_t n, int64_t capacity, int32_t tiles, size_t *b
  * ties by primitive id.  Implemented as an LSD radix sort whose low (depth)
  * digits are sorted once per primitive and whose high (tile) digits are
  * sorted per instance; the resulting order is that of the 64-bit key.
+ * Rectangles over 256 tiles may instead be listed from coverage masks in
+ * depth order and merged with the sorted rest (cfg->wide_rects); the output
+ * is the same.
  * If K > capacity: writes K to out->d_count, stores HGS_ERR_CAPACITY in
  * *dev_err, zeroes the ranges, and writes no instance (no out-of-bounds
  * write).  The caller grows the buffers and calls again.
  * ws: device workspace of at least hgs_bin_sort_workspace() bytes, A16.
- * Errors: INVALID_ARG for NULL pointers, ws_bytes too small, capacity < 0. */
+ * Errors: INVALID_ARG for NULL pointers, ws_bytes too small, capacity < 0,
+ * cfg->wide_rects outside 0..2. */
 int hgs_bin_sort(int64_t n, const hgs_projected *proj, const hgs_camera *cam,
                  const hgs_config *cfg, void *ws, size_t ws_bytes, int64_t capacity,
                  hgs_binning *out, int32_t *dev_err, hgs_stream_t stream);

@@ -12,6 +12,11 @@
 // from device memory, so the whole pipeline needs no host synchronisation;
 // capacity overflow is detected on the device and reported through the
 // error word with nothing written out of bounds.
+//
+// When rectangles over kBigRect tiles carry most of the instances (heavy-
+// tailed scenes), their instances skip the tile sort: they are listed from
+// per-word coverage masks in depth order and merged with the sorted small
+// instances (the wide path below).  The lists are the same either way.
 #include <algorithm>
 
 #include "common.cuh"
@@ -483,37 +488,31 @@ __global__ void __launch_bounds__(1024)
     k_scan_top(uint64_t *__restrict__ blk, int nblocks, int64_t capacity, int wide_cfg, int64_t wide_cap,
                int tiles, int64_t *counters, int64_t *d_count, int32_t *dev_err) {
   __shared__ uint64_t wsum[3][32];
+  __shared__ int s_wide;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  uint64_t v[3], incl[3];
+  uint64_t v[3];
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    v[k] = tid < nblocks ? blk[(size_t)k * kSortBlocks + tid] : 0ull;
-    incl[k] = v[k];
+  for (int k = 0; k < 3; ++k) v[k] = tid < nblocks ? blk[(size_t)k * kSortBlocks + tid] : 0ull;
+  // the three totals decide the path
+  {
+    uint64_t r[3] = {v[0], v[1], v[2]};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) r[k] += __shfl_xor_sync(0xffffffffu, r[k], o);
+    if (lane == 0)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) wsum[k][warp] = r[k];
   }
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1)
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const uint64_t u = __shfl_up_sync(0xffffffffu, incl[k], o);
-      if (lane >= o) incl[k] += u;
-    }
-  if (lane == 31)
-#pragma unroll
-    for (int k = 0; k < 3; ++k) wsum[k][warp] = incl[k];
   __syncthreads();
-  uint64_t tot[3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    uint64_t wb = 0, all = 0;
-    for (int w = 0; w < 32; ++w) {
-      if (w < warp) wb += wsum[k][w];
-      all += wsum[k][w];
-    }
-    if (tid < nblocks) blk[(size_t)k * kSortBlocks + tid] = wb + incl[k] - v[k];
-    tot[k] = all;
-  }
   if (tid == 0) {
-    const uint64_t K = tot[0], Ks = tot[1], B = tot[2], Kw = K - Ks;
+    uint64_t K = 0, Ks = 0, B = 0;
+    for (int w = 0; w < 32; ++w) {
+      K += wsum[0][w];
+      Ks += wsum[1][w];
+      B += wsum[2][w];
+    }
+    const uint64_t Kw = K - Ks;
     counters[1] = (int64_t)K;
     if (d_count) *d_count = (int64_t)K;
     const bool over = (int64_t)K > capacity || K > 0xffffffffull;
@@ -526,13 +525,34 @@ __global__ void __launch_bounds__(1024)
     counters[5] = (int64_t)Ks;
     counters[6] = (int64_t)B;
     counters[7] = wide ? (int64_t)Ks : (int64_t)K;
+    s_wide = wide ? 1 : 0;
+  }
+  __syncthreads();
+  // exclusive scans of the rows the path reads: all instances (radix path),
+  // or the small instances and the wide primitives (wide path)
+  const int k0 = s_wide ? 1 : 0, k1 = s_wide ? 3 : 1;
+  for (int k = k0; k < k1; ++k) {
+    uint64_t incl = k == 0 ? v[0] : (k == 1 ? v[1] : v[2]);
+    const uint64_t own = incl;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t u = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += u;
+    }
+    __syncthreads();
+    if (lane == 31) wsum[0][warp] = incl;
+    __syncthreads();
+    uint64_t wb = 0;
+    for (int w = 0; w < warp; ++w) wb += wsum[0][w];
+    if (tid < nblocks) blk[(size_t)k * kSortBlocks + tid] = wb + incl - own;
   }
 }
 
 // Offsets of each primitive's instances in the radix sort's input: all its
 // instances, or on the wide path only those of small rectangles, where the
 // wide primitives' depth-order positions are listed too (wide_j), and every
-// position j gets the number of wide primitives ahead of it (kpos).
+// position j gets (number of wide primitives ahead of it, primitive id) in
+// the pair array kpos.
 template <bool WIDE>
 __device__ __forceinline__ void scan_final_body(const uint32_t *__restrict__ ids,
                                                 const uint32_t *__restrict__ touched, const int64_t *counters,
@@ -551,7 +571,8 @@ __device__ __forceinline__ void scan_final_body(const uint32_t *__restrict__ ids
   __syncthreads();
   for (int64_t tb = b0; tb < b1; tb += kSortThreads) {
     const int64_t j = tb + tid;
-    const uint32_t t = j < b1 ? __ldg(touched + __ldg(ids + j)) : 0u;
+    const uint32_t pid = j < b1 ? __ldg(ids + j) : 0u;
+    const uint32_t t = j < b1 ? __ldg(touched + pid) : 0u;
     uint32_t v[NS];
     v[0] = WIDE ? (t <= kBigRect ? t : 0u) : t;
     if (WIDE) v[NS - 1] = t > kBigRect ? 1u : 0u;
@@ -582,7 +603,8 @@ __device__ __forceinline__ void scan_final_body(const uint32_t *__restrict__ ids
       offs[j] = carry[0] + wb[0] + incl[0] - v[0];
       if (WIDE) {
         const uint32_t before = carry[NS - 1] + wb[NS - 1] + incl[NS - 1] - v[NS - 1];
-        kpos[j] = before;  // wide primitives ahead of j in depth order
+        // wide primitives ahead of j in depth order, and j's primitive id
+        reinterpret_cast<uint2 *>(kpos)[j] = make_uint2(before, pid);
         if (v[NS - 1]) wide_j[before] = (uint32_t)j;
       }
     }
@@ -753,7 +775,7 @@ struct WideArgs {
   const uint32_t *ids;       // depth order -> primitive id
   const uint32_t *wide_j;    // [B] depth-order positions of the wide primitives, ascending
   uint32_t *wide_id;         // [B] their primitive ids
-  const uint32_t *kpos;      // [M] wide primitives ahead of each depth-order position
+  const uint32_t *kpos;      // [M][2] per depth-order position: wide primitives ahead of it, primitive id
   const uint16_t *rect;
   int64_t *counters;         // 4 = wide path, 5 = small instances, 6 = B, 8 = next write item
   int TX, TY, tiles, strips, R;
@@ -882,8 +904,9 @@ __global__ void __launch_bounds__(256) k_wide_tiles(WideArgs a) {
     for (int i = 0; i < 4; ++i) j[i] = q0 + i < Ks ? small[q0 + i] : 0u;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      k[i] = __ldg(a.kpos + j[i]);
-      p[i] = __ldg(a.ids + j[i]);
+      const uint2 kp = __ldg(reinterpret_cast<const uint2 *>(a.kpos) + j[i]);
+      k[i] = kp.x;
+      p[i] = kp.y;
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -1004,20 +1027,23 @@ __global__ void __launch_bounds__(kWideWarps * 32) k_wide_write(WideArgs a) {
     // copies every lane's buffered run to its list (coalesced per run),
     // never past the tile's range
     auto flush = [&]() {
+      const uint32_t nfit = out + cnt <= end ? cnt : (out < end ? end - out : 0u);
       __syncwarp();
       for (int l = 0; l < 32; ++l) {
-        const uint32_t n = __shfl_sync(0xffffffffu, cnt, l);
+        const uint32_t n = __shfl_sync(0xffffffffu, nfit, l);
         if (n == 0) continue;
         const uint32_t dst = __shfl_sync(0xffffffffu, out, l);
-        const uint32_t lim = __shfl_sync(0xffffffffu, end, l);
-        const uint64_t tk = __shfl_sync(0xffffffffu, tkey, l);
         const uint32_t *src = sbuf[warp] + l * kWBufStride;
-        for (uint32_t q = lane; q < n; q += 32) {
-          const uint32_t p = src[q];
-          if (dst + q < lim) {
+        if (a.keys) {
+          const uint64_t tk = __shfl_sync(0xffffffffu, tkey, l);
+          for (uint32_t q = lane; q < n; q += 32) {
+            const uint32_t p = src[q];
             a.vals[dst + q] = p;
-            if (a.keys) a.keys[dst + q] = tk | __ldg(a.depth_key + p);
+            a.keys[dst + q] = tk | __ldg(a.depth_key + p);
           }
+        } else {
+          uint32_t *dv = a.vals + dst;
+          for (uint32_t q = lane; q < n; q += 32) dv[q] = src[q];
         }
       }
       out += cnt;
@@ -1064,42 +1090,29 @@ __global__ void __launch_bounds__(kWideWarps * 32) k_wide_write(WideArgs a) {
       for (int i = 0; i < nb; ++i) {
         const uint32_t kb = (uint32_t)(wb + i) * 32u;
         uint32_t mw = mk[i * 32 + lane];
-        const bool sdue = rk[0] < kb + 32u;
-        if (!__any_sync(0xffffffffu, mw != 0u || sdue)) continue;
-        if (__any_sync(0xffffffffu, cnt > (uint32_t)(kWBuf - 33))) flush();
+        if (!__any_sync(0xffffffffu, mw != 0u || rk[0] < kb + 32u)) continue;
         const uint32_t *ids = wid + i * 32;
-        if (!__any_sync(0xffffffffu, sdue)) {
-          // the word's wide bits in order
-          while (mw) {
-            const uint32_t b = (uint32_t)(__ffs(mw) - 1);
-            mw &= mw - 1u;
+        // rounds: the wide bits before the lane's next due small instance
+        // (all of them when none is due), then that small instance
+        for (;;) {
+          if (__any_sync(0xffffffffu, cnt > (uint32_t)(kWBuf - 34))) flush();
+          const uint32_t lmt = rk[0] < kb + 32u ? rk[0] - kb : 32u;
+          uint32_t seg = lmt >= 32u ? mw : (mw & ((1u << lmt) - 1u));
+          mw ^= seg;
+          while (seg) {
+            const uint32_t b = (uint32_t)(__ffs(seg) - 1);
+            seg &= seg - 1u;
             buf[cnt++] = ids[b];
           }
-          continue;
-        }
-        // with the small instances whose kappa falls before each wide bit
-        for (;;) {
-          int guard = 0;
-          while (guard < 32) {
-            const bool due = rk[0] < kb + 32u;
-            if (!mw && !due) break;
-            const uint32_t b = mw ? (uint32_t)(__ffs(mw) - 1) : 32u;
-            if (due && rk[0] <= kb + b) {
-              buf[cnt++] = pop_small();
-            } else {
-              buf[cnt++] = ids[b];
-              mw &= mw - 1u;
-            }
-            ++guard;
-          }
-          if (!__any_sync(0xffffffffu, mw != 0u || rk[0] < kb + 32u)) break;
-          if (__any_sync(0xffffffffu, cnt > (uint32_t)(kWBuf - 33))) flush();
+          const bool due = rk[0] < kb + 32u;
+          if (!__any_sync(0xffffffffu, due)) break;
+          if (due) buf[cnt++] = pop_small();
         }
       }
     }
     // small instances after the range's last word
     while (__any_sync(0xffffffffu, nleft != 0u)) {
-      if (__any_sync(0xffffffffu, cnt > (uint32_t)(kWBuf - 33))) flush();
+      if (__any_sync(0xffffffffu, cnt > (uint32_t)(kWBuf - 34))) flush();
       for (int guard = 0; guard < 32 && nleft; ++guard) buf[cnt++] = pop_small();
     }
     flush();
@@ -1188,8 +1201,8 @@ int launch_bin_sort(const BinArgs &a, const BinWorkspace &ws, cudaStream_t s) {
       std::min<int64_t>(ws.wide_max, (int64_t)(ws.mask_words / (size_t)(a.TX + TY)) * 32);
   k_scan_top<<<1, 1024, 0, s>>>(ws.blk, kSortBlocks, a.capacity, a.wide_cfg, wide_cap, a.tiles, ctr, a.d_count,
                                 a.dev_err);
-  // dk[0] is free once the depth sort is done: it holds the deferred queue,
-  // or, on the wide path, kpos
+  // dk[0] and dv[0] (contiguous) are free once the depth sort is done: dk[0]
+  // holds the deferred queue, or, on the wide path, dk[0]..dv[0] the kpos pairs
   k_scan_final<<<kSortBlocks, kSortThreads, 0, s>>>(ids, a.touched, ctr, ws.blk, ws.offs, ws.wide_j, ws.dk[0]);
   // 3) emit, then the tile digits, split evenly over the passes (13 bits ->
   //    7 + 6): fewer buckets per pass give longer runs in the write-out
@@ -1250,7 +1263,8 @@ int launch_bin_sort(const BinArgs &a, const BinWorkspace &ws, cudaStream_t s) {
     wa.TY = TY;
     wa.tiles = a.tiles;
     wa.strips = TY * ((a.TX + 31) / 32);
-    wa.R = std::max(1, std::min(kWideRangesMax, (sms * 32 + wa.strips - 1) / wa.strips));
+    // about four (strip, range) items per resident warp of k_wide_write
+    wa.R = std::max(1, std::min(kWideRangesMax, (gw * kWideWarps * 4 + wa.strips - 1) / wa.strips));
     wa.masks = ws.masks;
     wa.cnt = ws.wide_cnt;
     wa.len = ws.wide_len;

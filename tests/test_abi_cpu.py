@@ -35,6 +35,7 @@ def test_defaults_and_status_strings():
     c = abi.hgs_config()
     abi.hgs_default_config(C.byref(c))
     assert c.tile == 16 and abs(c.alpha_min - 1 / 255) < 1e-9 and abs(c.theta_z - 1.05) < 1e-6
+    assert c.wide_rects == 0  # the device picks the binning path per frame
     assert abi.hgs_status_string(abi.HGS_ERR_CAPACITY) == b"HGS_ERR_CAPACITY"
     assert abi.hgs_status_string(12345) == b"HGS_ERR_UNKNOWN"
 
@@ -80,7 +81,13 @@ def test_invalid_arguments_rejected_before_launch():
     sm = abi.hgs_scene_mut(1, 16, 1, 5)
     x = abi.hgs_exchange_cfg(abi.HGS_EXCHANGE_MASK, 2.05, None)
     assert abi.hgs_exchange_types(C.byref(sm), C.byref(x), None, None, None) == abi.HGS_ERR_INVALID_ARG
+    # binning path other than 0 (device picks), 1 (masks), 2 (radix sort)
+    cam.width = 16
+    for bad in (-1, 3):
+        cfg.wide_rects = bad
+        assert abi.hgs_preprocess(C.byref(scene), C.byref(cam), C.byref(cfg), C.byref(proj), None, None) \
+            == abi.HGS_ERR_INVALID_ARG
+    cfg.wide_rects = 0
     # an empty scene is valid and launches nothing
     scene.n = 0
-    cam.width = 16
     assert abi.hgs_preprocess(C.byref(scene), C.byref(cam), C.byref(cfg), C.byref(proj), None, None) == 0
