@@ -59,6 +59,10 @@ def parse():
     p.add_argument("--no-fdo", action="store_true")
     p.add_argument("--no-train", action="store_true")
     p.add_argument("--no-stress", action="store_true")
+    p.add_argument("--binning-probe", action="store_true",
+                   help="time only the binning of the stress scene recipe at --prims primitives and "
+                        "--width x --height, path --wide-rects, over --steps calls (one JSON line)")
+    p.add_argument("--wide-rects", type=int, default=0, choices=[0, 1, 2])
     p.add_argument("--serving-seconds", type=float, default=5.0)
     p.add_argument("--serving-rate", type=float, default=200.0)
     return p.parse_args()
@@ -426,11 +430,52 @@ def profiled_traffic(args):
     return int(fields["dram_bytes_per_launch"])
 
 
+def binning_probe(args):
+    """The binning alone on the stress scene's recipe (90% surfels, log-scales
+    -4.5 + 0.8 t_3) at a chosen size: one checked frame, then --steps timed
+    hgs_bin_sort calls (CUDA events).  A small case with the stress scene's
+    per-tile statistics, for kernel captures."""
+    import dataclasses
+
+    import numpy as np
+    import torch
+
+    import synthetic as S
+    from paper_2512_02932_gb300 import Rasterizer, SceneTensors
+    dev = torch.device("cuda", 0)
+    scene = S.surface_scene(args.n, seed=4, frac3d=0.1, ls_loc=-4.5, ls_scale=0.8, heavy_df=3)
+    cam = S.orbit_camera(30.0, 20.0, 3.0, args.width, args.height, 50.0)
+    cfg = dataclasses.replace(S.RenderConfig(), wide_rects=args.wide_rects)
+    r = Rasterizer(dev)
+    st = SceneTensors.from_numpy(scene, dev)
+    r.forward(st, cam, cfg)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(max(1, args.steps)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        r.preprocess(st, cam, cfg)
+        e0.record()
+        r.bin_sort(sync_check=False)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    r.check()
+    t = r.touched[: scene.n].cpu().numpy().astype(np.int64)
+    wide = t > 256
+    print(json.dumps({"binning_probe": {"prims": args.n, "width": args.width, "height": args.height,
+                                        "wide_rects": args.wide_rects, "instances_K": r.last_K,
+                                        "wide_prims": int(wide.sum()), "wide_instances": int(t[wide].sum()),
+                                        "bin_sort_ms": round(statistics.median(ts), 4)}}), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_init(args)
     if args.impl == "reference":
         reference_arm(args, world, rank)
+        return
+    if args.binning_probe:
+        binning_probe(args)
         return
     import torch
 

@@ -159,10 +159,12 @@ struct PassArgs {
   uint32_t *ranges_init;              // optional: set to (0xffffffff, 0) for `tiles` tiles
   int tiles;
   // tile passes: *wide != 0 on the wide path.  The first pass then also sets
-  // wide_ranges_init like ranges_init; the last one sends the values to
-  // vals_out_wide and the ranges to ranges_wide and writes no keys.
+  // wide_ranges_init like ranges_init and zeroes wide_zero[0, wide_zero_n);
+  // the last one sends the values to vals_out_wide and the ranges to
+  // ranges_wide and writes no keys.
   const int64_t *wide;
-  uint32_t *wide_ranges_init;
+  uint32_t *wide_ranges_init, *wide_zero;
+  int64_t wide_zero_n;
   uint32_t *vals_out_wide, *ranges_wide;
   uint32_t *keys_out, *vals_out;      // keys_out optional
   uint32_t *ranges;                   // optional (last tile pass): [start, end) per key
@@ -193,9 +195,12 @@ __global__ void __launch_bounds__(kSortThreads) k_chunk_hist(PassArgs a) {
   if (a.ranges_init)
     for (int t = blockIdx.x * blockDim.x + tid; t < a.tiles; t += gridDim.x * blockDim.x)
       reinterpret_cast<uint2 *>(a.ranges_init)[t] = make_uint2(0xffffffffu, 0u);
-  if (a.wide_ranges_init && *a.wide)
+  if (a.wide_ranges_init && *a.wide) {
     for (int t = blockIdx.x * blockDim.x + tid; t < a.tiles; t += gridDim.x * blockDim.x)
       reinterpret_cast<uint2 *>(a.wide_ranges_init)[t] = make_uint2(0xffffffffu, 0u);
+    for (int64_t t = blockIdx.x * blockDim.x + tid; t < a.wide_zero_n; t += gridDim.x * blockDim.x)
+      a.wide_zero[t] = 0u;
+  }
   int64_t t0, t1;
   chunk_tiles(n, t0, t1);
   const int64_t e0 = t0 * kTileElems, e1 = min(n, t1 * kTileElems);
@@ -609,12 +614,15 @@ __device__ __forceinline__ void scan_final_body(const uint32_t *__restrict__ ids
       }
     }
     __syncthreads();
-    if (tid < NS) carry[tid] += all[tid];
+    if (tid == 0) {
+      carry[0] += all[0];
+      if (WIDE) carry[NS - 1] += all[NS - 1];
+    }
     __syncthreads();
   }
 }
 
-__global__ void __launch_bounds__(kSortThreads)
+__global__ void __launch_bounds__(kSortThreads, 8)
     k_scan_final(const uint32_t *__restrict__ ids, const uint32_t *__restrict__ touched,
                  const int64_t *counters, const uint64_t *__restrict__ blk,
                  uint32_t *__restrict__ offs, uint32_t *__restrict__ wide_j, uint32_t *__restrict__ kpos) {
@@ -767,7 +775,7 @@ __global__ void __launch_bounds__(256)
 // Masks are stored word-major ([word][tx], then [word][ty]), so one warp's
 // column masks are 32 consecutive words and its row mask one broadcast word.
 constexpr int kWB = 8;              // words per prefetched batch
-constexpr int kWBuf = 96;           // entries per lane buffer
+constexpr int kWBuf = 64;           // entries per lane buffer
 constexpr int kWBufStride = kWBuf + 1;
 constexpr int kWideWarps = 2;
 
@@ -780,7 +788,7 @@ struct WideArgs {
   int64_t *counters;         // 4 = wide path, 5 = small instances, 6 = B, 8 = next write item
   int TX, TY, tiles, strips, R;
   uint32_t *masks;           // [NW][TX] column masks, then [NW][TY] row masks
-  uint32_t *cnt;             // [R][tiles] wide instances per (range, tile) -> exclusive over ranges
+  uint32_t *cnt;             // [R][tiles] wide instances per (range, tile) -> exclusive over ranges (zeroed by the first tile pass)
   uint32_t *len;             // [tiles] list lengths
   uint32_t *small;           // small instances by tile: depth-order positions -> primitive ids
   uint32_t *kappa;           // [Ks] their kappa
@@ -849,18 +857,24 @@ __device__ __forceinline__ void strip_of(const WideArgs &a, int item, int &r, in
   tx = (st - ty * spr) * 32 + (int)(threadIdx.x & 31);
 }
 
-// Counting pass, a warp per (strip, range): cnt[r][t] = covering wide
-// primitives of the range's words.
+// Counting pass: cnt[r][t] = covering wide primitives of range r's words.
+// A warp takes a strip and a chunk of up to kCountWords words of one range
+// and adds its lanes' popcounts (cnt is zeroed by the first tile pass).
+constexpr int kCountWords = 64;
 __global__ void __launch_bounds__(256) k_wide_count(WideArgs a) {
   if (a.counters[2] || !a.counters[4]) return;
   const int NW = wide_words(a.counters), wpr = wide_wpr(NW, a.R);
+  const int subs = (wpr + kCountWords - 1) / kCountWords;  // chunks per range
   const uint32_t *colT = a.masks, *rowT = a.masks + (size_t)NW * a.TX;
-  const int items = a.strips * a.R;
-  const int nwarps = gridDim.x * (blockDim.x >> 5);
-  for (int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); item < items; item += nwarps) {
+  const int64_t items = (int64_t)a.strips * a.R * subs;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t item = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); item < items; item += nwarps) {
+    const int sub = (int)(item % subs);
     int r, ty, tx;
-    strip_of(a, item, r, ty, tx);
-    const int w0 = r * wpr, w1 = min(NW, w0 + wpr);
+    strip_of(a, (int)(item / subs), r, ty, tx);
+    const int w0 = r * wpr + sub * kCountWords;
+    const int w1 = min(min(NW, r * wpr + wpr), w0 + kCountWords);
+    if (w0 >= w1) continue;
     const bool ok = tx < a.TX;
     uint32_t c = 0;
     for (int w = w0; w < w1; w += kWB) {
@@ -874,7 +888,7 @@ __global__ void __launch_bounds__(256) k_wide_count(WideArgs a) {
 #pragma unroll
       for (int i = 0; i < kWB; ++i) c += __popc(cm[i] & rm[i]);
     }
-    if (ok) a.cnt[(size_t)r * a.tiles + (size_t)ty * a.TX + tx] = c;
+    if (ok && c) atomicAdd(a.cnt + (size_t)r * a.tiles + (size_t)ty * a.TX + tx, c);
   }
 }
 
@@ -898,21 +912,19 @@ __global__ void __launch_bounds__(256) k_wide_tiles(WideArgs a) {
   const int64_t Ks = a.counters[5];
   uint32_t *__restrict__ small = a.small;
   uint32_t *__restrict__ kappa = a.kappa;
-  for (int64_t q0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; q0 < Ks; q0 += stride * 4) {
-    uint32_t j[4], k[4], p[4];
+  // eight independent gathers in flight per thread: element q0 + i * stride
+  for (int64_t q0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q0 < Ks; q0 += stride * 8) {
+    uint32_t j[8];
+    uint2 kp[8];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) j[i] = q0 + i < Ks ? small[q0 + i] : 0u;
+    for (int i = 0; i < 8; ++i) j[i] = q0 + i * stride < Ks ? small[q0 + i * stride] : 0u;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const uint2 kp = __ldg(reinterpret_cast<const uint2 *>(a.kpos) + j[i]);
-      k[i] = kp.x;
-      p[i] = kp.y;
-    }
+    for (int i = 0; i < 8; ++i) kp[i] = __ldg(reinterpret_cast<const uint2 *>(a.kpos) + j[i]);
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-      if (q0 + i < Ks) {
-        kappa[q0 + i] = k[i];
-        small[q0 + i] = p[i];
+    for (int i = 0; i < 8; ++i)
+      if (q0 + i * stride < Ks) {
+        kappa[q0 + i * stride] = kp[i].x;
+        small[q0 + i * stride] = kp[i].y;
       }
   }
 }
@@ -1235,7 +1247,11 @@ int launch_bin_sort(const BinArgs &a, const BinWorkspace &ws, cudaStream_t s) {
     w.vals_out = vbuf[(p + 1) & 1];
     w.ranges = last ? a.ranges : nullptr;
     w.wide = &ctr[4];
-    if (p == 0) w.wide_ranges_init = ws.small_ranges;
+    if (p == 0) {
+      w.wide_ranges_init = ws.small_ranges;
+      w.wide_zero = ws.wide_cnt;
+      w.wide_zero_n = (int64_t)kWideRangesMax * a.tiles;
+    }
     if (last) {
       // wide path: the sorted small instances go to the key buffer this pass
       // would otherwise fill, their ranges to small_ranges

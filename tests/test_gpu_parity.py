@@ -362,3 +362,25 @@ def test_wide_path_mixed_with_small_instances(loc):
     assert_lists_bitexact(r, scene, cam, cfg)
     m = _oracle_maps(scene, cam, cfg)
     assert_images_match(g, m, m["amb"], max_amb_frac=0.03)  # large splats: more pairs near a threshold
+
+
+def test_wide_path_with_no_small_instances():
+    """Every binned primitive spans more than 256 tiles: the radix pass runs
+    over nothing and the lists come from the masks alone (several words,
+    ragged last word)."""
+    import dataclasses
+    rng = np.random.default_rng(31)
+    scene, _ = S.tiny_scene(31, n=700)
+    n = scene.n
+    scene.means[:] = np.stack([rng.uniform(-0.2, 0.2, n), rng.uniform(-0.2, 0.2, n),
+                               rng.uniform(3.0, 4.0, n)], axis=1).astype(np.float32)
+    scene.types[:] = 1
+    scene.log_scales[:] = rng.uniform(-0.7, -0.4, size=(n, 3)).astype(np.float32)
+    scene.opacity_logits[:] = 3.0
+    cam = S.pinhole(1024, 640, 60.0)
+    cfg = dataclasses.replace(CFG, wide_rects=1)
+    r, st, g = gpu_forward(scene, cam, cfg)
+    K = assert_lists_bitexact(r, scene, cam, cfg)
+    touched = r.touched[: scene.n].cpu().numpy().astype(np.int64)
+    binned = touched > 0
+    assert binned.sum() == n and (touched > 256).all() and K > 0

@@ -49,6 +49,25 @@ def test_batch_equals_alone_bit_for_bit():
     assert_images_match(g, m, m["amb"], max_amb_frac=0.05)
 
 
+def test_batch_wide_rectangles_same_on_both_paths():
+    """A batch of heavy-tailed scenes (many rectangles over 256 tiles of the
+    stacked grid): the mask path and the radix path give the same images,
+    bit for bit."""
+    import dataclasses
+    host = [S.surface_scene(30_000, seed=50 + k, frac3d=0.3, ls_loc=-4.0, ls_scale=0.8, heavy_df=3)
+            for k in range(2)]
+    dev = [SceneTensors.from_numpy(h) for h in host]
+    cams = [S.orbit_camera(15.0, 25.0, 2.6, 1024, 640, 55.0), S.orbit_camera(200.0, 10.0, 2.8, 800, 600, 50.0)]
+    outs = {}
+    for mode in (1, 2):
+        o, K = render_batch_once(dev, cams, dataclasses.replace(CFG, wide_rects=mode))
+        assert K > 0
+        outs[mode] = [{k: x[k].cpu().numpy() for k in KEYS} for x in o]
+    for a, b in zip(outs[1], outs[2]):
+        for k in KEYS:
+            np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+
+
 def test_server_burst_matches_alone():
     host, dev = _scenes()
     rng = np.random.default_rng(1)
