@@ -487,8 +487,10 @@ __global__ void __launch_bounds__(kSortThreads)
 // instances, 6 = wide primitives B, 7 = instances the radix sort takes.
 // The wide path is taken when it is allowed (B within wide_cap) and asked
 // for (wide_cfg 1), or, under wide_cfg 0, when the wide instances outnumber
-// both 8x the (32 tiles, 32 wide primitives) mask visits it costs and half
-// the small instances it re-reads in the merge.
+// both 8x the (32 tiles, 32 wide primitives) mask visits it costs and 10x
+// the small instances it merges in (measured: with small instances at 13%
+// of the wide ones the radix path was faster, at 6% the mask path took
+// less than half its time).
 __global__ void __launch_bounds__(1024)
     k_scan_top(uint64_t *__restrict__ blk, int nblocks, int64_t capacity, int wide_cfg, int64_t wide_cap,
                int tiles, int64_t *counters, int64_t *d_count, int32_t *dev_err) {
@@ -525,7 +527,7 @@ __global__ void __launch_bounds__(1024)
     if (over) set_error(dev_err, HGS_ERR_CAPACITY);
     const uint64_t visits = (uint64_t)tiles * ((B + 31) / 32) / 32;
     const bool fits = B > 0 && (int64_t)B <= wide_cap;
-    const bool wide = fits && (wide_cfg == 1 || (wide_cfg == 0 && Kw > 8 * visits && 2 * Kw > Ks));
+    const bool wide = fits && (wide_cfg == 1 || (wide_cfg == 0 && Kw > 8 * visits && Kw > 10 * Ks));
     counters[4] = wide ? 1 : 0;
     counters[5] = (int64_t)Ks;
     counters[6] = (int64_t)B;
