@@ -389,8 +389,16 @@ def run_stress(args, dev, cfg):
                 acc[n] += ev[i].elapsed_time(ev[i + 1])
     rast.check()
     ph = {n: round(v / reps, 3) for n, v in acc.items()}
+    rg = rast.ranges.to(torch.int64)
+    lens = (rg[:, 1] - rg[:, 0]).to(torch.float64)
+    ws_bytes = sum(t.numel() * t.element_size() for t in (rast.ws, rast.vals, rast.keys, rast.ranges, rast.rec,
+                                                         rast.grad_ws) if t is not None)
     out = {"workload": "stress: 6M prims (90% 2D, log-scales -4.5 + 0.8 t_3), 3840x2160, fwd+bwd (rgb cotangent)",
-           "ms_per_step": round(sum(ph.values()), 3), "phases_ms": ph, "instances_K": K}
+           "ms_per_step": round(sum(ph.values()), 3), "phases_ms": ph, "instances_K": K,
+           "tile_list_len": {"max": int(lens.max().item()), "p99": int(torch.quantile(lens, 0.99).item()),
+                             "mean": round(float(lens.mean().item()), 1)},
+           "device_buffers_gb": round(ws_bytes / 1e9, 2),
+           "peak_allocated_gb": round(torch.cuda.max_memory_allocated(dev) / 1e9, 2)}
     del rast, st
     torch.cuda.empty_cache()
     return out

@@ -772,8 +772,9 @@ __global__ void __launch_bounds__(256)
 // covering primitives to a shared-memory buffer, with the tile's small
 // instances (as the radix sort ordered them) slotted in by kappa, the number
 // of wide primitives ahead of them in depth order.  Full buffers are copied
-// out with coalesced stores.  A counting pass over the same (strip, range)
-// items gives every range its output offset within the tile's list.
+// out with coalesced stores.  A counting pass (popcounts of the same masks,
+// a strip and up to 64 words of one range per warp) gives every (range,
+// tile) its output offset within the tile's list.
 // Masks are stored word-major ([word][tx], then [word][ty]), so one warp's
 // column masks are 32 consecutive words and its row mask one broadcast word.
 constexpr int kWB = 8;              // words per prefetched batch
