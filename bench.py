@@ -389,7 +389,7 @@ def run_stress(args, dev, cfg):
                 acc[n] += ev[i].elapsed_time(ev[i + 1])
     rast.check()
     ph = {n: round(v / reps, 3) for n, v in acc.items()}
-    rg = rast.ranges.to(torch.int64)
+    rg = rast.ranges.to(torch.int64) & 0xFFFFFFFF  # uint32 offsets (K may pass 2^31)
     lens = (rg[:, 1] - rg[:, 0]).to(torch.float64)
     ws_bytes = sum(t.numel() * t.element_size() for t in (rast.ws, rast.vals, rast.keys, rast.ranges, rast.rec,
                                                          rast.grad_ws) if t is not None)
