@@ -222,6 +222,15 @@ int hgs_bin_sort(int64_t n, const hgs_projected *proj, const hgs_camera *cam,
                  const hgs_config *cfg, void *ws, size_t ws_bytes, int64_t capacity,
                  hgs_binning *out, int32_t *dev_err, hgs_stream_t stream);
 
+/* hgs_fp32_probe -- a measurement, not part of the path: launches `blocks`
+ * CTAs of 256 threads, each thread running 8 independent chains of `iters`
+ * binary32 fused multiply-adds, so the caller can time the device's FP32
+ * rate (the denominator of the render kernels' roofline).  d_out: device
+ * float[blocks], written only by a branch that is never taken.  *flops
+ * (host) receives the floating-point operations launched (2 per FMA).
+ * Errors: INVALID_ARG for blocks < 1, iters < 1, NULL d_out or flops. */
+int hgs_fp32_probe(int32_t blocks, int32_t iters, float *d_out, double *flops, hgs_stream_t stream);
+
 /* hgs_bin_sort_static -- hgs_bin_sort without a caller-supplied workspace,
  * for callers that cannot allocate device memory while they render: a host
  * application that owns the GPU allocator and forbids other cudaMalloc calls,

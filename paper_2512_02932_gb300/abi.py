@@ -116,6 +116,7 @@ SYMBOLS = {
     "hgs_exchange_types": (C.c_int, [C.POINTER(hgs_scene_mut), C.POINTER(hgs_exchange_cfg), P, P, P]),
     "hgs_image_losses": (C.c_int, [P, P, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double,
                                    P, P, P, P, P]),
+    "hgs_fp32_probe": (C.c_int, [C.c_int32, C.c_int32, P, C.POINTER(C.c_double), P]),
     "hgs_render_bwd_fdo": (C.c_int, [C.POINTER(hgs_scene), C.POINTER(hgs_projected), C.POINTER(hgs_binning),
                                      C.POINTER(hgs_camera), C.POINTER(hgs_config), C.POINTER(hgs_image),
                                      P, P, P, P, C.POINTER(hgs_scene_grad), P, P, P]),
@@ -200,3 +201,4 @@ hgs_densify_workspace = _fwd("hgs_densify_workspace")
 hgs_densify_plan = _fwd("hgs_densify_plan")
 hgs_densify_apply = _fwd("hgs_densify_apply")
 hgs_reset_opacity = _fwd("hgs_reset_opacity")
+hgs_fp32_probe = _fwd("hgs_fp32_probe")

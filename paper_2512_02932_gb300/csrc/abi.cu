@@ -603,4 +603,10 @@ int hgs_exchange_types(hgs_scene_mut *scene, const hgs_exchange_cfg *xcfg, int64
   return launched();
 }
 
+int hgs_fp32_probe(int32_t blocks, int32_t iters, float *d_out, double *flops, hgs_stream_t stream) {
+  if (blocks < 1 || iters < 1 || !d_out || !flops) return HGS_ERR_INVALID_ARG;
+  launch_fp32_probe(blocks, iters, d_out, flops, reinterpret_cast<cudaStream_t>(stream));
+  return launched();
+}
+
 }  // extern "C"

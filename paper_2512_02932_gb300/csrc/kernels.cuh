@@ -212,4 +212,7 @@ struct ExchangeArgs {
 
 int launch_exchange(const ExchangeArgs &a, cudaStream_t s);
 
+// FP32 peak probe (roofline denominator of the render kernels)
+int launch_fp32_probe(int blocks, int iters, float *out, double *flops, cudaStream_t s);
+
 }  // namespace hgs

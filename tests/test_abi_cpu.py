@@ -81,6 +81,10 @@ def test_invalid_arguments_rejected_before_launch():
     sm = abi.hgs_scene_mut(1, 16, 1, 5)
     x = abi.hgs_exchange_cfg(abi.HGS_EXCHANGE_MASK, 2.05, None)
     assert abi.hgs_exchange_types(C.byref(sm), C.byref(x), None, None, None) == abi.HGS_ERR_INVALID_ARG
+    # the FP32 probe needs a launch size and an output
+    fl = C.c_double()
+    assert abi.hgs_fp32_probe(0, 10, None, C.byref(fl), None) == abi.HGS_ERR_INVALID_ARG
+    assert abi.hgs_fp32_probe(4, 0, None, C.byref(fl), None) == abi.HGS_ERR_INVALID_ARG
     # binning path other than 0 (device picks), 1 (masks), 2 (radix sort)
     cam.width = 16
     for bad in (-1, 3):
