@@ -487,10 +487,10 @@ __global__ void __launch_bounds__(kSortThreads)
 // instances, 6 = wide primitives B, 7 = instances the radix sort takes.
 // The wide path is taken when it is allowed (B within wide_cap) and asked
 // for (wide_cfg 1), or, under wide_cfg 0, when the wide instances outnumber
-// both 8x the (32 tiles, 32 wide primitives) mask visits it costs and 10x
+// both 8x the (32 tiles, 32 wide primitives) mask visits it costs and 5x
 // the small instances it merges in (measured: with small instances at 13%
-// of the wide ones the radix path was faster, at 6% the mask path took
-// less than half its time).
+// of the wide ones the mask path took 82% of the radix path's time, at 6%
+// under 40%).
 __global__ void __launch_bounds__(1024)
     k_scan_top(uint64_t *__restrict__ blk, int nblocks, int64_t capacity, int wide_cfg, int64_t wide_cap,
                int tiles, int64_t *counters, int64_t *d_count, int32_t *dev_err) {
@@ -527,7 +527,7 @@ __global__ void __launch_bounds__(1024)
     if (over) set_error(dev_err, HGS_ERR_CAPACITY);
     const uint64_t visits = (uint64_t)tiles * ((B + 31) / 32) / 32;
     const bool fits = B > 0 && (int64_t)B <= wide_cap;
-    const bool wide = fits && (wide_cfg == 1 || (wide_cfg == 0 && Kw > 8 * visits && Kw > 10 * Ks));
+    const bool wide = fits && (wide_cfg == 1 || (wide_cfg == 0 && Kw > 8 * visits && Kw > 5 * Ks));
     counters[4] = wide ? 1 : 0;
     counters[5] = (int64_t)Ks;
     counters[6] = (int64_t)B;
@@ -768,18 +768,16 @@ __global__ void __launch_bounds__(256)
 // span that column, and one per tile row; the word's primitives that cover
 // tile (tx, ty) are the bits of colmask[tx] & rowmask[ty], in depth order.
 // A warp takes a strip of 32 tiles of one row (a lane per tile) and a range
-// of words; walking the words in order, each lane appends its tile's
-// covering primitives to a shared-memory buffer, with the tile's small
-// instances (as the radix sort ordered them) slotted in by kappa, the number
-// of wide primitives ahead of them in depth order.  Full buffers are copied
-// out with coalesced stores.  A counting pass (popcounts of the same masks,
+// of words; walking the words in order, each lane writes its tile's
+// covering primitives to the tile's list, with the tile's small instances
+// (as the radix sort ordered them) slotted in by kappa, the number of wide
+// primitives ahead of them in depth order.  Each lane stores groups of four
+// entries as one 16-byte store.  A counting pass (popcounts of the same masks,
 // a strip and up to 64 words of one range per warp) gives every (range,
 // tile) its output offset within the tile's list.
 // Masks are stored word-major ([word][tx], then [word][ty]), so one warp's
 // column masks are 32 consecutive words and its row mask one broadcast word.
 constexpr int kWB = 8;              // words per prefetched batch
-constexpr int kWBuf = 64;           // entries per lane buffer
-constexpr int kWBufStride = kWBuf + 1;
 constexpr int kWideWarps = 2;
 
 struct WideArgs {
@@ -974,14 +972,14 @@ __global__ void __launch_bounds__(1024) k_wide_prefix(WideArgs a) {
   }
 }
 
-// Write pass, a warp per (strip, range), taken from a counter.
+// Write pass, a warp per (strip, range), taken from a counter.  Each lane
+// writes its tile's entries straight to the list: single words up to a
+// 16-byte boundary, then groups of four as 16-byte stores.
 __global__ void __launch_bounds__(kWideWarps * 32) k_wide_write(WideArgs a) {
-  __shared__ uint32_t sbuf[kWideWarps][32 * kWBufStride];
   __shared__ uint32_t smask[kWideWarps][kWB * 32];  // the batch's colmask & rowmask, per lane
   __shared__ uint32_t sid[kWideWarps][kWB * 32];    // the batch's wide primitive ids
   if (a.counters[2] || !a.counters[4]) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t *buf = sbuf[warp] + lane * kWBufStride;
   uint32_t *mk = smask[warp];
   uint32_t *wid = sid[warp];
   const int NW = wide_words(a.counters), wpr = wide_wpr(NW, a.R);
@@ -989,6 +987,7 @@ __global__ void __launch_bounds__(kWideWarps * 32) k_wide_write(WideArgs a) {
   const uint32_t *colT = a.masks, *rowT = a.masks + (size_t)NW * a.TX;
   const int items = a.strips * a.R;
   unsigned long long *next = reinterpret_cast<unsigned long long *>(a.counters + 8);
+  const bool vec = (reinterpret_cast<uintptr_t>(a.vals) & 15u) == 0 && !a.keys;
   constexpr uint32_t kNone = 0xffffffffu;
   for (;;) {
     unsigned long long it = 0;
@@ -998,11 +997,11 @@ __global__ void __launch_bounds__(kWideWarps * 32) k_wide_write(WideArgs a) {
     int r, ty, tx;
     strip_of(a, item, r, ty, tx);
     const int w0 = r * wpr, w1 = min(NW, w0 + wpr);
-    const uint32_t K0 = (uint32_t)w0 * 32u;  // this range's small instances: kappa in [K0, K1)
+    const uint32_t K0 = (uint32_t)w0 * 32u;
     const uint32_t K1 = r + 1 < a.R ? (uint32_t)(w0 + wpr) * 32u : kNone;
     const int64_t t = (int64_t)ty * a.TX + tx;
     bool ok = tx < a.TX;
-    uint32_t out = 0, end = 0, sp = 0, se = 0;
+    uint32_t pos = 0, end = 0, sp = 0, se = 0;
     if (ok) {
       const uint2 rg = reinterpret_cast<const uint2 *>(a.ranges)[t];
       ok = rg.x != rg.y;
@@ -1010,7 +1009,6 @@ __global__ void __launch_bounds__(kWideWarps * 32) k_wide_write(WideArgs a) {
         const uint2 sr = reinterpret_cast<const uint2 *>(a.small_ranges)[t];
         uint32_t lo = 0, hi = 0;
         if (sr.x != 0xffffffffu) { lo = sr.x; hi = sr.y; }
-        // [sp, se): the small instances with kappa in [K0, K1)
         uint32_t l = lo, h = hi;
         while (l < h) {
           const uint32_t mid = (l + h) >> 1;
@@ -1024,12 +1022,11 @@ __global__ void __launch_bounds__(kWideWarps * 32) k_wide_write(WideArgs a) {
             if (__ldg(a.kappa + mid) < K1) l = mid + 1; else h = mid;
           }
         se = h;
-        out = rg.x + a.cnt[(size_t)r * a.tiles + t] + (sp - lo);
+        pos = rg.x + a.cnt[(size_t)r * a.tiles + t] + (sp - lo);
         end = rg.y;
       }
     }
     const uint64_t tkey = (uint64_t)t << 32;
-    // ring of the next four small instances (kappa, id); kNone past the end
     uint32_t rk[4], ri[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -1037,33 +1034,27 @@ __global__ void __launch_bounds__(kWideWarps * 32) k_wide_write(WideArgs a) {
       rk[i] = in ? __ldg(a.kappa + sp + i) : kNone;
       ri[i] = in ? __ldg(a.small + sp + i) : 0u;
     }
-    uint32_t nleft = ok ? se - sp : 0u;  // small instances not yet taken
-    uint32_t cnt = 0;
-    // copies every lane's buffered run to its list (coalesced per run),
-    // never past the tile's range
-    auto flush = [&]() {
-      const uint32_t nfit = out + cnt <= end ? cnt : (out < end ? end - out : 0u);
-      __syncwarp();
-      for (int l = 0; l < 32; ++l) {
-        const uint32_t n = __shfl_sync(0xffffffffu, nfit, l);
-        if (n == 0) continue;
-        const uint32_t dst = __shfl_sync(0xffffffffu, out, l);
-        const uint32_t *src = sbuf[warp] + l * kWBufStride;
-        if (a.keys) {
-          const uint64_t tk = __shfl_sync(0xffffffffu, tkey, l);
-          for (uint32_t q = lane; q < n; q += 32) {
-            const uint32_t p = src[q];
-            a.vals[dst + q] = p;
-            a.keys[dst + q] = tk | __ldg(a.depth_key + p);
-          }
-        } else {
-          uint32_t *dv = a.vals + dst;
-          for (uint32_t q = lane; q < n; q += 32) dv[q] = src[q];
+    uint32_t nleft = ok ? se - sp : 0u;
+    // output staging: q0..q3 hold np entries for the 16-byte store at pos
+    uint32_t q0 = 0, q1 = 0, q2 = 0, q3 = 0, np = 0;
+    auto emit = [&](uint32_t v) {
+      if (!vec || (pos & 3u) != 0u) {  // up to the boundary (or no vector stores): single words
+        if (pos < end) {
+          a.vals[pos] = v;
+          if (a.keys) a.keys[pos] = tkey | __ldg(a.depth_key + v);
         }
+        ++pos;
+        return;
       }
-      out += cnt;
-      cnt = 0;
-      __syncwarp();
+      q0 = np == 0 ? v : q0;
+      q1 = np == 1 ? v : q1;
+      q2 = np == 2 ? v : q2;
+      q3 = np == 3 ? v : q3;
+      if (++np == 4) {
+        if (pos + 4 <= end) *reinterpret_cast<uint4 *>(a.vals + pos) = make_uint4(q0, q1, q2, q3);
+        pos += 4;
+        np = 0;
+      }
     };
     auto pop_small = [&]() -> uint32_t {
       const uint32_t v = ri[0];
@@ -1105,32 +1096,28 @@ __global__ void __launch_bounds__(kWideWarps * 32) k_wide_write(WideArgs a) {
       for (int i = 0; i < nb; ++i) {
         const uint32_t kb = (uint32_t)(wb + i) * 32u;
         uint32_t mw = mk[i * 32 + lane];
-        if (!__any_sync(0xffffffffu, mw != 0u || rk[0] < kb + 32u)) continue;
         const uint32_t *ids = wid + i * 32;
-        // rounds: the wide bits before the lane's next due small instance
-        // (all of them when none is due), then that small instance
+        // the word's wide bits in order, each small instance before the
+        // first wide bit it does not follow
         for (;;) {
-          if (__any_sync(0xffffffffu, cnt > (uint32_t)(kWBuf - 34))) flush();
-          const uint32_t lmt = rk[0] < kb + 32u ? rk[0] - kb : 32u;
-          uint32_t seg = lmt >= 32u ? mw : (mw & ((1u << lmt) - 1u));
-          mw ^= seg;
-          while (seg) {
-            const uint32_t b = (uint32_t)(__ffs(seg) - 1);
-            seg &= seg - 1u;
-            buf[cnt++] = ids[b];
+          const uint32_t b = mw ? (uint32_t)(__ffs(mw) - 1) : 31u;
+          if (rk[0] <= kb + b) {
+            emit(pop_small());
+          } else if (mw) {
+            emit(ids[b]);
+            mw &= mw - 1u;
+          } else {
+            break;
           }
-          const bool due = rk[0] < kb + 32u;
-          if (!__any_sync(0xffffffffu, due)) break;
-          if (due) buf[cnt++] = pop_small();
         }
       }
     }
-    // small instances after the range's last word
-    while (__any_sync(0xffffffffu, nleft != 0u)) {
-      if (__any_sync(0xffffffffu, cnt > (uint32_t)(kWBuf - 34))) flush();
-      for (int guard = 0; guard < 32 && nleft; ++guard) buf[cnt++] = pop_small();
+    while (nleft) emit(pop_small());
+    // the staged tail
+    for (uint32_t k = 0; k < np; ++k) {
+      const uint32_t v = k == 0 ? q0 : (k == 1 ? q1 : (k == 2 ? q2 : q3));
+      if (pos + k < end) a.vals[pos + k] = v;
     }
-    flush();
   }
 }
 

@@ -384,3 +384,19 @@ def test_wide_path_with_no_small_instances():
     touched = r.touched[: scene.n].cpu().numpy().astype(np.int64)
     binned = touched > 0
     assert binned.sum() == n and (touched > 256).all() and K > 0
+
+
+def test_wide_path_lists_without_keys():
+    """Without the optional 64-bit keys the mask path writes each tile's list
+    with 16-byte stores (single words up to the boundary): values and ranges
+    stay bit-exact against the oracle."""
+    import dataclasses
+    scene = S.surface_scene(60_000, seed=21, frac3d=0.3, ls_loc=-4.0, ls_scale=0.8, heavy_df=3)
+    cam = S.orbit_camera(15.0, 25.0, 2.6, 1024, 640, 55.0)
+    cfg = dataclasses.replace(CFG, wide_rects=1)
+    r, st, g = gpu_forward(scene, cam, cfg, keep_keys=False)
+    keys, vals, ranges, _ = O.tile_lists(scene, cam, cfg)
+    K = int(r.d_count.item())
+    assert K == len(vals)
+    np.testing.assert_array_equal(r.vals[:K].cpu().numpy().view(np.uint32), vals)
+    np.testing.assert_array_equal(r.ranges.cpu().numpy().view(np.uint32), ranges)
