@@ -838,20 +838,76 @@ __device__ __forceinline__ void store_zero_grad(const PrepGradArgs &g, int64_t i
   store_pgrad<DEG>(g, i, z, nullptr);
 }
 
+// The SH gradient rows of a warp's 32 primitives are contiguous: where a row
+// is a whole number of 16-byte words (degrees 1 and 3) the warp stages 16
+// rows at a time in shared memory and writes them as one contiguous run, so
+// every store covers whole lines instead of 32 partial sectors.
+template <int DEG>
+__device__ __forceinline__ void store_sh_rows_warp(float *sh, int64_t n, int64_t i, const float *v,
+                                                   float4 *stage) {
+  constexpr int NB = (DEG + 1) * (DEG + 1);
+  constexpr int RW = NB * 3 / 4;  // float4 words per row
+  const int lane = threadIdx.x & 31;
+  const int64_t i0 = i - lane;
+  float4 *dst = reinterpret_cast<float4 *>(sh);
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    if ((lane >> 4) == half) {
+      float4 *row = stage + (lane & 15) * RW;
+#pragma unroll
+      for (int k = 0; k < RW; ++k)
+        row[k] = v ? make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3])
+                   : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncwarp();
+    const int64_t r0 = i0 + 16 * half;
+    const int64_t left = n - r0;
+    const int words = left <= 0 ? 0 : (int)(left < 16 ? left : 16) * RW;
+    for (int k = lane; k < words; k += 32) dst[r0 * RW + k] = stage[k];
+    __syncwarp();
+  }
+}
+
 template <int DEG>
 __global__ void __launch_bounds__(256) preprocess_bwd_kernel(PrepArgs a, PrepGradArgs g) {
+  constexpr int NB = (DEG + 1) * (DEG + 1);
+  constexpr bool kWarpRows = DEG == 1 || DEG == 3;
+  __shared__ float4 stage[kWarpRows ? 8 : 1][kWarpRows ? 16 * NB * 3 / 4 : 1];
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n) return;
-  if (__ldg(a.touched + i) == 0u) {
-    store_zero_grad<DEG>(g, i);
-    return;
+  const bool in = i < a.n;
+  const bool binned = in && __ldg(a.touched + i) != 0u;
+  PGrad r;
+  float out[NB * 3];
+  if (binned) {
+    BwdCtx<DEG> x;
+    bwd_ctx<DEG>(a, i, x);
+    float G[kGradW];
+    load_rec_grad(g.rec_grad, i, G);
+    r = chain_grad<DEG>(a, x, G);
+#pragma unroll
+    for (int k = 0; k < NB; ++k)
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) out[3 * k + ch] = r.dv[ch] * x.Yb[k];
+  } else {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) { r.mu[k] = 0.f; r.ls[k] = 0.f; r.dv[k] = 0.f; }
+    r.logit = 0.f;
+    r.q = make_float4(0.f, 0.f, 0.f, 0.f);
   }
-  BwdCtx<DEG> x;
-  bwd_ctx<DEG>(a, i, x);
-  float G[kGradW];
-  load_rec_grad(g.rec_grad, i, G);
-  const PGrad r = chain_grad<DEG>(a, x, G);
-  store_pgrad<DEG>(g, i, r, x.Yb);
+  if (in) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      g.means[3 * i + k] = r.mu[k];
+      g.log_scales[3 * i + k] = r.ls[k];
+    }
+    reinterpret_cast<float4 *>(g.quats)[i] = r.q;
+    g.logits[i] = r.logit;
+  }
+  if constexpr (kWarpRows) {
+    store_sh_rows_warp<DEG>(g.sh, a.n, i, binned ? out : nullptr, stage[threadIdx.x >> 5]);
+  } else {
+    if (in) store_sh<DEG>(g.sh + i * NB * 3, binned ? out : nullptr);
+  }
 }
 
 
