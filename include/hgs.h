@@ -240,10 +240,13 @@ int hgs_fp32_probe(int32_t blocks, int32_t iters, float *d_out, double *flops, h
  * caller still owns proj and out); the sort's scratch is a library-owned
  * device array of HGS_BIN_SORT_STATIC_BYTES that every GPU loading the
  * library reserves until the process exits.
- * Limits: returns HGS_ERR_INVALID_ARG, launching nothing, when
- * hgs_bin_sort_workspace(n, capacity, tiles) exceeds HGS_BIN_SORT_STATIC_BYTES
- * (for example n = 1M with capacity 3.5M fits; the 3M-primitive scene does
- * not).  The first call on each device looks up the array's device address
+ * It always sorts every instance by radix passes (rectangles over 256 tiles
+ * included, whatever cfg->wide_rects says), so its scratch holds those
+ * passes' buffers only.
+ * Limits: returns HGS_ERR_INVALID_ARG, launching nothing, when that scratch
+ * (hgs_bin_sort_workspace(n, capacity, tiles) less the wide-rectangle
+ * buffers) exceeds HGS_BIN_SORT_STATIC_BYTES (for example n = 1M with
+ * capacity 3.5M fits; the 3M-primitive scene does not).  The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
  * before any stream capture.  All calls share the one array and it keeps the
  * previous call's contents (the kernels clear what must start at zero): calls

@@ -65,11 +65,13 @@ extern "C" int hgs_bin_sort_static(int64_t n, const hgs_projected *proj, const h
   const int TX = (cam->width + hgs::kTile - 1) / hgs::kTile;
   const int TY = (cam->height + hgs::kTile - 1) / hgs::kTile;
   hgs::BinWorkspace probe;
-  if (hgs::bin_layout(nullptr, n, capacity, TX * TY, &probe) > kStaticScratchBytes) return HGS_ERR_INVALID_ARG;
+  // the fixed array holds the radix path's buffers only: no wide-rectangle path
+  if (hgs::bin_layout(nullptr, n, capacity, TX * TY, &probe, false) > kStaticScratchBytes)
+    return HGS_ERR_INVALID_ARG;
   void *scratch = scratch_on_current_device();
   if (!scratch) return HGS_ERR_CUDA;
   hgs::BinWorkspace w;
-  hgs::bin_layout(scratch, n, capacity, TX * TY, &w);
+  hgs::bin_layout(scratch, n, capacity, TX * TY, &w, false);
   int tile_bits = 1;
   while ((1 << tile_bits) < TX * TY) ++tile_bits;
   hgs::BinArgs a;

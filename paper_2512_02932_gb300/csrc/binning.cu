@@ -33,7 +33,7 @@ constexpr int kWideRangesMax = 16;                 // word ranges per strip of t
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-size_t bin_layout(void *base, int64_t n, int64_t capacity, int tiles, BinWorkspace *ws) {
+size_t bin_layout(void *base, int64_t n, int64_t capacity, int tiles, BinWorkspace *ws, bool wide) {
   size_t off = 0;
   char *b = static_cast<char *>(base);
   auto take = [&](size_t bytes) -> void * {
@@ -61,7 +61,16 @@ size_t bin_layout(void *base, int64_t n, int64_t capacity, int tiles, BinWorkspa
   // wide path: the wide primitives' depth-order positions and ids, their
   // coverage masks (TX + TY words per 32 wide primitives, a budget that
   // scales with the tiles: TX + TY <= tiles + 1), the per-(range, tile)
-  // counts, the list lengths, the small instances' ranges.
+  // counts, the list lengths, the small instances' ranges.  Without the
+  // wide path (wide == false) none of it is reserved and every frame takes
+  // the radix sort.
+  if (!wide) {
+    ws->wide_max = 0;
+    ws->wide_j = ws->wide_id = ws->masks = ws->wide_cnt = ws->wide_len = ws->small_ranges = nullptr;
+    ws->mask_words = 0;
+    ws->bytes = off;
+    return off;
+  }
   const int64_t wmax = std::min<int64_t>((int64_t)nn, kWideMax);
   ws->wide_max = wmax;
   ws->wide_j = (uint32_t *)take(sizeof(uint32_t) * (size_t)wmax);

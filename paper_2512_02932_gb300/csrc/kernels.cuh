@@ -76,7 +76,8 @@ constexpr int kSortBlocks = 1024;  // fixed grid of every sort/scan pass
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 8;      // per thread per tile (tile = 2048 keys)
 
-size_t bin_layout(void *base, int64_t n, int64_t capacity, int tiles, BinWorkspace *ws);
+// wide = false reserves nothing for the wide-rectangle path (it is then never taken)
+size_t bin_layout(void *base, int64_t n, int64_t capacity, int tiles, BinWorkspace *ws, bool wide = true);
 
 struct BinArgs {
   int64_t n, capacity;

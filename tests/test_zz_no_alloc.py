@@ -59,6 +59,26 @@ def test_static_scratch_matches_workspace_binning_twice():
             np.testing.assert_array_equal(got[2], ref[2])
 
 
+def test_static_scratch_sorts_wide_rectangles_like_the_mask_path():
+    """The static call keeps only the radix path; on a heavy-tailed scene
+    whose workspace binning takes the coverage-mask path it still produces
+    the same lists."""
+    import dataclasses
+    cfg = dataclasses.replace(CFG, wide_rects=1)
+    scene = S.surface_scene(60_000, seed=21, frac3d=0.3, ls_loc=-4.0, ls_scale=0.8, heavy_df=3)
+    cam = S.orbit_camera(15.0, 25.0, 2.6, 1024, 640, 55.0)
+    r = Rasterizer("cuda", keep_keys=True)
+    r.forward(SceneTensors.from_numpy(scene), cam, cfg)
+    torch.cuda.synchronize()
+    ref = _workspace_lists(r)
+    touched = r.touched[: scene.n].cpu().numpy().astype(np.int64)
+    assert (touched > 256).sum() > 100
+    got = _static_lists(r, ref[3] + 4096)
+    assert got[3] == ref[3]
+    for a, b in zip(got[:3], ref[:3]):
+        np.testing.assert_array_equal(a, b)
+
+
 def test_static_scratch_rejects_sizes_beyond_its_limit():
     scene, cam = S.tiny_scene(1)
     r = Rasterizer("cuda")
