@@ -400,3 +400,28 @@ def test_wide_path_lists_without_keys():
     assert K == len(vals)
     np.testing.assert_array_equal(r.vals[:K].cpu().numpy().view(np.uint32), vals)
     np.testing.assert_array_equal(r.ranges.cpu().numpy().view(np.uint32), ranges)
+
+
+def test_capacity_overflow_on_the_wide_path():
+    """Overflow with the mask path forced: reported, nothing written past the
+    buffer, ranges cleared; the managed retry gives the oracle's lists."""
+    import dataclasses
+    scene = S.surface_scene(60_000, seed=21, frac3d=0.3, ls_loc=-4.0, ls_scale=0.8, heavy_df=3)
+    cam = S.orbit_camera(15.0, 25.0, 2.6, 1024, 640, 55.0)
+    cfg = dataclasses.replace(CFG, wide_rects=1)
+    K_ref = len(O.tile_lists(scene, cam, cfg)[1])
+    cap = K_ref // 2
+    r = Rasterizer("cuda", capacity=cap, keep_keys=True)
+    r.preprocess(SceneTensors.from_numpy(scene), cam, cfg)
+    r._ensure_capacity(cap)
+    guard = torch.full((cap + 8192,), 7, dtype=torch.int32, device="cuda")
+    r.vals = guard[:cap]
+    r.bin_sort(sync_check=False)
+    torch.cuda.synchronize()
+    assert int(r.d_count.item()) == K_ref > cap
+    assert int(r.dev_err.item()) == -2
+    assert torch.all(guard[cap:] == 7)
+    assert torch.all(r.ranges == 0)
+    r2, st2, g = gpu_forward(scene, cam, cfg, capacity=cap)
+    assert r2.capacity >= K_ref
+    assert_lists_bitexact(r2, scene, cam, cfg)
