@@ -114,6 +114,9 @@ class Rasterizer:
         self.keep_keys = keep_keys
         self.sync_check = sync_check
         self.n = -1
+        # when a list, every backward appends the (start, end) CUDA events it
+        # records around its record-gradient stage on the current stream
+        self.bwd_events = None
         self.hw = None
         self.dev_err = torch.zeros(1, dtype=torch.int32, device=self.device)
         self.d_count = torch.zeros(1, dtype=torch.int64, device=self.device)
@@ -273,6 +276,20 @@ class Rasterizer:
                                                  C.byref(self._cam_s), C.byref(self._cfg_s), _ptr(self.grad_ws),
                                                  C.byref(out), _ptr(self.dev_err), _stream()), "hgs_preprocess_bwd")
             return grads, records, prep
+        if self.bwd_events is not None:
+            st = torch.cuda.current_stream(self.device)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            abi.check(abi.hgs_render_bwd_records(C.byref(self._scene_s), C.byref(self._proj_s), C.byref(bins),
+                                                 C.byref(self._cam_s), C.byref(self._cfg_s), C.byref(self._img_s),
+                                                 C.byref(dl), _ptr(self.grad_ws), _ptr(self.dev_err), _stream()),
+                      "hgs_render_bwd_records")
+            e1.record(st)
+            self.bwd_events.append((e0, e1))
+            abi.check(abi.hgs_preprocess_bwd(C.byref(self._scene_s), C.byref(self._proj_s), C.byref(self._cam_s),
+                                             C.byref(self._cfg_s), _ptr(self.grad_ws), C.byref(out),
+                                             _ptr(self.dev_err), _stream()), "hgs_preprocess_bwd")
+            return grads
         abi.check(abi.hgs_render_bwd(C.byref(self._scene_s), C.byref(self._proj_s), C.byref(bins),
                                      C.byref(self._cam_s), C.byref(self._cfg_s), C.byref(self._img_s),
                                      C.byref(dl), _ptr(self.grad_ws), C.byref(out), _ptr(self.dev_err),
