@@ -499,6 +499,47 @@ __device__ __forceinline__ float sum1(float v) {
   return v;
 }
 
+// Transpose sum of 32 values over the warp: after the five exchange steps
+// lane l holds the warp total of value l.
+__device__ __forceinline__ float sum32(float (&v)[32], int lane) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const bool hi = lane & o;
+#pragma unroll
+    for (int i = 0; i < o; ++i) {
+      const float send = hi ? v[i] : v[i + o];
+      v[i] = (hi ? v[i + o] : v[i]) + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  return v[0];
+}
+
+// The three gradient sets of the frequency-decoupled backward in one
+// transpose: 3D, 27 values (9 slots per set); surfels, 32 of the 36 values
+// and a 4-value tail (set 2's slots 9..12).
+__device__ __forceinline__ void reduce_record3(float (&g)[3][16], bool is3d, int lane, float *const (&rows)[3],
+                                               uint32_t id) {
+  // the reduced slots 0..5, 7.. (slot 6, the depth term, is absent without
+  // a depth cotangent): the s-th is s + (s >= 6)
+  auto slot = [](int s) { return s + (s >= 6 ? 1 : 0); };
+  float v[32];
+  const int per = is3d ? 9 : 12;
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    // value k: set k / per, its (k % per)-th slot; zero past the 27 3D values
+    const float a3 = k < 27 ? g[k / 9][slot(k % 9)] : 0.0f;
+    const float a2 = g[k / 12][slot(k % 12)];
+    v[k] = is3d ? a3 : a2;
+  }
+  float tail[4] = {g[2][slot(8)], g[2][slot(9)], g[2][slot(10)], g[2][slot(11)]};
+  const float t = sum32(v, lane);
+  if (lane < 3 * per) atomicAdd(rows[lane / per] + (size_t)id * kGradW + slot(lane % per), t);
+  if (!is3d) {
+    const float u = sum4(tail, lane);
+    if ((lane & 7) == 0) atomicAdd(rows[2] + (size_t)id * kGradW + slot(8 + ((lane >> 3) & 3)), u);
+  }
+}
+
 // Warp-reduce one record's gradient and add it to the record's row.
 template <bool FULL>
 __device__ __forceinline__ void reduce_record(float (&g)[16], bool is3d, int lane, float *row) {
@@ -669,8 +710,12 @@ __global__ void __launch_bounds__(kRW * 32, NC == 1 ? 5 : 4) render_bwd_rgb_kern
     const float4 r3 = r[3];
     if (c0) pair_grad_rgb<NC>(g, s[0], e0, r0, r1, r2, r3, a.cfg);
     if (c1) pair_grad_rgb<NC>(g, s[1], e1, r0, r1, r2, r3, a.cfg);
+    if constexpr (NC == 3) {
+      reduce_record3(g, r0.w > 0.0f, lane, a.rec_grads, id);
+    } else {
 #pragma unroll
-    for (int c = 0; c < NC; ++c) reduce_record<false>(g[c], r0.w > 0.0f, lane, a.rec_grads[c] + (size_t)id * kGradW);
+      for (int c = 0; c < NC; ++c) reduce_record<false>(g[c], r0.w > 0.0f, lane, a.rec_grads[c] + (size_t)id * kGradW);
+    }
   });
 }
 
