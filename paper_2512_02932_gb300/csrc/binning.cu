@@ -1060,7 +1060,7 @@ __global__ void __launch_bounds__(kWideWarps * 32) k_wide_write(WideArgs a) {
       q2 = np == 2 ? v : q2;
       q3 = np == 3 ? v : q3;
       if (++np == 4) {
-        if (pos + 4 <= end) *reinterpret_cast<uint4 *>(a.vals + pos) = make_uint4(q0, q1, q2, q3);
+        if (pos < end && end - pos >= 4u) *reinterpret_cast<uint4 *>(a.vals + pos) = make_uint4(q0, q1, q2, q3);
         pos += 4;
         np = 0;
       }
@@ -1125,7 +1125,7 @@ __global__ void __launch_bounds__(kWideWarps * 32) k_wide_write(WideArgs a) {
     // the staged tail
     for (uint32_t k = 0; k < np; ++k) {
       const uint32_t v = k == 0 ? q0 : (k == 1 ? q1 : (k == 2 ? q2 : q3));
-      if (pos + k < end) a.vals[pos + k] = v;
+      if (pos < end && k < end - pos) a.vals[pos + k] = v;
     }
   }
 }
