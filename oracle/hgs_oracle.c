@@ -47,26 +47,36 @@ enum {
   CF_T_Z, CF_DILATION, CF_BG0, CF_BG1, CF_BG2, CF_COUNT
 };
 
-/* ambiguity bands: a pixel whose result could legitimately differ between an
- * FP32 evaluation and this FP64 one is flagged and reported, not compared.
- * In binary32 a contribution alpha*exp(-d/2) carries a relative error of
- * about 1e-5 (d ~ 11 near the cutoff, ~1e-6 relative error in d), and the
+/* Threshold decisions.  Eq. 2 with the contribution rule of Sec. 3.1 takes
+ * three kinds of discrete decision per (pixel, primitive) pair: does the pair
+ * clear alpha_min, does a surfel's hit lie beyond the near plane, and does
+ * the pixel stop before it (T' < T_min); the normal map adds the sign that
+ * turns a primitive's normal to the camera.  Where the FP64 value sits within
+ * a band around the threshold that a binary32 evaluation could cross, the
+ * decision is ambiguous: both outcomes are correct results of the method
+ * evaluated in binary32.  The renderer then enumerates the outcomes of up to
+ * ORC_MAXDEC such decisions met before the pixel terminates (at most
+ * 2^ORC_MAXDEC results, "variants"); a pixel that meets more is reported as
+ * not comparable.  In binary32 a contribution alpha*exp(-d/2) carries a
+ * relative error of about 1e-5 (d ~ 11 near the cutoff), and the
  * transmittance after a few hundred contributors about 1e-4; the bands are
  * five to ten times wider. */
 #define AMB_ALPHA_REL 5e-5   /* |alpha*G - alpha_min| <= this * alpha_min  */
 #define AMB_T_REL     1e-3   /* |T' - T_min| <= this * T_min               */
 #define AMB_NEAR_REL  1e-5   /* |z - near| <= this * max(1, near)          */
 #define AMB_FLIP      1e-5   /* |n . mu_c| / |mu_c| below this             */
-/* conditioning: in binary32, (u, v) evaluated from the pixel's offset to the
- * projected centre carry an error of up to COND_ULPS ulps of the magnitude of
- * the terms that cancel, |du/dx dx| + |du/dy dy| (likewise v): a few ulps for
- * the record's coefficients and two for the evaluation.  A pixel is not
- * comparable when that error can move one contribution by more than
- * COND_ALPHA (twice that is still under the 1e-3 image tolerance).  Only
- * extremely anisotropic footprints evaluated far from their centre (e.g. a
- * 1e5:1 ribbon thousands of pixels along its length) reach it. */
+#define ORC_MAXDEC    3
+#define ORC_MAXV      (1 << ORC_MAXDEC)
+/* Conditioning.  In binary32, (u, v) evaluated from the pixel's offset to
+ * the projected centre carry an error of up to COND_ULPS ulps of the
+ * magnitude of the terms that cancel, |du/dx dx| + |du/dy dy| (likewise v):
+ * a few ulps for the record's coefficients and two for the evaluation.  That
+ * bounds the error of each contribution (dag below); the renderer carries it
+ * through Eq. 2 as a per-channel tolerance on the pixel's result, and widens
+ * the alpha_min and T_min bands by it.  It is negligible except for extremely
+ * anisotropic footprints evaluated far from their centre (e.g. a 1e5:1
+ * ribbon thousands of pixels along its length). */
 #define COND_ULPS     8.0
-#define COND_ALPHA    4e-4
 #define EPS32         5.960464477539063e-08
 
 /* ------------------------------------------------------------------------ */
@@ -359,7 +369,7 @@ float orc_contract_log(float x) { return orc_c_log(x); }
 /* (1) FP64 per-pixel renderer                                               */
 /* ------------------------------------------------------------------------ */
 typedef struct {
-  int type, valid, amb_near;
+  int type, valid;
   double alpha;                   /* opacity used for contributions */
   double col[3], nrm[3];
   double X, Y, Z;                 /* camera-space centre */
@@ -415,8 +425,8 @@ static void prep_prim(orc_ctx *C, int64_t i, const double *mu64, const double *l
                       (float)nearz, (float)amin, (float)C->cfg[CF_DILATION], rr, &dbb))
       return;
   }
-  if (fabs(p->Z - nearz) <= AMB_NEAR_REL * fmax(1.0, nearz)) p->amb_near = 1;
-  if (!(p->Z > nearz) && !p->amb_near) return;
+  /* (the contract's binary32 centre depth is beyond the near plane; the FP64
+   * depth may differ from it by a rounding, which changes nothing below) */
   /* activations (Sec. 3.1): scale = exp(log s), unit quaternion, sigmoid */
   double s[3] = {exp(ls64[0]), exp(ls64[1]), exp(ls64[2])};
   double q[4] = {q64[0], q64[1], q64[2], q64[3]};
@@ -619,7 +629,17 @@ void orc_free(void *ctx) {
   free(C->P); free(C->cstart); free(C->citems); free(C);
 }
 
-typedef struct { uint32_t key; int32_t id; int amb; double at, z; } contrib_t;
+/* a listed (pixel, primitive) pair */
+enum { PA_ALPHA = 1, PA_NEAR = 2, PA_FLIP = 4 };
+typedef struct {
+  uint32_t key;
+  int32_t id;
+  uint8_t flags;        /* PA_*: which of its decisions sit in a band */
+  uint8_t a_ok, z_ok;   /* the FP64 outcomes: ag >= alpha_min, hit beyond near */
+  double ag;            /* alpha exp(-d/2), unclamped */
+  double dag;           /* conditioning bound on the binary32 error of ag */
+  double z;             /* per-pixel depth: centre depth (3D), hit depth (2D) */
+} contrib_t;
 
 static int cmp_contrib(const void *A, const void *B) {
   const contrib_t *a = (const contrib_t *)A, *b = (const contrib_t *)B;
@@ -664,81 +684,182 @@ static int surfel_hit(const orc_ctx *C, const prim_t *p, double px, double py, d
 }
 
 /* Unified distance (Eq. 1) and contribution (Sec. 3.1) of primitive p at the
- * pixel centre (px, py).  Returns 1 if the pair must be listed: it
- * contributes (*at_out > 0), or its contribution decision sits inside an
- * ambiguity band (*amb = 1; *at_out = 0 if it does not contribute).  Whether
- * an ambiguous pair matters is decided by the blend: only pairs reached
- * before the pixel terminates can change the result. */
-static int eval_pair(const orc_ctx *C, const prim_t *p, double px, double py,
-                     double *at_out, double *z_out, int *amb) {
-  double d, z;
-  int a = 0;
+ * pixel centre (px, py).  Returns 1 and fills *c if the pair must be listed:
+ * it contributes, or one of its decisions sits in a band (c->flags).  The
+ * blend decides whether a listed pair matters: only pairs reached before the
+ * pixel terminates can change the result. */
+static int eval_pair(const orc_ctx *C, const prim_t *p, double px, double py, contrib_t *c) {
+  double d, z, u, v;
   const double amin = C->cfg[CF_ALPHA_MIN], nearz = C->cfg[CF_NEAR];
+  uint8_t flags = 0;
+  int z_ok = 1;
   if (p->type == 1) {
     double dx = px - p->mx, dy = py - p->my;
-    double u = p->ca * dx + p->cb * dy, v = p->cc * dy;
+    u = p->ca * dx + p->cb * dy;
+    v = p->cc * dy;
     d = u * u + v * v;
     z = p->Z;
   } else {
     double sol[3];
     if (!surfel_hit(C, p, px, py, sol)) return 0;
-    double u = sol[0], v = sol[1];
+    u = sol[0];
+    v = sol[1];
     z = sol[2];
     d = u * u + v * v;
-    if (fabs(z - nearz) <= AMB_NEAR_REL * fmax(1.0, nearz)) {
-      if (p->alpha * exp(-0.5 * d) >= amin * (1.0 - AMB_ALPHA_REL)) a = 1;
-    }
-    if (!(z > nearz)) {
-      if (!a) return 0;
-      *at_out = 0.0; *z_out = z; *amb = 1;
-      return 1;
-    }
+    z_ok = z > nearz;
+    if (fabs(z - nearz) <= AMB_NEAR_REL * fmax(1.0, nearz)) flags |= PA_NEAR;
   }
-  double ag = p->alpha * exp(-0.5 * d);
-  if (fabs(ag - amin) <= AMB_ALPHA_REL * amin) a = 1;
-  int contributes = ag >= amin;
-  if (contributes && !a) {
-    /* conditioning of (u, v) as functions of the offset to the centre */
-    double ex = px - p->mx, ey = py - p->my, u, v, dux, duy, dvx, dvy;
+  const double ag = p->alpha * exp(-0.5 * d);
+  if (ag < 0.1 * amin && !(flags & PA_NEAR)) return 0;  /* no binary32 error reaches the threshold from here */
+  /* conditioning of (u, v) as functions of the offset to the centre */
+  double dag = 0.0;
+  {
+    double ex = px - p->mx, ey = py - p->my, dux, duy, dvx, dvy;
     if (p->type == 1) {
-      u = p->ca * ex + p->cb * ey; v = p->cc * ey;
       dux = p->ca; duy = p->cb; dvx = 0.0; dvy = p->cc;
     } else {
-      double s0[3], s1[3], s2[3];
+      double s1[3], s2[3];
       const double hh = 1e-3;
-      if (surfel_hit(C, p, px, py, s0) && surfel_hit(C, p, px + hh, py, s1) &&
-          surfel_hit(C, p, px, py + hh, s2)) {
-        u = s0[0]; v = s0[1];
-        dux = (s1[0] - s0[0]) / hh; dvx = (s1[1] - s0[1]) / hh;
-        duy = (s2[0] - s0[0]) / hh; dvy = (s2[1] - s0[1]) / hh;
+      if (surfel_hit(C, p, px + hh, py, s1) && surfel_hit(C, p, px, py + hh, s2)) {
+        dux = (s1[0] - u) / hh; dvx = (s1[1] - v) / hh;
+        duy = (s2[0] - u) / hh; dvy = (s2[1] - v) / hh;
       } else {
-        u = v = dux = duy = dvx = dvy = 0.0;
+        dux = duy = dvx = dvy = 0.0;
       }
     }
-    double du = COND_ULPS * EPS32 * (fabs(dux * ex) + fabs(duy * ey));
-    double dv = COND_ULPS * EPS32 * (fabs(dvx * ex) + fabs(dvy * ey));
+    const double eps32 = 5.960464477539063e-08;
+    double du = COND_ULPS * eps32 * (fabs(dux * ex) + fabs(duy * ey));
+    double dv = COND_ULPS * eps32 * (fabs(dvx * ex) + fabs(dvy * ey));
     double dd = 2.0 * (fabs(u) * du + fabs(v) * dv) + du * du + dv * dv;
-    if (ag * 0.5 * dd > COND_ALPHA) a = 1;
+    /* ag moves by at most ag (e^(dd/2) - 1) when d moves by dd */
+    dag = ag * expm1(0.5 * dd);
   }
-  if (contributes && p->ndot < AMB_FLIP) a = 1;
-  if (p->amb_near && (contributes || a)) {
-    a = 1;
-    if (!(p->Z > nearz)) contributes = 0;
-  }
-  if (!contributes && !a) return 0;
-  double amax = C->cfg[CF_ALPHA_MAX];
-  *at_out = contributes ? (ag < amax ? ag : amax) : 0.0;
-  *z_out = z;
-  *amb = a;
+  const int a_ok = ag >= amin;
+  if (fabs(ag - amin) <= fmax(AMB_ALPHA_REL * amin, dag)) flags |= PA_ALPHA;
+  if (p->ndot < AMB_FLIP) flags |= PA_FLIP;
+  if (!(a_ok && z_ok) && !(flags & (PA_ALPHA | PA_NEAR))) return 0;
+  c->flags = flags;
+  c->a_ok = (uint8_t)a_ok;
+  c->z_ok = (uint8_t)z_ok;
+  c->ag = ag;
+  c->dag = dag;
+  c->z = z;
   return 1;
 }
 
+/* One blend of a pixel's sorted pairs (Eq. 2, front to back) with the
+ * outcome of the j-th ambiguous decision met taken from bit j of `choice`
+ * (0: the FP64 outcome, 1: the other one).  o: r, g, b, depth, nx, ny, nz,
+ * alpha, T_final, contributors; tol: per-output bound of the conditioning
+ * errors (dag) carried through Eq. 2.  Returns the number of ambiguous
+ * decisions met. */
+static int blend_run(const orc_ctx *C, const contrib_t *buf, int cnt, uint32_t choice, const double vmax[10],
+                     double o[10], double tol[10]) {
+  const double Tmin = C->cfg[CF_T_MIN], amax = C->cfg[CF_ALPHA_MAX];
+  double T = 1.0, Cc[3] = {0, 0, 0}, D = 0, Nn[3] = {0, 0, 0}, tT = 0.0;
+  int used = 0, nd = 0;
+  for (int k = 0; k < 10; ++k) tol[k] = 0.0;
+#define TAKE_BIT() (nd < 32 ? (int)((choice >> nd++) & 1u) : (nd++, 0))
+  for (int k = 0; k < cnt; ++k) {
+    const contrib_t *c = &buf[k];
+    const prim_t *p = &C->P[c->id];
+    int a_ok = c->a_ok, z_ok = c->z_ok;
+    if (c->flags & PA_ALPHA) a_ok ^= TAKE_BIT();
+    if (c->flags & PA_NEAR) z_ok ^= TAKE_BIT();
+    if (!(a_ok && z_ok)) continue;
+    const double at = c->ag < amax ? c->ag : amax;
+    const double Tn = T * (1.0 - at);
+    int stop = Tn < Tmin;
+    if (fabs(Tn - Tmin) <= fmax(AMB_T_REL * Tmin, tT)) stop ^= TAKE_BIT();
+    if (stop) break;
+    double sg = 1.0;
+    if (c->flags & PA_FLIP) sg = TAKE_BIT() ? -1.0 : 1.0;
+    const double w = at * T;
+    for (int r = 0; r < 3; ++r) { Cc[r] += w * p->col[r]; Nn[r] += w * sg * p->nrm[r]; }
+    D += w * c->z;
+    /* conditioning: moving this contribution by dat moves output ch by at
+     * most dat T (|v_ch| + max |v| over the pixel's pairs and background) */
+    const double dat = (c->ag - c->dag > amax) ? 0.0 : c->dag;
+    if (dat > 0.0) {
+      const double v[10] = {p->col[0], p->col[1], p->col[2], c->z, p->nrm[0], p->nrm[1], p->nrm[2], 1.0, 1.0, 0.0};
+      for (int ch = 0; ch < 9; ++ch) tol[ch] += dat * T * (fabs(v[ch]) + vmax[ch]);
+      tT += dat * T;
+    }
+    T = Tn;
+    used++;
+  }
+#undef TAKE_BIT
+  o[0] = Cc[0] + T * C->cfg[CF_BG0];
+  o[1] = Cc[1] + T * C->cfg[CF_BG1];
+  o[2] = Cc[2] + T * C->cfg[CF_BG2];
+  o[3] = D;
+  o[4] = Nn[0]; o[5] = Nn[1]; o[6] = Nn[2];
+  o[7] = 1.0 - T;
+  o[8] = T;
+  o[9] = used;
+  return nd;
+}
+
+/* All outcomes of the first ORC_MAXDEC ambiguous decisions, depth first:
+ * a run that meets a decision beyond its fixed prefix splits there.  leaves:
+ * up to ORC_MAXV x 20 doubles (o[10], tol[10]).  Sets *over when a run meets
+ * more than ORC_MAXDEC decisions. */
+static void enum_leaves(const orc_ctx *C, const contrib_t *buf, int cnt, uint32_t prefix, int plen,
+                        const double vmax[10], double *leaves, int *nleaves, int *over) {
+  double o[10], tol[10];
+  const int nd = blend_run(C, buf, cnt, prefix, vmax, o, tol);
+  if (nd <= plen) {
+    double *L = leaves + 20 * (*nleaves);
+    for (int k = 0; k < 10; ++k) { L[k] = o[k]; L[10 + k] = tol[k]; }
+    (*nleaves)++;
+    return;
+  }
+  if (plen == ORC_MAXDEC) {
+    *over = 1;
+    double *L = leaves + 20 * (*nleaves);
+    for (int k = 0; k < 10; ++k) { L[k] = o[k]; L[10 + k] = tol[k]; }
+    (*nleaves)++;
+    return;
+  }
+  enum_leaves(C, buf, cnt, prefix, plen + 1, vmax, leaves, nleaves, over);
+  enum_leaves(C, buf, cnt, prefix | (1u << plen), plen + 1, vmax, leaves, nleaves, over);
+}
+
+/* The sorted pairs of pixel (ix, iy) and the per-output magnitudes bounding
+ * what lies behind a pair (for the conditioning tolerance). */
+static int pixel_pairs(const orc_ctx *C, int ix, int iy, contrib_t *buf, double vmax[10]) {
+  double px = ix + 0.5, py = iy + 0.5;
+  int cxi = ix / C->cell, cyi = iy / C->cell;
+  int64_t c = (int64_t)cyi * C->gx + cxi;
+  int cnt = 0;
+  for (int k = 0; k < 10; ++k) vmax[k] = 0.0;
+  for (int r = 0; r < 3; ++r) vmax[r] = fabs(C->cfg[CF_BG0 + r]);
+  vmax[7] = vmax[8] = 1.0;
+  for (int64_t k = C->cstart[c]; k < C->cstart[c + 1]; ++k) {
+    int32_t id = C->citems[k];
+    const prim_t *p = &C->P[id];
+    if (!p->valid) continue;
+    if (eval_pair(C, p, px, py, &buf[cnt])) {
+      buf[cnt].key = p->key;
+      buf[cnt].id = id;
+      const double v[7] = {p->col[0], p->col[1], p->col[2], buf[cnt].z, p->nrm[0], p->nrm[1], p->nrm[2]};
+      for (int ch = 0; ch < 7; ++ch)
+        if (fabs(v[ch]) > vmax[ch]) vmax[ch] = fabs(v[ch]);
+      cnt++;
+    }
+  }
+  qsort(buf, cnt, sizeof(contrib_t), cmp_contrib);
+  return cnt;
+}
+
 /* Render npix pixels (pix: npix x 2 int32 pixel indices, or NULL = full frame
- * in row-major order).  out: npix x 10 doubles
- *   [r, g, b, depth, nx, ny, nz, alpha, T_final, n_contrib]
- * amb: npix flags (1 = ambiguous: a pair reached before termination sits in
- * one of the bands above). */
-void orc_render(void *ctx, int64_t npix, const int32_t *pix, double *out, uint8_t *amb) {
+ * in row-major order), taking every decision the FP64 way.
+ * out: npix x 10 doubles [r, g, b, depth, nx, ny, nz, alpha, T_final,
+ * n_contrib].  flags (npix): bit 0 = ambiguous decisions met (more results
+ * are correct: orc_render_variants lists them), bit 1 = more than ORC_MAXDEC
+ * of them (not comparable).  tol (npix x 10, may be NULL): the conditioning
+ * tolerance of this result. */
+void orc_render(void *ctx, int64_t npix, const int32_t *pix, double *out, uint8_t *flags, double *tol) {
   orc_ctx *C = (orc_ctx *)ctx;
   if (!pix) npix = (int64_t)C->W * C->H;
 #pragma omp parallel
@@ -749,53 +870,60 @@ void orc_render(void *ctx, int64_t npix, const int32_t *pix, double *out, uint8_
       int ix, iy;
       if (pix) { ix = pix[2 * q]; iy = pix[2 * q + 1]; }
       else { ix = (int)(q % C->W); iy = (int)(q / C->W); }
-      double px = ix + 0.5, py = iy + 0.5;
-      int cxi = ix / C->cell, cyi = iy / C->cell;
-      int64_t c = (int64_t)cyi * C->gx + cxi;
-      int cnt = 0, am = 0;
-      for (int64_t k = C->cstart[c]; k < C->cstart[c + 1]; ++k) {
-        int32_t id = C->citems[k];
-        const prim_t *p = &C->P[id];
-        if (!p->valid) continue;
-        double at = 0, z = 0;
-        int a = 0;
-        if (eval_pair(C, p, px, py, &at, &z, &a)) {
-          buf[cnt].key = p->key; buf[cnt].id = id; buf[cnt].at = at; buf[cnt].z = z;
-          buf[cnt].amb = a;
-          cnt++;
-        }
+      double vmax[10], t[10];
+      const int cnt = pixel_pairs(C, ix, iy, buf, vmax);
+      const int nd = blend_run(C, buf, cnt, 0u, vmax, out + 10 * q, t);
+      uint8_t f = 0;
+      if (nd > 0) f |= 1;
+      if (nd > ORC_MAXDEC) f |= 2;
+      else if (nd > 0) {
+        /* a branch can meet decisions the FP64 path does not */
+        double lv[ORC_MAXV * 20];
+        int nl = 0, over = 0;
+        enum_leaves(C, buf, cnt, 0u, 0, vmax, lv, &nl, &over);
+        if (over) f |= 2;
       }
-      qsort(buf, cnt, sizeof(contrib_t), cmp_contrib);
-      /* front-to-back alpha blending, Eq. 2 */
-      double T = 1.0, Cc[3] = {0, 0, 0}, D = 0, Nn[3] = {0, 0, 0};
-      int used = 0;
-      const double Tmin = C->cfg[CF_T_MIN];
-      for (int k = 0; k < cnt; ++k) {
-        const prim_t *p = &C->P[buf[k].id];
-        if (buf[k].amb) am = 1;
-        double at = buf[k].at;
-        if (at <= 0.0) continue;
-        double Tn = T * (1.0 - at);
-        if (fabs(Tn - Tmin) <= AMB_T_REL * Tmin) am = 1;
-        if (Tn < Tmin) break;
-        double w = at * T;
-        for (int r = 0; r < 3; ++r) { Cc[r] += w * p->col[r]; Nn[r] += w * p->nrm[r]; }
-        D += w * buf[k].z;
-        T = Tn;
-        used++;
-      }
-      double *o = out + 10 * q;
-      o[0] = Cc[0] + T * C->cfg[CF_BG0];
-      o[1] = Cc[1] + T * C->cfg[CF_BG1];
-      o[2] = Cc[2] + T * C->cfg[CF_BG2];
-      o[3] = D;
-      o[4] = Nn[0]; o[5] = Nn[1]; o[6] = Nn[2];
-      o[7] = 1.0 - T;
-      o[8] = T;
-      o[9] = used;
-      amb[q] = (uint8_t)am;
+      flags[q] = f;
+      if (tol)
+        for (int k = 0; k < 10; ++k) tol[10 * q + k] = t[k];
     }
     free(buf);
+  }
+}
+
+/* Every correct result of npix pixels: nvar[q] results (1 .. ORC_MAXV) of 20
+ * doubles each in leaves[q * ORC_MAXV * 20 ..]: the 10 outputs of orc_render
+ * and their conditioning tolerance.  The first is orc_render's. */
+void orc_render_variants(void *ctx, int64_t npix, const int32_t *pix, int32_t *nvar, double *leaves) {
+  orc_ctx *C = (orc_ctx *)ctx;
+#pragma omp parallel
+  {
+    contrib_t *buf = (contrib_t *)malloc(sizeof(contrib_t) * (C->maxcell > 0 ? C->maxcell : 1));
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t q = 0; q < npix; ++q) {
+      double vmax[10];
+      const int cnt = pixel_pairs(C, pix[2 * q], pix[2 * q + 1], buf, vmax);
+      int nl = 0, over = 0;
+      enum_leaves(C, buf, cnt, 0u, 0, vmax, leaves + (int64_t)q * ORC_MAXV * 20, &nl, &over);
+      nvar[q] = nl;
+    }
+    free(buf);
+  }
+}
+
+int orc_max_variants(void) { return ORC_MAXV; }
+
+/* The contribution alpha exp(-d/2) (unclamped) of primitive i alone at npix
+ * pixels, 0 where it does not contribute (Sec. 3.1); used to pick the pixels
+ * a primitive's finite-difference check looks at. */
+void orc_pair_alpha(void *ctx, int64_t i, int64_t npix, const int32_t *pix, double *ag) {
+  orc_ctx *C = (orc_ctx *)ctx;
+  const prim_t *p = &C->P[i];
+#pragma omp parallel for schedule(static)
+  for (int64_t q = 0; q < npix; ++q) {
+    contrib_t c;
+    ag[q] = 0.0;
+    if (p->valid && eval_pair(C, p, pix[2 * q] + 0.5, pix[2 * q + 1] + 0.5, &c) && c.a_ok && c.z_ok) ag[q] = c.ag;
   }
 }
 

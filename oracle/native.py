@@ -2,7 +2,9 @@
 
 Functions and what pins them (tests/test_oracle_*.py):
   Oracle.render      FP64 per-pixel renderer, Eq. 1, Sec. 3.1 contribution,
-                     Eq. 2 blending, App. C projections.  Pinned by closed forms
+                     Eq. 2 blending, App. C projections; render_checked adds
+                     every correct result where a threshold decision is
+                     ambiguous, and the conditioning tolerance.  Pinned by closed forms
                      (isotropic 3D Gaussian, face-on surfel), the edge-on surfel
                      vanishing, 3D->2D convergence as s_z -> 0, brute-force
                      compositing, order-of-input invariance, and the
@@ -38,7 +40,13 @@ def lib():
         L.orc_prepare.restype = P
         L.orc_prepare.argtypes = [C.c_int64, P, P, P, P, P, P, C.c_int, P, C.c_int, C.c_int, P]
         L.orc_render.restype = None
-        L.orc_render.argtypes = [P, C.c_int64, P, P, P]
+        L.orc_render.argtypes = [P, C.c_int64, P, P, P, P]
+        L.orc_render_variants.restype = None
+        L.orc_render_variants.argtypes = [P, C.c_int64, P, P, P]
+        L.orc_max_variants.restype = C.c_int
+        L.orc_max_variants.argtypes = []
+        L.orc_pair_alpha.restype = None
+        L.orc_pair_alpha.argtypes = [P, C.c_int64, C.c_int64, P, P]
         L.orc_set_prim.restype = None
         L.orc_set_prim.argtypes = [P, C.c_int64, P, P, P, C.c_double, P, C.c_int]
         L.orc_free.restype = None
@@ -101,9 +109,7 @@ class Oracle:
         except Exception:
             pass
 
-    def render(self, pixels=None):
-        """pixels: (P, 2) int pixel indices (x, y) or None for the full frame
-        (row-major).  Returns (out (P, 10) float64, amb (P,) bool)."""
+    def _render(self, pixels):
         if pixels is None:
             npix = self.W * self.H
             pp = None
@@ -112,19 +118,66 @@ class Oracle:
             npix = len(pixels)
             pp = _p(pixels)
         out = np.zeros((npix, 10), np.float64)
-        amb = np.zeros(npix, np.uint8)
-        lib().orc_render(self.ctx, npix, pp, _p(out), _p(amb))
-        return out, amb.astype(bool)
+        flags = np.zeros(npix, np.uint8)
+        tol = np.zeros((npix, 10), np.float64)
+        lib().orc_render(self.ctx, npix, pp, _p(out), _p(flags), _p(tol))
+        return out, flags, tol
+
+    def render(self, pixels=None):
+        """pixels: (P, 2) int pixel indices (x, y) or None for the full frame
+        (row-major).  Returns (out (P, 10) float64, amb (P,) bool): the result
+        with every threshold decision taken the FP64 way, and whether the
+        pixel met an ambiguous decision (other results are correct too)."""
+        out, flags, _ = self._render(pixels)
+        return out, flags != 0
+
+    def render_checked(self, pixels=None):
+        """Everything an image comparison needs for `pixels` (None = full
+        frame, row-major): out (P, 10) and tol (P, 10), the FP64-decision
+        result and its conditioning tolerance; flags (P,) (bit 0: ambiguous
+        decisions met, bit 1: more than the renderer enumerates); variants:
+        {pixel row: (nv, 20) every correct result and its tolerance} for the
+        pixels with bit 0 set."""
+        out, flags, tol = self._render(pixels)
+        if pixels is None:
+            yy, xx = np.mgrid[0:self.H, 0:self.W]
+            pixels = np.stack([xx.ravel(), yy.ravel()], 1)
+        pixels = np.ascontiguousarray(pixels, np.int32)
+        rows = np.nonzero(flags & 1)[0]
+        variants = {}
+        if len(rows):
+            mv = int(lib().orc_max_variants())
+            sub = np.ascontiguousarray(pixels[rows], np.int32)
+            nv = np.zeros(len(rows), np.int32)
+            leaves = np.zeros((len(rows), mv, 20), np.float64)
+            lib().orc_render_variants(self.ctx, len(rows), _p(sub), _p(nv), _p(leaves))
+            for k, r in enumerate(rows):
+                variants[int(r)] = leaves[k, :nv[k]].copy()
+        return {"pixels": pixels, "out": out, "tol": tol, "flags": flags, "variants": variants}
 
     def render_maps(self):
         """Full frame as planar maps: dict rgb (3,H,W), depth, normal (3,H,W),
-        alpha, T, n_contrib, amb (H,W)."""
-        out, amb = self.render(None)
+        alpha, T, n_contrib, amb (H,W) (ambiguous decisions met, or a
+        conditioning tolerance above 1e-4: pixels whose gradient the
+        comparison leaves out), and `checked`, the render_checked() record of
+        the frame."""
+        chk = self.render_checked(None)
+        out, flags = chk["out"], chk["flags"]
         H, W = self.H, self.W
         o = out.reshape(H, W, 10)
+        amb = (flags != 0) | (chk["tol"][:, :8].max(1) > 1e-4)
         return {"rgb": np.moveaxis(o[..., 0:3], -1, 0), "depth": o[..., 3],
                 "normal": np.moveaxis(o[..., 4:7], -1, 0), "alpha": o[..., 7],
-                "T": o[..., 8], "n_contrib": o[..., 9], "amb": amb.reshape(H, W)}
+                "T": o[..., 8], "n_contrib": o[..., 9], "amb": amb.reshape(H, W),
+                "checked": chk}
+
+    def pair_alpha(self, i, pixels):
+        """alpha exp(-d/2) of primitive i alone at `pixels` (P, 2), 0 where
+        it does not contribute."""
+        pixels = np.ascontiguousarray(pixels, np.int32)
+        out = np.zeros(len(pixels), np.float64)
+        lib().orc_pair_alpha(self.ctx, int(i), len(pixels), _p(pixels), _p(out))
+        return out
 
     def set_prim(self, i, mean, log_scale, quat, logit, sh, type_):
         a = [np.ascontiguousarray(x, np.float64) for x in (mean, log_scale, quat, sh)]

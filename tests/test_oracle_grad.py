@@ -1,6 +1,8 @@
 """The FP64 autograd formulation's gradients against central finite
 differences of the C oracle (an independent implementation of the same image
 function).  CPU only."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -21,19 +23,23 @@ def _scenes():
     sc, _ = S.tiny_scene(0)
     sc = sc.subset(np.arange(300))
     cam = S.pinhole(64, 64, 60.0)
-    yield "tiny-deg0", sc, cam
+    yield "tiny-deg0", sc, cam, CFG
     sc3 = S.surface_scene(300, seed=7, frac3d=0.5, ls_loc=-2.6, ls_scale=0.4)
     cam3 = S.orbit_camera(20.0, 15.0, 3.0, 64, 48, 50.0)
-    yield "surface-deg3", sc3, cam3
+    yield "surface-deg3", sc3, cam3, CFG
+    # surfels whose buffered s_z lies in the gate of Eqs. 6-7
+    scm = sc.copy()
+    scm.log_scales[scm.types == 0, 2] = np.log(np.random.default_rng(4).uniform(0.9, 1.2, (scm.types == 0).sum()))
+    yield "tiny-modulated", scm, cam, dataclasses.replace(CFG, lambda_z=1.7, T_z=0.1)
 
 
 @pytest.mark.parametrize("case", list(_scenes()), ids=lambda c: c[0])
 def test_autograd_matches_finite_differences(case):
-    name, sc, cam = case
+    name, sc, cam, cfg = case
     H, W = cam.height, cam.width
     cot = S.random_cotangents(11, H, W)
-    _, grads = AR.vjp(sc, cam, CFG, cot)
-    orc = O.Oracle(sc, cam, CFG)
+    _, grads = AR.vjp(sc, cam, cfg, cot)
+    orc = O.Oracle(sc, cam, cfg)
     base_out, _ = orc.render()
     rng = np.random.default_rng(3)
     # primitives that touch the image
@@ -51,7 +57,8 @@ def test_autograd_matches_finite_differences(case):
             else:
                 comps = [(int(rng.integers(ncomp)),)]
             if fname == "log_scales" and sc.types[i] == 0:
-                comps = [(int(rng.integers(2)),)]
+                # s_z of a surfel enters only through the modulation (Eqs. 6-7)
+                comps = [(int(rng.integers(2)),)] + ([(2,)] if name == "tiny-modulated" else [])
             for c in comps:
                 base = {k: getattr(sc, k)[i].astype(np.float64).copy() for k in
                         ("means", "log_scales", "quats", "sh")}

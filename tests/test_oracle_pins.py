@@ -345,3 +345,174 @@ def test_contract_depth_order_matches_fp64_depth():
     z32 = db.view(np.float32).astype(np.float64)
     z64 = sc.means.astype(np.float64) @ np.asarray(cam.R, np.float64)[2] + float(cam.t[2])
     np.testing.assert_allclose(z32, z64, rtol=2e-7)
+
+
+# ---------------------------------------------------------------------------
+# scale modulation of 2D Gaussians (Sec. 3.2, Eqs. 6-7)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("sz,lam,theta,Tz", [
+    (0.9, 1.0, 1.05, 1e-3),    # gate closed: alpha unchanged
+    (1.2, 1.0, 1.05, 1e-3),    # gate open: alpha * exp(-s_z)
+    (1.05, 1.7, 1.05, 0.1),    # gate at one half, lambda_z != 1
+    (1.10, 2.3, 1.05, 0.05),   # gate sigmoid(1)
+    (0.95, 0.6, 1.05, 0.08),   # gate sigmoid(-1.25)
+])
+def test_scale_modulation_closed_form(sz, lam, theta, Tz):
+    """A face-on surfel whose buffered s_z sits anywhere around theta_z: every
+    pixel is the face-on closed form with alpha replaced by
+    alpha * exp(-lambda_z * sigmoid((s_z - theta_z) / T_z) * s_z)."""
+    import dataclasses
+    cfg = dataclasses.replace(CFG, lambda_z=lam, theta_z=theta, T_z=Tz)
+    cam = S.pinhole(64, 48, 55.0)
+    z, su, sv, logit = 2.0, 0.07, 0.05, 2.5
+    sc = one_prim_scene((0.05, -0.02, z), (math.log(su), math.log(sv), math.log(sz)), (1, 0, 0, 0), logit,
+                        type_=0)
+    m = O.Oracle(sc, cam, cfg).render_maps()
+    X, Y = pixel_centres(cam)
+    mu = sc.means[0].astype(np.float64)
+    u = ((X - cam.cx) / cam.fx * mu[2] - mu[0]) / math.exp(float(sc.log_scales[0, 0]))
+    v = ((Y - cam.cy) / cam.fy * mu[2] - mu[1]) / math.exp(float(sc.log_scales[0, 1]))
+    s_z = math.exp(float(sc.log_scales[0, 2]))
+    gate = 1.0 / (1.0 + math.exp(-(s_z - theta) / Tz))
+    alpha = 1 / (1 + math.exp(-float(sc.opacity_logits[0]))) * math.exp(-lam * gate * s_z)
+    a = alpha * np.exp(-0.5 * (u * u + v * v))
+    a = np.where(a >= cfg.alpha_min, np.minimum(a, cfg.alpha_max), 0.0)
+    ok = ~m["amb"]
+    assert ok.mean() > 0.99
+    np.testing.assert_allclose(m["alpha"][ok], a[ok], atol=1e-12)
+    # the torch formulation agrees with the C oracle on the same config
+    r = AR.render(sc, cam, cfg)
+    np.testing.assert_allclose(r["alpha"].detach().numpy().reshape(cam.height, cam.width)[ok], a[ok], atol=1e-12)
+
+
+def test_scale_modulation_leaves_3d_gaussians_alone():
+    """Eqs. 6-7 act on 2D Gaussians only: a 3D Gaussian with s_z above
+    theta_z renders the same with and without the modulation."""
+    import dataclasses
+    cam = S.pinhole(48, 48, 60.0)
+    sc = one_prim_scene((0.0, 0.0, 4.0), (math.log(0.08), math.log(0.05), math.log(1.3)), (0.9, 0.1, 0.2, 0.3),
+                        1.0, type_=1)
+    m0 = O.Oracle(sc, cam, dataclasses.replace(CFG, lambda_z=0.0)).render_maps()
+    m1 = O.Oracle(sc, cam, dataclasses.replace(CFG, lambda_z=2.0, T_z=0.1)).render_maps()
+    assert m0["alpha"].max() > 0.3
+    np.testing.assert_array_equal(m0["alpha"], m1["alpha"])
+
+
+@pytest.mark.parametrize("sz,lam,Tz", [(1.05, 1.7, 0.1), (1.12, 0.8, 0.05), (0.97, 2.0, 0.04)])
+def test_scale_modulation_gradient_closed_form(sz, lam, Tz):
+    """d alpha_pix / d log s_z of Eqs. 6-7 in closed form at pixels of a
+    face-on surfel: with g = sigmoid((s - theta)/T) and s = exp(l),
+    d alpha* / d l = -lambda alpha* s (g + s g (1 - g) / T), and alpha_pix =
+    alpha* exp(-d/2) below the clamp.  The torch formulation's autograd must
+    reproduce it."""
+    import dataclasses
+    cfg = dataclasses.replace(CFG, lambda_z=lam, theta_z=1.05, T_z=Tz)
+    cam = S.pinhole(32, 32, 55.0)
+    sc = one_prim_scene((0.0, 0.0, 2.0), (math.log(0.15), math.log(0.12), math.log(sz)), (1, 0, 0, 0), 0.3,
+                        type_=0)
+    cot = {"rgb": np.zeros((3, 32, 32)), "depth": np.zeros((32, 32)), "normal": np.zeros((3, 32, 32)),
+           "alpha": np.zeros((32, 32))}
+    pix = [(16, 16), (18, 15), (13, 19)]
+    for (x, y) in pix:
+        cot["alpha"][y, x] = 1.0
+    out, grads = AR.vjp(sc, cam, cfg, cot)
+    s = math.exp(float(sc.log_scales[0, 2]))
+    g = 1.0 / (1.0 + math.exp(-(s - 1.05) / Tz))
+    dlog = -lam * s * (g + s * g * (1.0 - g) / Tz)
+    expect = sum(out["alpha"][y, x] for (x, y) in pix) * dlog
+    assert all(0.0 < out["alpha"][y, x] < CFG.alpha_max for (x, y) in pix)
+    assert abs(grads["log_scales"][0, 2] - expect) <= 1e-10 * abs(expect)
+    # and the C oracle's central difference
+    orc = O.Oracle(sc, cam, cfg)
+    h = 1e-6
+    vals = []
+    for sgn in (1, -1):
+        ls = sc.log_scales[0].astype(np.float64).copy()
+        ls[2] += sgn * h
+        orc.set_prim(0, sc.means[0].astype(np.float64), ls, sc.quats[0].astype(np.float64),
+                     float(sc.opacity_logits[0]), sc.sh[0].astype(np.float64), 0)
+        o, _ = orc.render(np.array(pix, np.int32))
+        vals.append(o[:, 7].sum())
+    fd = (vals[0] - vals[1]) / (2 * h)
+    assert abs(fd - expect) <= 1e-6 * abs(expect)
+
+
+# ---------------------------------------------------------------------------
+# view-dependent colour (Sec. 3.1): degree-1 SH in closed form
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("az", [0.0, 35.0, 160.0])
+def test_sh_degree1_view_direction_closed_form(az):
+    """Colour at degree 1 is 0.5 + C0 f_0 + k1 (-f_{1,-1} d_y + f_{1,0} d_z -
+    f_{1,1} d_x), k1 = sqrt(3 / 4 pi), with d the unit vector from the camera
+    centre to the primitive's mean in world coordinates.  An isotropic 3D
+    Gaussian at the world origin seen from an orbiting camera: the centre
+    pixel's rgb divided by its alpha is that colour, and a flipped view
+    direction would move every odd-degree term's sign."""
+    cam = S.orbit_camera(az, 25.0, 3.0, 33, 33, 40.0)
+    sc = one_prim_scene((0.0, 0.0, 0.0), (math.log(0.1),) * 3, (1, 0, 0, 0), 1.0, type_=1, deg=1)
+    f = np.array([[0.2, -0.1, 0.3], [0.5, 0.25, -0.4], [-0.3, 0.6, 0.15], [0.35, -0.45, 0.2]], np.float32)
+    sc.sh[0] = f
+    m = O.Oracle(sc, cam, CFG).render_maps()
+    R = np.asarray(cam.R, np.float64)
+    t = np.asarray(cam.t, np.float64)
+    centre = -R.T @ t
+    d = (np.zeros(3) - centre)
+    d /= np.linalg.norm(d)
+    k0, k1 = 0.5 / math.sqrt(math.pi), math.sqrt(3.0 / (4.0 * math.pi))
+    f64 = f.astype(np.float64)
+    col = 0.5 + k0 * f64[0] + k1 * (-f64[1] * d[1] + f64[2] * d[2] - f64[3] * d[0])
+    col = np.maximum(col, 0.0)
+    cy, cx = 16, 16
+    a = m["alpha"][cy, cx]
+    assert a > 0.3
+    np.testing.assert_allclose(m["rgb"][:, cy, cx] / a, col, rtol=1e-12)
+    # the sign matters: the opposite direction gives a different colour
+    wrong = np.maximum(0.5 + k0 * f64[0] - k1 * (-f64[1] * d[1] + f64[2] * d[2] - f64[3] * d[0]), 0.0)
+    assert np.abs(wrong - col).max() > 0.05
+    r = AR.render(sc, cam, CFG, pixels=np.array([[cx, cy]]))
+    np.testing.assert_allclose(r["rgb"].detach().numpy()[0] / r["alpha"].detach().numpy()[0], col, rtol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# ambiguous threshold decisions: every correct result is listed
+# ---------------------------------------------------------------------------
+def test_alpha_threshold_decision_lists_both_results():
+    """An isotropic 3D Gaussian whose contribution at one pixel lies 1e-5
+    (relative) above alpha_min: a binary32 evaluation may land on either side
+    of the threshold, so the pixel has two correct results, with and without
+    the pair (Sec. 3.1 contribution rule), and the renderer lists both."""
+    cam = S.pinhole(48, 48, 60.0)
+    z, s = 3.0, 0.1
+    s64 = math.exp(float(np.float32(math.log(s))))
+    sig = cam.fx * s64 / z
+    px, py = 26, 24  # pixel centre (26.5, 24.5); the Gaussian sits at (24, 24)
+    r2 = (px + 0.5 - cam.cx) ** 2 + (py + 0.5 - cam.cy) ** 2
+    target = CFG.alpha_min * (1 + 1e-5)
+    alpha = target * math.exp(r2 / (2 * sig ** 2))
+    logit = float(np.float32(math.log(alpha / (1 - alpha))))
+    sc = one_prim_scene((0.0, 0.0, z), (math.log(s),) * 3, (1, 0, 0, 0), logit)
+    chk = O.Oracle(sc, cam, CFG).render_checked(np.array([[px, py], [24, 24]], np.int32))
+    assert chk["flags"][0] & 1 and not chk["flags"][0] & 2
+    assert not chk["flags"][1]
+    v = chk["variants"][0]
+    a_exact = (1 / (1 + math.exp(-logit))) * math.exp(-r2 / (2 * sig ** 2))
+    assert abs(a_exact - CFG.alpha_min) < 1e-4 * CFG.alpha_min
+    got = sorted(v[:, 7])
+    assert len(v) == 2
+    assert got[0] == 0.0 and abs(got[1] - a_exact) < 1e-15
+
+
+def test_termination_decision_lists_both_results():
+    """Two opaque face-on surfels at the same pixel: each contributes the clamp
+    0.99, so the transmittance after the second is (0.01)^2 = T_min exactly and
+    whether the pixel stops before it is ambiguous (Eq. 2 with the T_min
+    rule): alpha is 0.99 or 0.9999."""
+    cam = S.pinhole(32, 32, 60.0)
+    prims = [one_prim_scene((0.0, 0.0, z), (math.log(3.0), math.log(3.0), S.SURFEL_LOG_SZ), (1, 0, 0, 0), 9.0,
+                            type_=0) for z in (2.0, 2.5)]
+    sc = cat_scenes(prims)
+    chk = O.Oracle(sc, cam, CFG).render_checked(np.array([[16, 16]], np.int32))
+    assert chk["flags"][0] & 1
+    v = chk["variants"][0]
+    np.testing.assert_allclose(sorted(v[:, 7]), [0.99, 1 - 0.01 ** 2], atol=1e-12)
+    np.testing.assert_array_equal(sorted(v[:, 9]), [1, 2])
