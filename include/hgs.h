@@ -144,6 +144,10 @@ typedef struct {
   float *T_final;   /* [H,W] final transmittance (needed by the backward) */
   uint32_t *n_last; /* [H,W] list entries consumed (needed by the backward) */
   uint32_t *n_contrib; /* [H,W] optional (may be NULL): contributing pairs */
+  uint32_t *tile_sched; /* optional (may be NULL): [2 * tiles + 1] scratch in which the
+                           rgb-only backward orders the tiles longest first (no
+                           counterpart in the paper: scheduling only); NULL takes
+                           them in grid order, with the same result */
 } hgs_image;
 
 /* Upstream gradients dL/d(outputs), same shapes as hgs_image; any may be NULL
@@ -201,7 +205,9 @@ int hgs_preprocess(const hgs_scene *scene, const hgs_camera *cam, const hgs_conf
                    hgs_projected *out, int32_t *dev_err, hgs_stream_t stream);
 
 /* Bytes of device workspace hgs_bin_sort needs for n primitives, `capacity`
- * instances and `tiles` tiles.  Host only. */
+ * instances and `tiles` tiles.  Host only.  INVALID_ARG for capacity outside
+ * 0 .. HGS_MAX_CAPACITY. */
+#define HGS_MAX_CAPACITY 0xffffffffLL /* list offsets are 32-bit: at most 2^32 - 1 instances */
 int hgs_bin_sort_workspace(int64_t n, int64_t capacity, int32_t tiles, size_t *bytes);
 
 /* hgs_bin_sort -- duplicate each binned primitive into the tiles of its
@@ -216,8 +222,8 @@ int hgs_bin_sort_workspace(int64_t n, int64_t capacity, int32_t tiles, size_t *b
  * *dev_err, zeroes the ranges, and writes no instance (no out-of-bounds
  * write).  The caller grows the buffers and calls again.
  * ws: device workspace of at least hgs_bin_sort_workspace() bytes, A16.
- * Errors: INVALID_ARG for NULL pointers, ws_bytes too small, capacity < 0,
- * cfg->wide_rects outside 0..2. */
+ * Errors: INVALID_ARG for NULL pointers, ws_bytes too small, capacity
+ * outside 0 .. HGS_MAX_CAPACITY, cfg->wide_rects outside 0..2. */
 int hgs_bin_sort(int64_t n, const hgs_projected *proj, const hgs_camera *cam,
                  const hgs_config *cfg, void *ws, size_t ws_bytes, int64_t capacity,
                  hgs_binning *out, int32_t *dev_err, hgs_stream_t stream);
@@ -231,6 +237,24 @@ int hgs_bin_sort(int64_t n, const hgs_projected *proj, const hgs_camera *cam,
  * Errors: INVALID_ARG for blocks < 1, iters < 1, NULL d_out or flops. */
 int hgs_fp32_probe(int32_t blocks, int32_t iters, float *d_out, double *flops, hgs_stream_t stream);
 
+/* hgs_alu_probe -- a measurement, not part of the path, with no counterpart
+ * in the paper: like hgs_fp32_probe, `blocks` CTAs of 256 threads each run 8
+ * independent chains of `iters` steps of one kind of operation, so that the
+ * caller can time the peak rate of the unit the render kernels' per-pair loop
+ * issues to:
+ *   HGS_PROBE_FFMA   binary32 fused multiply-add, *ops = 2 flops per step
+ *   HGS_PROBE_FFMA2  packed two-lane binary32 fused multiply-add (the form
+ *                    the render kernels use for a lane's two pixels),
+ *                    *ops = 4 flops per step
+ *   HGS_PROBE_EX2    special-function base-2 exponential, *ops = 1 per step
+ *   HGS_PROBE_RCP    special-function reciprocal (plus one add that keeps the
+ *                    chain from being shortened), *ops = 1 per step
+ * d_out: device float[blocks], written only by a branch never taken.
+ * Errors: INVALID_ARG for an unknown kind, blocks < 1, iters < 1, NULL d_out
+ * or ops. */
+enum { HGS_PROBE_FFMA = 0, HGS_PROBE_FFMA2 = 1, HGS_PROBE_EX2 = 2, HGS_PROBE_RCP = 3 };
+int hgs_alu_probe(int32_t kind, int32_t blocks, int32_t iters, float *d_out, double *ops, hgs_stream_t stream);
+
 /* hgs_bin_sort_static -- hgs_bin_sort without a caller-supplied workspace,
  * for callers that cannot allocate device memory while they render: a host
  * application that owns the GPU allocator and forbids other cudaMalloc calls,
@@ -243,7 +267,8 @@ int hgs_fp32_probe(int32_t blocks, int32_t iters, float *d_out, double *flops, h
  * It always sorts every instance by radix passes (rectangles over 256 tiles
  * included, whatever cfg->wide_rects says), so its scratch holds those
  * passes' buffers only.
- * Limits: returns HGS_ERR_INVALID_ARG, launching nothing, when that scratch
+ * Limits: returns HGS_ERR_INVALID_ARG, launching nothing, for a capacity
+ * outside 0 .. HGS_MAX_CAPACITY and when that scratch
  * (hgs_bin_sort_workspace(n, capacity, tiles) less the wide-rectangle
  * buffers) exceeds HGS_BIN_SORT_STATIC_BYTES (for example n = 1M with
  * capacity 3.5M fits; the 3M-primitive scene does not).  The first call on each device looks up the array's device address
@@ -290,7 +315,8 @@ typedef struct {
 #define HGS_MAX_BATCH 16
 
 /* Bytes of device workspace hgs_render_batch needs for these requests and
- * `capacity` tile instances in total.  Host only. */
+ * `capacity` tile instances in total.  Host only.  INVALID_ARG for capacity
+ * outside 0 .. HGS_MAX_CAPACITY (hgs_render_batch likewise). */
 int hgs_render_batch_workspace(int nreq, const hgs_request *reqs, int64_t capacity, size_t *bytes);
 
 /* hgs_render_batch -- the forward rasterizer (hgs_preprocess + hgs_bin_sort +

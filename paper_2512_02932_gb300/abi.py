@@ -19,7 +19,9 @@ HGS_ERR_UNSUPPORTED = -5
 HGS_EXCHANGE_ERANK = 0
 HGS_EXCHANGE_MASK = 1
 HGS_BIN_SORT_STATIC_BYTES = 64 << 20
+HGS_MAX_CAPACITY = 0xffffffff
 HGS_MAX_BATCH = 16
+HGS_PROBE_FFMA, HGS_PROBE_FFMA2, HGS_PROBE_EX2, HGS_PROBE_RCP = 0, 1, 2, 3
 
 P = C.c_void_p
 
@@ -55,7 +57,7 @@ class hgs_binning(C.Structure):
 
 class hgs_image(C.Structure):
     _fields_ = [("rgb", P), ("depth", P), ("normal", P), ("alpha", P), ("T_final", P), ("n_last", P),
-                ("n_contrib", P)]
+                ("n_contrib", P), ("tile_sched", P)]
 
 
 class hgs_image_grad(C.Structure):
@@ -117,6 +119,7 @@ SYMBOLS = {
     "hgs_image_losses": (C.c_int, [P, P, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double,
                                    P, P, P, P, P]),
     "hgs_fp32_probe": (C.c_int, [C.c_int32, C.c_int32, P, C.POINTER(C.c_double), P]),
+    "hgs_alu_probe": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, P, C.POINTER(C.c_double), P]),
     "hgs_render_bwd_fdo": (C.c_int, [C.POINTER(hgs_scene), C.POINTER(hgs_projected), C.POINTER(hgs_binning),
                                      C.POINTER(hgs_camera), C.POINTER(hgs_config), C.POINTER(hgs_image),
                                      P, P, P, P, C.POINTER(hgs_scene_grad), P, P, P]),
@@ -202,3 +205,4 @@ hgs_densify_plan = _fwd("hgs_densify_plan")
 hgs_densify_apply = _fwd("hgs_densify_apply")
 hgs_reset_opacity = _fwd("hgs_reset_opacity")
 hgs_fp32_probe = _fwd("hgs_fp32_probe")
+hgs_alu_probe = _fwd("hgs_alu_probe")

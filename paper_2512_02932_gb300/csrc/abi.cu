@@ -144,7 +144,7 @@ int hgs_preprocess(const hgs_scene *scene, const hgs_camera *cam, const hgs_conf
 }
 
 int hgs_bin_sort_workspace(int64_t n, int64_t capacity, int32_t tiles, size_t *bytes) {
-  if (!bytes || n < 0 || capacity < 0 || tiles <= 0) return HGS_ERR_INVALID_ARG;
+  if (!bytes || n < 0 || capacity < 0 || capacity > kMaxCapacity || tiles <= 0) return HGS_ERR_INVALID_ARG;
   BinWorkspace ws;
   *bytes = bin_layout(nullptr, n, capacity, tiles, &ws);
   return HGS_OK;
@@ -154,7 +154,8 @@ int hgs_bin_sort(int64_t n, const hgs_projected *proj, const hgs_camera *cam, co
                  void *ws, size_t ws_bytes, int64_t capacity, hgs_binning *out, int32_t *dev_err,
                  hgs_stream_t stream) {
   int st;
-  if (n < 0 || n >= (int64_t(1) << 31) || capacity < 0 || !out || !out->ranges || !out->d_count)
+  if (n < 0 || n >= (int64_t(1) << 31) || capacity < 0 || capacity > kMaxCapacity || !out || !out->ranges ||
+      !out->d_count)
     return HGS_ERR_INVALID_ARG;
   if (capacity > 0 && !out->vals) return HGS_ERR_INVALID_ARG;
   CamK ck;
@@ -236,6 +237,7 @@ int hgs_render_bwd_records(const hgs_scene *scene, const hgs_projected *proj, co
   r.n_last = fwd->n_last;
   r.g_rgb = dL->rgb; r.g_depth = dL->depth; r.g_normal = dL->normal; r.g_alpha = dL->alpha;
   r.rec_grad = grad_ws;
+  r.tile_sched = fwd->tile_sched;
   launch_render_bwd(r, s);
   return launched();
 }
@@ -459,7 +461,8 @@ struct BatchLayout {
 size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
 int batch_layout(int nreq, const hgs_request *reqs, int64_t capacity, BatchLayout *L) {
-  if (nreq < 1 || nreq > HGS_MAX_BATCH || !reqs || capacity < 0) return HGS_ERR_INVALID_ARG;
+  if (nreq < 1 || nreq > HGS_MAX_BATCH || !reqs || capacity < 0 || capacity > kMaxCapacity)
+    return HGS_ERR_INVALID_ARG;
   int64_t n = 0;
   int TXmax = 0, rows = 0;
   for (int r = 0; r < nreq; ++r) {
@@ -605,7 +608,14 @@ int hgs_exchange_types(hgs_scene_mut *scene, const hgs_exchange_cfg *xcfg, int64
 
 int hgs_fp32_probe(int32_t blocks, int32_t iters, float *d_out, double *flops, hgs_stream_t stream) {
   if (blocks < 1 || iters < 1 || !d_out || !flops) return HGS_ERR_INVALID_ARG;
-  launch_fp32_probe(blocks, iters, d_out, flops, reinterpret_cast<cudaStream_t>(stream));
+  launch_alu_probe(HGS_PROBE_FFMA, blocks, iters, d_out, flops, reinterpret_cast<cudaStream_t>(stream));
+  return launched();
+}
+
+int hgs_alu_probe(int32_t kind, int32_t blocks, int32_t iters, float *d_out, double *ops, hgs_stream_t stream) {
+  if (kind < HGS_PROBE_FFMA || kind > HGS_PROBE_RCP) return HGS_ERR_INVALID_ARG;
+  if (blocks < 1 || iters < 1 || !d_out || !ops) return HGS_ERR_INVALID_ARG;
+  launch_alu_probe(kind, blocks, iters, d_out, ops, reinterpret_cast<cudaStream_t>(stream));
   return launched();
 }
 

@@ -53,7 +53,8 @@ void *scratch_on_current_device() {
 extern "C" int hgs_bin_sort_static(int64_t n, const hgs_projected *proj, const hgs_camera *cam,
                                    const hgs_config *cfg, int64_t capacity, hgs_binning *out,
                                    int32_t *dev_err, hgs_stream_t stream) {
-  if (n < 0 || n >= (int64_t(1) << 31) || capacity < 0 || !out || !out->ranges || !out->d_count)
+  if (n < 0 || n >= (int64_t(1) << 31) || capacity < 0 || capacity > hgs::kMaxCapacity || !out || !out->ranges ||
+      !out->d_count)
     return HGS_ERR_INVALID_ARG;
   if (capacity > 0 && !out->vals) return HGS_ERR_INVALID_ARG;
   if (!cam || !cfg || !proj) return HGS_ERR_INVALID_ARG;

@@ -72,6 +72,10 @@ struct BinWorkspace {
   size_t bytes;
 };
 
+// Instance capacity limit: list offsets and ranges are 32-bit, so a frame
+// lists at most 2^32 - 1 instances (a larger count is an overflow), and no
+// buffer size computed from a capacity can wrap.
+constexpr int64_t kMaxCapacity = HGS_MAX_CAPACITY;
 constexpr int kSortBlocks = 1024;  // fixed grid of every sort/scan pass
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 8;      // per thread per tile (tile = 2048 keys)
@@ -122,6 +126,7 @@ struct RenderBwdArgs {
   int nc;
   const float *g_rgbs[3];
   float *rec_grads[3];
+  uint32_t *tile_sched;  // optional [2 * tiles + 1]: tile work, order, hand-out counter
 };
 
 int launch_render_fwd(const RenderArgs &a, cudaStream_t s);
@@ -214,6 +219,6 @@ struct ExchangeArgs {
 int launch_exchange(const ExchangeArgs &a, cudaStream_t s);
 
 // FP32 peak probe (roofline denominator of the render kernels)
-int launch_fp32_probe(int blocks, int iters, float *out, double *flops, cudaStream_t s);
+int launch_alu_probe(int kind, int blocks, int iters, float *out, double *ops, cudaStream_t s);
 
 }  // namespace hgs

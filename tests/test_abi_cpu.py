@@ -49,6 +49,35 @@ def test_workspace_query_is_host_only():
     assert abi.hgs_bin_sort_workspace(-1, 10, 1, C.byref(nb)) == abi.HGS_ERR_INVALID_ARG
 
 
+def test_capacity_beyond_32_bit_offsets_is_rejected():
+    """List offsets are 32-bit: a capacity above 2^32 - 1 is rejected by every
+    entry point that sizes buffers from it, before any size can wrap and
+    before anything is launched (no GPU is touched here)."""
+    nb = C.c_size_t(7)
+    for cap in (abi.HGS_MAX_CAPACITY + 1, 1 << 62, (1 << 63) - 1):
+        assert abi.hgs_bin_sort_workspace(1000, cap, 64, C.byref(nb)) == abi.HGS_ERR_INVALID_ARG
+    assert nb.value == 7
+    assert abi.hgs_bin_sort_workspace(1000, abi.HGS_MAX_CAPACITY, 64, C.byref(nb)) == 0
+    cam = abi.hgs_camera()
+    cam.R[0] = cam.R[4] = cam.R[8] = 1.0
+    cam.fx = cam.fy = 100.0
+    cam.width = cam.height = 64
+    cfg = abi.hgs_config()
+    abi.hgs_default_config(C.byref(cfg))
+    proj = abi.hgs_projected(16, 16, 16, 16)
+    out = abi.hgs_binning(16, None, 16, 16)
+    cap = 1 << 62
+    assert abi.hgs_bin_sort(10, C.byref(proj), C.byref(cam), C.byref(cfg), C.c_void_p(16), 1 << 30, cap,
+                            C.byref(out), None, None) == abi.HGS_ERR_INVALID_ARG
+    assert abi.hgs_bin_sort_static(10, C.byref(proj), C.byref(cam), C.byref(cfg), cap, C.byref(out),
+                                   None, None) == abi.HGS_ERR_INVALID_ARG
+    req = (abi.hgs_request * 1)()
+    req[0].scene.n = 10
+    req[0].cam.width = req[0].cam.height = 64
+    assert abi.hgs_render_batch_workspace(1, req, 1000, C.byref(nb)) == 0
+    assert abi.hgs_render_batch_workspace(1, req, cap, C.byref(nb)) == abi.HGS_ERR_INVALID_ARG
+
+
 def test_invalid_arguments_rejected_before_launch():
     cam = abi.hgs_camera()
     cfg = abi.hgs_config()
@@ -85,6 +114,11 @@ def test_invalid_arguments_rejected_before_launch():
     fl = C.c_double()
     assert abi.hgs_fp32_probe(0, 10, None, C.byref(fl), None) == abi.HGS_ERR_INVALID_ARG
     assert abi.hgs_fp32_probe(4, 0, None, C.byref(fl), None) == abi.HGS_ERR_INVALID_ARG
+    # the unit probes also need a known kind
+    for kind in (-1, 4):
+        assert abi.hgs_alu_probe(kind, 4, 10, C.c_void_p(16), C.byref(fl), None) == abi.HGS_ERR_INVALID_ARG
+    assert abi.hgs_alu_probe(abi.HGS_PROBE_EX2, 0, 10, C.c_void_p(16), C.byref(fl), None) \
+        == abi.HGS_ERR_INVALID_ARG
     # binning path other than 0 (device picks), 1 (masks), 2 (radix sort)
     cam.width = 16
     for bad in (-1, 3):
