@@ -38,8 +38,10 @@ def workload(args):
 
 
 def base_config(args, world):
+    """The config both arms print (the GPU arm and the reference arm)."""
     return {"workload": workload(args), "n_prims": args.n, "width": args.width, "height": args.height,
-            "sh_degree": 3, "parallelism": "replicas" if world > 1 else "single"}
+            "sh_degree": 3, "parallelism": "replicas" if world > 1 else "single",
+            "l2": "inputs larger than L2 (scene 708 MB, records 240 MB, lists > 100 MB)"}
 
 
 def parse():
@@ -63,7 +65,7 @@ def parse():
                    help="time only the binning of the stress scene recipe at --prims primitives and "
                         "--width x --height, path --wide-rects, over --steps calls (one JSON line)")
     p.add_argument("--wide-rects", type=int, default=0, choices=[0, 1, 2])
-    p.add_argument("--serving-seconds", type=float, default=5.0)
+    p.add_argument("--serving-seconds", type=float, default=20.0)
     p.add_argument("--serving-rate", type=float, default=200.0)
     return p.parse_args()
 
@@ -172,10 +174,11 @@ def cpu_baseline(scene, cam, cfg, sample_pixels, seed=0):
     return {
         "value": round(per_frame * 1e3, 3), "unit": "ms", "cores": O.num_threads(),
         "kind": "oracle",
-        "sample": (f"FP64 C oracle: prepare all {scene.n} prims ({t1 - t0:.2f} s) + render "
-                   f"{sample_pixels} random pixels ({t2 - t1:.2f} s), extrapolated to one "
-                   f"{W}x{H} forward; backward not included (the oracle's gradients are "
-                   f"finite differences / FP64 autograd on small scenes)"),
+        "sample": (f"forward only, extrapolated from {sample_pixels} sampled pixels: FP64 C oracle, "
+                   f"prepare all {scene.n} prims ({t1 - t0:.2f} s) + render the sampled pixels "
+                   f"({t2 - t1:.2f} s), scaled to one {W}x{H} frame; the backward is not included (the "
+                   f"oracle's gradients are finite differences and FP64 autograd on small scenes)"),
+        "forward_only": True, "extrapolated": True, "measured_s": round(t2 - t0, 3),
         "host_cpus": os.cpu_count(),
     }
 
@@ -187,20 +190,22 @@ def reference_arm(args, world, rank):
     scene, cam = S.scene_scale(args.n, seed=1)
     cam = S.orbit_camera(30.0, 20.0, 3.0, args.width, args.height, 50.0)
     cfg = S.RenderConfig()
-    per_step = []
+    per_step, measured = [], []
     sample = max(2000, args.cpu_sample_pixels // max(1, args.steps))
     res = None
     for k in range(args.warmup + args.steps):
         res = cpu_baseline(scene, cam, cfg, sample, seed=k)
         if k >= args.warmup:
             per_step.append(res["value"])
+            measured.append(res["measured_s"])
     v = float(np.median(per_step))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": base_config(args, world),
             "cpu_baseline": {"value": v, "unit": "ms", "cores": res["cores"], "kind": "oracle",
-                             "sample": res["sample"]},
+                             "sample": res["sample"], "forward_only": True, "extrapolated": True,
+                             "measured_s_per_step": round(float(np.median(measured)), 3)},
             "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -269,10 +274,12 @@ def busy_launch(dev, iters):
     return out
 
 
-def fp32_peak(dev):
-    """The device's FP32 rate, measured in this run: hgs_fp32_probe (8
-    independent FMA chains per thread, every SM full) sized to run ~10 ms,
-    best of three CUDA-event timings.  Returns (TFLOP/s, description)."""
+def alu_peak(dev, kind=0):
+    """Peak rate of one unit, measured in this run by hgs_alu_probe (8
+    independent chains per thread, 8 CTAs of 256 threads per SM) sized to run
+    ~10 ms, best of three CUDA-event timings.  kind: HGS_PROBE_FFMA (FP32
+    flops), _FFMA2, _EX2 or _RCP (special-function ops).  Returns (T ops/s,
+    description)."""
     import ctypes as C
 
     import torch
@@ -281,22 +288,23 @@ def fp32_peak(dev):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     blocks = sms * 8
     out = torch.empty(blocks, dtype=torch.float32, device=dev)
-    fl = C.c_double()
+    ops = C.c_double()
     s = torch.cuda.current_stream(dev)
 
     def run(iters):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(s)
-        abi.check(abi.hgs_fp32_probe(blocks, iters, C.c_void_p(out.data_ptr()), C.byref(fl),
-                                     C.c_void_p(s.cuda_stream)), "hgs_fp32_probe")
+        abi.check(abi.hgs_alu_probe(kind, blocks, iters, C.c_void_p(out.data_ptr()), C.byref(ops),
+                                    C.c_void_p(s.cuda_stream)), "hgs_alu_probe")
         e1.record(s)
         torch.cuda.synchronize(dev)
-        return fl.value / (e0.elapsed_time(e1) * 1e-3) / 1e12, e0.elapsed_time(e1)
+        return ops.value / (e0.elapsed_time(e1) * 1e-3) / 1e12, e0.elapsed_time(e1)
 
-    _, ms = run(20000)
-    iters = max(1000, int(20000 * 10.0 / max(ms, 1e-3)))
+    _, ms = run(2000)
+    iters = max(1000, int(2000 * 10.0 / max(ms, 1e-3)))
     best = max(run(iters)[0] for _ in range(3))
-    return best, f"measured: hgs_fp32_probe, {blocks} CTAs x 256 threads x 8 FMA chains x {iters} steps"
+    name = {0: "FFMA", 1: "FFMA2", 2: "EX2", 3: "RCP"}[kind]
+    return best, f"measured: hgs_alu_probe {name}, {blocks} CTAs x 256 threads x 8 chains x {iters} steps"
 
 
 def hbm_phases(phases, n, n_binned, K, tile_passes, peak, peak_src):
@@ -322,6 +330,14 @@ def hbm_phases(phases, n, n_binned, K, tile_passes, peak, peak_src):
             gbs = b / (phases[k] * 1e-3) / 1e9
             out[k] = {"bytes": int(b), "achieved_gbs": round(gbs, 1), "peak_gbs": peak,
                       "frac": round(gbs / peak, 4)}
+    if "bin_sort" in out:
+        # the same phase against an unfactored sort's bytes: emit 12 B and
+        # ranges 8 B per instance, six 24-B passes of 8 digit bits over the
+        # 64-bit keys, a 4-B scan per primitive
+        sv = 164 * K + 4 * n
+        gbs = sv / (phases["bin_sort"] * 1e-3) / 1e9
+        out["bin_sort"]["unfactored_sort_bytes"] = int(sv)
+        out["bin_sort"]["unfactored_frac"] = round(gbs / peak, 4)
     out["peak_source"] = peak_src
     return out
 
@@ -476,40 +492,6 @@ def run_stress(args, dev, cfg):
     del rast, st
     torch.cuda.empty_cache()
     return out
-
-
-TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "render_bwd_traffic_3M_1600x1064.md")
-TRAFFIC_SOURCES = [os.path.join(ROOT, "paper_2512_02932_gb300", "csrc", f) for f in ("render.cu", "common.cuh")]
-
-
-def source_sha256():
-    import hashlib
-    h = hashlib.sha256()
-    for f in TRAFFIC_SOURCES:
-        with open(f, "rb") as fh:
-            h.update(fh.read())
-    return h.hexdigest()
-
-
-def profiled_traffic(args):
-    """DRAM bytes per render_bwd launch from the committed ncu capture, used
-    only when the kernel sources hash to what was captured and the workload is
-    the captured one; otherwise None."""
-    if (args.n, args.width, args.height) != (3_000_000, 1600, 1064):
-        return None
-    try:
-        with open(TRAFFIC_PROFILE) as fh:
-            text = fh.read()
-    except OSError:
-        return None
-    fields = {}
-    for ln in text.splitlines():
-        if ln.startswith(("source_sha256:", "dram_bytes_per_launch:")):
-            k, v = ln.split(":", 1)
-            fields[k] = v.strip()
-    if fields.get("source_sha256") != source_sha256():
-        return None
-    return int(fields["dram_bytes_per_launch"])
 
 
 def binning_probe(args):
@@ -742,30 +724,50 @@ def main():
 
     roofline = None
     if phases:
-        # dominant kernel: the blend backward (FP32 issue bound), rgb-only
-        # cotangent (L1 image loss).  Algorithmic FP32 work (FMA = 2 flops):
-        # 16 flops per (pixel, list entry) the pixel consumed (70/30 mix of the
-        # 12-flop 3D and 24-flop surfel evaluation) + 56 per contributing pair
-        # (46 of gradient, ~10 of the per-record sum over pixels).  Peak: the
-        # FP32 rate measured by hgs_fp32_probe in this run (and, for context,
-        # 152 SMs x 128 FP32 lanes x 2 flops x the max SM clock).
+        # dominant kernel: the blend backward the L1 step runs (rgb-only
+        # cotangent; one warp per tile, tiles longest first), bound by FP32
+        # issue.  Algorithmic FP32 work (FMA = 2 flops): 16 flops per (pixel,
+        # list entry) the pixel consumed (70/30 mix of the 12-flop 3D and
+        # 24-flop surfel evaluation) + 56 per contributing pair (46 of
+        # gradient, ~10 of the per-record sum over pixels).  Peaks measured in
+        # this run by hgs_alu_probe (FFMA for FP32; EX2 and RCP for the
+        # special-function unit), with 152 SMs x 128 lanes x 2 x the max SM
+        # clock beside them for context.
         sm_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
         derived = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-        peak, peak_source = fp32_peak(dev)
+        peak, peak_source = alu_peak(dev, 0)
+        ex2_peak, _ = alu_peak(dev, 2)
+        rcp_peak, _ = alu_peak(dev, 3)
         flops = 16.0 * n_last_sum + 56.0 * n_contrib_sum
         # the kernel's mean duration inside the timed steps (CUDA events on its
         # stream around the record-gradient stage), else the per-phase loop's
         kernel_ms = statistics.mean(bwd_timed) if bwd_timed else phases["render_bwd"]
-        achieved = flops / (kernel_ms * 1e-3) / 1e12
-        roofline = {"kernel": "render_bwd_kernel", "bound": "alu", "achieved": round(achieved, 3),
+        sec = kernel_ms * 1e-3
+        achieved = flops / sec / 1e12
+        # the survey's count: ~61 ops per evaluated pair (2.5 x the forward's
+        # 20 (3D) / 35 (surfel) ops at the 70/30 mix)
+        survey = 61.0 * n_last_sum / sec / 1e12
+        # special-function work: one EX2 per (pixel, entry), one RCP per
+        # surfel entry (30% of the entries at this mix, an estimate) and one
+        # RCP per contributing pair (the transmittance recovered by division)
+        ex2_ops, rcp_ops = float(n_last_sum), 0.3 * n_last_sum + float(n_contrib_sum)
+        mufu_busy = (ex2_ops / (ex2_peak * 1e12) + rcp_ops / (rcp_peak * 1e12)) / sec
+        roofline = {"kernel": "render_bwd_rgb4_kernel", "bound": "alu", "achieved": round(achieved, 3),
                     "kernel_ms": round(kernel_ms, 4),
                     "kernel_ms_source": "timed steps" if bwd_timed else "per-phase loop",
                     "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                    "traffic": profiled_traffic(args),
+                    "traffic": None,
                     "peak_source": peak_source,
                     "peak_derived": round(derived, 2),
+                    "flop_convention": "16 flops per (pixel, list entry) consumed + 56 per contributing pair",
                     "units": {"pixel_list_entries": n_last_sum, "contributing_pairs": n_contrib_sum,
-                              "flops_per_entry": 16, "flops_per_contributing_pair": 56}}
+                              "flops_per_entry": 16, "flops_per_contributing_pair": 56},
+                    "pairs_per_s": round(n_last_sum / sec, 1),
+                    "survey_convention": {"ops_per_entry": 61, "achieved": round(survey, 3),
+                                          "frac": round(survey / peak, 4)},
+                    "special_function": {"ex2_ops": ex2_ops, "rcp_ops": rcp_ops,
+                                         "peak_ex2_tops": round(ex2_peak, 3), "peak_rcp_tops": round(rcp_peak, 3),
+                                         "busy_frac": round(mufu_busy, 4)}}
     serving = None
     if not args.no_serving and world == 1:
         serving = run_serving(args, dev, cfg)
@@ -785,8 +787,8 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {**base_config(args, world), "instances_K": K, "pixel_list_entries": n_last_sum,
-                   "l2": "inputs larger than L2 (scene 708 MB, records 240 MB, lists > 100 MB)"},
+        "config": base_config(args, world),
+        "workload_stats": {"instances_K": K, "pixel_list_entries": n_last_sum, "binned_prims": n_binned},
         "phases_ms": phases,
         "hbm_phases": hbm_phases(phases, scene.n, n_binned, K, tile_passes, *hbm_peak()) if phases else None,
         "step_ms": {"min": round(min(step_ms), 4), "median": round(statistics.median(step_ms), 4),

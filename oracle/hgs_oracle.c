@@ -54,10 +54,11 @@ enum {
  * turns a primitive's normal to the camera.  Where the FP64 value sits within
  * a band around the threshold that a binary32 evaluation could cross, the
  * decision is ambiguous: both outcomes are correct results of the method
- * evaluated in binary32.  The renderer then enumerates the outcomes of up to
- * ORC_MAXDEC such decisions met before the pixel terminates (at most
- * 2^ORC_MAXDEC results, "variants"); a pixel that meets more is reported as
- * not comparable.  In binary32 a contribution alpha*exp(-d/2) carries a
+ * evaluated in binary32.  The renderer then enumerates the outcomes of the
+ * ambiguous decisions met before the pixel terminates, depth first, up to
+ * ORC_MAXV results ("variants"); a pixel with more is reported as not
+ * comparable.  (A stop decision ends the walk, so a run of ambiguous stops
+ * over consecutive faint contributors adds one result each, not a doubling.)  In binary32 a contribution alpha*exp(-d/2) carries a
  * relative error of about 1e-5 (d ~ 11 near the cutoff), and the
  * transmittance after a few hundred contributors about 1e-4; the bands are
  * five to ten times wider. */
@@ -65,8 +66,14 @@ enum {
 #define AMB_T_REL     1e-3   /* |T' - T_min| <= this * T_min               */
 #define AMB_NEAR_REL  1e-5   /* |z - near| <= this * max(1, near)          */
 #define AMB_FLIP      1e-5   /* |n . mu_c| / |mu_c| below this             */
-#define ORC_MAXDEC    3
-#define ORC_MAXV      (1 << ORC_MAXDEC)
+#define ORC_MAXDEC    31   /* decisions along one path (bits of the choice word) */
+#define ORC_MAXV      64   /* results enumerated per pixel */
+/* An ambiguous alpha_min decision whose whole weight alpha T is at most
+ * ORC_FAINT moves the pixel's outputs by at most that weight times the
+ * magnitudes involved (a few 1e-6, far below the 1e-3 image tolerance): it is
+ * taken the FP64 way and its effect added to the tolerance (and one to the
+ * contributor count's slack) instead of doubling the results. */
+#define ORC_FAINT     2e-6
 /* Conditioning.  In binary32, (u, v) evaluated from the pixel's offset to
  * the projected centre carry an error of up to COND_ULPS ulps of the
  * magnitude of the terms that cancel, |du/dx dx| + |du/dy dy| (likewise v):
@@ -751,26 +758,53 @@ static int eval_pair(const orc_ctx *C, const prim_t *p, double px, double py, co
  * outcome of the j-th ambiguous decision met taken from bit j of `choice`
  * (0: the FP64 outcome, 1: the other one).  o: r, g, b, depth, nx, ny, nz,
  * alpha, T_final, contributors; tol: per-output bound of the conditioning
- * errors (dag) carried through Eq. 2.  Returns the number of ambiguous
- * decisions met. */
+ * errors (dag) and of the faint decisions carried through Eq. 2, and in
+ * tol[9] the number of faint decisions (the contributor count's slack).
+ * Returns the number of ambiguous decisions met. */
 static int blend_run(const orc_ctx *C, const contrib_t *buf, int cnt, uint32_t choice, const double vmax[10],
-                     double o[10], double tol[10]) {
+                     double o[10], double tol[10], int *loose) {
   const double Tmin = C->cfg[CF_T_MIN], amax = C->cfg[CF_ALPHA_MAX];
   double T = 1.0, Cc[3] = {0, 0, 0}, D = 0, Nn[3] = {0, 0, 0}, tT = 0.0;
   int used = 0, nd = 0;
+  *loose = 0;
   for (int k = 0; k < 10; ++k) tol[k] = 0.0;
 #define TAKE_BIT() (nd < 32 ? (int)((choice >> nd++) & 1u) : (nd++, 0))
   for (int k = 0; k < cnt; ++k) {
     const contrib_t *c = &buf[k];
     const prim_t *p = &C->P[c->id];
     int a_ok = c->a_ok, z_ok = c->z_ok;
-    if (c->flags & PA_ALPHA) a_ok ^= TAKE_BIT();
+    if (c->flags & PA_ALPHA) {
+      const double wmax = (c->ag < amax ? c->ag : amax) * T;
+      if (wmax <= ORC_FAINT && !(c->flags & PA_NEAR)) {
+        const double v[9] = {p->col[0], p->col[1], p->col[2], c->z, p->nrm[0], p->nrm[1], p->nrm[2], 1.0, 1.0};
+        for (int ch = 0; ch < 9; ++ch) tol[ch] += wmax * (fabs(v[ch]) + vmax[ch]);
+        tol[9] += 1.0;
+        tT += wmax;
+      } else {
+        a_ok ^= TAKE_BIT();
+      }
+    }
     if (c->flags & PA_NEAR) z_ok ^= TAKE_BIT();
     if (!(a_ok && z_ok)) continue;
     const double at = c->ag < amax ? c->ag : amax;
     const double Tn = T * (1.0 - at);
     int stop = Tn < Tmin;
-    if (fabs(Tn - Tmin) <= fmax(AMB_T_REL * Tmin, tT)) stop ^= TAKE_BIT();
+    const double band = fmax(AMB_T_REL * Tmin, tT);
+    if (fabs(Tn - Tmin) <= band) {
+      if (band > 0.5 * Tmin) {
+        /* the conditioning errors make the binary32 transmittance too
+         * uncertain to place the stop: stopping here or at any later pair
+         * moves each output by at most T (|v| + max |v|), since everything
+         * blended from here on weighs at most T; added once, and the
+         * contributor count is left unchecked */
+        if (!*loose)
+          for (int ch = 0; ch < 9; ++ch) tol[ch] += T * 2.0 * vmax[ch];
+        *loose = 1;
+        tol[9] = 1e9;
+      } else {
+        stop ^= TAKE_BIT();
+      }
+    }
     if (stop) break;
     double sg = 1.0;
     if (c->flags & PA_FLIP) sg = TAKE_BIT() ? -1.0 : 1.0;
@@ -800,15 +834,21 @@ static int blend_run(const orc_ctx *C, const contrib_t *buf, int cnt, uint32_t c
   return nd;
 }
 
-/* All outcomes of the first ORC_MAXDEC ambiguous decisions, depth first:
- * a run that meets a decision beyond its fixed prefix splits there.  leaves:
- * up to ORC_MAXV x 20 doubles (o[10], tol[10]).  Sets *over when a run meets
- * more than ORC_MAXDEC decisions. */
+/* Every outcome of the ambiguous decisions, depth first: a run that meets a
+ * decision beyond its fixed prefix splits there.  leaves: up to ORC_MAXV x 20
+ * doubles (o[10], tol[10]).  Sets *over (and stops) when the results would
+ * exceed ORC_MAXV or a path meets more than ORC_MAXDEC decisions. */
 static void enum_leaves(const orc_ctx *C, const contrib_t *buf, int cnt, uint32_t prefix, int plen,
                         const double vmax[10], double *leaves, int *nleaves, int *over) {
+  if (*over) return;
   double o[10], tol[10];
-  const int nd = blend_run(C, buf, cnt, prefix, vmax, o, tol);
+  int loose;
+  const int nd = blend_run(C, buf, cnt, prefix, vmax, o, tol, &loose);
   if (nd <= plen) {
+    if (*nleaves == ORC_MAXV) {
+      *over = 1;
+      return;
+    }
     double *L = leaves + 20 * (*nleaves);
     for (int k = 0; k < 10; ++k) { L[k] = o[k]; L[10 + k] = tol[k]; }
     (*nleaves)++;
@@ -816,9 +856,6 @@ static void enum_leaves(const orc_ctx *C, const contrib_t *buf, int cnt, uint32_
   }
   if (plen == ORC_MAXDEC) {
     *over = 1;
-    double *L = leaves + 20 * (*nleaves);
-    for (int k = 0; k < 10; ++k) { L[k] = o[k]; L[10 + k] = tol[k]; }
-    (*nleaves)++;
     return;
   }
   enum_leaves(C, buf, cnt, prefix, plen + 1, vmax, leaves, nleaves, over);
@@ -827,7 +864,7 @@ static void enum_leaves(const orc_ctx *C, const contrib_t *buf, int cnt, uint32_
 
 /* The sorted pairs of pixel (ix, iy) and the per-output magnitudes bounding
  * what lies behind a pair (for the conditioning tolerance). */
-static int pixel_pairs(const orc_ctx *C, int ix, int iy, contrib_t *buf, double vmax[10]) {
+static int pixel_pairs(const orc_ctx *C, int ix, int iy, contrib_t *buf, double vmax[10], int64_t skip) {
   double px = ix + 0.5, py = iy + 0.5;
   int cxi = ix / C->cell, cyi = iy / C->cell;
   int64_t c = (int64_t)cyi * C->gx + cxi;
@@ -838,7 +875,7 @@ static int pixel_pairs(const orc_ctx *C, int ix, int iy, contrib_t *buf, double 
   for (int64_t k = C->cstart[c]; k < C->cstart[c + 1]; ++k) {
     int32_t id = C->citems[k];
     const prim_t *p = &C->P[id];
-    if (!p->valid) continue;
+    if (!p->valid || id == skip) continue;
     if (eval_pair(C, p, px, py, &buf[cnt])) {
       buf[cnt].key = p->key;
       buf[cnt].id = id;
@@ -856,29 +893,33 @@ static int pixel_pairs(const orc_ctx *C, int ix, int iy, contrib_t *buf, double 
  * in row-major order), taking every decision the FP64 way.
  * out: npix x 10 doubles [r, g, b, depth, nx, ny, nz, alpha, T_final,
  * n_contrib].  flags (npix): bit 0 = ambiguous decisions met (more results
- * are correct: orc_render_variants lists them), bit 1 = more than ORC_MAXDEC
- * of them (not comparable).  tol (npix x 10, may be NULL): the conditioning
- * tolerance of this result. */
+ * are correct: orc_render_variants lists them), bit 1 = more correct results
+ * than the renderer enumerates (ORC_MAXV), or more than ORC_MAXDEC decisions
+ * on one path (not comparable), bit 2 = the conditioning errors leave the
+ * stop point unplaceable (its effect is in the tolerance, the contributor
+ * count unchecked).  tol (npix x 10, may be NULL): the tolerance of this
+ * result (tol[9]: the contributor count's slack). */
 void orc_render(void *ctx, int64_t npix, const int32_t *pix, double *out, uint8_t *flags, double *tol) {
   orc_ctx *C = (orc_ctx *)ctx;
   if (!pix) npix = (int64_t)C->W * C->H;
 #pragma omp parallel
   {
     contrib_t *buf = (contrib_t *)malloc(sizeof(contrib_t) * (C->maxcell > 0 ? C->maxcell : 1));
+    double *lv = (double *)malloc(sizeof(double) * ORC_MAXV * 20);
 #pragma omp for schedule(dynamic, 64)
     for (int64_t q = 0; q < npix; ++q) {
       int ix, iy;
       if (pix) { ix = pix[2 * q]; iy = pix[2 * q + 1]; }
       else { ix = (int)(q % C->W); iy = (int)(q / C->W); }
       double vmax[10], t[10];
-      const int cnt = pixel_pairs(C, ix, iy, buf, vmax);
-      const int nd = blend_run(C, buf, cnt, 0u, vmax, out + 10 * q, t);
-      uint8_t f = 0;
+      int loose;
+      const int cnt = pixel_pairs(C, ix, iy, buf, vmax, -1);
+      const int nd = blend_run(C, buf, cnt, 0u, vmax, out + 10 * q, t, &loose);
+      uint8_t f = loose ? 4 : 0;
       if (nd > 0) f |= 1;
       if (nd > ORC_MAXDEC) f |= 2;
       else if (nd > 0) {
         /* a branch can meet decisions the FP64 path does not */
-        double lv[ORC_MAXV * 20];
         int nl = 0, over = 0;
         enum_leaves(C, buf, cnt, 0u, 0, vmax, lv, &nl, &over);
         if (over) f |= 2;
@@ -888,6 +929,7 @@ void orc_render(void *ctx, int64_t npix, const int32_t *pix, double *out, uint8_
         for (int k = 0; k < 10; ++k) tol[10 * q + k] = t[k];
     }
     free(buf);
+    free(lv);
   }
 }
 
@@ -902,7 +944,7 @@ void orc_render_variants(void *ctx, int64_t npix, const int32_t *pix, int32_t *n
 #pragma omp for schedule(dynamic, 16)
     for (int64_t q = 0; q < npix; ++q) {
       double vmax[10];
-      const int cnt = pixel_pairs(C, pix[2 * q], pix[2 * q + 1], buf, vmax);
+      const int cnt = pixel_pairs(C, pix[2 * q], pix[2 * q + 1], buf, vmax, -1);
       int nl = 0, over = 0;
       enum_leaves(C, buf, cnt, 0u, 0, vmax, leaves + (int64_t)q * ORC_MAXV * 20, &nl, &over);
       nvar[q] = nl;
@@ -912,6 +954,99 @@ void orc_render_variants(void *ctx, int64_t npix, const int32_t *pix, int32_t *n
 }
 
 int orc_max_variants(void) { return ORC_MAXV; }
+
+/* Finite differences of one primitive.  A central difference changes only
+ * primitive i, so the pairs of every other primitive at the pixels looked at
+ * are evaluated and sorted once (orc_fd_begin); each orc_fd_render then
+ * evaluates primitive i with its current parameters (orc_set_prim), inserts
+ * its pair in the sorted order and blends: the same pairs, order and Eq. 2
+ * as orc_render, at a fraction of the cost. */
+typedef struct {
+  int64_t i, npix;
+  int32_t *pix;
+  contrib_t **list;
+  int *cnt;
+  double *vmax;
+} orc_fd_t;
+
+void *orc_fd_begin(void *ctx, int64_t i, int64_t npix, const int32_t *pix) {
+  orc_ctx *C = (orc_ctx *)ctx;
+  orc_fd_t *F = (orc_fd_t *)calloc(1, sizeof(orc_fd_t));
+  F->i = i;
+  F->npix = npix;
+  F->pix = (int32_t *)malloc(sizeof(int32_t) * 2 * (npix > 0 ? npix : 1));
+  memcpy(F->pix, pix, sizeof(int32_t) * 2 * npix);
+  F->list = (contrib_t **)calloc(npix > 0 ? npix : 1, sizeof(contrib_t *));
+  F->cnt = (int *)calloc(npix > 0 ? npix : 1, sizeof(int));
+  F->vmax = (double *)calloc(10 * (npix > 0 ? npix : 1), sizeof(double));
+#pragma omp parallel
+  {
+    contrib_t *buf = (contrib_t *)malloc(sizeof(contrib_t) * (C->maxcell > 0 ? C->maxcell : 1));
+#pragma omp for schedule(dynamic, 1)
+    for (int64_t q = 0; q < npix; ++q) {
+      const int cnt = pixel_pairs(C, pix[2 * q], pix[2 * q + 1], buf, F->vmax + 10 * q, i);
+      F->list[q] = (contrib_t *)malloc(sizeof(contrib_t) * (cnt + 1));
+      memcpy(F->list[q], buf, sizeof(contrib_t) * cnt);
+      F->cnt[q] = cnt;
+    }
+    free(buf);
+  }
+  return F;
+}
+
+/* out: npix x 10 as orc_render (every decision the FP64 way); flags: bit 0
+ * if an ambiguous decision was met (the difference is then not a
+ * derivative), bit 2 as orc_render; tol (may be NULL): as orc_render. */
+void orc_fd_render(void *ctx, void *fd, double *out, uint8_t *flags, double *tol) {
+  orc_ctx *C = (orc_ctx *)ctx;
+  orc_fd_t *F = (orc_fd_t *)fd;
+  const prim_t *p = &C->P[F->i];
+#pragma omp parallel
+  {
+    contrib_t *buf = (contrib_t *)malloc(sizeof(contrib_t) * (C->maxcell + 1));
+#pragma omp for schedule(static)
+    for (int64_t q = 0; q < F->npix; ++q) {
+      const int n0 = F->cnt[q];
+      double vmax[10];
+      memcpy(vmax, F->vmax + 10 * q, sizeof(vmax));
+      int cnt = 0;
+      contrib_t c;
+      memset(&c, 0, sizeof(c));
+      const int listed = p->valid && eval_pair(C, p, F->pix[2 * q] + 0.5, F->pix[2 * q + 1] + 0.5, &c);
+      if (listed) {
+        c.key = p->key;
+        c.id = (int32_t)F->i;
+        const double v[7] = {p->col[0], p->col[1], p->col[2], c.z, p->nrm[0], p->nrm[1], p->nrm[2]};
+        for (int ch = 0; ch < 7; ++ch)
+          if (fabs(v[ch]) > vmax[ch]) vmax[ch] = fabs(v[ch]);
+      }
+      /* merge primitive i's pair into the sorted list */
+      int placed = !listed;
+      for (int k = 0; k < n0; ++k) {
+        if (!placed && cmp_contrib(&c, &F->list[q][k]) < 0) {
+          buf[cnt++] = c;
+          placed = 1;
+        }
+        buf[cnt++] = F->list[q][k];
+      }
+      if (!placed) buf[cnt++] = c;
+      double t[10];
+      int loose;
+      const int nd = blend_run(C, buf, cnt, 0u, vmax, out + 10 * q, t, &loose);
+      flags[q] = (uint8_t)((nd > 0 ? 1 : 0) | (loose ? 4 : 0));
+      if (tol)
+        for (int k = 0; k < 10; ++k) tol[10 * q + k] = t[k];
+    }
+    free(buf);
+  }
+}
+
+void orc_fd_end(void *fd) {
+  orc_fd_t *F = (orc_fd_t *)fd;
+  if (!F) return;
+  for (int64_t q = 0; q < F->npix; ++q) free(F->list[q]);
+  free(F->list); free(F->cnt); free(F->vmax); free(F->pix); free(F);
+}
 
 /* The contribution alpha exp(-d/2) (unclamped) of primitive i alone at npix
  * pixels, 0 where it does not contribute (Sec. 3.1); used to pick the pixels

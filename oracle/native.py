@@ -47,6 +47,12 @@ def lib():
         L.orc_max_variants.argtypes = []
         L.orc_pair_alpha.restype = None
         L.orc_pair_alpha.argtypes = [P, C.c_int64, C.c_int64, P, P]
+        L.orc_fd_begin.restype = P
+        L.orc_fd_begin.argtypes = [P, C.c_int64, C.c_int64, P]
+        L.orc_fd_render.restype = None
+        L.orc_fd_render.argtypes = [P, P, P, P, P]
+        L.orc_fd_end.restype = None
+        L.orc_fd_end.argtypes = [P]
         L.orc_set_prim.restype = None
         L.orc_set_prim.argtypes = [P, C.c_int64, P, P, P, C.c_double, P, C.c_int]
         L.orc_free.restype = None
@@ -179,10 +185,49 @@ class Oracle:
         lib().orc_pair_alpha(self.ctx, int(i), len(pixels), _p(pixels), _p(out))
         return out
 
+    def fd_session(self, i, pixels):
+        """A finite-difference session for primitive i at `pixels`: the other
+        primitives' pairs there are evaluated and sorted once; render() then
+        re-evaluates primitive i with its current parameters (set_prim) and
+        blends, returning (out (P, 10), amb (P,) bool) as Oracle.render."""
+        return _FDSession(self, i, pixels)
+
     def set_prim(self, i, mean, log_scale, quat, logit, sh, type_):
         a = [np.ascontiguousarray(x, np.float64) for x in (mean, log_scale, quat, sh)]
         lib().orc_set_prim(self.ctx, int(i), _p(a[0]), _p(a[1]), _p(a[2]), float(logit),
                            _p(a[3]), int(type_))
+
+
+class _FDSession:
+    def __init__(self, orc, i, pixels):
+        self.orc = orc
+        self.pixels = np.ascontiguousarray(pixels, np.int32)
+        self.h = lib().orc_fd_begin(orc.ctx, int(i), len(self.pixels), _p(self.pixels))
+
+    def render(self, with_tol=False):
+        P = len(self.pixels)
+        out = np.zeros((P, 10), np.float64)
+        flags = np.zeros(P, np.uint8)
+        tol = np.zeros((P, 10), np.float64)
+        lib().orc_fd_render(self.orc.ctx, self.h, _p(out), _p(flags), _p(tol))
+        return (out, flags != 0, tol) if with_tol else (out, flags != 0)
+
+    def close(self):
+        if self.h:
+            lib().orc_fd_end(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def contract_bin(scene, cam, cfg):

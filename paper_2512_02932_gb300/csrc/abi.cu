@@ -206,6 +206,7 @@ int hgs_render_fwd(int64_t n, const hgs_projected *proj, const hgs_binning *bins
   a.cfg = fk;
   a.rgb = out->rgb; a.depth = out->depth; a.normal = out->normal; a.alpha = out->alpha;
   a.T_final = out->T_final; a.n_last = out->n_last; a.n_contrib = out->n_contrib;
+  a.tile_sched = out->tile_sched;
   launch_render_fwd(a, reinterpret_cast<cudaStream_t>(stream));
   return launched();
 }
@@ -551,6 +552,7 @@ int hgs_render_batch(int nreq, const hgs_request *reqs, const hgs_config *cfg, v
     a.cfg = fk;
     a.rgb = o.rgb; a.depth = o.depth; a.normal = o.normal; a.alpha = o.alpha;
     a.T_final = o.T_final; a.n_last = o.n_last; a.n_contrib = o.n_contrib;
+    a.tile_sched = nullptr;
     br.row_off[r] = row;
     prim += q.scene.n;
     row += ck.TY;

@@ -108,7 +108,8 @@ struct RenderArgs {
   CfgK cfg;
   float *rgb, *depth, *normal, *alpha, *T_final;
   uint32_t *n_last;
-  uint32_t *n_contrib;  // optional
+  uint32_t *n_contrib;   // optional
+  uint32_t *tile_sched;  // optional [2 * tiles + 1]: tile work, order, hand-out counter
 };
 
 struct RenderBwdArgs {

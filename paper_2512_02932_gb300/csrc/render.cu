@@ -1,17 +1,29 @@
 // render.cu -- per-tile blending of the hybrid rasterizer (EGGS Sec. 3.1,
 // Eq. 1, Eq. 2) and its backward.
 //
-// One CTA per 16x16 tile, 4 warps; each warp owns an 8x8 pixel block, two
-// pixels per lane (rows y and y + 4), and walks the tile's sorted list on its
-// own: it stages the list 32 records at a time into a private double buffer
-// in shared memory with cp.async, skips records whose pixel box misses its
-// block, and leaves as soon as a ballot says every one of its pixels has
-// terminated (transmittance below T_min).  No CTA-wide barrier is ever
-// taken, so warps of a tile never wait for each other.
+// Every tile (16x16 pixels) is split into four 8x8 quadrants; a lane owns two
+// pixels of a quadrant, (x, y) and (x, y + 4), which share their column, so
+// the per-pair evaluation after the x offset runs on both at once with the
+// packed two-lane binary32 instructions (eval_pair2).
 //
-// The per-pair evaluation (eval_pair) is written with explicitly rounded
-// operations so the backward kernel reproduces the forward's contribution
-// decisions bit for bit.
+// Forward: a warp owns one quadrant and walks its tile's sorted list on its
+// own, staging 32 records at a time into a private cp.async double buffer,
+// skipping records that cannot reach its quadrant (block_may_hit), and
+// leaving once every one of its pixels has terminated (T below T_min).  With
+// a scheduling scratch the grid is persistent: warps take (tile, quadrant)
+// items, tiles with the longest lists first.
+//
+// Backward (rgb cotangent, the image-loss case): one warp per tile walks the
+// list once from the latest contributor of any of its pixels back to the
+// start, evaluates each record against the quadrants it can reach, and sums a
+// record's gradient over all 256 pixels before one warp reduction and one set
+// of atomics per (record, tile).  Tiles are handed out longest walk first.
+// The general backward (depth, normal or alpha cotangents) and the three-set
+// backward of frequency-decoupled optimisation keep one warp per quadrant.
+//
+// The per-pair evaluation is written with explicitly rounded operations, and
+// the scalar and packed forms run the same operations in the same order, so
+// every backward reproduces the forward's contribution decisions bit for bit.
 #include <cuda_fp16.h>
 
 #include "common.cuh"
@@ -206,125 +218,271 @@ __device__ __forceinline__ uint32_t chunk_mask(const float4 *buf, int cnt, int l
 }
 
 // ---------------------------------------------------------------------------
-// forward
+// Two pixels per lane with the packed two-lane binary32 instructions
 // ---------------------------------------------------------------------------
-struct FwdPix {
-  float px, py, T, C0, C1, C2, D, N0, N1, N2;
-  uint32_t last, nc;
-  bool inside, done;
+// A lane owns the pixels (x, y) and (x, y + 4) of an 8x8 quadrant: they share
+// the column, so the pair's x offset is one scalar and everything after it is
+// evaluated for both pixels at once with the packed add / multiply / fused
+// multiply-add (one instruction for two lanes of arithmetic).  Each packed
+// operation rounds exactly like its scalar counterpart, and eval_pair2 runs
+// the same operations in the same order as eval_pair, so both give the same
+// contribution decisions bit for bit.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 sel2(bool k0, bool k1, float2 a, float2 b) {
+  return make_float2(k0 ? a.x : b.x, k1 ? a.y : b.y);
+}
+
+struct Eval2 {
+  float dx;
+  float2 dy, u, v, g, araw, at, z, inv;
+  bool c0, c1;
 };
 
-// front-to-back blending of one contributor (Eq. 2), stopping before the
-// first one that would take T below T_min
-__device__ __forceinline__ void blend(FwdPix &s, const float4 *r, const float4 &r0, const float4 &r1,
-                                      const float4 &r2, const float4 &r4, const CfgK &cfg, uint32_t idx) {
-  if (s.done) return;
-  PairEval e;
-  if (!eval_pair(r0, r1, r2, r4, s.px, s.py, cfg, e)) return;
-  const float Tn = s.T * (1.0f - e.at);
-  if (Tn < cfg.T_min) {
-    s.done = true;
-    return;
+// eval_pair for the pixels (px, py.x) and (px, py.y).  For a pixel that does
+// not contribute the fields are finite (a surfel's reciprocal is replaced by
+// 0 where the ray misses the plane's front), so a caller may blend it in with
+// weight 0.
+__device__ __forceinline__ void eval_pair2(const float4 &r0, const float4 &r1, const float4 &r2, const float4 &r4,
+                                           float px, float2 py, const CfgK &f, Eval2 &e) {
+  e.dx = __fsub_rn(__fsub_rn(px, r0.x), r4.x);
+  e.dy = add2(add2(py, f2(-r0.y)), f2(-r4.y));
+  float2 q;
+  float alpha;
+  if (r0.w > 0.0f) {
+    e.u = fma2(f2(r1.x), f2(e.dx), mul2(f2(r1.y), e.dy));
+    e.v = mul2(f2(r1.z), e.dy);
+    q = fma2(e.u, e.u, mul2(e.v, e.v));
+    alpha = r0.w;
+    e.z = f2(r0.z);
+    e.inv = f2(1.0f);
+    e.c0 = e.c1 = true;
+  } else {
+    const float2 p0 = fma2(f2(r1.x), f2(e.dx), mul2(f2(r1.y), e.dy));
+    const float2 p1 = fma2(f2(r1.z), f2(e.dx), mul2(f2(r1.w), e.dy));
+    const float2 p2 = fma2(f2(r2.x), f2(e.dx), fma2(f2(r2.y), e.dy, f2(1.0f)));
+    e.c0 = p2.x > 0.0f;
+    e.c1 = p2.y > 0.0f;
+    e.inv = make_float2(e.c0 ? rcp_approx(p2.x) : 0.0f, e.c1 ? rcp_approx(p2.y) : 0.0f);
+    e.z = mul2(f2(r0.z), e.inv);
+    e.c0 = e.c0 && e.z.x > f.near_z;
+    e.c1 = e.c1 && e.z.y > f.near_z;
+    e.u = mul2(p0, e.inv);
+    e.v = mul2(p1, e.inv);
+    q = fma2(e.u, e.u, mul2(e.v, e.v));
+    alpha = -r0.w;
   }
-  const float w = e.at * s.T;
-  const float4 r3 = r[3];
-  s.C0 = fmaf(w, r2.z, s.C0);
-  s.C1 = fmaf(w, r2.w, s.C1);
-  s.C2 = fmaf(w, r3.x, s.C2);
-  s.D = fmaf(w, e.z, s.D);
-  s.N0 = fmaf(w, r3.y, s.N0);
-  s.N1 = fmaf(w, r3.z, s.N1);
-  s.N2 = fmaf(w, r3.w, s.N2);
-  s.T = Tn;
-  s.last = idx;
-  s.nc += 1u;
+  const float2 x = mul2(q, f2(-0.5f * kLog2e));
+  e.g = make_float2(ex2_approx(x.x), ex2_approx(x.y));
+  e.araw = mul2(f2(alpha), e.g);
+  e.c0 = e.c0 && e.araw.x >= f.alpha_min;
+  e.c1 = e.c1 && e.araw.y >= f.alpha_min;
+  e.at = make_float2(fminf(e.araw.x, f.alpha_max), fminf(e.araw.y, f.alpha_max));
 }
 
-__device__ __forceinline__ void write_pix(const RenderArgs &a, const FwdPix &s) {
-  if (!s.inside) return;
-  const size_t HW = (size_t)a.cam.W * a.cam.H;
-  const size_t p = (size_t)(s.py - 0.5f) * a.cam.W + (size_t)(s.px - 0.5f);
-  a.rgb[p] = s.C0 + s.T * a.cfg.bg[0];
-  a.rgb[p + HW] = s.C1 + s.T * a.cfg.bg[1];
-  a.rgb[p + 2 * HW] = s.C2 + s.T * a.cfg.bg[2];
-  a.depth[p] = s.D;
-  a.normal[p] = s.N0;
-  a.normal[p + HW] = s.N1;
-  a.normal[p + 2 * HW] = s.N2;
-  a.alpha[p] = 1.0f - s.T;
-  a.T_final[p] = s.T;
-  a.n_last[p] = s.last;
-  if (a.n_contrib) a.n_contrib[p] = s.nc;
-}
-
-// One 16x16 tile: `tile` indexes the ranges, `local` is the tile within the
-// request's own grid (a.cam.TX columns).
-__device__ __forceinline__ void render_tile_fwd(const RenderArgs &a, int tile, int local,
-                                                float4 (*sm)[2][kCh * kRecF4]) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int bx, by;
-  block_of(local, a.cam.TX, warp, bx, by);
-  FwdPix s[2];
+// Block tests of one staged chunk against QW quadrants of a tile: bit l of
+// m[k] is set iff staged record l (l < cnt) may hit quadrant q0 + k, tested
+// only for the quadrants whose bit is set in `want` (the others get 0).
+template <int QW>
+__device__ __forceinline__ void chunk_masks(const float4 *buf, int cnt, int lane, float tx0, float ty0, int q0,
+                                            uint32_t want, const CfgK &f, uint32_t (&m)[QW]) {
+  float4 r0, r1, r2, b;
+  const bool live = lane < cnt;
+  float2 bxr, byr;
+  if (live) {
+    const float4 *r = buf + lane * kRecF4;
+    r0 = r[0];
+    r1 = r[1];
+    r2 = r[2];
+    b = r[4];
+    bxr = unpack_box(b.z);
+    byr = unpack_box(b.w);
+  }
 #pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const int x = bx + (lane & 7), y = by + (lane >> 3) + 4 * k;
-    s[k].px = (float)x + 0.5f;
-    s[k].py = (float)y + 0.5f;
-    s[k].inside = x < a.cam.W && y < a.cam.H;
-    s[k].done = !s[k].inside;
-    s[k].T = 1.0f;
-    s[k].C0 = s[k].C1 = s[k].C2 = s[k].D = s[k].N0 = s[k].N1 = s[k].N2 = 0.0f;
-    s[k].last = s[k].nc = 0u;
+  for (int k = 0; k < QW; ++k) {
+    const int q = q0 + k;
+    const float bx = tx0 + 8.0f * (float)(q & 1), by = ty0 + 8.0f * (float)(q >> 1);
+    bool hit = false;
+    if (live && ((want >> k) & 1u)) {
+      hit = bxr.x <= bx + 7.5f && bxr.y >= bx + 0.5f && byr.x <= by + 7.5f && byr.y >= by + 0.5f;
+      if (hit) hit = block_may_hit(r0, r1, r2, b, bx, by, f);
+    }
+    m[k] = __ballot_sync(0xffffffffu, hit);
   }
-  if (__all_sync(0xffffffffu, s[0].done && s[1].done)) return;
+}
+
+// ---------------------------------------------------------------------------
+// forward
+// ---------------------------------------------------------------------------
+// Forward with packed pixel pairs: a warp owns QW quadrants of a tile (the
+// CTA has 4 / QW warps), walks the tile's list once for all of them, and
+// skips a quadrant once all its pixels have terminated.
+struct Fwd2 {
+  float2 T, C0, C1, C2, D, N0, N1, N2;
+  uint32_t last0, last1, nc0, nc1;
+  bool done0, done1;
+};
+
+// Eq. 2 for the two pixels at once; a pixel that does not contribute, or has
+// terminated, takes weight 0 and keeps its state.
+__device__ __forceinline__ void blend2(Fwd2 &s, const Eval2 &e, const float4 &r2, const float4 &r3,
+                                       const CfgK &cfg, uint32_t idx) {
+  const bool a0 = e.c0 && !s.done0, a1 = e.c1 && !s.done1;
+  const float2 at = sel2(a0, a1, e.at, f2(0.0f));
+  const float2 Tn = mul2(s.T, add2(f2(1.0f), neg2(at)));
+  const bool st0 = a0 && Tn.x < cfg.T_min, st1 = a1 && Tn.y < cfg.T_min;
+  s.done0 = s.done0 || st0;
+  s.done1 = s.done1 || st1;
+  const bool t0 = a0 && !st0, t1 = a1 && !st1;
+  const float2 w = mul2(sel2(t0, t1, at, f2(0.0f)), s.T);
+  const float2 z = sel2(t0, t1, e.z, f2(0.0f));
+  s.T = sel2(t0, t1, Tn, s.T);
+  s.C0 = fma2(w, f2(r2.z), s.C0);
+  s.C1 = fma2(w, f2(r2.w), s.C1);
+  s.C2 = fma2(w, f2(r3.x), s.C2);
+  s.D = fma2(w, z, s.D);
+  s.N0 = fma2(w, f2(r3.y), s.N0);
+  s.N1 = fma2(w, f2(r3.z), s.N1);
+  s.N2 = fma2(w, f2(r3.w), s.N2);
+  s.last0 = t0 ? idx : s.last0;
+  s.last1 = t1 ? idx : s.last1;
+  s.nc0 += t0 ? 1u : 0u;
+  s.nc1 += t1 ? 1u : 0u;
+}
+
+__device__ __forceinline__ void write_pix1(const RenderArgs &a, int x, int y, float T, float C0, float C1, float C2,
+                                           float D, float N0, float N1, float N2, uint32_t last, uint32_t nc) {
+  if (x >= a.cam.W || y >= a.cam.H) return;
+  const size_t HW = (size_t)a.cam.W * a.cam.H;
+  const size_t p = (size_t)y * a.cam.W + x;
+  a.rgb[p] = C0 + T * a.cfg.bg[0];
+  a.rgb[p + HW] = C1 + T * a.cfg.bg[1];
+  a.rgb[p + 2 * HW] = C2 + T * a.cfg.bg[2];
+  a.depth[p] = D;
+  a.normal[p] = N0;
+  a.normal[p + HW] = N1;
+  a.normal[p + 2 * HW] = N2;
+  a.alpha[p] = 1.0f - T;
+  a.T_final[p] = T;
+  a.n_last[p] = last;
+  if (a.n_contrib) a.n_contrib[p] = nc;
+}
+
+template <int QW>
+__device__ __forceinline__ void render_tile_fwd2(const RenderArgs &a, int tile, int local, int q0,
+                                                 float4 (*smw)[kCh * kRecF4]) {
+  const int lane = threadIdx.x & 31;
+  const int tx0 = (local % a.cam.TX) * kTile, ty0 = (local / a.cam.TX) * kTile;
+  const int lx = lane & 7, ly = lane >> 3;
+  Fwd2 s[QW];
+  uint32_t live = 0;
+#pragma unroll
+  for (int k = 0; k < QW; ++k) {
+    const int q = q0 + k;
+    const int x = tx0 + 8 * (q & 1) + lx, y = ty0 + 8 * (q >> 1) + ly;
+    s[k].T = f2(1.0f);
+    s[k].C0 = s[k].C1 = s[k].C2 = s[k].D = s[k].N0 = s[k].N1 = s[k].N2 = f2(0.0f);
+    s[k].last0 = s[k].last1 = s[k].nc0 = s[k].nc1 = 0u;
+    s[k].done0 = !(x < a.cam.W && y < a.cam.H);
+    s[k].done1 = !(x < a.cam.W && y + 4 < a.cam.H);
+    if (!__all_sync(0xffffffffu, s[k].done0 && s[k].done1)) live |= 1u << k;
+  }
   const uint32_t start = a.ranges[2 * tile], end = a.ranges[2 * tile + 1];
-  const float4 *rec = reinterpret_cast<const float4 *>(a.rec);
-  const float fbx = (float)bx, fby = (float)by;
-
-  if (start < end) stage_chunk(rec, a.vals, start, end, &sm[warp][0][0], nullptr, lane);
-  int buf = 0;
-  for (uint32_t base = start; base < end; base += kCh) {
-    if (base + kCh < end) {
-      stage_chunk(rec, a.vals, base + kCh, end, &sm[warp][buf ^ 1][0], nullptr, lane);
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
+  if (live && start < end) {
+    const float4 *rec = reinterpret_cast<const float4 *>(a.rec);
+    const float px = (float)(tx0 + lx) + 0.5f;  // + 8 for the right quadrants
+    stage_chunk(rec, a.vals, start, end, &smw[0][0], nullptr, lane);
+    int buf = 0;
+    for (uint32_t base = start; base < end; base += kCh) {
+      if (base + kCh < end) {
+        stage_chunk(rec, a.vals, base + kCh, end, &smw[buf ^ 1][0], nullptr, lane);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      __syncwarp();
+      const float4 *chunk = &smw[buf][0];
+      uint32_t m[QW];
+      chunk_masks<QW>(chunk, (int)min((uint32_t)kCh, end - base), lane, (float)tx0, (float)ty0, q0, live, a.cfg, m);
+      uint32_t any = 0;
+#pragma unroll
+      for (int k = 0; k < QW; ++k) any |= m[k];
+      while (any && live) {
+        const int j = __ffs(any) - 1;
+        any &= any - 1;
+        const float4 *r = chunk + j * kRecF4;
+        const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4];
+        const uint32_t idx = base - start + (uint32_t)j + 1u;
+#pragma unroll
+        for (int k = 0; k < QW; ++k) {
+          if (!((live >> k) & 1u) || !((m[k] >> j) & 1u)) continue;
+          const int q = q0 + k;
+          const float pyq = (float)(ty0 + 8 * (q >> 1) + ly) + 0.5f;
+          Eval2 e;
+          eval_pair2(r0, r1, r2, r4, px + 8.0f * (float)(q & 1), make_float2(pyq, pyq + 4.0f), a.cfg, e);
+          blend2(s[k], e, r2, r3, a.cfg, idx);
+          if (__all_sync(0xffffffffu, s[k].done0 && s[k].done1)) live &= ~(1u << k);
+        }
+      }
+      if (!live) break;
+      __syncwarp();
+      buf ^= 1;
     }
-    __syncwarp();
-    const float4 *chunk = &sm[warp][buf][0];
-    uint32_t mask = chunk_mask(chunk, (int)min((uint32_t)kCh, end - base), lane, fbx, fby, a.cfg);
-    while (mask) {
-      const int j = __ffs(mask) - 1;
-      mask &= mask - 1;
-      if (s[0].done && s[1].done) continue;
-      const float4 *r = chunk + j * kRecF4;
-      const float4 r0 = r[0], r1 = r[1], r2 = r[2], r4 = r[4];
-      const uint32_t idx = base - start + (uint32_t)j + 1u;
-      blend(s[0], r, r0, r1, r2, r4, a.cfg, idx);
-      blend(s[1], r, r0, r1, r2, r4, a.cfg, idx);
-    }
-    if (__all_sync(0xffffffffu, s[0].done && s[1].done)) break;
-    __syncwarp();
-    buf ^= 1;
+    cp_async_wait<0>();
   }
-  cp_async_wait<0>();
-  write_pix(a, s[0]);
-  write_pix(a, s[1]);
+#pragma unroll
+  for (int k = 0; k < QW; ++k) {
+    const int q = q0 + k;
+    const int x = tx0 + 8 * (q & 1) + lx, y = ty0 + 8 * (q >> 1) + ly;
+    write_pix1(a, x, y, s[k].T.x, s[k].C0.x, s[k].C1.x, s[k].C2.x, s[k].D.x, s[k].N0.x, s[k].N1.x, s[k].N2.x,
+               s[k].last0, s[k].nc0);
+    write_pix1(a, x, y + 4, s[k].T.y, s[k].C0.y, s[k].C1.y, s[k].C2.y, s[k].D.y, s[k].N0.y, s[k].N1.y, s[k].N2.y,
+               s[k].last1, s[k].nc1);
+  }
 }
 
-__global__ void __launch_bounds__(kRW * 32) render_fwd_kernel(RenderArgs a) {
-  __shared__ __align__(16) float4 sm[kRW][2][kCh * kRecF4];
-  render_tile_fwd(a, blockIdx.x, blockIdx.x, sm);
+// Forward CTAs: four warps, one quadrant (8x8 pixels) each; six CTAs per SM
+// (78 registers, no spills).
+constexpr int kFwdWarps = 4;
+constexpr int kFwdMinBlocks = 6;
+
+__global__ void __launch_bounds__(kFwdWarps * 32, kFwdMinBlocks) render_fwd2_kernel(RenderArgs a) {
+  __shared__ __align__(16) float4 sm[kFwdWarps][2][kCh * kRecF4];
+  const int warp = threadIdx.x >> 5;
+  render_tile_fwd2<1>(a, blockIdx.x, blockIdx.x, warp, sm[warp]);
 }
 
-__global__ void __launch_bounds__(kRW * 32) render_batch_kernel(BatchRenderArgs b) {
-  __shared__ __align__(16) float4 sm[kRW][2][kCh * kRecF4];
+// Persistent forward: every warp takes (tile, quadrant) items from `counter`
+// in the order `order` lists the tiles (longest list first), four items per
+// tile; warps never wait for each other.
+__global__ void __launch_bounds__(kFwdWarps * 32, kFwdMinBlocks) render_fwd_sched_kernel(RenderArgs a,
+                                                                                     const uint32_t *order,
+                                                                  uint32_t *counter, int tiles) {
+  __shared__ __align__(16) float4 sm[4][2][kCh * kRecF4];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  while (true) {
+    uint32_t item = 0;
+    if (lane == 0) item = atomicAdd(counter, 1u);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= 4u * (uint32_t)tiles) break;
+    const int tile = (int)__ldg(order + (item >> 2));
+    render_tile_fwd2<1>(a, tile, tile, (int)(item & 3u), sm[warp]);
+    __syncwarp();
+  }
+}
+
+__global__ void __launch_bounds__(kFwdWarps * 32, kFwdMinBlocks) render_batch2_kernel(BatchRenderArgs b) {
+  __shared__ __align__(16) float4 sm[kFwdWarps][2][kCh * kRecF4];
   const int gy = blockIdx.x / b.TXmax, tx = blockIdx.x % b.TXmax;
   int r = 0;
   while (r + 1 < b.nreq && gy >= b.row_off[r + 1]) ++r;
   const RenderArgs &a = b.req[r];
   if (tx >= a.cam.TX) return;
-  render_tile_fwd(a, blockIdx.x, (gy - b.row_off[r]) * a.cam.TX + tx, sm);
+  const int warp = threadIdx.x >> 5;
+  render_tile_fwd2<1>(a, blockIdx.x, (gy - b.row_off[r]) * a.cam.TX + tx, warp, sm[warp]);
 }
 
 // ---------------------------------------------------------------------------
@@ -719,6 +877,241 @@ __global__ void __launch_bounds__(kRW * 32, NC == 1 ? 5 : 4) render_bwd_rgb_kern
   });
 }
 
+// Tile scheduling for the one-warp-per-tile backward.  A tile's work is its
+// longest reverse walk (the largest n_last of its pixels); tiles are handed
+// out longest first from an atomic counter, so that no long tile starts last
+// and leaves the device idle behind it.
+__global__ void k_tile_work(const uint32_t *__restrict__ n_last, int W, int H, int TX, int tiles,
+                            uint32_t *__restrict__ work) {
+  const int t = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (t >= tiles) return;
+  const int tx0 = (t % TX) * kTile, ty0 = (t / TX) * kTile;
+  uint32_t m = 0;
+  for (int k = lane; k < kTilePix; k += 32) {
+    const int x = tx0 + (k & 15), y = ty0 + (k >> 4);
+    if (x < W && y < H) m = max(m, __ldg(n_last + (size_t)y * W + x));
+  }
+  m = __reduce_max_sync(0xffffffffu, m);
+  if (lane == 0) work[t] = m;
+}
+
+// A tile's forward work estimate: its list length.
+__global__ void k_tile_len(const uint32_t *__restrict__ ranges, int tiles, uint32_t *__restrict__ work) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < tiles) work[t] = ranges[2 * t + 1] - ranges[2 * t];
+}
+
+// Half-octave buckets of the work, longest first; order[] lists the tiles by
+// descending bucket.  One CTA; also clears the hand-out counter.
+__device__ __forceinline__ int work_bucket(uint32_t w) {
+  if (w == 0) return 0;
+  const int e = 31 - __clz(w);
+  return min(63, 2 * e + 1 + (e > 0 ? (int)((w >> (e - 1)) & 1u) : 0));
+}
+
+__global__ void __launch_bounds__(1024) k_tile_order(const uint32_t *__restrict__ work, int tiles,
+                                                     uint32_t *__restrict__ order, uint32_t *__restrict__ counter) {
+  __shared__ uint32_t cnt[64];
+  if (threadIdx.x < 64) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  for (int t = threadIdx.x; t < tiles; t += blockDim.x) atomicAdd(&cnt[work_bucket(work[t])], 1u);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t acc = 0;
+    for (int b = 63; b >= 0; --b) {
+      const uint32_t c = cnt[b];
+      cnt[b] = acc;
+      acc += c;
+    }
+    *counter = 0;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < tiles; t += blockDim.x) order[atomicAdd(&cnt[work_bucket(work[t])], 1u)] = (uint32_t)t;
+}
+
+// Per-pixel state of the one-warp-per-tile backward: transmittance and the
+// blended dot product S stay in registers; the read-only cotangent and n_last
+// of a lane's pixel pair sit in shared memory (lane-indexed, so the loads are
+// conflict-free), which keeps the kernel's registers low enough for 20 warps
+// per SM.
+struct Bwd4 {
+  float2 T, S;
+};
+struct Bwd4Smem {
+  float2 dC[4][3][32];  // [quadrant][channel][lane]: the lane's two pixels
+  uint2 last[4][32];    // [quadrant][lane]
+};
+
+// Reverse replay of one record for the two pixels of a lane, accumulated into
+// the per-record slots g (pair_grad_rgb for both pixels).
+__device__ __forceinline__ void pair_grad2s(float (&g)[13], Bwd4 &s, const float2 dC0, const float2 dC1,
+                                            const float2 dC2, const Eval2 &e, bool c0, bool c1, const float4 &r0,
+                                            const float4 &r1, const float4 &r2, const float4 &r3, const CfgK &cfg) {
+  const float2 at = sel2(c0, c1, e.at, f2(0.0f));
+  const float2 om = add2(f2(1.0f), neg2(at));
+  const float2 Ti = mul2(s.T, make_float2(rcp_approx(om.x), rcp_approx(om.y)));
+  s.T = sel2(c0, c1, Ti, s.T);
+  const float2 w = mul2(at, Ti);
+  const float2 cd = fma2(f2(r2.z), dC0, fma2(f2(r2.w), dC1, mul2(f2(r3.x), dC2)));
+  const float2 fsum = add2(cd, neg2(s.S));
+  const float2 dat = mul2(Ti, fsum);
+  s.S = fma2(at, fsum, s.S);
+  auto acc = [](float &gk, float2 a, float2 b) { gk = fmaf(a.x, b.x, fmaf(a.y, b.y, gk)); };
+  acc(g[1], w, dC0);
+  acc(g[2], w, dC1);
+  acc(g[3], w, dC2);
+  const bool o0 = c0 && e.araw.x <= cfg.alpha_max, o1 = c1 && e.araw.y <= cfg.alpha_max;
+  const float2 dato = sel2(o0, o1, dat, f2(0.0f));
+  acc(g[0], dato, e.g);
+  const float2 dd = mul2(dato, mul2(f2(-0.5f), at));
+  const float2 dx = f2(e.dx);
+  if (r0.w > 0.0f) {
+    const float2 ddx = mul2(dd, dx), ddy = mul2(dd, e.dy);
+    acc(g[7], ddx, dx);
+    acc(g[8], mul2(f2(2.0f), ddx), e.dy);
+    acc(g[9], ddy, e.dy);
+    const float2 dd2 = mul2(dd, f2(-2.0f));
+    acc(g[4], mul2(dd2, e.u), f2(r1.x));
+    acc(g[5], dd2, fma2(e.u, f2(r1.y), mul2(e.v, f2(r1.z))));
+  } else {
+    const float2 du = mul2(mul2(f2(2.0f), e.u), dd), dv = mul2(mul2(f2(2.0f), e.v), dd);
+    const float2 dp0 = mul2(du, e.inv), dp1 = mul2(dv, e.inv);
+    const float2 dp2 = mul2(fma2(du, e.u, mul2(dv, e.v)), neg2(e.inv));
+    acc(g[7], dp0, dx);
+    acc(g[8], dp0, e.dy);
+    acc(g[9], dp1, dx);
+    acc(g[10], dp1, e.dy);
+    acc(g[11], dp2, dx);
+    acc(g[12], dp2, e.dy);
+    acc(g[4], fma2(dp0, f2(-r1.x), fma2(dp1, f2(-r1.z), mul2(dp2, f2(-r2.x)))), f2(1.0f));
+    acc(g[5], fma2(dp0, f2(-r1.y), fma2(dp1, f2(-r1.w), mul2(dp2, f2(-r2.y)))), f2(1.0f));
+  }
+}
+
+// One tile of the rgb-only backward by one warp (all four quadrants).
+__device__ __forceinline__ void bwd4_tile(const RenderBwdArgs &a, int tile, int lane, float4 (*sm)[kCh * kRecF4],
+                                          uint32_t (*sid)[kCh], Bwd4Smem &ps) {
+  const int tx0 = (tile % a.cam.TX) * kTile, ty0 = (tile / a.cam.TX) * kTile;
+  const int lx = lane & 7, ly = lane >> 3;
+  const float *g = a.g_rgbs[0];
+  const size_t HW = (size_t)a.cam.W * a.cam.H;
+  Bwd4 s[4];
+  uint32_t qmax[4];
+  uint32_t wmax = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int x = tx0 + 8 * (k & 1) + lx, y = ty0 + 8 * (k >> 1) + ly;
+    float Ts[2] = {1.0f, 1.0f}, d[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    uint32_t l[2] = {0u, 0u};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int yy = y + 4 * h;
+      if (x < a.cam.W && yy < a.cam.H) {
+        const size_t p = (size_t)yy * a.cam.W + x;
+        Ts[h] = a.T_final[p];
+        l[h] = a.n_last[p];
+        if (g) {
+          d[h][0] = g[p];
+          d[h][1] = g[p + HW];
+          d[h][2] = g[p + 2 * HW];
+        }
+      }
+    }
+    s[k].T = make_float2(Ts[0], Ts[1]);
+    const float2 dC0 = make_float2(d[0][0], d[1][0]), dC1 = make_float2(d[0][1], d[1][1]),
+                 dC2 = make_float2(d[0][2], d[1][2]);
+    ps.dC[k][0][lane] = dC0;
+    ps.dC[k][1][lane] = dC1;
+    ps.dC[k][2][lane] = dC2;
+    ps.last[k][lane] = make_uint2(l[0], l[1]);
+    s[k].S = fma2(f2(a.cfg.bg[0]), dC0, fma2(f2(a.cfg.bg[1]), dC1, mul2(f2(a.cfg.bg[2]), dC2)));
+    qmax[k] = __reduce_max_sync(0xffffffffu, max(l[0], l[1]));
+    wmax = max(wmax, qmax[k]);
+  }
+  if (wmax == 0) return;
+  const uint32_t start = a.ranges[2 * tile];
+  const float4 *rec = reinterpret_cast<const float4 *>(a.rec);
+  const float px = (float)(tx0 + lx) + 0.5f;
+  uint32_t ce = start + wmax;
+  uint32_t cs = ce - min((uint32_t)kCh, wmax);
+  stage_chunk(rec, a.vals, cs, ce, &sm[0][0], &sid[0][0], lane);
+  int buf = 0;
+  while (true) {
+    const bool has_next = cs > start;
+    const uint32_t ncs = has_next ? cs - min((uint32_t)kCh, cs - start) : cs;
+    if (has_next) {
+      stage_chunk(rec, a.vals, ncs, cs, &sm[buf ^ 1][0], &sid[buf ^ 1][0], lane);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncwarp();
+    const float4 *chunk = &sm[buf][0];
+    uint32_t want = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) want |= (qmax[k] > cs - start ? 1u : 0u) << k;
+    uint32_t m[4];
+    chunk_masks<4>(chunk, (int)(ce - cs), lane, (float)tx0, (float)ty0, 0, want, a.cfg, m);
+    uint32_t any = m[0] | m[1] | m[2] | m[3];
+    while (any) {
+      const int jj = 31 - __clz(any);
+      any &= ~(1u << jj);
+      const float4 *r = chunk + jj * kRecF4;
+      const uint32_t jrel = cs + (uint32_t)jj - start;
+      const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4];
+      float gs[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) gs[i] = 0.0f;
+      bool hit = false;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (!((m[k] >> jj) & 1u) || jrel >= qmax[k]) continue;
+        const float pyq = (float)(ty0 + 8 * (k >> 1) + ly) + 0.5f;
+        Eval2 e;
+        eval_pair2(r0, r1, r2, r4, px + 8.0f * (float)(k & 1), make_float2(pyq, pyq + 4.0f), a.cfg, e);
+        const uint2 l = ps.last[k][lane];
+        const bool c0 = e.c0 && jrel < l.x, c1 = e.c1 && jrel < l.y;
+        if (!__any_sync(0xffffffffu, c0 || c1)) continue;
+        hit = true;
+        pair_grad2s(reinterpret_cast<float(&)[13]>(gs), s[k], ps.dC[k][0][lane], ps.dC[k][1][lane],
+                    ps.dC[k][2][lane], e, c0, c1, r0, r1, r2, r3, a.cfg);
+      }
+      if (!hit) continue;
+      reduce_record<false>(gs, r0.w > 0.0f, lane, a.rec_grads[0] + (size_t)sid[buf][jj] * kGradW);
+    }
+    if (!has_next) break;
+    __syncwarp();
+    buf ^= 1;
+    ce = cs;
+    cs = ncs;
+  }
+  cp_async_wait<0>();
+}
+
+// 20 one-warp CTAs per SM: 96 registers, no spills.
+constexpr int kBwd4MinBlocks = 20;
+// One warp per tile; with `order`, a persistent grid takes tiles longest
+// first from `counter`, else CTA b takes tile b.
+__global__ void __launch_bounds__(32, kBwd4MinBlocks) render_bwd_rgb4_kernel(RenderBwdArgs a, const uint32_t *order,
+                                                                           uint32_t *counter, int tiles) {
+  __shared__ __align__(16) float4 sm[2][kCh * kRecF4];
+  __shared__ uint32_t sid[2][kCh];
+  __shared__ Bwd4Smem ps;
+  const int lane = threadIdx.x & 31;
+  if (!order) {
+    bwd4_tile(a, blockIdx.x, lane, sm, sid, ps);
+    return;
+  }
+  while (true) {
+    uint32_t t = 0;
+    if (lane == 0) t = atomicAdd(counter, 1u);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= (uint32_t)tiles) break;
+    bwd4_tile(a, (int)__ldg(order + t), lane, sm, sid, ps);
+    __syncwarp();
+  }
+}
+
 // general backward: any of the rgb, depth, normal and alpha cotangents
 __global__ void __launch_bounds__(kRW * 32, 5) render_bwd_kernel(RenderBwdArgs a) {
   __shared__ __align__(16) float4 sm[kRW][2][kCh * kRecF4];
@@ -757,26 +1150,64 @@ static void prefer_shared(const void *fn) {
 int launch_render_fwd(const RenderArgs &a, cudaStream_t s) {
   const int tiles = a.cam.TX * a.cam.TY;
   if (tiles <= 0) return 0;
-  static bool once = (prefer_shared((const void *)render_fwd_kernel), true);
+  static bool once = (prefer_shared((const void *)render_fwd2_kernel), true);
   (void)once;
-  render_fwd_kernel<<<tiles, kRW * 32, 0, s>>>(a);
+  if (!a.tile_sched) {
+    render_fwd2_kernel<<<tiles, kFwdWarps * 32, 0, s>>>(a);
+    return 0;
+  }
+  // longest lists first, every warp taking (tile, quadrant) items
+  static int resident = [] {
+    prefer_shared((const void *)render_fwd_sched_kernel);
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, render_fwd_sched_kernel, 128, 0);
+    return max(1, sms * max(per, 1));
+  }();
+  uint32_t *work = a.tile_sched, *order = a.tile_sched + tiles, *counter = a.tile_sched + 2 * (size_t)tiles;
+  k_tile_len<<<(tiles + 255) / 256, 256, 0, s>>>(a.ranges, tiles, work);
+  k_tile_order<<<1, 1024, 0, s>>>(work, tiles, order, counter);
+  render_fwd_sched_kernel<<<min(tiles, resident), 128, 0, s>>>(a, order, counter, tiles);
   return 0;
 }
 
 int launch_render_batch(const BatchRenderArgs &b, int rows, cudaStream_t s) {
   const int blocks = rows * b.TXmax;
   if (blocks <= 0) return 0;
-  static bool once = (prefer_shared((const void *)render_batch_kernel), true);
+  static bool once = (prefer_shared((const void *)render_batch2_kernel), true);
   (void)once;
-  render_batch_kernel<<<blocks, kRW * 32, 0, s>>>(b);
+  render_batch2_kernel<<<blocks, kFwdWarps * 32, 0, s>>>(b);
   return 0;
+}
+
+// The one-warp-per-tile rgb backward: with a scheduling scratch, the tiles'
+// work and a longest-first order are computed on the device and a persistent
+// grid (every resident CTA) takes the tiles in that order.
+static void launch_bwd4(const RenderBwdArgs &a, int tiles, cudaStream_t s) {
+  static int resident = [] {
+    prefer_shared((const void *)render_bwd_rgb4_kernel);
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, render_bwd_rgb4_kernel, 32, 0);
+    return max(1, sms * max(per, 1));
+  }();
+  if (!a.tile_sched) {
+    render_bwd_rgb4_kernel<<<tiles, 32, 0, s>>>(a, nullptr, nullptr, tiles);
+    return;
+  }
+  uint32_t *work = a.tile_sched, *order = a.tile_sched + tiles, *counter = a.tile_sched + 2 * (size_t)tiles;
+  k_tile_work<<<(tiles + 7) / 8, 256, 0, s>>>(a.n_last, a.cam.W, a.cam.H, a.cam.TX, tiles, work);
+  k_tile_order<<<1, 1024, 0, s>>>(work, tiles, order, counter);
+  render_bwd_rgb4_kernel<<<min(tiles, resident), 32, 0, s>>>(a, order, counter, tiles);
 }
 
 int launch_render_bwd(const RenderBwdArgs &a, cudaStream_t s) {
   const int tiles = a.cam.TX * a.cam.TY;
   if (tiles <= 0) return 0;
   static bool once = (prefer_shared((const void *)render_bwd_kernel),
-                      prefer_shared((const void *)render_bwd_rgb_kernel<1>),
+
                       prefer_shared((const void *)render_bwd_rgb_kernel<3>), true);
   (void)once;
   if (a.nc == 0 && (a.g_depth || a.g_normal || a.g_alpha)) {
@@ -797,7 +1228,7 @@ int launch_render_bwd(const RenderBwdArgs &a, cudaStream_t s) {
       RenderBwdArgs one = b;
       one.g_rgbs[0] = b.g_rgbs[c];
       one.rec_grads[0] = b.rec_grads[c];
-      render_bwd_rgb_kernel<1><<<tiles, kRW * 32, 0, s>>>(one);
+      launch_bwd4(one, tiles, s);
     }
   return 0;
 }

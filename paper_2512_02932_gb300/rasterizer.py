@@ -149,6 +149,7 @@ class Rasterizer:
         self.n_contrib = torch.empty((H, W), dtype=torch.int32, device=d)
         TX, TY = (W + TILE - 1) // TILE, (H + TILE - 1) // TILE
         self.ranges = torch.empty((TX * TY, 2), dtype=torch.int32, device=d)
+        self.tile_sched = torch.empty(2 * TX * TY + 1, dtype=torch.int32, device=d)
         self.hw = (W, H)
         self.ws = None
 
@@ -219,7 +220,7 @@ class Rasterizer:
         }
         img = abi.hgs_image(out["rgb"].data_ptr(), out["depth"].data_ptr(), out["normal"].data_ptr(),
                             out["alpha"].data_ptr(), self.T_final.data_ptr(), self.n_last.data_ptr(),
-                            self.n_contrib.data_ptr())
+                            self.n_contrib.data_ptr(), self.tile_sched.data_ptr())
         self._img_s = img
         bins = self.bin_struct()
         abi.check(abi.hgs_render_fwd(self.n, C.byref(self._proj_s), C.byref(bins), C.byref(self._cam_s),

@@ -143,8 +143,13 @@ class Server:
         self.device = torch.device(device)
         self.plain = plain
         if plain:
-            self.rast = Rasterizer(self.device, sync_check=True)
+            # the same fixed instance capacity as a batch, no per-frame read
+            # of the instance count: an overflow is seen on the device and
+            # the request is rendered again with room for it
+            self.rast = Rasterizer(self.device, capacity=self.scfg.capacity, sync_check=False)
             self.stream = torch.cuda.Stream(device=self.device)
+            self.h_err = torch.zeros(1, dtype=torch.int32).pin_memory()
+            self.h_count = torch.zeros(1, dtype=torch.int64).pin_memory()
         else:
             self.br = BatchRenderer(self.device, cfg, self.scfg)
         # running estimate of tile instances per (scene, pixel): admission
@@ -168,12 +173,19 @@ class Server:
                     time.sleep(2e-5)
             now = time.perf_counter() - t0
             r.t_launch = max(now, r.t_arrival)
-            with torch.cuda.stream(self.stream):
-                out = self.rast.forward(self.scenes[r.scene_id], r.cam, self.cfg)
-                ev = torch.cuda.Event()
-                ev.record(self.stream)
-            while not ev.query():
-                time.sleep(2e-5)
+            while True:
+                with torch.cuda.stream(self.stream):
+                    self.rast.dev_err.zero_()
+                    out = self.rast.forward(self.scenes[r.scene_id], r.cam, self.cfg)
+                    self.h_err.copy_(self.rast.dev_err, non_blocking=True)
+                    self.h_count.copy_(self.rast.d_count, non_blocking=True)
+                    ev = torch.cuda.Event()
+                    ev.record(self.stream)
+                while not ev.query():
+                    time.sleep(2e-5)
+                if int(self.h_err.item()) != abi.HGS_ERR_CAPACITY:
+                    break
+                self.rast._ensure_capacity(int(int(self.h_count.item()) * 1.25) + 1024)
             r.t_done = time.perf_counter() - t0
             if keep:
                 r.out = {k: v.clone() for k, v in out.items()}

@@ -30,12 +30,10 @@ def test_tiny_lists_and_images(seed):
     K = assert_lists_bitexact(r, scene, cam)
     assert K > 1000
     m = _oracle_maps(scene, cam)
-    assert_images_match(g, m, m["amb"])
+    # contributor counts are integers: the matching result must have the same
+    assert_images_match(g, m, check_nc=True, max_excluded=0.0, label=f"tiny seed {seed}")
     # transmittance and alpha are consistent
     np.testing.assert_allclose(g["alpha"], 1 - g["T_final"], atol=1e-7)
-    # contributor counts are integers: exact wherever the oracle is unambiguous
-    ok = ~m["amb"]
-    np.testing.assert_array_equal(g["n_contrib"][ok], m["n_contrib"][ok].astype(np.int64))
 
 
 def _gpu_vjp(scene, cam, cot, cfg=CFG, rgb_only=False):
@@ -98,11 +96,38 @@ def test_sh_degree3_surface_gradients():
     cam = S.orbit_camera(20.0, 15.0, 3.0, 96, 72, 50.0)
     m = _oracle_maps(scene, cam)
     g = gpu_forward(scene, cam)[2]
-    assert_images_match(g, m, m["amb"])
+    assert_images_match(g, m, check_nc=True, label="sh3 surface")
     cot = _masked_cot(21, cam, m["amb"])
     _, ref = AR.vjp(scene, cam, CFG, cot)
     _, got = _gpu_vjp(scene, cam, cot)
     assert_grads_match(got, ref)
+
+
+@pytest.mark.parametrize("lam,Tz,rgb_only", [(1.0, 1e-3, False), (1.7, 0.1, False), (1.7, 0.1, True)])
+def test_scale_modulation_parity(lam, Tz, rgb_only):
+    """Surfels whose buffered s_z lies around theta_z = 1.05 (Sec. 3.2, Eqs.
+    6-7): with the paper's temperature (T_z = 0.001, nearly a step) and a soft
+    one (T_z = 0.1, lambda_z = 1.7).  Images against the oracle, gradients
+    (d/d log s_z of every surfel included) against the FP64 autograd
+    formulation."""
+    import dataclasses
+    cfg = dataclasses.replace(CFG, lambda_z=lam, T_z=Tz)
+    scene, cam = S.tiny_scene(7)
+    surf = scene.types == 0
+    rng = np.random.default_rng(70)
+    scene.log_scales[surf, 2] = np.log(rng.uniform(0.9, 1.2, int(surf.sum()))).astype(np.float32)
+    m = O.Oracle(scene, cam, cfg).render_maps()
+    g = gpu_forward(scene, cam, cfg)[2]
+    assert_images_match(g, m, check_nc=True, label=f"modulation T_z={Tz}")
+    cot = _masked_cot(71, cam, m["amb"])
+    if rgb_only:
+        for k in ("depth", "normal", "alpha"):
+            cot[k] = np.zeros_like(cot[k])
+    _, ref = AR.vjp(scene, cam, cfg, cot)
+    _, got = _gpu_vjp(scene, cam, cot, cfg, rgb_only=rgb_only)
+    assert_grads_match(got, ref)
+    dsz = ref["log_scales"][surf, 2]
+    assert np.count_nonzero(np.abs(dsz) > 1e-6 * np.abs(ref["log_scales"]).max()) > 20
 
 
 # ---------------------------------------------------------------------------
@@ -116,7 +141,7 @@ def test_ragged_image_and_tiles():
         r, st, g = gpu_forward(scene, cam)
         assert_lists_bitexact(r, scene, cam)
         m = _oracle_maps(scene, cam)
-        assert_images_match(g, m, m["amb"], max_amb_frac=1.0)
+        assert_images_match(g, m, check_nc=True, label=f"ragged {w}x{h}")
 
 
 def test_empty_scene_and_all_culled():
@@ -179,7 +204,7 @@ def test_long_tile_lists_and_termination():
     assert (ranges[:, 1] - ranges[:, 0]).max() > 1000
     m = _oracle_maps(scene, cam)
     assert (m["T"] < 1e-3).mean() > 0.3
-    assert_images_match(g, m, m["amb"], max_amb_frac=0.05)
+    assert_images_match(g, m, check_nc=True, max_excluded=0.0, label="long lists")
     cot = _masked_cot(3, cam, m["amb"])
     _, ref = AR.vjp(scene, cam, CFG, cot)
     _, got = _gpu_vjp(scene, cam, cot)
@@ -206,7 +231,7 @@ def test_degenerate_primitives():
     r, st, g = gpu_forward(scene, cam)
     assert_lists_bitexact(r, scene, cam)
     m = _oracle_maps(scene, cam)
-    assert_images_match(g, m, m["amb"], max_amb_frac=0.01)
+    assert_images_match(g, m, check_nc=True, label="degenerate")
     # the edge-on surfel alone renders nothing
     r1, _, g1 = gpu_forward(scene.subset([0]), cam)
     assert np.all(g1["alpha"] == 0)
@@ -269,7 +294,7 @@ def test_surfels_reaching_the_near_plane():
     r, st, g = gpu_forward(scene, cam)
     assert_lists_bitexact(r, scene, cam)
     m = _oracle_maps(scene, cam)
-    assert_images_match(g, m, m["amb"], max_amb_frac=0.02)
+    assert_images_match(g, m, check_nc=True, max_excluded=0.0, label="near plane")
     cot = _masked_cot(4, cam, m["amb"])
     _, ref = AR.vjp(scene, cam, CFG, cot)
     _, got = _gpu_vjp(scene, cam, cot)
@@ -361,7 +386,7 @@ def test_wide_path_mixed_with_small_instances(loc):
     r, st, g = gpu_forward(scene, cam, cfg)
     assert_lists_bitexact(r, scene, cam, cfg)
     m = _oracle_maps(scene, cam, cfg)
-    assert_images_match(g, m, m["amb"], max_amb_frac=0.03)  # large splats: more pairs near a threshold
+    assert_images_match(g, m, check_nc=True, max_excluded=0.0, label=f"wide mixed {loc}")
 
 
 def test_wide_path_with_no_small_instances():
