@@ -251,9 +251,16 @@ def launches_per_step(rast, exchange_steps, steps):
     # 4 depth passes and the tile passes (chunk histogram, chunk scan,
     # scatter each), offsets scan (3), emit (2), range fix-up, optional
     # 64-bit keys, the wide-rectangle path (5, launched every frame; they
-    # return at once when the frame takes the radix path)
-    bin_sort = 3 * (4 + passes) + 3 + 2 + 1 + (1 if rast.keys is not None else 0) + 5
-    per = 1 + bin_sort + 1 + 2
+    # return at once when the frame does not take it); on tile grids up to
+    # 8192 tiles the counting placement (4) replaces emit, tile passes, range
+    # fix-up and keys.  Render forward and
+    # backward: tile work, tile order and the kernel each; preprocess
+    # forward and backward one each.
+    if tiles <= 8192:   # counting placement instead of emit and the radix tile passes
+        bin_sort = 3 * 4 + 3 + 4 + 5
+    else:
+        bin_sort = 3 * (4 + passes) + 3 + 2 + 1 + (1 if rast.keys is not None else 0) + 5
+    per = 1 + bin_sort + 3 + 3 + 1
     return per * steps + exchange_steps
 
 

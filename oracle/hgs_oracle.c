@@ -690,6 +690,32 @@ static int surfel_hit(const orc_ctx *C, const prim_t *p, double px, double py, d
   return 1;
 }
 
+/* Conditioning of a pair's splat-frame coordinates (u, v) at the pixel
+ * centre (px, py): a binary32 evaluation from the offset (ex, ey) to the
+ * projected centre, u = du/dx ex + du/dy ey (likewise v), carries up to
+ * COND_ULPS ulps of the cancelling terms |du/dx ex| + |du/dy ey|; *du and *dv
+ * are those bounds.  A surfel's derivatives are taken by differences of the
+ * ray-splat solve 1e-3 px apart. */
+static void cond_uv(const orc_ctx *C, const prim_t *p, double px, double py, double u, double v, double *du,
+                    double *dv) {
+  double ex = px - p->mx, ey = py - p->my, dux, duy, dvx, dvy;
+  if (p->type == 1) {
+    dux = p->ca; duy = p->cb; dvx = 0.0; dvy = p->cc;
+  } else {
+    double s1[3], s2[3];
+    const double hh = 1e-3;
+    if (surfel_hit(C, p, px + hh, py, s1) && surfel_hit(C, p, px, py + hh, s2)) {
+      dux = (s1[0] - u) / hh; dvx = (s1[1] - v) / hh;
+      duy = (s2[0] - u) / hh; dvy = (s2[1] - v) / hh;
+    } else {
+      dux = duy = dvx = dvy = 0.0;
+    }
+  }
+  const double eps32 = 5.960464477539063e-08;
+  *du = COND_ULPS * eps32 * (fabs(dux * ex) + fabs(duy * ey));
+  *dv = COND_ULPS * eps32 * (fabs(dvx * ex) + fabs(dvy * ey));
+}
+
 /* Unified distance (Eq. 1) and contribution (Sec. 3.1) of primitive p at the
  * pixel centre (px, py).  Returns 1 and fills *c if the pair must be listed:
  * it contributes, or one of its decisions sits in a band (c->flags).  The
@@ -719,28 +745,11 @@ static int eval_pair(const orc_ctx *C, const prim_t *p, double px, double py, co
   const double ag = p->alpha * exp(-0.5 * d);
   if (ag < 0.1 * amin && !(flags & PA_NEAR)) return 0;  /* no binary32 error reaches the threshold from here */
   /* conditioning of (u, v) as functions of the offset to the centre */
-  double dag = 0.0;
-  {
-    double ex = px - p->mx, ey = py - p->my, dux, duy, dvx, dvy;
-    if (p->type == 1) {
-      dux = p->ca; duy = p->cb; dvx = 0.0; dvy = p->cc;
-    } else {
-      double s1[3], s2[3];
-      const double hh = 1e-3;
-      if (surfel_hit(C, p, px + hh, py, s1) && surfel_hit(C, p, px, py + hh, s2)) {
-        dux = (s1[0] - u) / hh; dvx = (s1[1] - v) / hh;
-        duy = (s2[0] - u) / hh; dvy = (s2[1] - v) / hh;
-      } else {
-        dux = duy = dvx = dvy = 0.0;
-      }
-    }
-    const double eps32 = 5.960464477539063e-08;
-    double du = COND_ULPS * eps32 * (fabs(dux * ex) + fabs(duy * ey));
-    double dv = COND_ULPS * eps32 * (fabs(dvx * ex) + fabs(dvy * ey));
-    double dd = 2.0 * (fabs(u) * du + fabs(v) * dv) + du * du + dv * dv;
-    /* ag moves by at most ag (e^(dd/2) - 1) when d moves by dd */
-    dag = ag * expm1(0.5 * dd);
-  }
+  double du, dv;
+  cond_uv(C, p, px, py, u, v, &du, &dv);
+  const double dd = 2.0 * (fabs(u) * du + fabs(v) * dv) + du * du + dv * dv;
+  /* ag moves by at most ag (e^(dd/2) - 1) when d moves by dd */
+  const double dag = ag * expm1(0.5 * dd);
   const int a_ok = ag >= amin;
   if (fabs(ag - amin) <= fmax(AMB_ALPHA_REL * amin, dag)) flags |= PA_ALPHA;
   if (p->ndot < AMB_FLIP) flags |= PA_FLIP;
@@ -955,6 +964,37 @@ void orc_render_variants(void *ctx, int64_t npix, const int32_t *pix, int32_t *n
 
 int orc_max_variants(void) { return ORC_MAXV; }
 
+/* The primitives whose pairs Eq. 2 blends at each of npix pixels (every
+ * decision the FP64 way), front to back: ids[q * maxc ..], at most maxc per
+ * pixel, count[q] of them.  Used to choose the primitives a finite-difference
+ * check looks at, among those an image shows. */
+void orc_pixel_contributors(void *ctx, int64_t npix, const int32_t *pix, int maxc, int32_t *ids, int32_t *count) {
+  orc_ctx *C = (orc_ctx *)ctx;
+  const double Tmin = C->cfg[CF_T_MIN], amax = C->cfg[CF_ALPHA_MAX];
+#pragma omp parallel
+  {
+    contrib_t *buf = (contrib_t *)malloc(sizeof(contrib_t) * (C->maxcell > 0 ? C->maxcell : 1));
+#pragma omp for schedule(dynamic, 4)
+    for (int64_t q = 0; q < npix; ++q) {
+      double vmax[10];
+      const int cnt = pixel_pairs(C, pix[2 * q], pix[2 * q + 1], buf, vmax, -1);
+      double T = 1.0;
+      int n = 0;
+      for (int k = 0; k < cnt; ++k) {
+        if (!(buf[k].a_ok && buf[k].z_ok)) continue;
+        const double at = buf[k].ag < amax ? buf[k].ag : amax;
+        const double Tn = T * (1.0 - at);
+        if (Tn < Tmin) break;
+        if (n < maxc) ids[q * maxc + n] = buf[k].id;
+        n++;
+        T = Tn;
+      }
+      count[q] = n < maxc ? n : maxc;
+    }
+    free(buf);
+  }
+}
+
 /* Finite differences of one primitive.  A central difference changes only
  * primitive i, so the pairs of every other primitive at the pixels looked at
  * are evaluated and sorted once (orc_fd_begin); each orc_fd_render then
@@ -996,8 +1036,11 @@ void *orc_fd_begin(void *ctx, int64_t i, int64_t npix, const int32_t *pix) {
 
 /* out: npix x 10 as orc_render (every decision the FP64 way); flags: bit 0
  * if an ambiguous decision was met (the difference is then not a
- * derivative), bit 2 as orc_render; tol (may be NULL): as orc_render. */
-void orc_fd_render(void *ctx, void *fd, double *out, uint8_t *flags, double *tol) {
+ * derivative), bit 2 as orc_render; tol (may be NULL): as orc_render; pos
+ * (may be NULL): primitive i's place in the pixel's sorted pairs, -1 if not
+ * listed (a change between two parameter values means the blend order
+ * changed, so the difference is not a derivative either). */
+void orc_fd_render(void *ctx, void *fd, double *out, uint8_t *flags, double *tol, int32_t *pos) {
   orc_ctx *C = (orc_ctx *)ctx;
   orc_fd_t *F = (orc_fd_t *)fd;
   const prim_t *p = &C->P[F->i];
@@ -1021,15 +1064,20 @@ void orc_fd_render(void *ctx, void *fd, double *out, uint8_t *flags, double *tol
           if (fabs(v[ch]) > vmax[ch]) vmax[ch] = fabs(v[ch]);
       }
       /* merge primitive i's pair into the sorted list */
-      int placed = !listed;
+      int placed = !listed, at = -1;
       for (int k = 0; k < n0; ++k) {
         if (!placed && cmp_contrib(&c, &F->list[q][k]) < 0) {
+          at = cnt;
           buf[cnt++] = c;
           placed = 1;
         }
         buf[cnt++] = F->list[q][k];
       }
-      if (!placed) buf[cnt++] = c;
+      if (!placed) {
+        at = cnt;
+        buf[cnt++] = c;
+      }
+      if (pos) pos[q] = at;
       double t[10];
       int loose;
       const int nd = blend_run(C, buf, cnt, 0u, vmax, out + 10 * q, t, &loose);
@@ -1059,6 +1107,35 @@ void orc_pair_alpha(void *ctx, int64_t i, int64_t npix, const int32_t *pix, doub
     contrib_t c;
     ag[q] = 0.0;
     if (p->valid && eval_pair(C, p, pix[2 * q] + 0.5, pix[2 * q + 1] + 0.5, &c) && c.a_ok && c.z_ok) ag[q] = c.ag;
+  }
+}
+
+/* For npairs (primitive, pixel) pairs: the conditioning bounds (du, dv) of
+ * the primitive's splat-frame coordinates at the pixel (cond_uv), out[2 k],
+ * out[2 k + 1]; -1 where the ray misses a surfel's plane.  A gradient
+ * through Eq. 1 carries binary32 errors of about that size relative to the
+ * footprint; finite-difference checks use pairs where it is small. */
+void orc_pair_conditioning(void *ctx, int64_t npairs, const int64_t *ids, const int32_t *pix, double *out) {
+  orc_ctx *C = (orc_ctx *)ctx;
+#pragma omp parallel for schedule(static)
+  for (int64_t k = 0; k < npairs; ++k) {
+    const prim_t *p = &C->P[ids[k]];
+    const double px = pix[2 * k] + 0.5, py = pix[2 * k + 1] + 0.5;
+    double u, v;
+    if (p->type == 1) {
+      const double dx = px - p->mx, dy = py - p->my;
+      u = p->ca * dx + p->cb * dy;
+      v = p->cc * dy;
+    } else {
+      double sol[3];
+      if (!surfel_hit(C, p, px, py, sol)) {
+        out[2 * k] = out[2 * k + 1] = -1.0;
+        continue;
+      }
+      u = sol[0];
+      v = sol[1];
+    }
+    cond_uv(C, p, px, py, u, v, out + 2 * k, out + 2 * k + 1);
   }
 }
 

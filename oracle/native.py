@@ -47,10 +47,14 @@ def lib():
         L.orc_max_variants.argtypes = []
         L.orc_pair_alpha.restype = None
         L.orc_pair_alpha.argtypes = [P, C.c_int64, C.c_int64, P, P]
+        L.orc_pixel_contributors.restype = None
+        L.orc_pair_conditioning.restype = None
+        L.orc_pair_conditioning.argtypes = [P, C.c_int64, P, P, P]
+        L.orc_pixel_contributors.argtypes = [P, C.c_int64, P, C.c_int, P, P]
         L.orc_fd_begin.restype = P
         L.orc_fd_begin.argtypes = [P, C.c_int64, C.c_int64, P]
         L.orc_fd_render.restype = None
-        L.orc_fd_render.argtypes = [P, P, P, P, P]
+        L.orc_fd_render.argtypes = [P, P, P, P, P, P]
         L.orc_fd_end.restype = None
         L.orc_fd_end.argtypes = [P]
         L.orc_set_prim.restype = None
@@ -185,6 +189,25 @@ class Oracle:
         lib().orc_pair_alpha(self.ctx, int(i), len(pixels), _p(pixels), _p(out))
         return out
 
+    def pixel_contributors(self, pixels, maxc=256):
+        """For each pixel, the ids of the primitives Eq. 2 blends there (every
+        decision the FP64 way), front to back: list of int arrays."""
+        pixels = np.ascontiguousarray(pixels, np.int32)
+        ids = np.zeros((len(pixels), maxc), np.int32)
+        cnt = np.zeros(len(pixels), np.int32)
+        lib().orc_pixel_contributors(self.ctx, len(pixels), _p(pixels), int(maxc), _p(ids), _p(cnt))
+        return [ids[k, :cnt[k]].copy() for k in range(len(pixels))]
+
+    def pair_conditioning(self, ids, pixels):
+        """For (primitive, pixel) pairs: the binary32 conditioning bounds
+        (du, dv) of the primitive's splat-frame coordinates at the pixel
+        centre, (P, 2) float64 (-1 where a surfel's plane is missed)."""
+        ids = np.ascontiguousarray(ids, np.int64)
+        pixels = np.ascontiguousarray(pixels, np.int32)
+        out = np.zeros((len(ids), 2), np.float64)
+        lib().orc_pair_conditioning(self.ctx, len(ids), _p(ids), _p(pixels), _p(out))
+        return out
+
     def fd_session(self, i, pixels):
         """A finite-difference session for primitive i at `pixels`: the other
         primitives' pairs there are evaluated and sorted once; render() then
@@ -205,12 +228,15 @@ class _FDSession:
         self.h = lib().orc_fd_begin(orc.ctx, int(i), len(self.pixels), _p(self.pixels))
 
     def render(self, with_tol=False):
+        """(out (P, 10), amb (P,) bool, place (P,) int32: the primitive's place
+        in each pixel's sorted pairs, -1 if absent[, tol (P, 10)])."""
         P = len(self.pixels)
         out = np.zeros((P, 10), np.float64)
         flags = np.zeros(P, np.uint8)
         tol = np.zeros((P, 10), np.float64)
-        lib().orc_fd_render(self.orc.ctx, self.h, _p(out), _p(flags), _p(tol))
-        return (out, flags != 0, tol) if with_tol else (out, flags != 0)
+        place = np.zeros(P, np.int32)
+        lib().orc_fd_render(self.orc.ctx, self.h, _p(out), _p(flags), _p(tol), _p(place))
+        return (out, flags != 0, place, tol) if with_tol else (out, flags != 0, place)
 
     def close(self):
         if self.h:

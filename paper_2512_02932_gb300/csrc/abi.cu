@@ -336,6 +336,7 @@ int hgs_render_bwd_fdo(const hgs_scene *scene, const hgs_projected *proj, const 
   r.T_final = fwd->T_final;
   r.n_last = fwd->n_last;
   r.nc = 3;
+  r.tile_sched = fwd->tile_sched;
   r.g_rgbs[0] = g_color; r.g_rgbs[1] = g_low; r.g_rgbs[2] = g_high;
   for (int k = 0; k < 3; ++k) r.rec_grads[k] = grad_ws + k * stride;
   launch_render_bwd(r, s);

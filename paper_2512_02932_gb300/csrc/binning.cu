@@ -68,8 +68,24 @@ size_t bin_layout(void *base, int64_t n, int64_t capacity, int tiles, BinWorkspa
     ws->wide_max = 0;
     ws->wide_j = ws->wide_id = ws->masks = ws->wide_cnt = ws->wide_len = ws->small_ranges = nullptr;
     ws->mask_words = 0;
+    ws->count_tab = ws->count_tot = ws->count_bounds = nullptr;
+    ws->count_chunks = 0;
     ws->bytes = off;
     return off;
+  }
+  // counting placement: a [chunks][tiles] table and the per-tile totals.  The
+  // table's reservation does not depend on the tile count (chunks x tiles
+  // never exceeds kCountMaxSMs x kCountSmem bytes), so that a workspace
+  // sized for more tiles is large enough for fewer.
+  {
+    uint32_t *tab = (uint32_t *)take((size_t)kCountMaxSMs * kCountSmem);
+    uint32_t *tot = (uint32_t *)take(sizeof(uint32_t) * tt);
+    uint32_t *bounds = (uint32_t *)take(sizeof(uint32_t) * (kCountMaxChunks + 1));
+    const bool use = tiles > 0 && tiles <= kCountTiles;
+    ws->count_chunks = use ? kCountMaxSMs * count_warps(tiles) : 0;
+    ws->count_tab = use ? tab : nullptr;
+    ws->count_tot = use ? tot : nullptr;
+    ws->count_bounds = use ? bounds : nullptr;
   }
   const int64_t wmax = std::min<int64_t>((int64_t)nn, kWideMax);
   ws->wide_max = wmax;
@@ -493,7 +509,8 @@ __global__ void __launch_bounds__(kSortThreads)
 
 // single block: exclusive scans of the block partials; K, the path, and the
 // capacity check.  counters: 1 = K, 2 = overflow, 4 = wide path, 5 = small
-// instances, 6 = wide primitives B, 7 = instances the radix sort takes.
+// instances, 6 = wide primitives B, 7 = instances the radix sort takes,
+// 9 = counting placement (instead of emit and the radix tile passes).
 // The wide path is taken when it is allowed (B within wide_cap) and asked
 // for (wide_cfg 1), or, under wide_cfg 0, when the wide instances outnumber
 // both 8x the (32 tiles, 32 wide primitives) mask visits it costs and 5x
@@ -502,7 +519,7 @@ __global__ void __launch_bounds__(kSortThreads)
 // under 40%).
 __global__ void __launch_bounds__(1024)
     k_scan_top(uint64_t *__restrict__ blk, int nblocks, int64_t capacity, int wide_cfg, int64_t wide_cap,
-               int tiles, int64_t *counters, int64_t *d_count, int32_t *dev_err) {
+               int tiles, int count_ok, int64_t *counters, int64_t *d_count, int32_t *dev_err) {
   __shared__ uint64_t wsum[3][32];
   __shared__ int s_wide;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -538,6 +555,9 @@ __global__ void __launch_bounds__(1024)
     const bool fits = B > 0 && (int64_t)B <= wide_cap;
     const bool wide = fits && (wide_cfg == 1 || (wide_cfg == 0 && Kw > 8 * visits && Kw > 5 * Ks));
     counters[4] = wide ? 1 : 0;
+    // counting placement (small tile grids): the whole list, or on the wide
+    // path the small instances
+    counters[9] = (count_ok && !over) ? 1 : 0;
     counters[5] = (int64_t)Ks;
     counters[6] = (int64_t)B;
     counters[7] = wide ? (int64_t)Ks : (int64_t)K;
@@ -1130,6 +1150,293 @@ __global__ void __launch_bounds__(kWideWarps * 32) k_wide_write(WideArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// counting placement (tile grids up to kCountTiles)
+// ---------------------------------------------------------------------------
+// The binned primitives in depth order are cut into C contiguous chunks.
+//  k_count        per chunk, the instances per tile: a 2D difference array of
+//                 the chunk's rectangles in shared memory, summed in place
+//  k_count_scan   per tile, the exclusive prefix of those counts over the
+//                 chunks (in place) and the tile's total
+//  k_count_starts one block: list starts (exclusive prefix of the totals over
+//                 the tiles) and the ranges
+//  k_place        one warp per chunk with a counter per tile in shared memory
+//                 (list start + the chunk's offset): it takes its primitives
+//                 one at a time in depth order, a lane per tile of the
+//                 rectangle, and writes each instance at its tile's counter.
+// Within a tile, the instances are in chunk order and, inside a chunk, in
+// depth order: the order of the 64-bit key with ties by id, as the radix
+// sort gives it.  On the wide path the same kernels list only the
+// rectangles of at most kBigRect tiles, with the depth-order position as the
+// value, into the small-instance buffer the mask path merges (what the radix
+// tile passes give it on large grids); the first of them also clears the mask
+// path's per-(range, tile) counts.
+struct CountArgs {
+  const uint32_t *ids;       // depth order -> primitive id (counters[0] of them)
+  const uint16_t *rect;
+  const uint32_t *depth_key;
+  const int64_t *counters;   // 0 = binned primitives, 2 = overflow, 4 = wide path,
+                             // 7 = instances listed here, 9 = counting path
+  const uint32_t *offs;      // depth order -> first instance (exclusive prefix)
+  uint32_t *bounds;          // [C + 1] chunk starts in depth order
+  int TX, TY, tiles, C;
+  uint32_t *tab;             // [C][tiles]
+  uint32_t *tot;             // [tiles]
+  uint32_t *vals;            // output (radix-free path): primitive ids
+  uint64_t *keys;            // optional output
+  uint32_t *ranges;          // output ranges
+  uint32_t *small;           // wide path: small instances by tile (depth-order positions)
+  uint32_t *small_ranges;    // wide path: their ranges, (0xffffffff, 0) when empty
+  uint32_t *wide_cnt;        // wide path: [kWideRangesMax][tiles], cleared here
+};
+
+__device__ __forceinline__ void count_chunk(const CountArgs &a, int c, int64_t &j0, int64_t &j1) {
+  j0 = a.bounds[c];
+  j1 = a.bounds[c + 1];
+}
+
+// Chunk c starts at the first depth position j whose work prefix
+// F(j) = offs[j] + kCountPrimCost j reaches c / C of the total, so chunks
+// with large rectangles (the primitives nearest the camera) hold fewer
+// primitives and every warp of k_place gets about the same work.
+__global__ void __launch_bounds__(256) k_count_bounds(CountArgs a) {
+  if (!a.counters[9]) return;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c > a.C) return;
+  const int64_t M = a.counters[0];
+  const uint64_t total = (uint64_t)a.counters[7] + kCountPrimCost * (uint64_t)M;
+  // total < 2^38 and c <= kCountMaxChunks < 2^12: the product fits 64 bits
+  const uint64_t target = total * (uint64_t)c / (uint64_t)a.C;
+  int64_t lo = 0, hi = M;  // first j in [0, M] with F(j) >= target (F(M) = total)
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    const uint64_t f = (uint64_t)__ldg(a.offs + mid) + kCountPrimCost * (uint64_t)mid;
+    if (f >= target) hi = mid; else lo = mid + 1;
+  }
+  a.bounds[c] = (uint32_t)lo;
+}
+
+// the rectangle of depth-order position j: (x0, x1, y0, y1); false for a wide
+// rectangle on the wide path (the mask path lists it)
+__device__ __forceinline__ bool count_rect(const CountArgs &a, uint32_t id, bool wide, uint32_t &x0, uint32_t &x1,
+                                           uint32_t &y0, uint32_t &y1) {
+  const uint2 r = __ldg(reinterpret_cast<const uint2 *>(a.rect) + id);
+  x0 = r.x & 0xffffu;
+  x1 = r.x >> 16;
+  y0 = r.y & 0xffffu;
+  y1 = r.y >> 16;
+  return !wide || (x1 - x0 + 1u) * (y1 - y0 + 1u) <= kBigRect;
+}
+
+__global__ void __launch_bounds__(256) k_count(CountArgs a) {
+  extern __shared__ uint32_t diff[];  // [(TY + 1) * (TX + 1)]
+  if (!a.counters[9]) return;
+  const bool wide = a.counters[4] != 0;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int X = a.TX + 1, Y = a.TY + 1;
+  for (int k = tid; k < X * Y; k += blockDim.x) diff[k] = 0u;
+  __syncthreads();
+  int64_t j0, j1;
+  count_chunk(a, blockIdx.x, j0, j1);
+  for (int64_t j = j0 + tid; j < j1; j += blockDim.x) {
+    uint32_t x0, x1, y0, y1;
+    if (!count_rect(a, __ldg(a.ids + j), wide, x0, x1, y0, y1)) continue;
+    ++x1;
+    ++y1;
+    atomicAdd(&diff[y0 * X + x0], 1u);
+    atomicAdd(&diff[y0 * X + x1], 0xffffffffu);
+    atomicAdd(&diff[y1 * X + x0], 0xffffffffu);
+    atomicAdd(&diff[y1 * X + x1], 1u);
+  }
+  __syncthreads();
+  // prefix along each row (a warp per row), then down each column
+  for (int y = warp; y < a.TY; y += blockDim.x / 32) {
+    uint32_t carry = 0;
+    for (int x0 = 0; x0 < a.TX; x0 += 32) {
+      const int x = x0 + lane;
+      uint32_t v = x < a.TX ? diff[y * X + x] : 0u;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+      }
+      if (x < a.TX) diff[y * X + x] = v + carry;
+      carry += __shfl_sync(0xffffffffu, v, 31);
+    }
+  }
+  __syncthreads();
+  uint32_t *row = a.tab + (size_t)blockIdx.x * a.tiles;
+  for (int x = tid; x < a.TX; x += blockDim.x) {
+    uint32_t acc = 0;
+    for (int y = 0; y < a.TY; ++y) {
+      acc += diff[y * X + x];
+      row[y * a.TX + x] = acc;
+    }
+  }
+}
+
+// 32 tiles per block; warp w scans the chunks [w * S, (w + 1) * S), eight
+// loads in flight per lane
+__global__ void __launch_bounds__(256) k_count_scan(CountArgs a) {
+  __shared__ uint32_t seg[8][32];
+  if (!a.counters[9]) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int t = blockIdx.x * 32 + lane;
+  const bool in = t < a.tiles;
+  if (a.counters[4] && in)
+    for (int r = warp; r < kWideRangesMax; r += 8) a.wide_cnt[(size_t)r * a.tiles + t] = 0u;
+  const int S = (a.C + 7) / 8;
+  const int c0 = min(a.C, warp * S), c1 = min(a.C, c0 + S);
+  const uint32_t *col = a.tab + t;
+  uint32_t sum = 0;
+  if (in) {
+    int c = c0;
+    for (; c + 8 <= c1; c += 8) {
+      uint32_t v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = col[(size_t)(c + k) * a.tiles];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) sum += v[k];
+    }
+    for (; c < c1; ++c) sum += col[(size_t)c * a.tiles];
+  }
+  seg[warp][lane] = sum;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t run = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+      const uint32_t v = seg[w][lane];
+      seg[w][lane] = run;
+      run += v;
+    }
+    if (in) a.tot[t] = run;
+  }
+  __syncthreads();
+  if (!in) return;
+  uint32_t run = seg[warp][lane];
+  uint32_t *wcol = a.tab + t;
+  int c = c0;
+  for (; c + 8 <= c1; c += 8) {
+    uint32_t v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = wcol[(size_t)(c + k) * a.tiles];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      wcol[(size_t)(c + k) * a.tiles] = run;
+      run += v[k];
+    }
+  }
+  for (; c < c1; ++c) {
+    const uint32_t v = wcol[(size_t)c * a.tiles];
+    wcol[(size_t)c * a.tiles] = run;
+    run += v;
+  }
+}
+
+// One block: list starts and ranges ([0, 0) for an empty tile; on the wide
+// path the small ranges, (0xffffffff, 0) when empty).  On overflow it only
+// clears the ranges.
+__global__ void __launch_bounds__(1024) k_count_starts(CountArgs a) {
+  __shared__ uint32_t wsum[32];
+  __shared__ uint32_t carry;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (a.counters[2]) {
+    for (int t = tid; t < a.tiles; t += blockDim.x) reinterpret_cast<uint2 *>(a.ranges)[t] = make_uint2(0u, 0u);
+    return;
+  }
+  if (!a.counters[9]) return;
+  const bool wide = a.counters[4] != 0;
+  uint2 *out = reinterpret_cast<uint2 *>(wide ? a.small_ranges : a.ranges);
+  const uint2 empty = wide ? make_uint2(0xffffffffu, 0u) : make_uint2(0u, 0u);
+  if (tid == 0) carry = 0;
+  __syncthreads();
+  for (int t0 = 0; t0 < a.tiles; t0 += 1024) {
+    const int t = t0 + tid;
+    const uint32_t v = t < a.tiles ? a.tot[t] : 0u;
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += u;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    uint32_t wb = 0, all = 0;
+    for (int w = 0; w < 32; ++w) {
+      if (w < warp) wb += wsum[w];
+      all += wsum[w];
+    }
+    const uint32_t start = carry + wb + incl - v;
+    if (t < a.tiles) {
+      a.tot[t] = start;
+      out[t] = v ? make_uint2(start, start + v) : empty;
+    }
+    __syncthreads();
+    if (tid == 0) carry += all;
+    __syncthreads();
+  }
+}
+
+// k_place: each warp walks its chunk 32 primitives at a time: the lanes load
+// the batch's ids, rectangles and depth keys together (one round of global
+// latency per 32 primitives), then the warp places the batch's primitives one
+// after another in depth order, a lane per tile of the rectangle.  Tiles of
+// one rectangle are distinct, so each lane's counter update is private; the
+// warp barrier between primitives orders updates of a tile two of them share.
+__global__ void __launch_bounds__(512) k_place(CountArgs a) {
+  extern __shared__ uint32_t smem_all[];  // [warps][tiles]
+  if (!a.counters[9]) return;
+  const bool wide = a.counters[4] != 0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (c >= a.C) return;
+  uint32_t *cnt = smem_all + (size_t)warp * a.tiles;
+  const uint32_t *off = a.tab + (size_t)c * a.tiles;
+  for (int t = lane; t < a.tiles; t += 32) cnt[t] = __ldg(a.tot + t) + __ldg(off + t);
+  __syncwarp();
+  uint32_t *dst = wide ? a.small : a.vals;
+  uint64_t *keys = wide ? nullptr : a.keys;
+  const uint32_t TX = (uint32_t)a.TX;
+  int64_t j0, j1;
+  count_chunk(a, c, j0, j1);
+  for (int64_t jb = j0; jb < j1; jb += 32) {
+    const int64_t j = jb + lane;
+    uint32_t v = 0, x0 = 0, x1 = 0, y0 = 0, y1 = 0, w = 1, n = 0, dk = 0;
+    if (j < j1) {
+      const uint32_t id = __ldg(a.ids + j);
+      if (count_rect(a, id, wide, x0, x1, y0, y1)) {
+        w = x1 - x0 + 1u;
+        n = w * (y1 - y0 + 1u);
+      }
+      v = wide ? (uint32_t)j : id;
+      if (keys && n) dk = __ldg(a.depth_key + id);
+    }
+    const float iw = 1.0f / (float)w;
+    uint32_t todo = __ballot_sync(0xffffffffu, n != 0u);
+    while (todo) {
+      const int o = __ffs(todo) - 1;
+      todo &= todo - 1u;
+      const uint32_t on = __shfl_sync(0xffffffffu, n, o), ow = __shfl_sync(0xffffffffu, w, o);
+      const uint32_t ox0 = __shfl_sync(0xffffffffu, x0, o), oy0 = __shfl_sync(0xffffffffu, y0, o);
+      const uint32_t ov = __shfl_sync(0xffffffffu, v, o), odk = __shfl_sync(0xffffffffu, dk, o);
+      const float oiw = __shfl_sync(0xffffffffu, iw, o);
+      for (uint32_t l = lane; l < on; l += 32) {
+        // l = dy * w + dx; the binary32 quotient is off by at most one
+        uint32_t dy = (uint32_t)((float)l * oiw);
+        uint32_t dx = l - dy * ow;
+        if ((int)dx < 0) { dy -= 1; dx += ow; } else if (dx >= ow) { dy += 1; dx -= ow; }
+        const uint32_t t = (oy0 + dy) * TX + ox0 + dx;
+        const uint32_t pos = cnt[t];
+        cnt[t] = pos + 1u;
+        dst[pos] = ov;
+        if (keys) keys[pos] = ((uint64_t)t << 32) | odk;
+      }
+      __syncwarp();
+    }
+  }
+}
+
 // Chunks (blocks) of the radix passes: as many scatter blocks as fit on the
 // device at once, so every chunk is in flight from the start.
 static int pass_grid() {
@@ -1210,60 +1517,104 @@ int launch_bin_sort(const BinArgs &a, const BinWorkspace &ws, cudaStream_t s) {
   const int TY = a.tiles / a.TX;
   const int64_t wide_cap =
       std::min<int64_t>(ws.wide_max, (int64_t)(ws.mask_words / (size_t)(a.TX + TY)) * 32);
-  k_scan_top<<<1, 1024, 0, s>>>(ws.blk, kSortBlocks, a.capacity, a.wide_cfg, wide_cap, a.tiles, ctr, a.d_count,
-                                a.dev_err);
+  const bool counting = ws.count_tab != nullptr && a.tiles <= kCountTiles;
+  k_scan_top<<<1, 1024, 0, s>>>(ws.blk, kSortBlocks, a.capacity, a.wide_cfg, wide_cap, a.tiles, counting ? 1 : 0,
+                                ctr, a.d_count, a.dev_err);
   // dk[0] and dv[0] (contiguous) are free once the depth sort is done: dk[0]
   // holds the deferred queue, or, on the wide path, dk[0]..dv[0] the kpos pairs
   k_scan_final<<<kSortBlocks, kSortThreads, 0, s>>>(ids, a.touched, ctr, ws.blk, ws.offs, ws.wide_j, ws.dk[0]);
-  // 3) emit, then the tile digits, split evenly over the passes (13 bits ->
-  //    7 + 6): fewer buckets per pass give longer runs in the write-out
   const int passes = (a.tile_bits + 7) / 8;
-  const int per_pass = (a.tile_bits + passes - 1) / passes;
-  uint32_t *vbuf[2];
-  vbuf[0] = (passes % 2 == 0) ? a.vals : ws.tv;
-  vbuf[1] = (passes % 2 == 0) ? ws.tv : a.vals;
-  k_emit<<<kSortBlocks, 256, 0, s>>>(ids, ws.offs, a.rect, ctr, a.TX, ws.tk[0], vbuf[0], ws.dk[0]);
-  k_emit_big<<<kSortBlocks, 256, 0, s>>>(ids, ws.offs, a.rect, ctr, a.TX, ws.dk[0], ws.tk[0], vbuf[0]);
-  int tshift[4], tbits[4];
-  for (int p = 0; p < passes; ++p) {
-    tshift[p] = per_pass * p;
-    tbits[p] = std::min(per_pass, a.tile_bits - per_pass * p);
-  }
-  for (int p = 0; p < passes; ++p) {
-    const bool last = p + 1 == passes;
-    PassArgs w{};
-    w.keys_in = ws.tk[p & 1];
-    w.vals_in = vbuf[p & 1];
-    w.d_n = &ctr[7];
-    w.d_abort = &ctr[2];
-    w.shift = tshift[p];
-    w.bits = tbits[p];
-    w.ghist = ws.hist + 256 * (4 + p);
-    w.chist = ws.chist;
-    w.ranges_init = p == 0 ? a.ranges : nullptr;
-    w.tiles = a.tiles;
-    w.keys_out = (!last || a.keys) ? ws.tk[(p + 1) & 1] : nullptr;
-    w.vals_out = vbuf[(p + 1) & 1];
-    w.ranges = last ? a.ranges : nullptr;
-    w.wide = &ctr[4];
-    if (p == 0) {
-      w.wide_ranges_init = ws.small_ranges;
-      w.wide_zero = ws.wide_cnt;
-      w.wide_zero_n = (int64_t)kWideRangesMax * a.tiles;
+  uint32_t *small = ws.tk[passes & 1], *kappa = ws.tk[(passes + 1) & 1];
+  if (counting) {
+    // 3) small tile grids: counting placement (each kernel returns at once
+    //    unless counters[9], i.e. on overflow)
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int W = count_warps(a.tiles);
+    small = ws.tk[0];
+    kappa = ws.tk[1];
+    CountArgs ca{};
+    ca.ids = ids;
+    ca.rect = a.rect;
+    ca.depth_key = a.depth_key;
+    ca.counters = ctr;
+    ca.TX = a.TX;
+    ca.TY = TY;
+    ca.tiles = a.tiles;
+    ca.C = std::min(ws.count_chunks, std::max(1, std::min(sms, kCountMaxSMs)) * W);
+    ca.tab = ws.count_tab;
+    ca.tot = ws.count_tot;
+    ca.offs = ws.offs;
+    ca.bounds = ws.count_bounds;
+    ca.vals = a.vals;
+    ca.keys = a.keys;
+    ca.ranges = a.ranges;
+    ca.small = small;
+    ca.small_ranges = ws.small_ranges;
+    ca.wide_cnt = ws.wide_cnt;
+    const size_t dsm = sizeof(uint32_t) * (size_t)(a.TX + 1) * (TY + 1);
+    const size_t psm = sizeof(uint32_t) * (size_t)W * a.tiles;
+    static bool once = (cudaFuncSetAttribute(k_count, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024),
+                        cudaFuncSetAttribute(k_place, cudaFuncAttributeMaxDynamicSharedMemorySize, kCountSmem),
+                        true);
+    (void)once;
+    k_count_bounds<<<(ca.C + 256) / 256, 256, 0, s>>>(ca);
+    k_count<<<ca.C, 256, dsm, s>>>(ca);
+    k_count_scan<<<(a.tiles + 31) / 32, 256, 0, s>>>(ca);
+    k_count_starts<<<1, 1024, 0, s>>>(ca);
+    k_place<<<(ca.C + W - 1) / W, 32 * W, psm, s>>>(ca);
+  } else {
+    // 3) emit, then the tile digits, split evenly over the passes (13 bits ->
+    //    7 + 6): fewer buckets per pass give longer runs in the write-out
+    const int per_pass = (a.tile_bits + passes - 1) / passes;
+    uint32_t *vbuf[2];
+    vbuf[0] = (passes % 2 == 0) ? a.vals : ws.tv;
+    vbuf[1] = (passes % 2 == 0) ? ws.tv : a.vals;
+    k_emit<<<kSortBlocks, 256, 0, s>>>(ids, ws.offs, a.rect, ctr, a.TX, ws.tk[0], vbuf[0], ws.dk[0]);
+    k_emit_big<<<kSortBlocks, 256, 0, s>>>(ids, ws.offs, a.rect, ctr, a.TX, ws.dk[0], ws.tk[0], vbuf[0]);
+    int tshift[4], tbits[4];
+    for (int p = 0; p < passes; ++p) {
+      tshift[p] = per_pass * p;
+      tbits[p] = std::min(per_pass, a.tile_bits - per_pass * p);
     }
-    if (last) {
-      // wide path: the sorted small instances go to the key buffer this pass
-      // would otherwise fill, their ranges to small_ranges
-      w.vals_out_wide = ws.tk[(p + 1) & 1];
-      w.ranges_wide = ws.small_ranges;
+    for (int p = 0; p < passes; ++p) {
+      const bool last = p + 1 == passes;
+      PassArgs w{};
+      w.keys_in = ws.tk[p & 1];
+      w.vals_in = vbuf[p & 1];
+      w.d_n = &ctr[7];
+      w.d_abort = &ctr[2];
+      w.shift = tshift[p];
+      w.bits = tbits[p];
+      w.ghist = ws.hist + 256 * (4 + p);
+      w.chist = ws.chist;
+      w.ranges_init = p == 0 ? a.ranges : nullptr;
+      w.tiles = a.tiles;
+      w.keys_out = (!last || a.keys) ? ws.tk[(p + 1) & 1] : nullptr;
+      w.vals_out = vbuf[(p + 1) & 1];
+      w.ranges = last ? a.ranges : nullptr;
+      w.wide = &ctr[4];
+      if (p == 0) {
+        w.wide_ranges_init = ws.small_ranges;
+        w.wide_zero = ws.wide_cnt;
+        w.wide_zero_n = (int64_t)kWideRangesMax * a.tiles;
+      }
+      if (last) {
+        // wide path: the sorted small instances go to the key buffer this pass
+        // would otherwise fill, their ranges to small_ranges
+        w.vals_out_wide = ws.tk[(p + 1) & 1];
+        w.ranges_wide = ws.small_ranges;
+      }
+      radix_pass(w, G, s);
     }
-    radix_pass(w, G, s);
+    k_ranges_fix<<<(a.tiles + 255) / 256, 256, 0, s>>>(a.ranges, a.tiles);
+    if (a.keys) k_keys64<<<kSortBlocks, 256, 0, s>>>(ws.tk[passes & 1], a.vals, a.depth_key, ctr, a.keys);
   }
-  k_ranges_fix<<<(a.tiles + 255) / 256, 256, 0, s>>>(a.ranges, a.tiles);
-  if (a.keys) k_keys64<<<kSortBlocks, 256, 0, s>>>(ws.tk[passes & 1], a.vals, a.depth_key, ctr, a.keys);
-  // 4) wide path (every kernel returns at once on the radix path).  The
-  //    sorted small instances are in tk[passes & 1]; tk[(passes + 1) & 1]
-  //    is free and takes their kappa.
+  // 4) wide path (every kernel returns at once when the frame does not take
+  //    it).  The small instances, sorted by tile, are in `small` (from the
+  //    counting placement or the radix tile passes); `kappa` is free and
+  //    takes their kappa.
   {
     int gb = 1, gw = 1, sms = 1;
     wide_grids(gb, gw, sms);
@@ -1283,8 +1634,8 @@ int launch_bin_sort(const BinArgs &a, const BinWorkspace &ws, cudaStream_t s) {
     wa.masks = ws.masks;
     wa.cnt = ws.wide_cnt;
     wa.len = ws.wide_len;
-    wa.small = ws.tk[passes & 1];
-    wa.kappa = ws.tk[(passes + 1) & 1];
+    wa.small = small;
+    wa.kappa = kappa;
     wa.small_ranges = ws.small_ranges;
     wa.vals = a.vals;
     wa.keys = a.keys;

@@ -40,8 +40,13 @@ constexpr int kRecF4 = 5;
 // Per-primitive gradient of the render record, accumulated by render_bwd
 // (16 floats):
 //   [0] d alpha  [1..3] d rgb  [4] d x_c  [5] d y_c  [6] d z_c
-//   3D: [7] d a  [8] d b  [9] d c          (b as the scalar in Eq. 1's form)
-//   2D: [7] dQ00 [8] dQ01 [9] dQ10 [10] dQ11 [11] dQ20 [12] dQ21
+//   3D: [7] d h00  [8] d h01  [9] d h11: the footprint shape in its own
+//       coordinates (u, v) = W (dx, dy), d = h00 u^2 + 2 h01 u v + h11 v^2
+//       at H = I.  dL/d(conic) = W^T dL/dH W, but a needle's conic is
+//       ill-conditioned and this form keeps the sums and the chain rule
+//       free of cancellation.
+//   2D: the homography's gradient in the splat's own coordinates (u, v):
+//       [7..10] sum (du, dv) (u, v)^T row-major, [11..12] sum p2 dL/dp2 (u, v)
 //   [13..15] d normal
 constexpr int kGradW = 16;
 

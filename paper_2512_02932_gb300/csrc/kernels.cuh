@@ -69,6 +69,11 @@ struct BinWorkspace {
   uint32_t *wide_cnt;    // [16][tiles] per (word range, tile) counts
   uint32_t *wide_len;    // [tiles] list lengths
   uint32_t *small_ranges;  // [tiles][2]
+  // counting placement (tile grids up to kCountTiles; null otherwise)
+  uint32_t *count_tab;   // [count_chunks][tiles] per-(chunk, tile) counts -> offsets
+  uint32_t *count_tot;   // [tiles] per-tile totals -> list starts
+  uint32_t *count_bounds;  // [kCountMaxChunks + 1] first depth position of each chunk
+  int count_chunks;      // chunks the table holds
   size_t bytes;
 };
 
@@ -77,6 +82,20 @@ struct BinWorkspace {
 // buffer size computed from a capacity can wrap.
 constexpr int64_t kMaxCapacity = HGS_MAX_CAPACITY;
 constexpr int kSortBlocks = 1024;  // fixed grid of every sort/scan pass
+// Tile grids up to kCountTiles tiles place the instances by counting (one
+// warp per chunk of the depth order with a counter per tile in shared
+// memory) instead of emitting them and radix-sorting the tile digits.
+constexpr int kCountTiles = 8192;
+constexpr int kCountSmem = 200 * 1024;    // shared memory of one placement block
+constexpr int kCountMaxSMs = 160;         // SMs the chunk table is sized for
+constexpr int kCountMaxChunks = kCountMaxSMs * 16;
+// a chunk's work, in instances: its instances + kCountPrimCost per primitive
+constexpr uint64_t kCountPrimCost = 32;
+// warps of a placement block: each holds a counter per tile
+__host__ __device__ inline int count_warps(int tiles) {
+  const int w = kCountSmem / (4 * (tiles > 0 ? tiles : 1));
+  return w < 1 ? 1 : (w > 16 ? 16 : w);
+}
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 8;      // per thread per tile (tile = 2048 keys)
 

@@ -456,11 +456,37 @@ __device__ __forceinline__ float pack_box(float lo, float hi) {
 // One primitive: scene row i of `a`, written to row i of a's outputs; the tile
 // rectangle's rows are shifted by row_off (the batched render stacks the
 // requests' tile grids vertically).
+// Ask L2 for a primitive's SH row ahead of its use, so that the row's DRAM
+// latency overlaps the contract arithmetic: only for primitives that pass a
+// cheap guess at the contract's culls (in front of the near plane, opacity
+// above alpha_min, centre within a margin of the image).  A hint only.
+template <int DEG>
+__device__ __forceinline__ void prefetch_sh(const PrepArgs &a, int64_t i, const float (&mu)[3], float logit) {
+  if constexpr (DEG > 0) {
+    constexpr int NB = (DEG + 1) * (DEG + 1);
+    const CamK &c = a.cam;
+    const float X = fmaf(c.R[0], mu[0], fmaf(c.R[1], mu[1], fmaf(c.R[2], mu[2], c.t[0])));
+    const float Y = fmaf(c.R[3], mu[0], fmaf(c.R[4], mu[1], fmaf(c.R[5], mu[2], c.t[1])));
+    const float Z = fmaf(c.R[6], mu[0], fmaf(c.R[7], mu[1], fmaf(c.R[8], mu[2], c.t[2])));
+    const bool front = Z > a.cfg.near_z && logit > -5.6f;
+    const float W = (float)c.W, H = (float)c.H;
+    const bool near_view = fabsf(fmaf(c.fx, X, (c.cx - 0.5f * W) * Z)) < W * Z &&
+                           fabsf(fmaf(c.fy, Y, (c.cy - 0.5f * H) * Z)) < H * Z;
+    if (front && near_view) {
+      const char *p = reinterpret_cast<const char *>(a.sh + (int64_t)i * NB * 3);
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+      if (NB * 12 > 96) asm volatile("prefetch.global.L2 [%0];" ::"l"(p + 96));
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(p + NB * 12 - 4));
+    }
+  }
+}
+
 template <int DEG>
 __device__ __forceinline__ void preprocess_one(const PrepArgs &a, int64_t i, int row_off) {
   float mu[3], ls[3], q[4], logit;
   int type;
   load_params(a, i, mu, ls, q, logit, type);
+  prefetch_sh<DEG>(a, i, mu, logit);
   Contract o;
   const bool binned = run_contract(mu, ls, q, logit, type, a.cam, a.cfg, o);
   a.depth_key[i] = o.dbits;
@@ -641,105 +667,109 @@ __device__ __forceinline__ PGrad chain_grad(const PrepArgs &a, const BwdCtx<DEG>
   const float dxc = G[4], dyc = G[5];
   if (type == 1) {
     dalpha = G[0];
-    // conic (a, b, c) = inverse of (s00, s01; s01, s11)
+    // Footprint factor T = J A S, column t_k = s_k J a_k (a_k the camera-space
+    // axes), Sigma' = T T^T + dilation I, conic C = Sigma'^-1 = W^T W.  The
+    // record gradient (slots 7-9) is Hg = dL/dH for the shape H in footprint
+    // coordinates (u, v) = W (dx, dy); with w_k = W t_k (so C t_k = W^T w_k)
+    // and Q_jk = w_j^T Hg w_k, the derivatives of L through T are
+    //   dL/dlog s_k = -2 Q_kk
+    //   dL/da_k     = -2 sum_j (s_k / s_j) Q_jk a_j      (a_j orthonormal)
+    //   dL/dX = (2/Z) sum_j R_j a_jx / s_j,  dL/dY likewise with a_jy,
+    //   dL/dZ = (2/Z) (tr Q + sum_j R_j a_jz / s_j),  R_j = sum_k Q_jk s_k a_kz,
+    // using J e_x = (fx/Z) e_x, J e_y = (fy/Z) e_y, J e_z = -Z (dJ/dZ part)
+    // and J a_j = t_j / s_j.  No term multiplies the conic's large
+    // eigenvalue into a needle's long axis, so binary32 keeps these
+    // accurate where dL/dC contracted with T would cancel.
     const Cov2 cv = projected_cov(o, c, a.cfg.dilation);
-    const float id = 1.0f / cv.det;
-    const float ca = cv.s11 * id, cb = -cv.s01 * id, cc = cv.s00 * id;
-    const float ga = G[7], gb = G[8], gc = G[9];
-    const float ds00 = -(ga * ca * ca + gb * ca * cb + gc * cb * cb);
-    const float ds11 = -(ga * cb * cb + gb * cb * cc + gc * cc * cc);
-    const float ds01 = -(2.f * ga * ca * cb + gb * (ca * cc + cb * cb) + 2.f * gc * cb * cc);
-    // Sigma' = J V J^T,  J0 = (j00, 0, j02), J1 = (0, j11, j12)
+    const float w00 = sqrtf(cv.s11 / cv.det);
+    const float w01 = -cv.s01 * rsqrtf(cv.s11 * cv.det);
+    const float w11 = rsqrtf(cv.s11);
+    const float h00 = G[7], h01 = 0.5f * G[8], h11 = G[9];
     const float j00 = fx * iz, j02 = -fx * X * iz * iz, j11 = fy * iz, j12 = -fy * Y * iz * iz;
-    const float cs0 = o.s[0] * o.s[0], cs1 = o.s[1] * o.s[1], cs2 = o.s[2] * o.s[2];
-    float V[3][3];
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-      for (int s = 0; s < 3; ++s)
-        V[r][s] = cs0 * o.a[0][r] * o.a[0][s] + cs1 * o.a[1][r] * o.a[1][s] + cs2 * o.a[2][r] * o.a[2][s];
-    const float J0[3] = {j00, 0.f, j02}, J1[3] = {0.f, j11, j12};
-    float VJ0[3], VJ1[3];
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      VJ0[r] = V[r][0] * J0[0] + V[r][1] * J0[1] + V[r][2] * J0[2];
-      VJ1[r] = V[r][0] * J1[0] + V[r][1] * J1[1] + V[r][2] * J1[2];
-    }
-    // dL/dV (full matrix): ds00 J0 J0^T + ds01 J0 J1^T + ds11 J1 J1^T
-    float dV[3][3];
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-      for (int s = 0; s < 3; ++s)
-        dV[r][s] = ds00 * J0[r] * J0[s] + ds01 * J0[r] * J1[s] + ds11 * J1[r] * J1[s];
-    // dJ0 = 2 ds00 V J0 + ds01 V J1;  dJ1 = ds01 V J0 + 2 ds11 V J1
-    const float dj00 = 2.f * ds00 * VJ0[0] + ds01 * VJ1[0];
-    const float dj02 = 2.f * ds00 * VJ0[2] + ds01 * VJ1[2];
-    const float dj11 = ds01 * VJ0[1] + 2.f * ds11 * VJ1[1];
-    const float dj12 = ds01 * VJ0[2] + 2.f * ds11 * VJ1[2];
-    const float iz2 = iz * iz, iz3 = iz2 * iz;
-    dX += dj02 * (-fx * iz2);
-    dY += dj12 * (-fy * iz2);
-    dZ += dj00 * (-fx * iz2) + dj02 * (2.f * fx * X * iz3) + dj11 * (-fy * iz2) + dj12 * (2.f * fy * Y * iz3);
-    // V = sum_k s_k^2 a_k a_k^T
-    const float csk[3] = {cs0, cs1, cs2};
+    float wu[3], wv[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      float dcs = 0.f;
-#pragma unroll
-      for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int s = 0; s < 3; ++s) dcs += dV[r][s] * o.a[k][r] * o.a[k][s];
-      dls[k] += 2.f * csk[k] * dcs;  // d/dlog s_k of s_k^2 = 2 s_k^2
-#pragma unroll
-      for (int m = 0; m < 3; ++m) {
-        float acc = 0.f;
-#pragma unroll
-        for (int r = 0; r < 3; ++r) acc += (dV[m][r] + dV[r][m]) * o.a[k][r];
-        dA[k][m] += csk[k] * acc;
-      }
+      const float tx = o.s[k] * fmaf(j00, o.a[k][0], j02 * o.a[k][2]);
+      const float ty = o.s[k] * fmaf(j11, o.a[k][1], j12 * o.a[k][2]);
+      wu[k] = fmaf(w00, tx, w01 * ty);
+      wv[k] = w11 * ty;
     }
+    float Q[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float pu = fmaf(h00, wu[k], h01 * wv[k]), pv = fmaf(h01, wu[k], h11 * wv[k]);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) Q[j][k] = fmaf(wu[j], pu, wv[j] * pv);
+    }
+    float is[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) is[k] = 1.0f / o.s[k];
+    float rx = 0.f, ry = 0.f, rz = 0.f, tr = 0.f;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const float Rj = Q[j][0] * o.s[0] * o.a[0][2] + Q[j][1] * o.s[1] * o.a[1][2] + Q[j][2] * o.s[2] * o.a[2][2];
+      rx = fmaf(Rj * is[j], o.a[j][0], rx);
+      ry = fmaf(Rj * is[j], o.a[j][1], ry);
+      rz = fmaf(Rj * is[j], o.a[j][2], rz);
+      tr += Q[j][j];
+      dls[j] += -2.0f * Q[j][j];
+    }
+    const float z2 = 2.0f * iz;
+    dX += z2 * rx;
+    dY += z2 * ry;
+    dZ += z2 * (tr + rz);
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const float q = -2.0f * o.s[k] * is[j] * Q[j][k];
+#pragma unroll
+        for (int m = 0; m < 3; ++m) dA[k][m] = fmaf(q, o.a[j][m], dA[k][m]);
+      }
   } else {
-    // re-centred homography block and its inverse
+    // Re-centred homography: c_k = P m_k (m_k = s_k a_k, P = [[1, 0, -x/z],
+    // [0, 1, -y/z]]), E = [c_0 c_1], Q = Z E^-1 F^-1 and h = -m_z^T E^-1 F^-1
+    // (F = diag(fx, fy)); a pixel has p = (Q xi, 1 + h xi), (u, v) = p / p_2.
+    // The record gradient (slots 7-12) is A' = sum (du, dv) (u, v)^T and
+    // b' = sum p_2 dL/dp_2 (u, v): with eta = E^-1 xi = (u, v) p_2 / Z,
+    // dL/dE = -E^-T M for M = A' - m_z b'^T / Z, dL/dZ gains tr(A') / Z and
+    // dL/dm_kz gains -b'_k / Z.  In the basis (a_0, a_1, n) of the splat,
+    // dL/dm_k . a_j = -M_jk / s_j (j < 2) and dL/dm_k . n = -M_.k . E^-1 P n,
+    // and dL/dlog s_k = -M_kk: E^-T never meets the thin axis's column, so a
+    // needle-thin surfel's gradients keep binary32 accuracy.
     const float m0z = o.s[0] * o.a[0][2], m1z = o.s[1] * o.a[1][2];
     const float detE = det2(o.e0, o.e1, o.f0, o.f1);
     const float ie = 1.0f / detE;
     const float E00 = o.f1 * ie, E01 = -o.e1 * ie, E10 = -o.f0 * ie, E11 = o.e0 * ie;
-    const float ifx = 1.0f / fx, ify = 1.0f / fy;
     const bool ok = isfinite(ie) && isfinite(E00) && isfinite(E01) && isfinite(E10) && isfinite(E11);
-    float dm0[3] = {0.f, 0.f, 0.f}, dm1[3] = {0.f, 0.f, 0.f};
     float dxz = dxc * fx, dyz = dyc * fy;
     if (ok) {
-      const float Q00 = Z * E00 * ifx, Q01 = Z * E01 * ify, Q10 = Z * E10 * ifx, Q11 = Z * E11 * ify;
-      const float gQ00 = G[7], gQ01 = G[8], gQ10 = G[9], gQ11 = G[10], gQ20 = G[11], gQ21 = G[12];
-      float dE00 = gQ00 * Z * ifx, dE01 = gQ01 * Z * ify, dE10 = gQ10 * Z * ifx, dE11 = gQ11 * Z * ify;
-      dZ += (gQ00 * Q00 + gQ01 * Q01 + gQ10 * Q10 + gQ11 * Q11) * iz;
-      const float dh0 = -gQ20 * ifx, dh1 = -gQ21 * ify;
-      dm0[2] += dh0 * E00 + dh1 * E01;
-      dm1[2] += dh0 * E10 + dh1 * E11;
-      dE00 += dh0 * m0z; dE10 += dh0 * m1z; dE01 += dh1 * m0z; dE11 += dh1 * m1z;
-      // dE = -Einv^T dEinv Einv^T
-      const float de0 = -(E00 * (dE00 * E00 + dE01 * E01) + E10 * (dE10 * E00 + dE11 * E01));
-      const float de1 = -(E00 * (dE00 * E10 + dE01 * E11) + E10 * (dE10 * E10 + dE11 * E11));
-      const float df0 = -(E01 * (dE00 * E00 + dE01 * E01) + E11 * (dE10 * E00 + dE11 * E01));
-      const float df1 = -(E01 * (dE00 * E10 + dE01 * E11) + E11 * (dE10 * E10 + dE11 * E11));
-      // e0 = m0x - xz m0z, e1 = m1x - xz m1z, f0 = m0y - yz m0z, f1 = m1y - yz m1z
-      dm0[0] += de0; dm0[2] += -de0 * o.xz; dxz += -de0 * m0z;
-      dm1[0] += de1; dm1[2] += -de1 * o.xz; dxz += -de1 * m1z;
-      dm0[1] += df0; dm0[2] += -df0 * o.yz; dyz += -df0 * m0z;
-      dm1[1] += df1; dm1[2] += -df1 * o.yz; dyz += -df1 * m1z;
+      const float bz0 = G[11] * iz, bz1 = G[12] * iz;
+      dZ += (G[7] + G[10]) * iz;
+      float M[2][2];
+      M[0][0] = G[7] - m0z * bz0;
+      M[0][1] = G[8] - m0z * bz1;
+      M[1][0] = G[9] - m1z * bz0;
+      M[1][1] = G[10] - m1z * bz1;
+      const float pnx = o.a[2][0] - o.xz * o.a[2][2], pny = o.a[2][1] - o.yz * o.a[2][2];
+      const float w0 = E00 * pnx + E01 * pny, w1 = E10 * pnx + E11 * pny;
+      const float is0 = 1.0f / o.s[0], is1 = 1.0f / o.s[1];
+      const float mz[2] = {m0z, m1z}, bz[2] = {bz0, bz1};
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const float c0 = -M[0][k] * is0, c1 = -M[1][k] * is1, c2 = -(M[0][k] * w0 + M[1][k] * w1);
+#pragma unroll
+        for (int m = 0; m < 3; ++m) dA[k][m] += o.s[k] * (c0 * o.a[0][m] + c1 * o.a[1][m] + c2 * o.a[2][m]);
+        // the h row: dL/dm_kz
+        dA[k][2] += -o.s[k] * bz[k];
+        dls[k] += -M[k][k] - o.s[k] * bz[k] * o.a[k][2];
+        dxz += mz[k] * (E00 * M[0][k] + E10 * M[1][k]);
+        dyz += mz[k] * (E01 * M[0][k] + E11 * M[1][k]);
+      }
     }
     dX += dxz * iz;
     dY += dyz * iz;
     dZ += -(dxz * X + dyz * Y) * iz * iz;
-    // m0 = s_x a0, m1 = s_y a1
-    dls[0] += o.s[0] * (dm0[0] * o.a[0][0] + dm0[1] * o.a[0][1] + dm0[2] * o.a[0][2]);
-    dls[1] += o.s[1] * (dm1[0] * o.a[1][0] + dm1[1] * o.a[1][1] + dm1[2] * o.a[1][2]);
-#pragma unroll
-    for (int m = 0; m < 3; ++m) {
-      dA[0][m] += o.s[0] * dm0[m];
-      dA[1][m] += o.s[1] * dm1[m];
-    }
     // scale modulation (Eqs. 6-7)
     float gate, fac;
     const float am = modulate(o.alpha, o.s[2], a.cfg, &gate, &fac);

@@ -13,13 +13,14 @@
 // a scheduling scratch the grid is persistent: warps take (tile, quadrant)
 // items, tiles with the longest lists first.
 //
-// Backward (rgb cotangent, the image-loss case): one warp per tile walks the
-// list once from the latest contributor of any of its pixels back to the
-// start, evaluates each record against the quadrants it can reach, and sums a
-// record's gradient over all 256 pixels before one warp reduction and one set
-// of atomics per (record, tile).  Tiles are handed out longest walk first.
-// The general backward (depth, normal or alpha cotangents) and the three-set
-// backward of frequency-decoupled optimisation keep one warp per quadrant.
+// Backward (rgb cotangents, the image-loss case, one set or the three sets of
+// frequency-decoupled optimisation): one warp per tile walks the list once
+// from the latest contributor of any of its pixels back to the start,
+// evaluates each record against the quadrants it can reach, and sums a
+// record's gradient over all 256 pixels before one warp reduction and one
+// set of atomics per (record, tile).  Tiles are handed out longest walk
+// first.  The general backward (depth, normal or alpha cotangents) keeps one
+// warp per quadrant.
 //
 // The per-pair evaluation is written with explicitly rounded operations, and
 // the scalar and packed forms run the same operations in the same order, so
@@ -320,26 +321,73 @@ __device__ __forceinline__ void chunk_masks(const float4 *buf, int cnt, int lane
 // Forward with packed pixel pairs: a warp owns QW quadrants of a tile (the
 // CTA has 4 / QW warps), walks the tile's list once for all of them, and
 // skips a quadrant once all its pixels have terminated.
-struct Fwd2 {
-  float2 T, C0, C1, C2, D, N0, N1, N2;
-  uint32_t last0, last1, nc0, nc1;
-  bool done0, done1;
+// The forward's evaluation: eval_pair2's operations (so the same decisions),
+// with the contribution decision as a 0/1 float m, so that the blend can
+// mask by multiplication (packed) instead of selecting (one lane at a time).
+// Every value is finite for a pixel that does not contribute: a surfel's
+// reciprocal is 0 where the ray misses the plane's front, and where it hits,
+// p2 = Q20 dx + Q21 dy + 1 is an exact product plus one binary32 rounded
+// once, so a nonzero p2 is far above the range where 1/p2 overflows.
+struct EvalF2 {
+  float2 at, z, m;
 };
 
-// Eq. 2 for the two pixels at once; a pixel that does not contribute, or has
-// terminated, takes weight 0 and keeps its state.
-__device__ __forceinline__ void blend2(Fwd2 &s, const Eval2 &e, const float4 &r2, const float4 &r3,
-                                       const CfgK &cfg, uint32_t idx) {
-  const bool a0 = e.c0 && !s.done0, a1 = e.c1 && !s.done1;
-  const float2 at = sel2(a0, a1, e.at, f2(0.0f));
+__device__ __forceinline__ void eval_fwd2(const float4 &r0, const float4 &r1, const float4 &r2, const float4 &r4,
+                                          float px, float2 py, const CfgK &f, EvalF2 &e) {
+  const float dx = __fsub_rn(__fsub_rn(px, r0.x), r4.x);
+  const float2 dy = add2(add2(py, f2(-r0.y)), f2(-r4.y));
+  float2 q;
+  float alpha;
+  bool k0 = true, k1 = true;
+  if (r0.w > 0.0f) {
+    const float2 u = fma2(f2(r1.x), f2(dx), mul2(f2(r1.y), dy));
+    const float2 v = mul2(f2(r1.z), dy);
+    q = fma2(u, u, mul2(v, v));
+    alpha = r0.w;
+    e.z = f2(r0.z);
+  } else {
+    const float2 p0 = fma2(f2(r1.x), f2(dx), mul2(f2(r1.y), dy));
+    const float2 p1 = fma2(f2(r1.z), f2(dx), mul2(f2(r1.w), dy));
+    const float2 p2 = fma2(f2(r2.x), f2(dx), fma2(f2(r2.y), dy, f2(1.0f)));
+    k0 = p2.x > 0.0f;
+    k1 = p2.y > 0.0f;
+    const float2 inv = make_float2(k0 ? rcp_approx(p2.x) : 0.0f, k1 ? rcp_approx(p2.y) : 0.0f);
+    e.z = mul2(f2(r0.z), inv);
+    k0 = k0 && e.z.x > f.near_z;
+    k1 = k1 && e.z.y > f.near_z;
+    const float2 u = mul2(p0, inv), v = mul2(p1, inv);
+    q = fma2(u, u, mul2(v, v));
+    alpha = -r0.w;
+  }
+  const float2 x = mul2(q, f2(-0.5f * kLog2e));
+  const float2 araw = mul2(f2(alpha), make_float2(ex2_approx(x.x), ex2_approx(x.y)));
+  e.m = make_float2(k0 && araw.x >= f.alpha_min ? 1.0f : 0.0f, k1 && araw.y >= f.alpha_min ? 1.0f : 0.0f);
+  e.at = make_float2(fminf(araw.x, f.alpha_max), fminf(araw.y, f.alpha_max));
+}
+
+// Forward state of a lane's two pixels: live is 1 until the pixel
+// terminates; last (the 1-based index of the last contributor) and nc (the
+// contributors) are counted in binary32, exact below 2^24.
+struct Fwd2 {
+  float2 T, C0, C1, C2, D, N0, N1, N2, live, last, nc;
+};
+
+// Eq. 2 for the two pixels at once.  A pair counts where it contributes and
+// the pixel is live (m); the pixel stops before it if T would fall below
+// T_min; a pair that does not count has weight 0, and T * (1 - 0) leaves the
+// transmittance as it was.
+__device__ __forceinline__ void blend2(Fwd2 &s, const EvalF2 &e, const float4 &r2, const float4 &r3,
+                                       const CfgK &cfg, float idx) {
+  const float2 m = mul2(e.m, s.live);
+  const float2 at = mul2(e.at, m);
   const float2 Tn = mul2(s.T, add2(f2(1.0f), neg2(at)));
-  const bool st0 = a0 && Tn.x < cfg.T_min, st1 = a1 && Tn.y < cfg.T_min;
-  s.done0 = s.done0 || st0;
-  s.done1 = s.done1 || st1;
-  const bool t0 = a0 && !st0, t1 = a1 && !st1;
-  const float2 w = mul2(sel2(t0, t1, at, f2(0.0f)), s.T);
-  const float2 z = sel2(t0, t1, e.z, f2(0.0f));
-  s.T = sel2(t0, t1, Tn, s.T);
+  const float2 st = make_float2(Tn.x < cfg.T_min ? 1.0f : 0.0f, Tn.y < cfg.T_min ? 1.0f : 0.0f);
+  s.live = fma2(neg2(st), s.live, s.live);
+  const float2 keep = fma2(neg2(st), m, m);
+  const float2 a2 = mul2(e.at, keep);
+  const float2 w = mul2(a2, s.T);
+  s.T = mul2(s.T, add2(f2(1.0f), neg2(a2)));
+  const float2 z = make_float2(keep.x != 0.0f ? e.z.x : 0.0f, keep.y != 0.0f ? e.z.y : 0.0f);
   s.C0 = fma2(w, f2(r2.z), s.C0);
   s.C1 = fma2(w, f2(r2.w), s.C1);
   s.C2 = fma2(w, f2(r3.x), s.C2);
@@ -347,10 +395,8 @@ __device__ __forceinline__ void blend2(Fwd2 &s, const Eval2 &e, const float4 &r2
   s.N0 = fma2(w, f2(r3.y), s.N0);
   s.N1 = fma2(w, f2(r3.z), s.N1);
   s.N2 = fma2(w, f2(r3.w), s.N2);
-  s.last0 = t0 ? idx : s.last0;
-  s.last1 = t1 ? idx : s.last1;
-  s.nc0 += t0 ? 1u : 0u;
-  s.nc1 += t1 ? 1u : 0u;
+  s.last = fma2(keep, add2(f2(idx), neg2(s.last)), s.last);
+  s.nc = add2(s.nc, keep);
 }
 
 __device__ __forceinline__ void write_pix1(const RenderArgs &a, int x, int y, float T, float C0, float C1, float C2,
@@ -385,10 +431,9 @@ __device__ __forceinline__ void render_tile_fwd2(const RenderArgs &a, int tile, 
     const int x = tx0 + 8 * (q & 1) + lx, y = ty0 + 8 * (q >> 1) + ly;
     s[k].T = f2(1.0f);
     s[k].C0 = s[k].C1 = s[k].C2 = s[k].D = s[k].N0 = s[k].N1 = s[k].N2 = f2(0.0f);
-    s[k].last0 = s[k].last1 = s[k].nc0 = s[k].nc1 = 0u;
-    s[k].done0 = !(x < a.cam.W && y < a.cam.H);
-    s[k].done1 = !(x < a.cam.W && y + 4 < a.cam.H);
-    if (!__all_sync(0xffffffffu, s[k].done0 && s[k].done1)) live |= 1u << k;
+    s[k].last = s[k].nc = f2(0.0f);
+    s[k].live = make_float2(x < a.cam.W && y < a.cam.H ? 1.0f : 0.0f, x < a.cam.W && y + 4 < a.cam.H ? 1.0f : 0.0f);
+    if (__any_sync(0xffffffffu, s[k].live.x + s[k].live.y != 0.0f)) live |= 1u << k;
   }
   const uint32_t start = a.ranges[2 * tile], end = a.ranges[2 * tile + 1];
   if (live && start < end) {
@@ -415,16 +460,16 @@ __device__ __forceinline__ void render_tile_fwd2(const RenderArgs &a, int tile, 
         any &= any - 1;
         const float4 *r = chunk + j * kRecF4;
         const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4];
-        const uint32_t idx = base - start + (uint32_t)j + 1u;
+        const float idx = (float)(base - start + (uint32_t)j + 1u);
 #pragma unroll
         for (int k = 0; k < QW; ++k) {
           if (!((live >> k) & 1u) || !((m[k] >> j) & 1u)) continue;
           const int q = q0 + k;
           const float pyq = (float)(ty0 + 8 * (q >> 1) + ly) + 0.5f;
-          Eval2 e;
-          eval_pair2(r0, r1, r2, r4, px + 8.0f * (float)(q & 1), make_float2(pyq, pyq + 4.0f), a.cfg, e);
+          EvalF2 e;
+          eval_fwd2(r0, r1, r2, r4, px + 8.0f * (float)(q & 1), make_float2(pyq, pyq + 4.0f), a.cfg, e);
           blend2(s[k], e, r2, r3, a.cfg, idx);
-          if (__all_sync(0xffffffffu, s[k].done0 && s[k].done1)) live &= ~(1u << k);
+          if (!__any_sync(0xffffffffu, s[k].live.x + s[k].live.y != 0.0f)) live &= ~(1u << k);
         }
       }
       if (!live) break;
@@ -438,9 +483,9 @@ __device__ __forceinline__ void render_tile_fwd2(const RenderArgs &a, int tile, 
     const int q = q0 + k;
     const int x = tx0 + 8 * (q & 1) + lx, y = ty0 + 8 * (q >> 1) + ly;
     write_pix1(a, x, y, s[k].T.x, s[k].C0.x, s[k].C1.x, s[k].C2.x, s[k].D.x, s[k].N0.x, s[k].N1.x, s[k].N2.x,
-               s[k].last0, s[k].nc0);
+               (uint32_t)s[k].last.x, (uint32_t)s[k].nc.x);
     write_pix1(a, x, y + 4, s[k].T.y, s[k].C0.y, s[k].C1.y, s[k].C2.y, s[k].D.y, s[k].N0.y, s[k].N1.y, s[k].N2.y,
-               s[k].last1, s[k].nc1);
+               (uint32_t)s[k].last.y, (uint32_t)s[k].nc.y);
   }
 }
 
@@ -587,21 +632,26 @@ __device__ __forceinline__ void pair_grad(float (&g)[16], BwdPix &s, const PairE
     dd = dat * (-0.5f * e.at);
   }
   if (r0.w > 0.0f) {
-    // conic-space gradient: d = a dx^2 + 2 b dx dy + c dy^2
-    const float ddx = dd * e.dx, ddy = dd * e.dy;
-    g[7] += ddx * e.dx;
-    g[8] += 2.0f * ddx * e.dy;
-    g[9] += ddy * e.dy;
+    // shape gradient in the footprint's own coordinates (u, v) = W (dx, dy):
+    // dL/dH for d = (u, v) H (u, v)^T at H = I (rounding-stable for needles)
+    const float ddu = dd * e.u, ddv = dd * e.v;
+    g[7] += ddu * e.u;
+    g[8] += 2.0f * ddu * e.v;
+    g[9] += ddv * e.v;
     g[4] -= dd * 2.0f * e.u * r1.x;
     g[5] -= dd * 2.0f * (e.u * r1.y + e.v * r1.z);
     if (FULL) g[6] += dzp;
   } else {
+    // the homography's gradient in the splat's own coordinates:
+    // (du, dv) (u, v)^T and p2 dL/dp2 (u, v) (the preprocess backward maps
+    // them back to the parameters)
     const float du = 2.0f * e.u * dd, dv = 2.0f * e.v * dd;
     const float dp0 = du * e.inv, dp1 = dv * e.inv;
-    const float dp2 = -(du * e.u + dv * e.v + dzp * e.z) * e.inv;
-    g[7] += dp0 * e.dx; g[8] += dp0 * e.dy;
-    g[9] += dp1 * e.dx; g[10] += dp1 * e.dy;
-    g[11] += dp2 * e.dx; g[12] += dp2 * e.dy;
+    const float dq2 = -(du * e.u + dv * e.v + dzp * e.z);
+    const float dp2 = dq2 * e.inv;
+    g[7] += du * e.u; g[8] += du * e.v;
+    g[9] += dv * e.u; g[10] += dv * e.v;
+    g[11] += dq2 * e.u; g[12] += dq2 * e.v;
     g[4] -= dp0 * r1.x + dp1 * r1.z + dp2 * r2.x;
     g[5] -= dp0 * r1.y + dp1 * r1.w + dp2 * r2.y;
     if (FULL) g[6] += dzp * e.inv;
@@ -722,83 +772,6 @@ __device__ __forceinline__ void reduce_record(float (&g)[16], bool is3d, int lan
   }
 }
 
-// Pixel state of the rgb-only backward with NC cotangent sets replayed at
-// once: the transmittance is shared, each set keeps its cotangent and its
-// blended dot product S (as in BwdPix).
-template <int NC>
-struct RgbPix {
-  float px, py, T;
-  uint32_t last;
-  float dC[NC][3];
-  float S[NC];
-  bool inside;
-};
-
-template <int NC>
-__device__ __forceinline__ void load_rgb_pix(RgbPix<NC> &s, const RenderBwdArgs &a, const float *const (&g)[3], int x,
-                                             int y) {
-  s.px = (float)x + 0.5f;
-  s.py = (float)y + 0.5f;
-  s.inside = x < a.cam.W && y < a.cam.H;
-  s.T = 1.0f;
-  s.last = 0;
-#pragma unroll
-  for (int c = 0; c < NC; ++c) { s.dC[c][0] = s.dC[c][1] = s.dC[c][2] = 0.f; s.S[c] = 0.f; }
-  if (!s.inside) return;
-  const size_t HW = (size_t)a.cam.W * a.cam.H;
-  const size_t p = (size_t)y * a.cam.W + x;
-  s.T = a.T_final[p];
-  s.last = a.n_last[p];
-#pragma unroll
-  for (int c = 0; c < NC; ++c) {
-    if (g[c]) { s.dC[c][0] = g[c][p]; s.dC[c][1] = g[c][p + HW]; s.dC[c][2] = g[c][p + 2 * HW]; }
-    s.S[c] = a.cfg.bg[0] * s.dC[c][0] + a.cfg.bg[1] * s.dC[c][1] + a.cfg.bg[2] * s.dC[c][2];
-  }
-}
-
-// pair_grad<false> for NC cotangent sets sharing one evaluation and one
-// transmittance step
-template <int NC>
-__device__ __forceinline__ void pair_grad_rgb(float (&g)[NC][16], RgbPix<NC> &s, const PairEval &e, const float4 &r0,
-                                              const float4 &r1, const float4 &r2, const float4 &r3,
-                                              const CfgK &cfg) {
-  const float c0 = r2.z, c1 = r2.w, c2 = r3.x;
-  const float Ti = __fdividef(s.T, 1.0f - e.at);
-  const float w = e.at * Ti;
-  s.T = Ti;
-  const bool open = e.araw <= cfg.alpha_max;
-#pragma unroll
-  for (int c = 0; c < NC; ++c) {
-    const float cd = fmaf(c0, s.dC[c][0], fmaf(c1, s.dC[c][1], c2 * s.dC[c][2]));
-    const float fsum = cd - s.S[c];
-    const float dat = Ti * fsum;
-    s.S[c] = fmaf(e.at, fsum, s.S[c]);
-    g[c][1] += w * s.dC[c][0]; g[c][2] += w * s.dC[c][1]; g[c][3] += w * s.dC[c][2];
-    float dd = 0.f;
-    if (open) {
-      g[c][0] += dat * e.g;
-      dd = dat * (-0.5f * e.at);
-    }
-    if (r0.w > 0.0f) {
-      const float ddx = dd * e.dx, ddy = dd * e.dy;
-      g[c][7] += ddx * e.dx;
-      g[c][8] += 2.0f * ddx * e.dy;
-      g[c][9] += ddy * e.dy;
-      g[c][4] -= dd * 2.0f * e.u * r1.x;
-      g[c][5] -= dd * 2.0f * (e.u * r1.y + e.v * r1.z);
-    } else {
-      const float du = 2.0f * e.u * dd, dv = 2.0f * e.v * dd;
-      const float dp0 = du * e.inv, dp1 = dv * e.inv;
-      const float dp2 = -(du * e.u + dv * e.v) * e.inv;
-      g[c][7] += dp0 * e.dx; g[c][8] += dp0 * e.dy;
-      g[c][9] += dp1 * e.dx; g[c][10] += dp1 * e.dy;
-      g[c][11] += dp2 * e.dx; g[c][12] += dp2 * e.dy;
-      g[c][4] -= dp0 * r1.x + dp1 * r1.z + dp2 * r2.x;
-      g[c][5] -= dp0 * r1.y + dp1 * r1.w + dp2 * r2.y;
-    }
-  }
-}
-
 // Reverse walk over a warp's part of one tile list (shared by both backward
 // kernels): stage chunks of 32 records from the back with cp.async, test
 // them against the warp's block, and call body(record, id, jrel) for each
@@ -838,43 +811,6 @@ __device__ __forceinline__ void bwd_walk(const RenderBwdArgs &a, int tile, int w
     cs = ncs;
   }
   cp_async_wait<0>();
-}
-
-// rgb-only backward (image losses): NC cotangent sets replayed together
-template <int NC>
-__global__ void __launch_bounds__(kRW * 32, NC == 1 ? 5 : 4) render_bwd_rgb_kernel(RenderBwdArgs a) {
-  __shared__ __align__(16) float4 sm[kRW][2][kCh * kRecF4];
-  __shared__ uint32_t sid[kRW][2][kCh];
-  const int tile = blockIdx.x;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int bx, by;
-  block_of(tile, a.cam.TX, warp, bx, by);
-  RgbPix<NC> s[2];
-#pragma unroll
-  for (int k = 0; k < 2; ++k) load_rgb_pix<NC>(s[k], a, a.g_rgbs, bx + (lane & 7), by + (lane >> 3) + 4 * k);
-  const uint32_t wmax = __reduce_max_sync(0xffffffffu, max(s[0].last, s[1].last));
-  if (wmax == 0) return;
-  bwd_walk(a, tile, warp, lane, bx, by, wmax, sm, sid, [&](const float4 *r, uint32_t id, uint32_t jrel) {
-    const float4 r0 = r[0], r1 = r[1], r2 = r[2], r4 = r[4];
-    PairEval e0, e1;
-    const bool c0 = s[0].inside && jrel < s[0].last && eval_pair(r0, r1, r2, r4, s[0].px, s[0].py, a.cfg, e0);
-    const bool c1 = s[1].inside && jrel < s[1].last && eval_pair(r0, r1, r2, r4, s[1].px, s[1].py, a.cfg, e1);
-    if (!__any_sync(0xffffffffu, c0 || c1)) return;
-    float g[NC][16];
-#pragma unroll
-    for (int c = 0; c < NC; ++c)
-#pragma unroll
-      for (int k = 0; k < 16; ++k) g[c][k] = 0.f;
-    const float4 r3 = r[3];
-    if (c0) pair_grad_rgb<NC>(g, s[0], e0, r0, r1, r2, r3, a.cfg);
-    if (c1) pair_grad_rgb<NC>(g, s[1], e1, r0, r1, r2, r3, a.cfg);
-    if constexpr (NC == 3) {
-      reduce_record3(g, r0.w > 0.0f, lane, a.rec_grads, id);
-    } else {
-#pragma unroll
-      for (int c = 0; c < NC; ++c) reduce_record<false>(g[c], r0.w > 0.0f, lane, a.rec_grads[c] + (size_t)id * kGradW);
-    }
-  });
 }
 
 // Tile scheduling for the one-warp-per-tile backward.  A tile's work is its
@@ -934,100 +870,116 @@ __global__ void __launch_bounds__(1024) k_tile_order(const uint32_t *__restrict_
 // of a lane's pixel pair sit in shared memory (lane-indexed, so the loads are
 // conflict-free), which keeps the kernel's registers low enough for 20 warps
 // per SM.
+template <int NC>
 struct Bwd4 {
-  float2 T, S;
+  float2 T, S[NC];
 };
+template <int NC>
 struct Bwd4Smem {
-  float2 dC[4][3][32];  // [quadrant][channel][lane]: the lane's two pixels
-  uint2 last[4][32];    // [quadrant][lane]
+  float2 dC[4][3 * NC][32];  // [quadrant][set * 3 + channel][lane]: the lane's two pixels
+  uint2 last[4][32];         // [quadrant][lane]
 };
 
-// Reverse replay of one record for the two pixels of a lane, accumulated into
-// the per-record slots g (pair_grad_rgb for both pixels).
-__device__ __forceinline__ void pair_grad2s(float (&g)[13], Bwd4 &s, const float2 dC0, const float2 dC1,
-                                            const float2 dC2, const Eval2 &e, bool c0, bool c1, const float4 &r0,
+// Reverse replay of one record for the two pixels of a lane and NC cotangent
+// sets (sharing the evaluation and the transmittance step), accumulated into
+// the per-record slots g[set] (pair_grad_rgb for both pixels).
+template <int NC>
+__device__ __forceinline__ void pair_grad2s(float (&g)[NC][16], Bwd4<NC> &s, const Bwd4Smem<NC> &ps, int k,
+                                            int lane, const Eval2 &e, bool c0, bool c1, const float4 &r0,
                                             const float4 &r1, const float4 &r2, const float4 &r3, const CfgK &cfg) {
   const float2 at = sel2(c0, c1, e.at, f2(0.0f));
   const float2 om = add2(f2(1.0f), neg2(at));
   const float2 Ti = mul2(s.T, make_float2(rcp_approx(om.x), rcp_approx(om.y)));
   s.T = sel2(c0, c1, Ti, s.T);
   const float2 w = mul2(at, Ti);
-  const float2 cd = fma2(f2(r2.z), dC0, fma2(f2(r2.w), dC1, mul2(f2(r3.x), dC2)));
-  const float2 fsum = add2(cd, neg2(s.S));
-  const float2 dat = mul2(Ti, fsum);
-  s.S = fma2(at, fsum, s.S);
-  auto acc = [](float &gk, float2 a, float2 b) { gk = fmaf(a.x, b.x, fmaf(a.y, b.y, gk)); };
-  acc(g[1], w, dC0);
-  acc(g[2], w, dC1);
-  acc(g[3], w, dC2);
   const bool o0 = c0 && e.araw.x <= cfg.alpha_max, o1 = c1 && e.araw.y <= cfg.alpha_max;
-  const float2 dato = sel2(o0, o1, dat, f2(0.0f));
-  acc(g[0], dato, e.g);
-  const float2 dd = mul2(dato, mul2(f2(-0.5f), at));
-  const float2 dx = f2(e.dx);
-  if (r0.w > 0.0f) {
-    const float2 ddx = mul2(dd, dx), ddy = mul2(dd, e.dy);
-    acc(g[7], ddx, dx);
-    acc(g[8], mul2(f2(2.0f), ddx), e.dy);
-    acc(g[9], ddy, e.dy);
-    const float2 dd2 = mul2(dd, f2(-2.0f));
-    acc(g[4], mul2(dd2, e.u), f2(r1.x));
-    acc(g[5], dd2, fma2(e.u, f2(r1.y), mul2(e.v, f2(r1.z))));
-  } else {
-    const float2 du = mul2(mul2(f2(2.0f), e.u), dd), dv = mul2(mul2(f2(2.0f), e.v), dd);
-    const float2 dp0 = mul2(du, e.inv), dp1 = mul2(dv, e.inv);
-    const float2 dp2 = mul2(fma2(du, e.u, mul2(dv, e.v)), neg2(e.inv));
-    acc(g[7], dp0, dx);
-    acc(g[8], dp0, e.dy);
-    acc(g[9], dp1, dx);
-    acc(g[10], dp1, e.dy);
-    acc(g[11], dp2, dx);
-    acc(g[12], dp2, e.dy);
-    acc(g[4], fma2(dp0, f2(-r1.x), fma2(dp1, f2(-r1.z), mul2(dp2, f2(-r2.x)))), f2(1.0f));
-    acc(g[5], fma2(dp0, f2(-r1.y), fma2(dp1, f2(-r1.w), mul2(dp2, f2(-r2.y)))), f2(1.0f));
+  const float2 oTi = sel2(o0, o1, Ti, f2(0.0f));
+  auto acc = [](float &gk, float2 a, float2 b) { gk = fmaf(a.x, b.x, fmaf(a.y, b.y, gk)); };
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const float2 dC0 = ps.dC[k][3 * c][lane], dC1 = ps.dC[k][3 * c + 1][lane], dC2 = ps.dC[k][3 * c + 2][lane];
+    const float2 cd = fma2(f2(r2.z), dC0, fma2(f2(r2.w), dC1, mul2(f2(r3.x), dC2)));
+    const float2 fsum = add2(cd, neg2(s.S[c]));
+    s.S[c] = fma2(at, fsum, s.S[c]);
+    acc(g[c][1], w, dC0);
+    acc(g[c][2], w, dC1);
+    acc(g[c][3], w, dC2);
+    const float2 dato = mul2(oTi, fsum);
+    acc(g[c][0], dato, e.g);
+    const float2 dd = mul2(dato, mul2(f2(-0.5f), at));
+    if (r0.w > 0.0f) {
+      const float2 ddu = mul2(dd, e.u), ddv = mul2(dd, e.v);
+      acc(g[c][7], ddu, e.u);
+      acc(g[c][8], mul2(f2(2.0f), ddu), e.v);
+      acc(g[c][9], ddv, e.v);
+      const float2 dd2 = mul2(dd, f2(-2.0f));
+      acc(g[c][4], mul2(dd2, e.u), f2(r1.x));
+      acc(g[c][5], dd2, fma2(e.u, f2(r1.y), mul2(e.v, f2(r1.z))));
+    } else {
+      const float2 du = mul2(mul2(f2(2.0f), e.u), dd), dv = mul2(mul2(f2(2.0f), e.v), dd);
+      const float2 dp0 = mul2(du, e.inv), dp1 = mul2(dv, e.inv);
+      const float2 dq2 = neg2(fma2(du, e.u, mul2(dv, e.v)));
+      const float2 dp2 = mul2(dq2, e.inv);
+      acc(g[c][7], du, e.u);
+      acc(g[c][8], du, e.v);
+      acc(g[c][9], dv, e.u);
+      acc(g[c][10], dv, e.v);
+      acc(g[c][11], dq2, e.u);
+      acc(g[c][12], dq2, e.v);
+      acc(g[c][4], fma2(dp0, f2(-r1.x), fma2(dp1, f2(-r1.z), mul2(dp2, f2(-r2.x)))), f2(1.0f));
+      acc(g[c][5], fma2(dp0, f2(-r1.y), fma2(dp1, f2(-r1.w), mul2(dp2, f2(-r2.y)))), f2(1.0f));
+    }
   }
 }
 
-// One tile of the rgb-only backward by one warp (all four quadrants).
+// One tile of the rgb-only backward by one warp (all four quadrants), NC
+// cotangent sets.
+template <int NC>
 __device__ __forceinline__ void bwd4_tile(const RenderBwdArgs &a, int tile, int lane, float4 (*sm)[kCh * kRecF4],
-                                          uint32_t (*sid)[kCh], Bwd4Smem &ps) {
+                                          uint32_t (*sid)[kCh], Bwd4Smem<NC> &ps) {
   const int tx0 = (tile % a.cam.TX) * kTile, ty0 = (tile / a.cam.TX) * kTile;
   const int lx = lane & 7, ly = lane >> 3;
-  const float *g = a.g_rgbs[0];
   const size_t HW = (size_t)a.cam.W * a.cam.H;
-  Bwd4 s[4];
+  Bwd4<NC> s[4];
   uint32_t qmax[4];
   uint32_t wmax = 0;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const int x = tx0 + 8 * (k & 1) + lx, y = ty0 + 8 * (k >> 1) + ly;
-    float Ts[2] = {1.0f, 1.0f}, d[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    float Ts[2] = {1.0f, 1.0f};
     uint32_t l[2] = {0u, 0u};
+    bool in[2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int yy = y + 4 * h;
-      if (x < a.cam.W && yy < a.cam.H) {
+      in[h] = x < a.cam.W && yy < a.cam.H;
+      if (in[h]) {
         const size_t p = (size_t)yy * a.cam.W + x;
         Ts[h] = a.T_final[p];
         l[h] = a.n_last[p];
-        if (g) {
-          d[h][0] = g[p];
-          d[h][1] = g[p + HW];
-          d[h][2] = g[p + 2 * HW];
-        }
       }
     }
     s[k].T = make_float2(Ts[0], Ts[1]);
-    const float2 dC0 = make_float2(d[0][0], d[1][0]), dC1 = make_float2(d[0][1], d[1][1]),
-                 dC2 = make_float2(d[0][2], d[1][2]);
-    ps.dC[k][0][lane] = dC0;
-    ps.dC[k][1][lane] = dC1;
-    ps.dC[k][2][lane] = dC2;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const float *gc = a.g_rgbs[c];
+      float2 d[3];
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        d[ch] = f2(0.0f);
+        if (gc) {
+          if (in[0]) d[ch].x = gc[(size_t)y * a.cam.W + x + ch * HW];
+          if (in[1]) d[ch].y = gc[(size_t)(y + 4) * a.cam.W + x + ch * HW];
+        }
+        ps.dC[k][3 * c + ch][lane] = d[ch];
+      }
+      s[k].S[c] = fma2(f2(a.cfg.bg[0]), d[0], fma2(f2(a.cfg.bg[1]), d[1], mul2(f2(a.cfg.bg[2]), d[2])));
+    }
     ps.last[k][lane] = make_uint2(l[0], l[1]);
-    s[k].S = fma2(f2(a.cfg.bg[0]), dC0, fma2(f2(a.cfg.bg[1]), dC1, mul2(f2(a.cfg.bg[2]), dC2)));
     qmax[k] = __reduce_max_sync(0xffffffffu, max(l[0], l[1]));
     wmax = max(wmax, qmax[k]);
   }
+  __syncwarp();
   if (wmax == 0) return;
   const uint32_t start = a.ranges[2 * tile];
   const float4 *rec = reinterpret_cast<const float4 *>(a.rec);
@@ -1059,9 +1011,11 @@ __device__ __forceinline__ void bwd4_tile(const RenderBwdArgs &a, int tile, int 
       const float4 *r = chunk + jj * kRecF4;
       const uint32_t jrel = cs + (uint32_t)jj - start;
       const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4];
-      float gs[16];
+      float gs[NC][16];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) gs[i] = 0.0f;
+      for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int i = 0; i < 16; ++i) gs[c][i] = 0.0f;
       bool hit = false;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
@@ -1073,11 +1027,15 @@ __device__ __forceinline__ void bwd4_tile(const RenderBwdArgs &a, int tile, int 
         const bool c0 = e.c0 && jrel < l.x, c1 = e.c1 && jrel < l.y;
         if (!__any_sync(0xffffffffu, c0 || c1)) continue;
         hit = true;
-        pair_grad2s(reinterpret_cast<float(&)[13]>(gs), s[k], ps.dC[k][0][lane], ps.dC[k][1][lane],
-                    ps.dC[k][2][lane], e, c0, c1, r0, r1, r2, r3, a.cfg);
+        pair_grad2s<NC>(gs, s[k], ps, k, lane, e, c0, c1, r0, r1, r2, r3, a.cfg);
       }
       if (!hit) continue;
-      reduce_record<false>(gs, r0.w > 0.0f, lane, a.rec_grads[0] + (size_t)sid[buf][jj] * kGradW);
+      const uint32_t id = sid[buf][jj];
+      if constexpr (NC == 3) {
+        reduce_record3(gs, r0.w > 0.0f, lane, a.rec_grads, id);
+      } else {
+        reduce_record<false>(gs[0], r0.w > 0.0f, lane, a.rec_grads[0] + (size_t)id * kGradW);
+      }
     }
     if (!has_next) break;
     __syncwarp();
@@ -1088,18 +1046,18 @@ __device__ __forceinline__ void bwd4_tile(const RenderBwdArgs &a, int tile, int 
   cp_async_wait<0>();
 }
 
-// 20 one-warp CTAs per SM: 96 registers, no spills.
-constexpr int kBwd4MinBlocks = 20;
 // One warp per tile; with `order`, a persistent grid takes tiles longest
-// first from `counter`, else CTA b takes tile b.
-__global__ void __launch_bounds__(32, kBwd4MinBlocks) render_bwd_rgb4_kernel(RenderBwdArgs a, const uint32_t *order,
-                                                                           uint32_t *counter, int tiles) {
+// first from `counter`, else CTA b takes tile b.  One cotangent set: 20
+// one-warp CTAs per SM (96 registers, no spills); three sets: 16.
+template <int NC>
+__global__ void __launch_bounds__(32, NC == 1 ? 20 : 16) render_bwd_rgb4_kernel(RenderBwdArgs a, const uint32_t *order,
+                                                                              uint32_t *counter, int tiles) {
   __shared__ __align__(16) float4 sm[2][kCh * kRecF4];
   __shared__ uint32_t sid[2][kCh];
-  __shared__ Bwd4Smem ps;
+  __shared__ Bwd4Smem<NC> ps;
   const int lane = threadIdx.x & 31;
   if (!order) {
-    bwd4_tile(a, blockIdx.x, lane, sm, sid, ps);
+    bwd4_tile<NC>(a, blockIdx.x, lane, sm, sid, ps);
     return;
   }
   while (true) {
@@ -1107,7 +1065,7 @@ __global__ void __launch_bounds__(32, kBwd4MinBlocks) render_bwd_rgb4_kernel(Ren
     if (lane == 0) t = atomicAdd(counter, 1u);
     t = __shfl_sync(0xffffffffu, t, 0);
     if (t >= (uint32_t)tiles) break;
-    bwd4_tile(a, (int)__ldg(order + t), lane, sm, sid, ps);
+    bwd4_tile<NC>(a, (int)__ldg(order + t), lane, sm, sid, ps);
     __syncwarp();
   }
 }
@@ -1184,31 +1142,30 @@ int launch_render_batch(const BatchRenderArgs &b, int rows, cudaStream_t s) {
 // The one-warp-per-tile rgb backward: with a scheduling scratch, the tiles'
 // work and a longest-first order are computed on the device and a persistent
 // grid (every resident CTA) takes the tiles in that order.
+template <int NC>
 static void launch_bwd4(const RenderBwdArgs &a, int tiles, cudaStream_t s) {
   static int resident = [] {
-    prefer_shared((const void *)render_bwd_rgb4_kernel);
+    prefer_shared((const void *)render_bwd_rgb4_kernel<NC>);
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, render_bwd_rgb4_kernel, 32, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, render_bwd_rgb4_kernel<NC>, 32, 0);
     return max(1, sms * max(per, 1));
   }();
   if (!a.tile_sched) {
-    render_bwd_rgb4_kernel<<<tiles, 32, 0, s>>>(a, nullptr, nullptr, tiles);
+    render_bwd_rgb4_kernel<NC><<<tiles, 32, 0, s>>>(a, nullptr, nullptr, tiles);
     return;
   }
   uint32_t *work = a.tile_sched, *order = a.tile_sched + tiles, *counter = a.tile_sched + 2 * (size_t)tiles;
   k_tile_work<<<(tiles + 7) / 8, 256, 0, s>>>(a.n_last, a.cam.W, a.cam.H, a.cam.TX, tiles, work);
   k_tile_order<<<1, 1024, 0, s>>>(work, tiles, order, counter);
-  render_bwd_rgb4_kernel<<<min(tiles, resident), 32, 0, s>>>(a, order, counter, tiles);
+  render_bwd_rgb4_kernel<NC><<<min(tiles, resident), 32, 0, s>>>(a, order, counter, tiles);
 }
 
 int launch_render_bwd(const RenderBwdArgs &a, cudaStream_t s) {
   const int tiles = a.cam.TX * a.cam.TY;
   if (tiles <= 0) return 0;
-  static bool once = (prefer_shared((const void *)render_bwd_kernel),
-
-                      prefer_shared((const void *)render_bwd_rgb_kernel<3>), true);
+  static bool once = (prefer_shared((const void *)render_bwd_kernel), true);
   (void)once;
   if (a.nc == 0 && (a.g_depth || a.g_normal || a.g_alpha)) {
     render_bwd_kernel<<<tiles, kRW * 32, 0, s>>>(a);
@@ -1221,15 +1178,16 @@ int launch_render_bwd(const RenderBwdArgs &a, cudaStream_t s) {
     b.g_rgbs[0] = a.g_rgb;
     b.rec_grads[0] = a.rec_grad;
   }
-  if (b.nc == 3)
-    render_bwd_rgb_kernel<3><<<tiles, kRW * 32, 0, s>>>(b);
-  else
-    for (int c = 0; c < b.nc; ++c) {
-      RenderBwdArgs one = b;
-      one.g_rgbs[0] = b.g_rgbs[c];
-      one.rec_grads[0] = b.rec_grads[c];
-      launch_bwd4(one, tiles, s);
-    }
+  if (b.nc == 3) {
+    launch_bwd4<3>(b, tiles, s);
+    return 0;
+  }
+  for (int c = 0; c < b.nc; ++c) {
+    RenderBwdArgs one = b;
+    one.g_rgbs[0] = b.g_rgbs[c];
+    one.rec_grads[0] = b.rec_grads[c];
+    launch_bwd4<1>(one, tiles, s);
+  }
   return 0;
 }
 

@@ -103,30 +103,50 @@ def _check_pixels(out, scene, cam, npix, seed, orc, max_excluded, label, max_loo
 # ---------------------------------------------------------------------------
 # finite differences, one primitive at a time
 # ---------------------------------------------------------------------------
-def _fd_pixels(orc, cam, i, rect, rng, per_prim, cand_max=2048):
-    """Up to per_prim pixels where primitive i contributes and the oracle's
-    result is unambiguous (one correct result, a conditioning tolerance
-    under 1e-4), and an oracle finite-difference session on them."""
-    tx0, tx1, ty0, ty1 = rect
-    x0, x1 = tx0 * 16, min((tx1 + 1) * 16, cam.width)
-    y0, y1 = ty0 * 16, min((ty1 + 1) * 16, cam.height)
-    npx = (x1 - x0) * (y1 - y0)
-    if npx <= cand_max:
-        ys, xs = np.mgrid[y0:y1, x0:x1]
-        cand = np.stack([xs.ravel(), ys.ravel()], 1)
-    else:
-        cand = np.unique(np.stack([rng.integers(x0, x1, cand_max), rng.integers(y0, y1, cand_max)], 1), axis=0)
-    cand = np.ascontiguousarray(cand, np.int32)
-    ag = orc.pair_alpha(i, cand)
-    hit = cand[ag >= CFG.alpha_min * 1.01]
-    if len(hit) == 0:
-        return hit, None
-    hit = np.ascontiguousarray(hit[rng.permutation(len(hit))[:3 * per_prim]])
-    with orc.fd_session(i, hit) as fd:
-        _, amb, tol = fd.render(with_tol=True)
-    good = ~amb & (tol[:, :8].max(1) < 1e-4)
-    pix = np.ascontiguousarray(hit[good][:per_prim])
-    return pix, (orc.fd_session(i, pix) if len(pix) else None)
+# A pair's gradient flows through its splat-frame coordinates (u, v) of Eq. 1,
+# which binary32 evaluates from the pixel's offset to the projected centre:
+# along a needle thousands of pixels long those cancelling terms leave (u, v)
+# with absolute errors of 1e-3 and more, and the gradient with relative errors
+# of the same size (measured: 2e-3 on a 576:1 surfel of the stress scene whose
+# 8-ulp bound is 8e-3), a limit of the data type, not of the method.  The
+# checks use pairs whose 8-ulp bound is at most COND_MAX (measured: it removes
+# 0.14% of the stress scene's candidate pairs and none at 3M).
+COND_MAX = 1e-3
+def _fd_plan(orc, cam, touched, strata, n_sample, per_prim, max_tol, rng, max_cond=COND_MAX):
+    """Primitives and pixels for the finite-difference checks.  Random pixels
+    are rendered by the oracle; those with one correct result and a
+    conditioning tolerance under max_tol are kept, and every primitive Eq. 2
+    blends at a kept pixel (so one the image shows there) may be checked at
+    it, where binary32 fixes its splat-frame coordinates to max_cond
+    (Oracle.pair_conditioning).  strata: [(mask over primitives, how many)],
+    drawn at random among the primitives with such a pixel.  Returns
+    [(primitive, pixels)]; prints the fraction of (primitive, pixel)
+    candidates the conditioning bound removed."""
+    pix = np.stack([rng.integers(0, cam.width, n_sample), rng.integers(0, cam.height, n_sample)], 1)
+    pix = np.ascontiguousarray(np.unique(pix, axis=0), np.int32)
+    _, flags, tol = orc._render(pix)
+    pix = pix[(flags == 0) & (tol[:, :8].max(1) < max_tol)]
+    pairs_p, pairs_i = [], []
+    for p, ids in zip(pix, orc.pixel_contributors(pix)):
+        for i in ids:
+            pairs_p.append(p)
+            pairs_i.append(int(i))
+    cond = orc.pair_conditioning(np.array(pairs_i, np.int64), np.array(pairs_p, np.int32).reshape(-1, 2))
+    ok = (cond.min(1) >= 0.0) & (cond.max(1) <= max_cond)
+    print(f"[fd plan] candidate pairs {len(ok)}, removed by the conditioning bound {1.0 - ok.mean():.4f}", flush=True)
+    where = {}
+    for p, i, good in zip(pairs_p, pairs_i, ok):
+        if good:
+            where.setdefault(i, []).append(p)
+    have = np.zeros(len(touched), bool)
+    have[list(where)] = True
+    plan = []
+    for mask, k in strata:
+        cand = np.nonzero(mask & have)[0]
+        for i in rng.choice(cand, min(k, len(cand)), replace=False):
+            p = np.array(where[int(i)], np.int32)
+            plan.append((int(i), np.ascontiguousarray(p[rng.permutation(len(p))[:per_prim]])))
+    return plan
 
 
 class _FD:
@@ -144,12 +164,13 @@ class _FD:
                       "quats": torch.empty((n, 4), device=d), "opacity_logits": torch.empty(n, device=d),
                       "sh": torch.empty((n, nb, 3), device=d)}
         self.records = []   # (field, fd, gpu)
+        self.where = []     # (primitive, type, component, pixels)
         self.skipped = 0
 
     def _loss(self, out, c):
         return float(np.sum(out[:, :8] * c))
 
-    def prim(self, i, pix, fd, rng, n_params):
+    def prim(self, i, pix, session, rng, n_params):
         sc = self.scene
         P = len(pix)
         c = rng.normal(size=(P, 8))
@@ -178,7 +199,7 @@ class _FD:
         params += [("sh", (a, b)) for a in range(sc.sh.shape[1]) for b in range(3)]
         if n_params < len(params):
             params = [params[k] for k in rng.choice(len(params), n_params, replace=False)]
-        h = 1e-5
+        h = 1e-6
         for fname, comp in params:
             Ls, ncs = [], []
             for sgn in (1.0, -1.0):
@@ -189,61 +210,60 @@ class _FD:
                     p[fname][comp] += sgn * h
                 self.orc.set_prim(i, p["means"], p["log_scales"], p["quats"], p["opacity_logits"], p["sh"],
                                   sc.types[i])
-                out, amb = fd.render()
+                out, amb, place = session.render()
                 Ls.append(self._loss(out, c))
-                ncs.append((out[:, 9].copy(), amb.copy()))
+                ncs.append((out[:, 9].copy(), amb.copy(), place.copy()))
             self.orc.set_prim(i, base["means"], base["log_scales"], base["quats"], base["opacity_logits"],
                               base["sh"], sc.types[i])
-            if not (np.array_equal(ncs[0][0], ncs[1][0]) and not ncs[0][1].any() and not ncs[1][1].any()):
-                self.skipped += 1   # a decision changed inside the step: the difference is not a derivative
+            if not (np.array_equal(ncs[0][0], ncs[1][0]) and not ncs[0][1].any() and not ncs[1][1].any()
+                    and np.array_equal(ncs[0][2], ncs[1][2])):
+                # a decision or the blend order changed inside the step: the
+                # difference is not a derivative
+                self.skipped += 1
                 continue
-            fd = (Ls[0] - Ls[1]) / (2 * h)
+            dfd = (Ls[0] - Ls[1]) / (2 * h)
             g = float(G[fname] if fname == "opacity_logits" else G[fname][comp])
-            self.records.append((fname, fd, g))
+            self.records.append((fname, dfd, g))
+            self.where.append((i, int(sc.types[i]), comp, len(pix)))
 
     def assert_ok(self, min_checks):
         checked = len(self.records)
         assert checked >= min_checks, (checked, min_checks)
         assert checked >= 0.9 * (checked + self.skipped), (checked, self.skipped)
-        rep = {}
+        rep, fails = {}, []
         for fname in FIELDS:
-            rows = [(fd, g) for f, fd, g in self.records if f == fname]
-            if not rows:
+            idx = [k for k, (f, _, _) in enumerate(self.records) if f == fname]
+            if not idx:
                 continue
-            fd = np.array([a for a, _ in rows])
-            g = np.array([b for _, b in rows])
+            fd = np.array([self.records[k][1] for k in idx])
+            g = np.array([self.records[k][2] for k in idx])
             rms = np.sqrt(np.mean(fd ** 2))
             rel = np.linalg.norm(g - fd) / max(np.linalg.norm(fd), 1e-300)
             bad = np.abs(g - fd) > 1e-3 * np.abs(fd) + 1e-3 * rms
-            rep[fname] = (len(rows), float(rel), int(bad.sum()))
-            assert rel <= 1e-3, (fname, rel)
-            assert not bad.any(), (fname, [rows[k] for k in np.nonzero(bad)[0][:5]])
-        print(f"[fd] checks {checked} skipped {self.skipped} " +
-              " ".join(f"{k}: n={v[0]} rel={v[1]:.2e}" for k, v in rep.items()), flush=True)
+            rep[fname] = (len(idx), float(rel), int(bad.sum()))
+            if rel > 1e-3 or bad.any():
+                worst = np.argsort(-np.abs(g - fd))[:5]
+                fails.append((fname, rel, int(bad.sum()), [(self.where[idx[k]], fd[k], g[k]) for k in worst]))
+        print(f"[fd rgb_only={self.rgb_only}] checks {checked} skipped {self.skipped} " +
+              " ".join(f"{k}: n={v[0]} rel={v[1]:.2e} bad={v[2]}" for k, v in rep.items()), flush=True)
+        assert not fails, fails
         return rep
 
 
-def _fd_run(scene, cam, r, orc, rect, prims, n_full, per_prim, seed, rgb_only_every=2, min_frac=0.5):
-    """All parameters for the first n_full primitives, 5 random ones for the
-    rest; every rgb_only_every-th primitive with an rgb-only cotangent (the
-    image-loss backward), the others with all four maps."""
+def _fd_run(scene, cam, r, orc, plan, n_full, seed, rgb_only_every=2):
+    """All parameters for the first n_full primitives of the plan, 5 random
+    ones for the rest; every rgb_only_every-th primitive with an rgb-only
+    cotangent (the image-loss backward), the others with all four maps."""
     rng = np.random.default_rng(seed)
     fds = [_FD(scene, cam, r, orc, rgb_only=False), _FD(scene, cam, r, orc, rgb_only=True)]
-    used = np.zeros(len(prims), bool)
-    for k, i in enumerate(prims):
-        i = int(i)
-        pix, fd = _fd_pixels(orc, cam, i, rect[i], rng, per_prim)
-        if len(pix) == 0:
-            continue
-        used[k] = True
-        with fd:
-            fds[1 if k % rgb_only_every == 0 else 0].prim(i, pix, fd, rng, 59 if k < n_full else 5)
+    for k, (i, pix) in enumerate(plan):
+        with orc.fd_session(i, pix) as session:
+            fds[1 if k % rgb_only_every == 0 else 0].prim(i, pix, session, rng, 59 if k < n_full else 5)
     torch.cuda.synchronize()
     r.check()
-    assert used.mean() >= min_frac, (int(used.sum()), len(prims))
     for f in fds:
         f.assert_ok(min_checks=1)
-    return used, sum(len(f.records) for f in fds)
+    return sum(len(f.records) for f in fds)
 
 
 def test_scene_scale_3m_fwd_bwd():
@@ -259,12 +279,13 @@ def test_scene_scale_3m_fwd_bwd():
     orc = O.Oracle(scene, cam, CFG)
     # measured on this scene: no pixel excluded, none with an unplaceable stop
     _check_pixels(out, scene, cam, npix=4000, seed=1, orc=orc, max_excluded=0.0, label="3M scene")
-    # 2,000 primitives: all 59 parameters for 200 of them, 5 for the rest
+    # 2,000 primitives the image shows: all 59 parameters for 200 of them, 5
+    # for the rest
     rng = np.random.default_rng(2)
-    binned = np.nonzero(touched > 0)[0]
-    prims = rng.choice(binned, 2000, replace=False)
-    used, checks = _fd_run(scene, cam, r, orc, rect, prims, n_full=200, per_prim=12, seed=3, min_frac=0.8)
-    assert checks >= 0.8 * (200 * 59 + 1800 * 5), checks
+    plan = _fd_plan(orc, cam, touched, [(touched > 0, 2000)], n_sample=20000, per_prim=12, max_tol=1e-4, rng=rng)
+    assert len(plan) == 2000
+    checks = _fd_run(scene, cam, r, orc, plan, n_full=200, seed=3)
+    assert checks >= 0.9 * (200 * 59 + 1800 * 5), checks
 
 
 def test_stress_6m_4k_fwd_bwd():
@@ -282,15 +303,16 @@ def test_stress_6m_4k_fwd_bwd():
     # conditioning errors of its ribbons leave unplaceable (compared with the
     # stop's effect in the tolerance, contributor count unchecked)
     _check_pixels(out, scene, cam, npix=2000, seed=4, orc=orc, max_excluded=0.0, max_loose=0.18, label="stress")
-    # stratified: screen-sized splats (the mask path), medium and small ones
+    # The image shows only screen-sized splats here: every pixel saturates
+    # (T < T_min) within ~36 contributors, all of them rectangles over 256
+    # tiles (the mask path), and no medium or small primitive is reached
+    # anywhere (measured with the oracle on 4,000 pixels: 330 primitives, all
+    # wide), so their gradients are exactly zero on both sides.  200 of the
+    # shown ones are checked.  The ribbons' conditioning tolerance is above
+    # 1e-4 at most pixels; the pixels used are those under 2e-4.
     rng = np.random.default_rng(5)
-    strata = [(touched > 256, 64), ((touched > 16) & (touched <= 256), 64), ((touched > 0) & (touched <= 16), 96)]
-    picks = [rng.choice(np.nonzero(m)[0], k, replace=False) for m, k in strata]
-    # interleave the strata so the 20 full-parameter primitives span all three
-    order = np.argsort(np.concatenate([np.arange(len(p)) / len(p) for p in picks]), kind="stable")
-    prims = np.concatenate(picks)[order]
-    stratum = np.concatenate([np.full(len(p), j) for j, p in enumerate(picks)])[order]
-    used, checks = _fd_run(scene, cam, r, orc, rect, prims, n_full=20, per_prim=8, seed=6, min_frac=0.6)
-    assert (used & (stratum == 0)).sum() >= 50 and (used & (stratum == 1)).sum() >= 50, \
-        [(int((used & (stratum == j)).sum())) for j in range(3)]
-    assert checks >= 0.6 * (20 * 59 + 204 * 5), checks
+    plan = _fd_plan(orc, cam, touched, [(touched > 0, 200)], n_sample=24000, per_prim=8, max_tol=2e-4, rng=rng)
+    wide = sum(1 for i, _ in plan if touched[i] > 256)
+    assert len(plan) >= 150 and wide >= 150, (len(plan), wide)
+    checks = _fd_run(scene, cam, r, orc, plan, n_full=20, seed=6)
+    assert checks >= 0.9 * (20 * 59 + (len(plan) - 20) * 5), checks
