@@ -218,11 +218,12 @@ static int c_range(float lo, float hi, int extent, int tile, int *t0, int *t1) {
 }
 
 /* One primitive through the contract.  cam: R[9] t[3] fx fy cx cy.
- * Returns 1 and fills rect {tx0,tx1,ty0,ty1} and depth bits if binned. */
+ * Returns 1 and fills rect {tx0,tx1,ty0,ty1}, depth bits and the tile-set
+ * parameters rowp (row_span) if binned. */
 static int contract_one(const float mu[3], const float ls[3], const float q[4],
                         float logit, int type, const float *cam, int W, int H,
                         int tile, float near_z, float alpha_min, float dil,
-                        int rect[4], uint32_t *dbits) {
+                        int rect[4], uint32_t *dbits, float rowp[8]) {
   const float *Rc = cam, *tc = cam + 9;
   const float fx = cam[12], fy = cam[13], cx = cam[14], cy = cam[15];
   float X = ((Rc[0] * mu[0] + Rc[1] * mu[1]) + Rc[2] * mu[2]) + tc[0];
@@ -256,6 +257,12 @@ static int contract_one(const float mu[3], const float ls[3], const float q[4],
   float iz = 1.0f / Z;
   float xz = X * iz, yz = Y * iz;
   float ctrx, ctry, hx, hy;
+  /* tile set: the footprint is the ellipse with centre (ctrx, ctry) and
+   * half extents hx, hy; its horizontal chord at height y is centred on
+   * ctrx + kslope (y - ctry) with half length wch sqrt(1 - ((y - ctry)/hy)^2),
+   * and its leftmost (rightmost) point lies at y = ctry - yoff (+ yoff) */
+  float kslope = 0.0f, wch = 0.0f, yoff = 0.0f;
+  int full = 0;
   int whole = 0;
   if (type == 1) {
     float c0 = sx * sx, c1 = sy * sy, c2 = sz * sz;
@@ -280,6 +287,23 @@ static int contract_one(const float mu[3], const float ls[3], const float q[4],
     ctry = fy * yz + cy;
     hx = sqrtf(dmax * s00);
     hy = sqrtf(dmax * s11);
+    /* det(Sigma') by Cauchy-Binet over the columns t_k = s_k J a_k (a sum of
+     * squares: no cancellation for a needle), then the chord through the
+     * centre: wch^2 = dmax det / s11 */
+    float sk[3] = {sx, sy, sz}, tX[3], tY[3];
+    for (int k = 0; k < 3; ++k) {
+      tX[k] = sk[k] * (j00 * a[k][0] + j02 * a[k][2]);
+      tY[k] = sk[k] * (j11 * a[k][1] + j12 * a[k][2]);
+    }
+    float m01 = tX[0] * tY[1] - tY[0] * tX[1];
+    float m02 = tX[0] * tY[2] - tY[0] * tX[2];
+    float m12 = tX[1] * tY[2] - tY[1] * tX[2];
+    float x2 = (tX[0] * tX[0] + tX[1] * tX[1]) + tX[2] * tX[2];
+    float y2 = (tY[0] * tY[0] + tY[1] * tY[1]) + tY[2] * tY[2];
+    float detS = ((m01 * m01 + m02 * m02) + m12 * m12) + (dil * (x2 + y2) + dil * dil);
+    kslope = s01 / s11;
+    wch = sqrtf((dmax * detS) / s11);
+    yoff = (dmax * s01) / hx;
   } else {
     float m0x = sx * a[0][0], m0y = sx * a[0][1], m0z = sx * a[0][2];
     float m1x = sy * a[1][0], m1y = sy * a[1][1], m1z = sy * a[1][2];
@@ -309,10 +333,20 @@ static int contract_one(const float mu[3], const float ls[3], const float q[4],
           ctry = fy * (yz + oy) + cy;
           hx = fx * (sqrtf(qx) / nD);
           hy = fy * (sqrtf(qy) / nD);
+          /* the image ellipse's shape from the dual conic D: Sigma_xy =
+           * fx fy (D02 D12 - D01 D22) / D22^2 and det Sigma = fx^2 fy^2
+           * dmax^2 det(M)^2 / nD^3, M = [e f m_z; ...] the re-centred splat
+           * frame (det D = -dmax^2 det(M)^2) */
+          float D01 = dmax * (e0 * f0 + e1 * f1) - e2 * f2;
+          kslope = (fx * (D02 * D12 - D01 * D22)) / (fy * qy);
+          float detM = (e0 * (f1 * Z - f2 * m1z) - e1 * (f0 * Z - f2 * m0z)) + e2 * (f0 * m1z - f1 * m0z);
+          wch = ((fx * dmax) * fabsf(detM)) / sqrtf(nD * qy);
+          yoff = (kslope * (hy * hy)) / hx;
         }
       }
     }
     if (whole) {
+      full = 1;
       /* the disc reaches the near plane: a contributing hit lies in the disc
        * (camera-space extents R) at depth in (near, Z + Rz], so x/z and y/z
        * are bounded by the extents divided by the depth bounds */
@@ -337,36 +371,118 @@ static int contract_one(const float mu[3], const float ls[3], const float q[4],
   int tx0, tx1, ty0, ty1;
   if (whole) {
     tx0 = 0; tx1 = (W - 1) / tile; ty0 = 0; ty1 = (H - 1) / tile;
+    full = 1;
   } else {
     float px = pad_f(hx), py = pad_f(hy);
     if (!c_range(ctrx - px, ctrx + px, W, tile, &tx0, &tx1)) return 0;
     if (!c_range(ctry - py, ctry + py, H, tile, &ty0, &ty1)) return 0;
   }
   rect[0] = tx0; rect[1] = tx1; rect[2] = ty0; rect[3] = ty1;
+  /* padded chord parameters: the half chord by pad_f plus 2^-10 hx for the
+   * rounding of kslope (y - ctry), the half height by pad_f */
+  float wp = pad_f(wch) + hx * 0x1p-10f, hyp = pad_f(hy);
+  float yl = ctry - yoff, yr = ctry + yoff;
+  if (!(isfinite(kslope) && isfinite(wp) && isfinite(yl) && isfinite(yr) && hyp > 0.0f && isfinite(hyp)))
+    full = 1;
+  rowp[0] = ctrx; rowp[1] = ctry; rowp[2] = kslope; rowp[3] = wp;
+  rowp[4] = hyp; rowp[5] = yl; rowp[6] = yr; rowp[7] = full ? 1.0f : 0.0f;
   return 1;
 }
 
+/* Tile columns [*c0, *c1] of tile row ty of a binned primitive's tile set:
+ * the pixel columns whose centres the padded footprint ellipse reaches in
+ * the row's band of pixel-centre heights [ty tile + 0.5, ty tile + tile -
+ * 0.5], within the rectangle.  Over the band the chord's left end is least
+ * at the band height nearest the ellipse's leftmost point (the left end is
+ * convex in y), the right end greatest nearest the rightmost point.  A
+ * primitive marked full lists every tile of its rectangle.  Returns 0 if the
+ * row lists no tile. */
+static int row_span(const float rowp[8], const int rect[4], int ty, int W, int tile, int *c0, int *c1) {
+  if (rowp[7] != 0.0f) {
+    *c0 = rect[0];
+    *c1 = rect[1];
+    return 1;
+  }
+  const float cxe = rowp[0], cye = rowp[1], kslope = rowp[2], wp = rowp[3], hyp = rowp[4];
+  const float ya = (float)(ty * tile) + 0.5f, yb = ya + (float)(tile - 1);
+  const float y1 = fminf(fmaxf(rowp[5], ya), yb), y2 = fminf(fmaxf(rowp[6], ya), yb);
+  const float d1 = y1 - cye, d2 = y2 - cye;
+  const float t1 = d1 / hyp, t2 = d2 / hyp;
+  const float r1 = fmaxf(1.0f - t1 * t1, 0.0f), r2 = fmaxf(1.0f - t2 * t2, 0.0f);
+  const float xl = (cxe + kslope * d1) - wp * sqrtf(r1);
+  const float xr = (cxe + kslope * d2) + wp * sqrtf(r2);
+  int a, b;
+  if (!c_range(xl, xr, W, tile, &a, &b)) return 0;
+  if (a < rect[0]) a = rect[0];
+  if (b > rect[1]) b = rect[1];
+  if (a > b) return 0;
+  *c0 = a;
+  *c1 = b;
+  return 1;
+}
+
+/* tiles of a binned primitive's tile set */
+static int64_t set_count(const float rowp[8], const int rect[4], int W, int tile) {
+  int64_t n = 0;
+  for (int ty = rect[2]; ty <= rect[3]; ++ty) {
+    int a, b;
+    if (row_span(rowp, rect, ty, W, tile, &a, &b)) n += b - a + 1;
+  }
+  return n;
+}
+
 /* cfg32: near, alpha_min, dilation.  rect: n x 4 (tx0,tx1,ty0,ty1), -1 if not
- * binned.  touched: tiles covered (0 if not binned). */
+ * binned.  touched: tiles in the primitive's tile set (0 if not binned; a
+ * binned primitive whose set is empty is not binned either).  rowp (n x 8,
+ * may be NULL): the tile-set parameters. */
 void orc_contract_bin(int64_t n, const float *means, const float *log_scales,
                       const float *quats, const float *logits, const uint8_t *types,
                       const float *cam, int W, int H, int tile, const float *cfg32,
-                      uint32_t *depth_bits, int32_t *rect, int64_t *touched) {
-#pragma omp parallel for schedule(static)
+                      uint32_t *depth_bits, int32_t *rect, int64_t *touched, float *rowp) {
+#pragma omp parallel for schedule(dynamic, 1024)
   for (int64_t i = 0; i < n; ++i) {
     int r[4];
     uint32_t db;
+    float rp[8];
     int ok = contract_one(means + 3 * i, log_scales + 3 * i, quats + 4 * i, logits[i],
-                          types[i], cam, W, H, tile, cfg32[0], cfg32[1], cfg32[2], r, &db);
+                          types[i], cam, W, H, tile, cfg32[0], cfg32[1], cfg32[2], r, &db, rp);
     depth_bits[i] = db;
-    if (ok) {
+    const int64_t cnt = ok ? set_count(rp, r, W, tile) : 0;
+    if (cnt > 0) {
       for (int k = 0; k < 4; ++k) rect[4 * i + k] = r[k];
-      touched[i] = (int64_t)(r[1] - r[0] + 1) * (int64_t)(r[3] - r[2] + 1);
+      touched[i] = cnt;
+      if (rowp) memcpy(rowp + 8 * i, rp, sizeof(rp));
     } else {
       for (int k = 0; k < 4; ++k) rect[4 * i + k] = -1;
       touched[i] = 0;
+      if (rowp) memset(rowp + 8 * i, 0, sizeof(rp));
     }
   }
+}
+
+/* The tile ids of every binned primitive's tile set, row by row and left to
+ * right: primitive i's at tiles[first[i] ..], touched[i] of them. */
+void orc_contract_tiles(int64_t n, const int32_t *rect, const float *rowp, const int64_t *touched,
+                        const int64_t *first, int W, int tile, uint32_t *tiles) {
+  const int TX = (W + tile - 1) / tile;
+#pragma omp parallel for schedule(dynamic, 1024)
+  for (int64_t i = 0; i < n; ++i) {
+    if (touched[i] <= 0) continue;
+    int64_t o = first[i];
+    const int *r = rect + 4 * i;
+    for (int ty = r[2]; ty <= r[3]; ++ty) {
+      int a, b;
+      if (!row_span(rowp + 8 * i, r, ty, W, tile, &a, &b)) continue;
+      for (int tx = a; tx <= b; ++tx) tiles[o++] = (uint32_t)(ty * TX + tx);
+    }
+  }
+}
+
+/* Whether tile (tx, ty) is in the tile set of a binned primitive. */
+static int set_has(const float rowp[8], const int rect[4], int tx, int ty, int W, int tile) {
+  if (ty < rect[2] || ty > rect[3] || tx < rect[0] || tx > rect[1]) return 0;
+  int a, b;
+  return row_span(rowp, rect, ty, W, tile, &a, &b) && tx >= a && tx <= b;
 }
 
 float orc_contract_exp(float x) { return orc_c_exp(x); }
@@ -386,6 +502,8 @@ typedef struct {
   double ndot;                    /* |n . mu_c| / |mu_c| */
   double bx0, bx1, by0, by1;      /* padded continuous bbox in pixels */
   int whole;
+  int rect[4];                    /* the contract's tile rectangle ... */
+  float rowp[8];                  /* ... and tile-set parameters (row_span) */
 } prim_t;
 
 typedef struct {
@@ -426,11 +544,11 @@ static void prep_prim(orc_ctx *C, int64_t i, const double *mu64, const double *l
      * rendered */
     const float ls32[3] = {(float)ls64[0], (float)ls64[1], (float)ls64[2]};
     const float q32[4] = {(float)q64[0], (float)q64[1], (float)q64[2], (float)q64[3]};
-    int rr[4];
     uint32_t dbb;
     if (!contract_one(mu32, ls32, q32, (float)logit64, type, C->cam32, C->W, C->H, 16,
-                      (float)nearz, (float)amin, (float)C->cfg[CF_DILATION], rr, &dbb))
+                      (float)nearz, (float)amin, (float)C->cfg[CF_DILATION], p->rect, &dbb, p->rowp))
       return;
+    if (set_count(p->rowp, p->rect, C->W, 16) == 0) return;
   }
   /* (the contract's binary32 centre depth is beyond the near plane; the FP64
    * depth may differ from it by a rounding, which changes nothing below) */
@@ -885,6 +1003,8 @@ static int pixel_pairs(const orc_ctx *C, int ix, int iy, contrib_t *buf, double 
     int32_t id = C->citems[k];
     const prim_t *p = &C->P[id];
     if (!p->valid || id == skip) continue;
+    /* a pair is evaluated only in the tiles of the primitive's tile set */
+    if (!set_has(p->rowp, p->rect, ix / 16, iy / 16, C->W, 16)) continue;
     if (eval_pair(C, p, px, py, &buf[cnt])) {
       buf[cnt].key = p->key;
       buf[cnt].id = id;
@@ -1055,7 +1175,8 @@ void orc_fd_render(void *ctx, void *fd, double *out, uint8_t *flags, double *tol
       int cnt = 0;
       contrib_t c;
       memset(&c, 0, sizeof(c));
-      const int listed = p->valid && eval_pair(C, p, F->pix[2 * q] + 0.5, F->pix[2 * q + 1] + 0.5, &c);
+      const int listed = p->valid && set_has(p->rowp, p->rect, F->pix[2 * q] / 16, F->pix[2 * q + 1] / 16, C->W, 16) &&
+                         eval_pair(C, p, F->pix[2 * q] + 0.5, F->pix[2 * q + 1] + 0.5, &c);
       if (listed) {
         c.key = p->key;
         c.id = (int32_t)F->i;
@@ -1097,8 +1218,9 @@ void orc_fd_end(void *fd) {
 }
 
 /* The contribution alpha exp(-d/2) (unclamped) of primitive i alone at npix
- * pixels, 0 where it does not contribute (Sec. 3.1); used to pick the pixels
- * a primitive's finite-difference check looks at. */
+ * pixels, 0 where it does not contribute (Sec. 3.1), whether or not the
+ * pixel's tile is in the primitive's tile set (the tests check with it that
+ * the tile set holds every contributing pixel). */
 void orc_pair_alpha(void *ctx, int64_t i, int64_t npix, const int32_t *pix, double *ag) {
   orc_ctx *C = (orc_ctx *)ctx;
   const prim_t *p = &C->P[i];

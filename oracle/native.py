@@ -62,7 +62,9 @@ def lib():
         L.orc_free.restype = None
         L.orc_free.argtypes = [P]
         L.orc_contract_bin.restype = None
-        L.orc_contract_bin.argtypes = [C.c_int64, P, P, P, P, P, P, C.c_int, C.c_int, C.c_int, P, P, P, P]
+        L.orc_contract_bin.argtypes = [C.c_int64, P, P, P, P, P, P, C.c_int, C.c_int, C.c_int, P, P, P, P, P]
+        L.orc_contract_tiles.restype = None
+        L.orc_contract_tiles.argtypes = [C.c_int64, P, P, P, P, C.c_int, C.c_int, P]
         L.orc_contract_exp.restype = C.c_float
         L.orc_contract_exp.argtypes = [C.c_float]
         L.orc_contract_log.restype = C.c_float
@@ -256,9 +258,11 @@ class _FDSession:
             pass
 
 
-def contract_bin(scene, cam, cfg):
+def contract_bin(scene, cam, cfg, with_rowp=False):
     """FP32 binning contract for every primitive: (depth_bits u32 (N,),
-    rect int32 (N,4) = tx0,tx1,ty0,ty1 (-1 if not binned), touched int64)."""
+    rect int32 (N,4) = tx0,tx1,ty0,ty1 (-1 if not binned), touched int64:
+    the tiles of the primitive's tile set[, rowp float32 (N,8): the tile-set
+    parameters])."""
     n = scene.n
     arrs = [np.ascontiguousarray(scene.means, np.float32),
             np.ascontiguousarray(scene.log_scales, np.float32),
@@ -270,32 +274,39 @@ def contract_bin(scene, cam, cfg):
     db = np.zeros(n, np.uint32)
     rect = np.zeros((n, 4), np.int32)
     touched = np.zeros(n, np.int64)
+    rowp = np.zeros((n, 8), np.float32)
     lib().orc_contract_bin(n, *[_p(a) for a in arrs], _p(cam16), cam.width, cam.height,
-                           cfg.tile, _p(cfg32), _p(db), _p(rect), _p(touched))
-    return db, rect, touched
+                           cfg.tile, _p(cfg32), _p(db), _p(rect), _p(touched), _p(rowp))
+    return (db, rect, touched, rowp) if with_rowp else (db, rect, touched)
+
+
+def contract_tiles(rect, rowp, touched, width, tile=16):
+    """The tile ids of every binned primitive's tile set (row by row, left to
+    right), concatenated in primitive order: (tiles (K,) uint32, first (N,)
+    int64 offsets)."""
+    touched = np.ascontiguousarray(touched, np.int64)
+    first = np.ascontiguousarray(np.cumsum(touched) - touched, np.int64)
+    K = int(touched.sum())
+    tiles = np.zeros(max(K, 1), np.uint32)
+    lib().orc_contract_tiles(len(touched), _p(np.ascontiguousarray(rect, np.int32)),
+                             _p(np.ascontiguousarray(rowp, np.float32)), _p(touched), _p(first), int(width),
+                             int(tile), _p(tiles))
+    return tiles[:K], first
 
 
 def tile_lists(scene, cam, cfg):
     """The binned instance list the contract defines: keys (K,) uint64 =
     tile_id << 32 | depth bits, vals (K,) uint32 primitive ids, sorted by
     (key, id); ranges (tiles, 2) uint32 [start, end)."""
-    db, rect, touched = contract_bin(scene, cam, cfg)
+    db, rect, touched, rowp = contract_bin(scene, cam, cfg, with_rowp=True)
     T = cfg.tile
     TX = (cam.width + T - 1) // T
     TY = (cam.height + T - 1) // T
     ids = np.nonzero(touched > 0)[0]
     cnt = touched[ids]
-    K = int(cnt.sum())
     rep = np.repeat(ids, cnt)
-    # local index of each instance within its primitive's rectangle
-    start = np.repeat(np.cumsum(cnt) - cnt, cnt)
-    loc = np.arange(K, dtype=np.int64) - start
-    r = rect[rep]
-    wdt = (r[:, 1] - r[:, 0] + 1).astype(np.int64)
-    tx = r[:, 0] + loc % wdt
-    ty = r[:, 2] + loc // wdt
-    tile = ty.astype(np.uint64) * np.uint64(TX) + tx.astype(np.uint64)
-    keys = (tile << np.uint64(32)) | db[rep].astype(np.uint64)
+    tile, _ = contract_tiles(rect, rowp, touched, cam.width, T)
+    keys = (tile.astype(np.uint64) << np.uint64(32)) | db[rep].astype(np.uint64)
     order = np.lexsort((rep, keys))
     keys = keys[order]
     vals = rep[order].astype(np.uint32)

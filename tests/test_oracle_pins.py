@@ -273,24 +273,105 @@ def test_torch_formulation_matches_c_oracle():
     np.testing.assert_allclose(r["alpha"].detach().numpy().reshape(H, W), m["alpha"], atol=1e-12)
 
 
-def test_contract_is_conservative():
+def _set_pairs(sc, cam):
+    """(primitive, tile) pairs of the contract's tile sets, encoded
+    primitive * tiles + tile, sorted."""
+    db, rect, touched, rowp = O.contract_bin(sc, cam, CFG, with_rowp=True)
+    tiles, _ = O.contract_tiles(rect, rowp, touched, cam.width)
+    ntiles = ((cam.width + 15) // 16) * ((cam.height + 15) // 16)
+    prim = np.repeat(np.arange(sc.n), touched)
+    return np.sort(prim.astype(np.int64) * ntiles + tiles), ntiles, rect, touched
+
+
+def _assert_sets_hold_contributions(sc, cam, min_pairs):
     """Every (pixel, primitive) pair whose FP64 contribution clears the 1/255
     threshold outside the ambiguity band lies in a tile of the primitive's
-    FP32 contract rectangle."""
+    FP32 tile set (and so of its rectangle)."""
+    enc, ntiles, rect, touched = _set_pairs(sc, cam)
+    yy, xx = np.mgrid[0:cam.height, 0:cam.width]
+    pix = np.stack([xx.ravel(), yy.ravel()], 1)
+    araw, ok = AR.pair_alpha(sc, cam, CFG, pix)
+    sure = ok & (araw >= CFG.alpha_min * (1 + 2e-4))
+    p_idx, g_idx = np.nonzero(sure)
+    tx = pix[p_idx, 0] // CFG.tile
+    ty = pix[p_idx, 1] // CFG.tile
+    TX = (cam.width + 15) // 16
+    r = rect[g_idx]
+    inside = (r[:, 0] <= tx) & (tx <= r[:, 1]) & (r[:, 2] <= ty) & (ty <= r[:, 3])
+    assert inside.all(), np.count_nonzero(~inside)
+    want = g_idx.astype(np.int64) * ntiles + ty * TX + tx
+    pos = np.searchsorted(enc, want)
+    found = (pos < len(enc)) & (enc[np.minimum(pos, len(enc) - 1)] == want)
+    assert found.all(), np.count_nonzero(~found)
+    assert len(p_idx) > min_pairs
+    return enc, touched
+
+
+def test_contract_is_conservative():
+    """Tile sets and rectangles hold every contributing pair (tiny scenes)."""
     for seed in (0, 1):
         sc, cam = S.tiny_scene(seed)
-        db, rect, touched = O.contract_bin(sc, cam, CFG)
-        yy, xx = np.mgrid[0:cam.height, 0:cam.width]
-        pix = np.stack([xx.ravel(), yy.ravel()], 1)
-        araw, ok = AR.pair_alpha(sc, cam, CFG, pix)
-        sure = ok & (araw >= CFG.alpha_min * (1 + 2e-4))
-        p_idx, g_idx = np.nonzero(sure)
-        tx = pix[p_idx, 0] // CFG.tile
-        ty = pix[p_idx, 1] // CFG.tile
-        r = rect[g_idx]
-        inside = (r[:, 0] <= tx) & (tx <= r[:, 1]) & (r[:, 2] <= ty) & (ty <= r[:, 3])
-        assert inside.all(), (seed, np.count_nonzero(~inside))
-        assert len(p_idx) > 1000
+        _assert_sets_hold_contributions(sc, cam, 1000)
+
+
+def test_tile_sets_are_conservative_for_needles():
+    """Heavy-tailed scales (needles and ribbons at every angle, both types):
+    the tile sets still hold every contributing pair, and drop most of the
+    rectangles' tiles."""
+    rng = np.random.default_rng(21)
+    n = 400
+    means = np.stack([rng.uniform(-0.8, 0.8, n), rng.uniform(-0.6, 0.6, n), rng.uniform(2.0, 4.0, n)], 1)
+    ls = rng.normal(-3.0, 0.3, (n, 3)) + np.where(rng.random((n, 3)) < 0.3, rng.uniform(1.0, 2.5, (n, 3)), 0.0)
+    types = (rng.random(n) < 0.5).astype(np.uint8)
+    ls[types == 0, 2] = S.SURFEL_LOG_SZ
+    q = rng.normal(size=(n, 4))
+    sh = np.zeros((n, 1, 3))
+    scene = S.Scene(means.astype(np.float32), ls.astype(np.float32), q.astype(np.float32),
+                    rng.normal(1.5, 1.0, n).astype(np.float32), sh.astype(np.float32), types, 0)
+    cam = S.pinhole(160, 128, 60.0)
+    enc, touched = _assert_sets_hold_contributions(scene, cam, 5000)
+    db, rect, _ = O.contract_bin(scene, cam, CFG)
+    b = touched > 0
+    area = (rect[b, 1] - rect[b, 0] + 1) * (rect[b, 3] - rect[b, 2] + 1)
+    assert np.all(touched[b] <= area)
+    assert touched.sum() < 0.8 * area.sum(), (touched.sum(), area.sum())
+
+
+def test_tile_set_of_a_disc_is_its_tile_rows_chords():
+    """An isotropic 3D Gaussian facing the camera: its footprint is a disc of
+    radius R = sqrt(dmax) sigma_px, and row ty of its tile set must cover the
+    tiles the disc's chord over that tile row reaches (pixel centres), and
+    no tile beyond the chord of radius R (1 + 2^-9) + 1/16."""
+    cam = S.pinhole(320, 256, 60.0)
+    for (x, y, logit, ls) in [(0.05, -0.03, 2.0, -2.2), (-0.31, 0.2, 0.3, -2.6), (0.0, 0.0, 4.0, -1.9)]:
+        z = 3.0
+        scene = S.Scene(np.array([[x, y, z]], np.float32), np.full((1, 3), ls, np.float32),
+                        np.array([[1, 0, 0, 0]], np.float32), np.array([logit], np.float32),
+                        np.zeros((1, 1, 3), np.float32), np.ones(1, np.uint8), 0)
+        db, rect, touched, rowp = O.contract_bin(scene, cam, CFG, with_rowp=True)
+        tiles, _ = O.contract_tiles(rect, rowp, touched, cam.width)
+        TX = (cam.width + 15) // 16
+        alpha = 1.0 / (1.0 + np.exp(-logit))
+        R = np.sqrt(2.0 * np.log(alpha / CFG.alpha_min)) * np.exp(ls) * cam.fx / z
+        cx, cy = cam.fx * x / z + cam.cx, cam.fy * y / z + cam.cy
+        got = {}
+        for t in tiles:
+            got.setdefault(int(t) // TX, []).append(int(t) % TX)
+
+        def chord_tiles(rad, ty):
+            # pixel centres (i + 0.5, j + 0.5) of tile row ty within radius rad
+            ys = np.arange(16 * ty, 16 * ty + 16) + 0.5
+            xs = np.arange(cam.width) + 0.5
+            inside = (xs[None] - cx) ** 2 + (ys[:, None] - cy) ** 2 <= rad * rad
+            cols = np.nonzero(inside.any(0))[0]
+            return set((cols // 16).tolist())
+
+        rows = range(int(rect[0, 2]), int(rect[0, 3]) + 1)
+        for ty in rows:
+            lo = chord_tiles(R * (1 - 1e-6), ty)
+            hi = chord_tiles(R * (1 + 2 ** -9) + 1 / 16, ty)
+            have = set(got.get(ty, []))
+            assert lo <= have <= hi, (ty, sorted(lo), sorted(have), sorted(hi))
 
 
 def test_contract_is_conservative_for_surfels_reaching_the_near_plane():
@@ -307,20 +388,10 @@ def test_contract_is_conservative_for_surfels_reaching_the_near_plane():
                     rng.normal(1.0, 1.0, n).astype(np.float32), sh.astype(np.float32),
                     np.zeros(n, np.uint8), 0)
     cam = S.pinhole(96, 80, 70.0)
-    db, rect, touched = O.contract_bin(scene, cam, CFG)
-    yy, xx = np.mgrid[0:cam.height, 0:cam.width]
-    pix = np.stack([xx.ravel(), yy.ravel()], 1)
-    araw, ok = AR.pair_alpha(scene, cam, CFG, pix)
-    sure = ok & (araw >= CFG.alpha_min * (1 + 2e-4))
-    p_idx, g_idx = np.nonzero(sure)
-    tx, ty = pix[p_idx, 0] // CFG.tile, pix[p_idx, 1] // CFG.tile
-    r = rect[g_idx]
-    inside = (r[:, 0] <= tx) & (tx <= r[:, 1]) & (r[:, 2] <= ty) & (ty <= r[:, 3])
-    assert inside.all(), np.count_nonzero(~inside)
+    _assert_sets_hold_contributions(scene, cam, 1000)
     # the branch is exercised: many discs reach the near plane
     m = means.astype(np.float64)
     assert (m[:, 2] - 3 * np.exp(ls[:, :2]).max(1) < CFG.near).sum() > 30
-    assert len(p_idx) > 1000
 
 
 def test_tile_list_structure():
@@ -337,6 +408,8 @@ def test_tile_list_structure():
         tx, ty = t % TX, t // TX
         rr = rect[vals[s:e]]
         assert np.all((rr[:, 0] <= tx) & (tx <= rr[:, 1]) & (rr[:, 2] <= ty) & (ty <= rr[:, 3]))
+    # every binned primitive is listed touched times, once per tile of its set
+    assert np.array_equal(np.bincount(vals, minlength=sc.n), touched)
 
 
 def test_contract_depth_order_matches_fp64_depth():
