@@ -63,8 +63,7 @@ def parse():
     p.add_argument("--no-stress", action="store_true")
     p.add_argument("--binning-probe", action="store_true",
                    help="time only the binning of the stress scene recipe at --prims primitives and "
-                        "--width x --height, path --wide-rects, over --steps calls (one JSON line)")
-    p.add_argument("--wide-rects", type=int, default=0, choices=[0, 1, 2])
+                        "--width x --height, over --steps calls (one JSON line)")
     p.add_argument("--serving-seconds", type=float, default=20.0)
     p.add_argument("--serving-rate", type=float, default=200.0)
     return p.parse_args()
@@ -250,16 +249,9 @@ def launches_per_step(rast, exchange_steps, steps):
     passes = (tile_bits + 7) // 8
     # 4 depth passes and the tile passes (chunk histogram, chunk scan,
     # scatter each), offsets scan (3), emit (2), range fix-up, optional
-    # 64-bit keys, the wide-rectangle path (5, launched every frame; they
-    # return at once when the frame does not take it); on tile grids up to
-    # 8192 tiles the counting placement (4) replaces emit, tile passes, range
-    # fix-up and keys.  Render forward and
-    # backward: tile work, tile order and the kernel each; preprocess
-    # forward and backward one each.
-    if tiles <= 8192:   # counting placement instead of emit and the radix tile passes
-        bin_sort = 3 * 4 + 3 + 4 + 5
-    else:
-        bin_sort = 3 * (4 + passes) + 3 + 2 + 1 + (1 if rast.keys is not None else 0) + 5
+    # 64-bit keys.  Render forward and backward: tile work, tile order and
+    # the kernel each; preprocess forward and backward one each.
+    bin_sort = 3 * (4 + passes) + 3 + 2 + 1 + (1 if rast.keys is not None else 0)
     per = 1 + bin_sort + 3 + 3 + 1
     return per * steps + exchange_steps
 
@@ -318,18 +310,19 @@ def hbm_phases(phases, n, n_binned, K, tile_passes, peak, peak_src):
     """Achieved HBM bandwidth of the memory-bound phases from their
     algorithmic bytes (each array read or written once) and their CUDA-event
     times.  preprocess: 45 B read + 16 B written per primitive, + 192 B of SH
-    read + 80 B of record written per binned one.  preprocess_bwd: 385 B read
-    per binned primitive (parameters, SH, record, record gradient) + 4 B per
-    culled one, 236 B written per primitive.  bin_sort: four depth passes over
-    the binned primitives (4 B histogram read + 8 B read + 8 B written) and
-    two scans (8 B) and the emit's reads (12 B), per instance the emit (8 B
-    written) and each tile pass (4 B histogram read + 8 B read + 8 B
-    written, the last 4 B written)."""
+    read + 80 B of record and 32 B of tile-set parameters written per binned
+    one.  preprocess_bwd: 385 B read per binned primitive (parameters, SH,
+    record, record gradient) + 4 B per culled one, 236 B written per
+    primitive.  bin_sort: four depth passes over the binned primitives (4 B
+    histogram read + 8 B read + 8 B written) and two scans (8 B) and the
+    emit's reads (id, offset, rectangle, count, tile set: 48 B), per instance
+    the emit (8 B written) and each tile pass (4 B histogram read + 8 B read
+    + 8 B written, the last 4 B written)."""
     nb, nc = n_binned, n - n_binned
     byts = {
-        "preprocess": 61 * n + 272 * nb,
+        "preprocess": 61 * n + 304 * nb,
         "preprocess_bwd": 385 * nb + 4 * nc + 236 * n,
-        "bin_sort": (4 * 20 + 16 + 12) * nb + 8 * K + tile_passes * 20 * K - 4 * K,
+        "bin_sort": (4 * 20 + 16 + 48) * nb + 8 * K + tile_passes * 20 * K - 4 * K,
     }
     out = {}
     for k, b in byts.items():
@@ -516,7 +509,7 @@ def binning_probe(args):
     dev = torch.device("cuda", 0)
     scene = S.surface_scene(args.n, seed=4, frac3d=0.1, ls_loc=-4.5, ls_scale=0.8, heavy_df=3)
     cam = S.orbit_camera(30.0, 20.0, 3.0, args.width, args.height, 50.0)
-    cfg = dataclasses.replace(S.RenderConfig(), wide_rects=args.wide_rects)
+    cfg = S.RenderConfig()
     r = Rasterizer(dev)
     st = SceneTensors.from_numpy(scene, dev)
     r.forward(st, cam, cfg)
@@ -532,10 +525,10 @@ def binning_probe(args):
         ts.append(e0.elapsed_time(e1))
     r.check()
     t = r.touched[: scene.n].cpu().numpy().astype(np.int64)
-    wide = t > 256
+    big = t > 256
     print(json.dumps({"binning_probe": {"prims": args.n, "width": args.width, "height": args.height,
-                                        "wide_rects": args.wide_rects, "instances_K": r.last_K,
-                                        "wide_prims": int(wide.sum()), "wide_instances": int(t[wide].sum()),
+                                        "instances_K": r.last_K, "prims_over_256_tiles": int(big.sum()),
+                                        "their_instances": int(t[big].sum()),
                                         "bin_sort_ms": round(statistics.median(ts), 4)}}), flush=True)
 
 

@@ -98,10 +98,6 @@ typedef struct {
   float dilation;  /* added to the diagonal of the projected 3D covariance */
   float bg[3];     /* background colour */
   int32_t tile;    /* tile edge in pixels; this build supports 16 only */
-  int32_t wide_rects; /* binning of rectangles over 256 tiles: 0 = the device picks,
-                         per frame, the counting path when they carry most of the
-                         instances; 1 = always the counting path; 2 = always the
-                         radix sort.  The lists are the same either way. */
 } hgs_config;
 
 /* Per-primitive output of hgs_preprocess (caller-allocated, n rows each):
@@ -110,13 +106,18 @@ typedef struct {
  *              box); its content is private to the library and valid for one
  *              camera.
  *   depth_key  [n] uint32: bits of the binary32 camera-space centre depth.
- *   rect       [n,4] uint16: covered tile rectangle tx0, tx1, ty0, ty1.
- *   touched    [n] uint32: tiles covered (0 = not binned). */
+ *   rect       [n,4] uint16: tile rectangle tx0, tx1, ty0, ty1 bounding the
+ *              footprint (the region where alpha exp(-d/2) >= alpha_min).
+ *   touched    [n] uint32: tiles in the primitive's tile set (0 = not binned).
+ *   tileset    [n,8] float, A16: the tile set's parameters, private to the
+ *              library: per tile row of the rectangle, the columns whose
+ *              pixel centres the footprint ellipse can reach. */
 typedef struct {
   float *rec;
   uint32_t *depth_key;
   uint16_t *rect;
   uint32_t *touched;
+  float *tileset;
 } hgs_projected;
 
 /* Output of hgs_bin_sort.
@@ -197,8 +198,12 @@ int hgs_check(const int32_t *dev_err, int32_t *host_err, hgs_stream_t stream);
  *          inverted and re-centred so Eq. 14's (u, v) are affine functions
  *          of the pixel offset up to one perspective divide;
  * the scale-modulated opacity for t = 0 (Eqs. 6-7), the normal, and the
- * binning contract: depth key and covered tile rectangle from one fixed
+ * binning contract: depth key, tile rectangle and tile set from one fixed
  * sequence of binary32 operations (exact rounding, no fused multiply-add).
+ * The tile set lists, per tile row, the tile columns that the footprint's
+ * ellipse (Eq. 1 at alpha exp(-d/2) = alpha_min, Sec. 3.1) reaches over the
+ * row's pixel-centre heights, padded for rounding; a surfel whose disc
+ * reaches the near plane keeps its whole rectangle.
  * Errors: HGS_ERR_INVALID_ARG for NULL pointers, n < 0, sh_degree outside
  * 0..3, a camera with non-positive size or focal, tile != 16 (UNSUPPORTED). */
 int hgs_preprocess(const hgs_scene *scene, const hgs_camera *cam, const hgs_config *cfg,
@@ -211,19 +216,16 @@ int hgs_preprocess(const hgs_scene *scene, const hgs_camera *cam, const hgs_conf
 int hgs_bin_sort_workspace(int64_t n, int64_t capacity, int32_t tiles, size_t *bytes);
 
 /* hgs_bin_sort -- duplicate each binned primitive into the tiles of its
- * rectangle and order the instances by the 64-bit key tile << 32 | depth key,
+ * tile set and order the instances by the 64-bit key tile << 32 | depth key,
  * ties by primitive id.  Implemented as an LSD radix sort whose low (depth)
  * digits are sorted once per primitive and whose high (tile) digits are
  * sorted per instance; the resulting order is that of the 64-bit key.
- * Rectangles over 256 tiles may instead be listed from coverage masks in
- * depth order and merged with the sorted rest (cfg->wide_rects); the output
- * is the same.
  * If K > capacity: writes K to out->d_count, stores HGS_ERR_CAPACITY in
  * *dev_err, zeroes the ranges, and writes no instance (no out-of-bounds
  * write).  The caller grows the buffers and calls again.
  * ws: device workspace of at least hgs_bin_sort_workspace() bytes, A16.
  * Errors: INVALID_ARG for NULL pointers, ws_bytes too small, capacity
- * outside 0 .. HGS_MAX_CAPACITY, cfg->wide_rects outside 0..2. */
+ * outside 0 .. HGS_MAX_CAPACITY. */
 int hgs_bin_sort(int64_t n, const hgs_projected *proj, const hgs_camera *cam,
                  const hgs_config *cfg, void *ws, size_t ws_bytes, int64_t capacity,
                  hgs_binning *out, int32_t *dev_err, hgs_stream_t stream);
@@ -264,14 +266,11 @@ int hgs_alu_probe(int32_t kind, int32_t blocks, int32_t iters, float *d_out, dou
  * caller still owns proj and out); the sort's scratch is a library-owned
  * device array of HGS_BIN_SORT_STATIC_BYTES that every GPU loading the
  * library reserves until the process exits.
- * It always sorts every instance by radix passes (rectangles over 256 tiles
- * included, whatever cfg->wide_rects says), so its scratch holds those
- * passes' buffers only.
  * Limits: returns HGS_ERR_INVALID_ARG, launching nothing, for a capacity
  * outside 0 .. HGS_MAX_CAPACITY and when that scratch
- * (hgs_bin_sort_workspace(n, capacity, tiles) less the wide-rectangle
- * buffers) exceeds HGS_BIN_SORT_STATIC_BYTES (for example n = 1M with
- * capacity 3.5M fits; the 3M-primitive scene does not).  The first call on each device looks up the array's device address
+ * (hgs_bin_sort_workspace(n, capacity, tiles)) exceeds
+ * HGS_BIN_SORT_STATIC_BYTES (for example n = 1M with capacity 3.5M fits; the
+ * 3M-primitive scene does not).  The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
  * before any stream capture.  All calls share the one array and it keeps the
  * previous call's contents (the kernels clear what must start at zero): calls
@@ -333,7 +332,7 @@ int hgs_render_batch_workspace(int nreq, const hgs_request *reqs, int64_t capaci
  * the background (nothing out of bounds): grow and retry.
  * Errors: INVALID_ARG for nreq outside 1..HGS_MAX_BATCH, a bad scene, camera
  * or output pointer, a too small workspace; UNSUPPORTED for tile != 16 or a
- * stacked grid over 65535 tile rows. */
+ * stacked grid over 32767 tile rows. */
 int hgs_render_batch(int nreq, const hgs_request *reqs, const hgs_config *cfg, void *ws, size_t ws_bytes,
                      int64_t capacity, int64_t *d_count, int32_t *dev_err, hgs_stream_t stream);
 

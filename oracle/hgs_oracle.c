@@ -380,16 +380,18 @@ static int contract_one(const float mu[3], const float ls[3], const float q[4],
   rect[0] = tx0; rect[1] = tx1; rect[2] = ty0; rect[3] = ty1;
   /* padded chord parameters: the half chord by pad_f plus 2^-10 hx for the
    * rounding of kslope (y - ctry), the half height by pad_f */
-  float wp = pad_f(wch) + hx * 0x1p-10f, hyp = pad_f(hy);
+  float wp = pad_f(wch) + hx * 0x1p-10f, hyp = pad_f(hy), ihy = 1.0f / hyp;
   float yl = ctry - yoff, yr = ctry + yoff;
-  if (!(isfinite(kslope) && isfinite(wp) && isfinite(yl) && isfinite(yr) && hyp > 0.0f && isfinite(hyp)))
+  if (!(isfinite(kslope) && isfinite(wp) && isfinite(yl) && isfinite(yr) && hyp > 0.0f && isfinite(ihy)))
     full = 1;
   rowp[0] = ctrx; rowp[1] = ctry; rowp[2] = kslope; rowp[3] = wp;
-  rowp[4] = hyp; rowp[5] = yl; rowp[6] = yr; rowp[7] = full ? 1.0f : 0.0f;
+  rowp[4] = ihy; rowp[5] = yl; rowp[6] = yr; rowp[7] = full ? 1.0f : 0.0f;
   return 1;
 }
 
-/* Tile columns [*c0, *c1] of tile row ty of a binned primitive's tile set:
+/* rowp: chord centre x and y, slope, padded half chord, reciprocal of the
+ * padded half height, heights of the leftmost and rightmost points, full.
+ * Tile columns [*c0, *c1] of tile row ty of a binned primitive's tile set:
  * the pixel columns whose centres the padded footprint ellipse reaches in
  * the row's band of pixel-centre heights [ty tile + 0.5, ty tile + tile -
  * 0.5], within the rectangle.  Over the band the chord's left end is least
@@ -403,11 +405,11 @@ static int row_span(const float rowp[8], const int rect[4], int ty, int W, int t
     *c1 = rect[1];
     return 1;
   }
-  const float cxe = rowp[0], cye = rowp[1], kslope = rowp[2], wp = rowp[3], hyp = rowp[4];
+  const float cxe = rowp[0], cye = rowp[1], kslope = rowp[2], wp = rowp[3], ihy = rowp[4];
   const float ya = (float)(ty * tile) + 0.5f, yb = ya + (float)(tile - 1);
   const float y1 = fminf(fmaxf(rowp[5], ya), yb), y2 = fminf(fmaxf(rowp[6], ya), yb);
   const float d1 = y1 - cye, d2 = y2 - cye;
-  const float t1 = d1 / hyp, t2 = d2 / hyp;
+  const float t1 = d1 * ihy, t2 = d2 * ihy;
   const float r1 = fmaxf(1.0f - t1 * t1, 0.0f), r2 = fmaxf(1.0f - t2 * t2, 0.0f);
   const float xl = (cxe + kslope * d1) - wp * sqrtf(r1);
   const float xr = (cxe + kslope * d2) + wp * sqrtf(r2);

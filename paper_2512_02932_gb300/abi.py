@@ -44,11 +44,11 @@ class hgs_config(C.Structure):
     _fields_ = [("near_z", C.c_float), ("alpha_min", C.c_float), ("alpha_max", C.c_float),
                 ("T_min", C.c_float), ("lambda_z", C.c_float), ("theta_z", C.c_float),
                 ("T_z", C.c_float), ("dilation", C.c_float), ("bg", C.c_float * 3),
-                ("tile", C.c_int32), ("wide_rects", C.c_int32)]
+                ("tile", C.c_int32)]
 
 
 class hgs_projected(C.Structure):
-    _fields_ = [("rec", P), ("depth_key", P), ("rect", P), ("touched", P)]
+    _fields_ = [("rec", P), ("depth_key", P), ("rect", P), ("touched", P), ("tileset", P)]
 
 
 class hgs_binning(C.Structure):

@@ -38,7 +38,6 @@ int cam_to_kernel(const hgs_camera *c, CamK *k) {
 int cfg_to_kernel(const hgs_config *c, CfgK *k) {
   if (!c) return HGS_ERR_INVALID_ARG;
   if (c->tile != kTile) return HGS_ERR_UNSUPPORTED;
-  if (c->wide_rects < 0 || c->wide_rects > 2) return HGS_ERR_INVALID_ARG;
   if (!(c->alpha_min > 0.f) || !(c->alpha_max >= c->alpha_min) || !(c->alpha_max < 1.f) ||
       !(c->T_min > 0.f) || !(c->T_z > 0.f) || !(c->near_z > 0.f) || !(c->dilation >= 0.f) ||
       !std::isfinite(c->lambda_z) || !std::isfinite(c->theta_z))
@@ -64,8 +63,9 @@ int scene_ok(const hgs_scene *s) {
 int proj_ok(const hgs_projected *p, int64_t n) {
   if (!p) return HGS_ERR_INVALID_ARG;
   if (n == 0) return HGS_OK;
-  if (!p->rec || !p->depth_key || !p->rect || !p->touched) return HGS_ERR_INVALID_ARG;
-  if (!aligned16(p->rec) || (reinterpret_cast<uintptr_t>(p->rect) & 7u)) return HGS_ERR_INVALID_ARG;
+  if (!p->rec || !p->depth_key || !p->rect || !p->touched || !p->tileset) return HGS_ERR_INVALID_ARG;
+  if (!aligned16(p->rec) || !aligned16(p->tileset) || (reinterpret_cast<uintptr_t>(p->rect) & 7u))
+    return HGS_ERR_INVALID_ARG;
   return HGS_OK;
 }
 
@@ -83,6 +83,7 @@ PrepArgs prep_args(const hgs_scene *s, const CamK &ck, const CfgK &fk, const hgs
   a.logits = s->opacity_logits; a.sh = s->sh; a.types = s->types; a.n = s->n;
   a.cam = ck; a.cfg = fk;
   a.rec = p->rec; a.depth_key = p->depth_key; a.rect = p->rect; a.touched = p->touched;
+  a.tileset = p->tileset;
   return a;
 }
 
@@ -102,7 +103,6 @@ void hgs_default_config(hgs_config *c) {
   c->dilation = 0.0f;
   c->bg[0] = c->bg[1] = c->bg[2] = 0.0f;
   c->tile = kTile;
-  c->wide_rects = 0;
 }
 
 const char *hgs_status_string(int s) {
@@ -146,7 +146,7 @@ int hgs_preprocess(const hgs_scene *scene, const hgs_camera *cam, const hgs_conf
 int hgs_bin_sort_workspace(int64_t n, int64_t capacity, int32_t tiles, size_t *bytes) {
   if (!bytes || n < 0 || capacity < 0 || capacity > kMaxCapacity || tiles <= 0) return HGS_ERR_INVALID_ARG;
   BinWorkspace ws;
-  *bytes = bin_layout(nullptr, n, capacity, tiles, &ws);
+  *bytes = bin_layout(nullptr, n, capacity, &ws);
   return HGS_OK;
 }
 
@@ -165,18 +165,18 @@ int hgs_bin_sort(int64_t n, const hgs_projected *proj, const hgs_camera *cam, co
   if ((st = proj_ok(proj, n)) != HGS_OK) return st;
   if (!ws || !aligned16(ws)) return HGS_ERR_INVALID_ARG;
   BinWorkspace w;
-  const size_t need = bin_layout(ws, n, capacity, ck.TX * ck.TY, &w);
+  const size_t need = bin_layout(ws, n, capacity, &w);
   if (ws_bytes < need) return HGS_ERR_INVALID_ARG;
   BinArgs a;
   a.n = n;
   a.capacity = capacity;
-  a.wide_cfg = cfg->wide_rects;
   a.tiles = ck.TX * ck.TY;
   a.tile_bits = tile_bits_for(a.tiles);
   a.TX = ck.TX;
   a.depth_key = proj->depth_key;
   a.touched = proj->touched;
   a.rect = proj->rect;
+  a.tileset = proj->tileset;
   a.vals = out->vals;
   a.keys = out->keys;
   a.ranges = out->ranges;
@@ -457,7 +457,7 @@ namespace {
 struct BatchLayout {
   int64_t total_n;
   int TXmax, rows;
-  size_t off_rec, off_key, off_rect, off_touched, off_vals, off_ranges, off_sort, bytes;
+  size_t off_rec, off_key, off_rect, off_touched, off_tileset, off_vals, off_ranges, off_sort, bytes;
 };
 
 size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -476,7 +476,7 @@ int batch_layout(int nreq, const hgs_request *reqs, int64_t capacity, BatchLayou
     rows += (c.height + kTile - 1) / kTile;
   }
   if (n >= (int64_t(1) << 31)) return HGS_ERR_INVALID_ARG;
-  if (rows > 65535) return HGS_ERR_UNSUPPORTED;
+  if (rows > 32767) return HGS_ERR_UNSUPPORTED;
   L->total_n = n;
   L->TXmax = TXmax;
   L->rows = rows;
@@ -486,11 +486,12 @@ int batch_layout(int nreq, const hgs_request *reqs, int64_t capacity, BatchLayou
   L->off_key = off; off += al256(nn * 4);
   L->off_rect = off; off += al256(nn * 8);
   L->off_touched = off; off += al256(nn * 4);
+  L->off_tileset = off; off += al256(nn * 32);
   L->off_vals = off; off += al256(cc * 4);
   L->off_ranges = off; off += al256((size_t)TXmax * rows * 8);
   L->off_sort = off;
   BinWorkspace w;
-  off += al256(bin_layout(nullptr, n, capacity, TXmax * rows, &w));
+  off += al256(bin_layout(nullptr, n, capacity, &w));
   L->bytes = off;
   return HGS_OK;
 }
@@ -521,6 +522,7 @@ int hgs_render_batch(int nreq, const hgs_request *reqs, const hgs_config *cfg, v
   uint32_t *key = reinterpret_cast<uint32_t *>(base + L.off_key);
   uint16_t *rect = reinterpret_cast<uint16_t *>(base + L.off_rect);
   uint32_t *touched = reinterpret_cast<uint32_t *>(base + L.off_touched);
+  float *tileset = reinterpret_cast<float *>(base + L.off_tileset);
   uint32_t *vals = reinterpret_cast<uint32_t *>(base + L.off_vals);
   uint32_t *ranges = reinterpret_cast<uint32_t *>(base + L.off_ranges);
   BatchPrepArgs bp;
@@ -541,6 +543,7 @@ int hgs_render_batch(int nreq, const hgs_request *reqs, const hgs_config *cfg, v
     p.depth_key = key + prim;
     p.rect = rect + (size_t)prim * 4;
     p.touched = touched + prim;
+    p.tileset = tileset + (size_t)prim * 8;
     bp.req[r] = prep_args(&q.scene, ck, fk, &p);
     bp.deg[r] = q.scene.sh_degree;
     bp.row_off[r] = row;
@@ -563,17 +566,17 @@ int hgs_render_batch(int nreq, const hgs_request *reqs, const hgs_config *cfg, v
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   launch_preprocess_batch(bp, s);
   BinWorkspace w;
-  bin_layout(base + L.off_sort, L.total_n, capacity, L.TXmax * L.rows, &w);
+  bin_layout(base + L.off_sort, L.total_n, capacity, &w);
   BinArgs b;
   b.n = L.total_n;
   b.capacity = capacity;
-  b.wide_cfg = cfg->wide_rects;
   b.tiles = L.TXmax * L.rows;
   b.tile_bits = tile_bits_for(b.tiles);
   b.TX = L.TXmax;
   b.depth_key = key;
   b.touched = touched;
   b.rect = rect;
+  b.tileset = tileset;
   b.vals = vals;
   b.keys = nullptr;
   b.ranges = ranges;

@@ -61,30 +61,30 @@ extern "C" int hgs_bin_sort_static(int64_t n, const hgs_projected *proj, const h
   if (cfg->tile != hgs::kTile) return HGS_ERR_UNSUPPORTED;
   if (cam->width <= 0 || cam->height <= 0 || cam->width > 16384 || cam->height > 16384)
     return HGS_ERR_INVALID_ARG;
-  if (n > 0 && (!proj->depth_key || !proj->touched || !proj->rect)) return HGS_ERR_INVALID_ARG;
-  if (cfg->wide_rects < 0 || cfg->wide_rects > 2) return HGS_ERR_INVALID_ARG;
+  if (n > 0 && (!proj->depth_key || !proj->touched || !proj->rect || !proj->tileset)) return HGS_ERR_INVALID_ARG;
+  if (n > 0 && ((reinterpret_cast<uintptr_t>(proj->tileset) & 15u) || (reinterpret_cast<uintptr_t>(proj->rect) & 7u)))
+    return HGS_ERR_INVALID_ARG;
   const int TX = (cam->width + hgs::kTile - 1) / hgs::kTile;
   const int TY = (cam->height + hgs::kTile - 1) / hgs::kTile;
   hgs::BinWorkspace probe;
-  // the fixed array holds the radix path's buffers only: no wide-rectangle path
-  if (hgs::bin_layout(nullptr, n, capacity, TX * TY, &probe, false) > kStaticScratchBytes)
+  if (hgs::bin_layout(nullptr, n, capacity, &probe) > kStaticScratchBytes)
     return HGS_ERR_INVALID_ARG;
   void *scratch = scratch_on_current_device();
   if (!scratch) return HGS_ERR_CUDA;
   hgs::BinWorkspace w;
-  hgs::bin_layout(scratch, n, capacity, TX * TY, &w, false);
+  hgs::bin_layout(scratch, n, capacity, &w);
   int tile_bits = 1;
   while ((1 << tile_bits) < TX * TY) ++tile_bits;
   hgs::BinArgs a;
   a.n = n;
   a.capacity = capacity;
-  a.wide_cfg = cfg->wide_rects;
   a.tiles = TX * TY;
   a.tile_bits = tile_bits;
   a.TX = TX;
   a.depth_key = proj->depth_key;
   a.touched = proj->touched;
   a.rect = proj->rect;
+  a.tileset = proj->tileset;
   a.vals = out->vals;
   a.keys = out->keys;
   a.ranges = out->ranges;

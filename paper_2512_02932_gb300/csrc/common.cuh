@@ -106,6 +106,74 @@ __device__ __forceinline__ float contract_log(float x) {
   return cadd(cmul(fe, 0x1.62e4p-1f), cadd(cmul(fe, 0x1.7f7d1cp-20f), lnm));
 }
 
+// Pixel boxes and tile sets of the contract.
+__device__ __forceinline__ float pad_extent(float r) {
+  return cadd(cmul(r, 1.0009765625f), 0.015625f);
+}
+
+// pixel-centre coverage of [lo, hi] along an axis of `extent` pixels ->
+// inclusive tile range; false if no pixel centre is covered
+__device__ __forceinline__ bool pixel_tiles(float lo, float hi, int extent, int *t0, int *t1) {
+  float flo = csub(lo, 0.5f), fhi = csub(hi, 0.5f);
+  if (!(flo <= fhi)) return false;
+  flo = fmaxf(flo, -1.0f);
+  fhi = fminf(fhi, (float)extent);
+  int p0 = (int)ceilf(flo), p1 = (int)floorf(fhi);
+  if (p0 < 0) p0 = 0;
+  if (p1 > extent - 1) p1 = extent - 1;
+  if (p0 > p1) return false;
+  *t0 = p0 / kTile;
+  *t1 = p1 / kTile;
+  return true;
+}
+
+// Tile-set parameters of a binned primitive (two float4, written by the
+// preprocess): t0 = (centre x, centre y, chord slope k, padded half chord
+// w), t1 = (1 / padded half height h, y of the leftmost point, y of the
+// rightmost point, flags).  The footprint's chord at height y is centred on
+// x + k (y - centre y) with half length w sqrt(1 - ((y - centre y) / h)^2).
+// flags (int bits): bit 0 = the whole rectangle, bits 1-15 = the tile-row
+// offset of the primitive's image in a stacked grid, bits 16-31 = the image
+// width in pixels.
+struct TileSet {
+  float4 t0, t1;
+};
+__device__ __forceinline__ uint32_t tileset_flags(bool full, int row_off, int width) {
+  return (full ? 1u : 0u) | ((uint32_t)row_off << 1) | ((uint32_t)width << 16);
+}
+
+// Tile columns [c0, c1] of (stacked) tile row ty of a primitive's tile set,
+// within its rectangle columns [tx0, tx1]: the pixel columns whose centres
+// the padded ellipse reaches in the row's band of pixel-centre heights
+// [16 ty + 0.5, 16 ty + 15.5].  Over the band the chord's left end is least
+// at the height nearest the leftmost point (the left end is convex in y) and
+// the right end greatest nearest the rightmost point.  false: no tile.
+__device__ __forceinline__ bool row_span(const TileSet &s, int ty, int tx0, int tx1, int *c0, int *c1) {
+  const uint32_t fl = __float_as_uint(s.t1.w);
+  if (fl & 1u) {
+    *c0 = tx0;
+    *c1 = tx1;
+    return true;
+  }
+  const int lty = ty - (int)((fl >> 1) & 0x7fffu);
+  const int width = (int)(fl >> 16);
+  const float ya = cadd((float)(lty * kTile), 0.5f), yb = cadd(ya, (float)(kTile - 1));
+  const float y1 = fminf(fmaxf(s.t1.y, ya), yb), y2 = fminf(fmaxf(s.t1.z, ya), yb);
+  const float d1 = csub(y1, s.t0.y), d2 = csub(y2, s.t0.y);
+  const float q1 = cmul(d1, s.t1.x), q2 = cmul(d2, s.t1.x);
+  const float r1 = fmaxf(csub(1.0f, cmul(q1, q1)), 0.0f), r2 = fmaxf(csub(1.0f, cmul(q2, q2)), 0.0f);
+  const float xl = csub(cadd(s.t0.x, cmul(s.t0.z, d1)), cmul(s.t0.w, csqrt(r1)));
+  const float xr = cadd(cadd(s.t0.x, cmul(s.t0.z, d2)), cmul(s.t0.w, csqrt(r2)));
+  int a, b;
+  if (!pixel_tiles(xl, xr, width, &a, &b)) return false;
+  a = max(a, tx0);
+  b = min(b, tx1);
+  if (a > b) return false;
+  *c0 = a;
+  *c1 = b;
+  return true;
+}
+
 // ---------------------------------------------------------------------------
 // fast hardware approximations for the per-pair loops
 // ---------------------------------------------------------------------------

@@ -15,6 +15,7 @@ struct PrepArgs {
   uint32_t *depth_key;
   uint16_t *rect;
   uint32_t *touched;
+  float *tileset;  // [n][8]: TileSet of each binned primitive
 };
 
 struct PrepGradArgs {
@@ -50,30 +51,15 @@ int launch_preprocess_bwd_fdo(const PrepArgs &a, const PrepGradFdoArgs &g, int d
 // ---------------------------------------------------------------------------
 struct BinWorkspace {
   // carved from the caller's workspace by bin_layout()
-  int64_t *counters;     // [16]: 0 = n_visible, 1 = K, 2 = overflow flag, 3 = deferred rects, 4..8 wide path
-  uint32_t *tile_ctr;    // [16] tile counters of the look-back passes
+  int64_t *counters;     // [16]: 0 = binned primitives, 1 = K, 2 = overflow flag, 3 = deferred primitives
   uint32_t *hist;        // [8][256] global digit histograms (4 depth + up to 4 tile passes)
-  size_t head_bytes;     // counters .. hist, cleared at the start of every sort
+  size_t head_bytes;     // counters and hist, cleared at the start of every sort
   uint64_t *blk;         // [kSortBlocks] scan partials
   uint32_t *dk[2], *dv[2];  // depth sort ping-pong, [n] each
   uint32_t *offs;        // [n] instance offsets in depth order
   uint32_t *tk[2];       // tile keys ping-pong, [capacity]
   uint32_t *tv;          // tile vals scratch, [capacity]
   uint32_t *chist;       // [256][kSortBlocks] per-chunk digit counts / offsets of a pass
-  // wide-rectangle path
-  int64_t wide_max;      // most wide primitives it takes
-  uint32_t *wide_j;      // [wide_max] their depth-order positions
-  uint32_t *wide_id;     // [wide_max] their primitive ids
-  size_t mask_words;
-  uint32_t *masks;       // [mask_words] coverage masks
-  uint32_t *wide_cnt;    // [16][tiles] per (word range, tile) counts
-  uint32_t *wide_len;    // [tiles] list lengths
-  uint32_t *small_ranges;  // [tiles][2]
-  // counting placement (tile grids up to kCountTiles; null otherwise)
-  uint32_t *count_tab;   // [count_chunks][tiles] per-(chunk, tile) counts -> offsets
-  uint32_t *count_tot;   // [tiles] per-tile totals -> list starts
-  uint32_t *count_bounds;  // [kCountMaxChunks + 1] first depth position of each chunk
-  int count_chunks;      // chunks the table holds
   size_t bytes;
 };
 
@@ -82,32 +68,18 @@ struct BinWorkspace {
 // buffer size computed from a capacity can wrap.
 constexpr int64_t kMaxCapacity = HGS_MAX_CAPACITY;
 constexpr int kSortBlocks = 1024;  // fixed grid of every sort/scan pass
-// Tile grids up to kCountTiles tiles place the instances by counting (one
-// warp per chunk of the depth order with a counter per tile in shared
-// memory) instead of emitting them and radix-sorting the tile digits.
-constexpr int kCountTiles = 8192;
-constexpr int kCountSmem = 200 * 1024;    // shared memory of one placement block
-constexpr int kCountMaxSMs = 160;         // SMs the chunk table is sized for
-constexpr int kCountMaxChunks = kCountMaxSMs * 16;
-// a chunk's work, in instances: its instances + kCountPrimCost per primitive
-constexpr uint64_t kCountPrimCost = 32;
-// warps of a placement block: each holds a counter per tile
-__host__ __device__ inline int count_warps(int tiles) {
-  const int w = kCountSmem / (4 * (tiles > 0 ? tiles : 1));
-  return w < 1 ? 1 : (w > 16 ? 16 : w);
-}
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 8;      // per thread per tile (tile = 2048 keys)
 
 // wide = false reserves nothing for the wide-rectangle path (it is then never taken)
-size_t bin_layout(void *base, int64_t n, int64_t capacity, int tiles, BinWorkspace *ws, bool wide = true);
+size_t bin_layout(void *base, int64_t n, int64_t capacity, BinWorkspace *ws);
 
 struct BinArgs {
   int64_t n, capacity;
   int tiles, tile_bits, TX;
-  int wide_cfg;  // rectangles over 256 tiles: 0 = path chosen per frame, 1 = counting path, 2 = radix sort
   const uint32_t *depth_key, *touched;
   const uint16_t *rect;
+  const float *tileset;
   uint32_t *vals;
   uint64_t *keys;   // optional
   uint32_t *ranges;

@@ -32,25 +32,14 @@ struct Contract {
   uint32_t dbits;
   int tx0, tx1, ty0, ty1;
   float bx0, bx1, by0, by1;  // padded pixel box of the alpha >= alpha_min region
+  // tile set: the footprint ellipse's centre, chord slope, padded half chord
+  // and reciprocal padded half height, heights of its leftmost and rightmost
+  // points; full =
+  // the whole rectangle (a surfel reaching the near plane, or a degenerate
+  // ellipse)
+  float ctrx, ctry, kslope, wp, ihy, yl, yr;
+  bool full;
 };
-
-__device__ __forceinline__ float pad_extent(float r) {
-  return cadd(cmul(r, 1.0009765625f), 0.015625f);
-}
-
-__device__ __forceinline__ bool pixel_tiles(float lo, float hi, int extent, int *t0, int *t1) {
-  float flo = csub(lo, 0.5f), fhi = csub(hi, 0.5f);
-  if (!(flo <= fhi)) return false;
-  flo = fmaxf(flo, -1.0f);
-  fhi = fminf(fhi, (float)extent);
-  int p0 = (int)ceilf(flo), p1 = (int)floorf(fhi);
-  if (p0 < 0) p0 = 0;
-  if (p1 > extent - 1) p1 = extent - 1;
-  if (p0 > p1) return false;
-  *t0 = p0 / kTile;
-  *t1 = p1 / kTile;
-  return true;
-}
 
 // The contract: a fixed sequence of correctly rounded binary32 operations.
 // Returns true if the primitive is binned.
@@ -96,7 +85,11 @@ __device__ bool run_contract(const float mu[3], const float ls[3], const float q
   o.yz = cmul(o.Y, o.iz);
   const float fx = c.fx, fy = c.fy, cx = c.cx, cy = c.cy;
   float ctrx = 0.f, ctry = 0.f, hx = 0.f, hy = 0.f;
-  bool whole = false;
+  // tile set: the ellipse's horizontal chord at height y is centred on
+  // ctrx + kslope (y - ctry) with half length wch sqrt(1 - ((y - ctry)/hy)^2);
+  // its leftmost (rightmost) point lies at y = ctry - yoff (+ yoff)
+  float kslope = 0.f, wch = 0.f, yoff = 0.f;
+  bool whole = false, full = false;
   if (type == 1) {
     const float c0 = cmul(o.s[0], o.s[0]), c1 = cmul(o.s[1], o.s[1]), c2 = cmul(o.s[2], o.s[2]);
     float V[3][3];
@@ -122,6 +115,25 @@ __device__ bool run_contract(const float mu[3], const float ls[3], const float q
     ctry = cadd(cmul(fy, o.yz), cy);
     hx = csqrt(cmul(o.dmax, o.s00));
     hy = csqrt(cmul(o.dmax, o.s11));
+    // det(Sigma') by Cauchy-Binet over the columns t_k = s_k J a_k (a sum of
+    // squares: no cancellation for a needle); wch^2 = dmax det / s11
+    float tX[3], tY[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      tX[k] = cmul(o.s[k], cadd(cmul(j00, o.a[k][0]), cmul(j02, o.a[k][2])));
+      tY[k] = cmul(o.s[k], cadd(cmul(j11, o.a[k][1]), cmul(j12, o.a[k][2])));
+    }
+    const float m01 = csub(cmul(tX[0], tY[1]), cmul(tY[0], tX[1]));
+    const float m02 = csub(cmul(tX[0], tY[2]), cmul(tY[0], tX[2]));
+    const float m12 = csub(cmul(tX[1], tY[2]), cmul(tY[1], tX[2]));
+    const float x2 = cadd(cadd(cmul(tX[0], tX[0]), cmul(tX[1], tX[1])), cmul(tX[2], tX[2]));
+    const float y2 = cadd(cadd(cmul(tY[0], tY[0]), cmul(tY[1], tY[1])), cmul(tY[2], tY[2]));
+    const float dil = f.dilation;
+    const float detS = cadd(cadd(cadd(cmul(m01, m01), cmul(m02, m02)), cmul(m12, m12)),
+                            cadd(cmul(dil, cadd(x2, y2)), cmul(dil, dil)));
+    kslope = cdiv(o.s01, o.s11);
+    wch = csqrt(cdiv(cmul(o.dmax, detS), o.s11));
+    yoff = cdiv(cmul(o.dmax, o.s01), hx);
   } else {
     const float m0x = cmul(o.s[0], o.a[0][0]), m0y = cmul(o.s[0], o.a[0][1]), m0z = cmul(o.s[0], o.a[0][2]);
     const float m1x = cmul(o.s[1], o.a[1][0]), m1y = cmul(o.s[1], o.a[1][1]), m1z = cmul(o.s[1], o.a[1][2]);
@@ -155,10 +167,22 @@ __device__ bool run_contract(const float mu[3], const float ls[3], const float q
           ctry = cadd(cmul(fy, cadd(o.yz, oy)), cy);
           hx = cmul(fx, cdiv(csqrt(qx), nD));
           hy = cmul(fy, cdiv(csqrt(qy), nD));
+          // the image ellipse's shape from the dual conic D: Sigma_xy =
+          // fx fy (D02 D12 - D01 D22) / D22^2 and det Sigma = fx^2 fy^2 dmax^2
+          // det(M)^2 / nD^3, M the re-centred splat frame (det D = -dmax^2
+          // det(M)^2)
+          const float D01 = csub(cmul(o.dmax, cadd(cmul(o.e0, o.f0), cmul(o.e1, o.f1))), cmul(e2, f2));
+          kslope = cdiv(cmul(fx, csub(cmul(D02, D12), cmul(D01, D22))), cmul(fy, qy));
+          const float detM = cadd(csub(cmul(o.e0, csub(cmul(o.f1, o.Z), cmul(f2, m1z))),
+                                       cmul(o.e1, csub(cmul(o.f0, o.Z), cmul(f2, m0z)))),
+                                  cmul(e2, csub(cmul(o.f0, m1z), cmul(o.f1, m0z))));
+          wch = cdiv(cmul(cmul(fx, o.dmax), fabsf(detM)), csqrt(cmul(nD, qy)));
+          yoff = cdiv(cmul(kslope, cmul(hy, hy)), hx);
         }
       }
     }
     if (whole) {
+      full = true;
       // The disc reaches the near plane (or its image conic is degenerate):
       // a contributing hit lies inside the disc's camera-space extents R at a
       // depth in (near, Z + R_z], which bounds x/z and y/z.
@@ -185,6 +209,7 @@ __device__ bool run_contract(const float mu[3], const float ls[3], const float q
     o.ty0 = 0; o.ty1 = (c.H - 1) / kTile;
     o.bx0 = o.by0 = -1e30f;
     o.bx1 = o.by1 = 1e30f;
+    full = true;
   } else {
     const float px = pad_extent(hx), py = pad_extent(hy);
     o.bx0 = csub(ctrx, px); o.bx1 = cadd(ctrx, px);
@@ -192,6 +217,19 @@ __device__ bool run_contract(const float mu[3], const float ls[3], const float q
     if (!pixel_tiles(o.bx0, o.bx1, c.W, &o.tx0, &o.tx1)) return false;
     if (!pixel_tiles(o.by0, o.by1, c.H, &o.ty0, &o.ty1)) return false;
   }
+  // padded chord parameters: the half chord by pad_extent plus 2^-10 hx for
+  // the rounding of kslope (y - ctry), the half height by pad_extent (its
+  // reciprocal is stored)
+  o.ctrx = ctrx;
+  o.ctry = ctry;
+  o.kslope = kslope;
+  o.wp = cadd(pad_extent(wch), cmul(hx, 0x1p-10f));
+  const float hyp = pad_extent(hy);
+  o.ihy = cdiv(1.0f, hyp);
+  o.yl = csub(ctry, yoff);
+  o.yr = cadd(ctry, yoff);
+  o.full = full || !(isfinite(o.kslope) && isfinite(o.wp) && isfinite(o.yl) && isfinite(o.yr) && hyp > 0.0f &&
+                     isfinite(o.ihy));
   return true;
 }
 
@@ -453,9 +491,6 @@ __device__ __forceinline__ float pack_box(float lo, float hi) {
 // ---------------------------------------------------------------------------
 // forward kernel
 // ---------------------------------------------------------------------------
-// One primitive: scene row i of `a`, written to row i of a's outputs; the tile
-// rectangle's rows are shifted by row_off (the batched render stacks the
-// requests' tile grids vertically).
 // Ask L2 for a primitive's SH row ahead of its use, so that the row's DRAM
 // latency overlaps the contract arithmetic: only for primitives that pass a
 // cheap guess at the contract's culls (in front of the near plane, opacity
@@ -481,24 +516,86 @@ __device__ __forceinline__ void prefetch_sh(const PrepArgs &a, int64_t i, const 
   }
 }
 
-template <int DEG>
-__device__ __forceinline__ void preprocess_one(const PrepArgs &a, int64_t i, int row_off) {
+// One primitive's parameters as loaded.
+struct PrimIn {
   float mu[3], ls[3], q[4], logit;
   int type;
-  load_params(a, i, mu, ls, q, logit, type);
-  prefetch_sh<DEG>(a, i, mu, logit);
-  Contract o;
-  const bool binned = run_contract(mu, ls, q, logit, type, a.cam, a.cfg, o);
+};
+
+// Contract part of the forward for primitive i: the depth key, and, if the
+// rectangle is not empty, the tile-set parameters (ts) and the number of
+// tile rows of the rectangle (0 if not binned).
+__device__ __forceinline__ int contract_part(const PrepArgs &a, int64_t i, int row_off, const PrimIn &p,
+                                             Contract &o, TileSet &ts) {
+  const bool binned = run_contract(p.mu, p.ls, p.q, p.logit, p.type, a.cam, a.cfg, o);
   a.depth_key[i] = o.dbits;
-  if (!binned) {
+  if (!binned) return 0;
+  ts.t0 = make_float4(o.ctrx, o.ctry, o.kslope, o.wp);
+  ts.t1 = make_float4(o.ihy, o.yl, o.yr, __uint_as_float(tileset_flags(o.full, row_off, a.cam.W)));
+  return o.ty1 - o.ty0 + 1;
+}
+
+// The size of each lane's tile set, counted by the warp's lanes together:
+// the (primitive, tile row) pairs of the warp are spread over the lanes (a
+// lane finds the primitive of its pair by a binary search over the exclusive
+// prefix of the lanes' row counts), so a primitive spanning many rows does
+// not hold up the other lanes.  Every lane of the warp calls it; sts and scnt
+// are the warp's shared-memory slots.
+__device__ __forceinline__ uint32_t warp_set_count(const TileSet &ts, int tx0, int tx1, int ty0, int nrows,
+                                                   TileSet *sts, uint32_t *scnt) {
+  const int lane = threadIdx.x & 31;
+  sts[lane] = ts;
+  scnt[lane] = 0u;
+  uint32_t incl = (uint32_t)nrows;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  const uint32_t rel = incl - (uint32_t)nrows;
+  const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+  __syncwarp();
+  for (uint32_t kb = 0; kb < total; kb += 32) {  // warp-uniform trip count
+    const uint32_t k = kb + lane;
+    int lo = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+      const uint32_t pr = __shfl_sync(0xffffffffu, rel, lo + step);
+      if (pr <= k) lo += step;
+    }
+    const uint32_t orel = __shfl_sync(0xffffffffu, rel, lo);
+    const int otx0 = __shfl_sync(0xffffffffu, tx0, lo), otx1 = __shfl_sync(0xffffffffu, tx1, lo);
+    const int oty0 = __shfl_sync(0xffffffffu, ty0, lo);
+    if (k < total) {
+      int c0, c1;
+      if (row_span(sts[lo], oty0 + (int)(k - orel), otx0, otx1, &c0, &c1))
+        atomicAdd(&scnt[lo], (uint32_t)(c1 - c0 + 1));
+    }
+  }
+  __syncwarp();
+  return scnt[lane];
+}
+
+// The rest of the forward for a primitive whose contract ran: its binning
+// outputs (a primitive whose tile set is empty is not binned) and its render
+// record.
+template <int DEG>
+__device__ __forceinline__ void finish_one(const PrepArgs &a, int64_t i, int row_off, const PrimIn &p,
+                                           const Contract &o, const TileSet &ts, uint32_t count) {
+  if (count == 0u) {
     a.touched[i] = 0u;
     reinterpret_cast<uint2 *>(a.rect)[i] = make_uint2(0u, 0u);
     return;
   }
-  a.touched[i] = (uint32_t)((o.tx1 - o.tx0 + 1) * (o.ty1 - o.ty0 + 1));
+  const float(&mu)[3] = p.mu;
+  const float(&ls)[3] = p.ls;
+  const int type = p.type;
+  a.touched[i] = count;
   reinterpret_cast<uint2 *>(a.rect)[i] =
       make_uint2((uint32_t)o.tx0 | ((uint32_t)o.tx1 << 16),
                  (uint32_t)(o.ty0 + row_off) | ((uint32_t)(o.ty1 + row_off) << 16));
+  reinterpret_cast<float4 *>(a.tileset)[2 * i] = ts.t0;
+  reinterpret_cast<float4 *>(a.tileset)[2 * i + 1] = ts.t1;
 
   const CamK &c = a.cam;
   // colour (Sec. 3.1): SH decoded along the view direction
@@ -567,25 +664,57 @@ __device__ __forceinline__ void preprocess_one(const PrepArgs &a, int64_t i, int
 }
 
 template <int DEG>
-__global__ void __launch_bounds__(256) preprocess_fwd_kernel(PrepArgs a) {
+__global__ void __launch_bounds__(256, 4) preprocess_fwd_kernel(PrepArgs a) {
+  __shared__ TileSet sts[8][32];
+  __shared__ uint32_t scnt[8][32];
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n) return;
-  preprocess_one<DEG>(a, i, 0);
+  const bool in = i < a.n;
+  if (__all_sync(0xffffffffu, !in)) return;
+  const int warp = threadIdx.x >> 5;
+  PrimIn p;
+  Contract o;
+  TileSet ts;
+  int nrows = 0;
+  if (in) {
+    load_params(a, i, p.mu, p.ls, p.q, p.logit, p.type);
+    prefetch_sh<DEG>(a, i, p.mu, p.logit);
+    nrows = contract_part(a, i, 0, p, o, ts);
+  }
+  const uint32_t count = warp_set_count(ts, o.tx0, o.tx1, o.ty0, nrows, sts[warp], scnt[warp]);
+  if (in) finish_one<DEG>(a, i, 0, p, o, ts, count);
 }
 
 // Batched: the requests' primitives are concatenated; request r covers global
-// rows [base[r], base[r+1]) and its outputs start at row base[r].
+// rows [base[r], base[r+1]) and its outputs start at row base[r]; the tile
+// rectangle's rows are shifted by row_off[r] (the batched render stacks the
+// requests' tile grids vertically).
 __global__ void __launch_bounds__(256) preprocess_batch_kernel(BatchPrepArgs b) {
+  __shared__ TileSet sts[8][32];
+  __shared__ uint32_t scnt[8][32];
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= b.base[b.nreq]) return;
+  const bool in = g < b.base[b.nreq];
+  if (__all_sync(0xffffffffu, !in)) return;
+  const int warp = threadIdx.x >> 5;
   int r = 0;
-  while (r + 1 < b.nreq && g >= b.base[r + 1]) ++r;
+  if (in)
+    while (r + 1 < b.nreq && g >= b.base[r + 1]) ++r;
   const int64_t i = g - b.base[r];
+  const PrepArgs &a = b.req[r];
+  PrimIn p;
+  Contract o;
+  TileSet ts;
+  int nrows = 0;
+  if (in) {
+    load_params(a, i, p.mu, p.ls, p.q, p.logit, p.type);
+    nrows = contract_part(a, i, b.row_off[r], p, o, ts);
+  }
+  const uint32_t count = warp_set_count(ts, o.tx0, o.tx1, o.ty0 + b.row_off[r], nrows, sts[warp], scnt[warp]);
+  if (!in) return;
   switch (b.deg[r]) {
-    case 0: preprocess_one<0>(b.req[r], i, b.row_off[r]); break;
-    case 1: preprocess_one<1>(b.req[r], i, b.row_off[r]); break;
-    case 2: preprocess_one<2>(b.req[r], i, b.row_off[r]); break;
-    default: preprocess_one<3>(b.req[r], i, b.row_off[r]); break;
+    case 0: finish_one<0>(a, i, b.row_off[r], p, o, ts, count); break;
+    case 1: finish_one<1>(a, i, b.row_off[r], p, o, ts, count); break;
+    case 2: finish_one<2>(a, i, b.row_off[r], p, o, ts, count); break;
+    default: finish_one<3>(a, i, b.row_off[r], p, o, ts, count); break;
   }
 }
 

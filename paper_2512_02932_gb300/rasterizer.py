@@ -55,7 +55,6 @@ def config_struct(cfg=None) -> abi.hgs_config:
     c.theta_z = cfg.theta_z
     c.T_z = cfg.T_z
     c.dilation = cfg.dilation
-    c.wide_rects = int(getattr(cfg, "wide_rects", 0))
     for i in range(3):
         c.bg[i] = float(cfg.bg[i])
     c.tile = int(cfg.tile)
@@ -136,6 +135,7 @@ class Rasterizer:
         self.depth_key = torch.empty(m, dtype=torch.int32, device=d)
         self.rect = torch.empty((m, 4), dtype=torch.int16, device=d)
         self.touched = torch.empty(m, dtype=torch.int32, device=d)
+        self.tileset = torch.empty((m, 8), dtype=torch.float32, device=d)
         self.grad_ws = torch.empty((m, GRAD_FLOATS), dtype=torch.float32, device=d)
         self.n = n
         self.ws = None
@@ -168,7 +168,7 @@ class Rasterizer:
 
     def proj_struct(self):
         return abi.hgs_projected(self.rec.data_ptr(), self.depth_key.data_ptr(), self.rect.data_ptr(),
-                                 self.touched.data_ptr())
+                                 self.touched.data_ptr(), self.tileset.data_ptr())
 
     def bin_struct(self):
         return abi.hgs_binning(self.vals.data_ptr(), self.keys.data_ptr() if self.keys is not None else None,

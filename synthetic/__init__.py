@@ -63,7 +63,6 @@ class RenderConfig:
     dilation: float = 0.0
     bg: tuple = (0.0, 0.0, 0.0)
     tile: int = 16
-    wide_rects: int = 0   # binning path for rectangles over 256 tiles (lists are the same)
 
     def as_oracle_array(self) -> np.ndarray:
         return np.array([self.near, self.alpha_min, self.alpha_max, self.T_min,

@@ -35,7 +35,6 @@ def test_defaults_and_status_strings():
     c = abi.hgs_config()
     abi.hgs_default_config(C.byref(c))
     assert c.tile == 16 and abs(c.alpha_min - 1 / 255) < 1e-9 and abs(c.theta_z - 1.05) < 1e-6
-    assert c.wide_rects == 0  # the device picks the binning path per frame
     assert abi.hgs_status_string(abi.HGS_ERR_CAPACITY) == b"HGS_ERR_CAPACITY"
     assert abi.hgs_status_string(12345) == b"HGS_ERR_UNKNOWN"
 
@@ -64,7 +63,7 @@ def test_capacity_beyond_32_bit_offsets_is_rejected():
     cam.width = cam.height = 64
     cfg = abi.hgs_config()
     abi.hgs_default_config(C.byref(cfg))
-    proj = abi.hgs_projected(16, 16, 16, 16)
+    proj = abi.hgs_projected(16, 16, 16, 16, 16)
     out = abi.hgs_binning(16, None, 16, 16)
     cap = 1 << 62
     assert abi.hgs_bin_sort(10, C.byref(proj), C.byref(cam), C.byref(cfg), C.c_void_p(16), 1 << 30, cap,
@@ -119,13 +118,16 @@ def test_invalid_arguments_rejected_before_launch():
         assert abi.hgs_alu_probe(kind, 4, 10, C.c_void_p(16), C.byref(fl), None) == abi.HGS_ERR_INVALID_ARG
     assert abi.hgs_alu_probe(abi.HGS_PROBE_EX2, 0, 10, C.c_void_p(16), C.byref(fl), None) \
         == abi.HGS_ERR_INVALID_ARG
-    # binning path other than 0 (device picks), 1 (masks), 2 (radix sort)
+    # the binning needs the tile-set array, 16-byte aligned (checked before
+    # anything launches)
     cam.width = 16
-    for bad in (-1, 3):
-        cfg.wide_rects = bad
-        assert abi.hgs_preprocess(C.byref(scene), C.byref(cam), C.byref(cfg), C.byref(proj), None, None) \
-            == abi.HGS_ERR_INVALID_ARG
-    cfg.wide_rects = 0
+    out = abi.hgs_binning(16, None, 16, 16)
+    for ts in (None, 24):
+        proj16 = abi.hgs_projected(16, 16, 16, 16, ts)
+        assert abi.hgs_bin_sort(10, C.byref(proj16), C.byref(cam), C.byref(cfg), C.c_void_p(16), 1 << 30, 1000,
+                                C.byref(out), None, None) == abi.HGS_ERR_INVALID_ARG
+        assert abi.hgs_bin_sort_static(10, C.byref(proj16), C.byref(cam), C.byref(cfg), 1000, C.byref(out),
+                                       None, None) == abi.HGS_ERR_INVALID_ARG
     # an empty scene is valid and launches nothing
     scene.n = 0
     assert abi.hgs_preprocess(C.byref(scene), C.byref(cam), C.byref(cfg), C.byref(proj), None, None) == 0

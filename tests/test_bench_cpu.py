@@ -63,16 +63,16 @@ def test_reference_arm_under_torchrun_two_ranks():
 
 def test_hbm_phases_counts_the_documented_bytes():
     """The memory-bound phases' algorithmic bytes: preprocess 61 B per
-    primitive + 272 B per binned one; its backward 385 B per binned + 4 B per
-    culled + 236 B per primitive; the sort 108 B per binned primitive + 8 B
+    primitive + 304 B per binned one; its backward 385 B per binned + 4 B per
+    culled + 236 B per primitive; the sort 144 B per binned primitive + 8 B
     per instance for the emit + 20 B per instance and tile pass, less 4 B
     (the last pass writes no keys)."""
     ph = {"preprocess": 1.0, "preprocess_bwd": 2.0, "bin_sort": 4.0}
     n, nb, K = 1000, 600, 10_000
     out = bench.hbm_phases(ph, n, nb, K, 2, 1000.0, "test")
-    assert out["preprocess"]["bytes"] == 61 * n + 272 * nb
+    assert out["preprocess"]["bytes"] == 61 * n + 304 * nb
     assert out["preprocess_bwd"]["bytes"] == 385 * nb + 4 * (n - nb) + 236 * n
-    assert out["bin_sort"]["bytes"] == 108 * nb + 8 * K + 2 * 20 * K - 4 * K
+    assert out["bin_sort"]["bytes"] == 144 * nb + 8 * K + 2 * 20 * K - 4 * K
     b = out["preprocess"]["bytes"]
     assert abs(out["preprocess"]["achieved_gbs"] - b / 1e-3 / 1e9) < 0.1
     assert abs(out["preprocess"]["frac"] - out["preprocess"]["achieved_gbs"] / 1000.0) < 1e-3

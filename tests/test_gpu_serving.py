@@ -49,23 +49,21 @@ def test_batch_equals_alone_bit_for_bit():
     assert_images_match(g, m, max_excluded=0.0, label="batched request")
 
 
-def test_batch_wide_rectangles_same_on_both_paths():
-    """A batch of heavy-tailed scenes (many rectangles over 256 tiles of the
-    stacked grid): the mask path and the radix path give the same images,
+def test_batch_of_heavy_tailed_scenes_matches_alone():
+    """A batch of heavy-tailed scenes (needles and ribbons, many rectangles
+    over 256 tiles, so the stacked grid's tile sets and deferred emits are
+    exercised): each request's images equal the same request rendered alone,
     bit for bit."""
-    import dataclasses
     host = [S.surface_scene(30_000, seed=50 + k, frac3d=0.3, ls_loc=-4.0, ls_scale=0.8, heavy_df=3)
             for k in range(2)]
     dev = [SceneTensors.from_numpy(h) for h in host]
     cams = [S.orbit_camera(15.0, 25.0, 2.6, 1024, 640, 55.0), S.orbit_camera(200.0, 10.0, 2.8, 800, 600, 50.0)]
-    outs = {}
-    for mode in (1, 2):
-        o, K = render_batch_once(dev, cams, dataclasses.replace(CFG, wide_rects=mode))
-        assert K > 0
-        outs[mode] = [{k: x[k].cpu().numpy() for k in KEYS} for x in o]
-    for a, b in zip(outs[1], outs[2]):
-        for k in KEYS:
-            np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+    o, K = render_batch_once(dev, cams, CFG)
+    assert K > 0
+    for k in range(2):
+        alone, _ = render_batch_once([dev[k]], [cams[k]], CFG)
+        for key in KEYS:
+            np.testing.assert_array_equal(o[k][key].cpu().numpy(), alone[0][key].cpu().numpy(), err_msg=key)
 
 
 def test_server_burst_matches_alone():

@@ -59,20 +59,17 @@ def test_static_scratch_matches_workspace_binning_twice():
             np.testing.assert_array_equal(got[2], ref[2])
 
 
-def test_static_scratch_sorts_wide_rectangles_like_the_mask_path():
-    """The static call keeps only the radix path; on a heavy-tailed scene
-    whose workspace binning takes the coverage-mask path it still produces
-    the same lists."""
-    import dataclasses
-    cfg = dataclasses.replace(CFG, wide_rects=1)
+def test_static_scratch_on_a_heavy_tailed_scene():
+    """Needles and ribbons (tile sets with many rows, deferred emits): the
+    static call produces the workspace call's lists."""
     scene = S.surface_scene(60_000, seed=21, frac3d=0.3, ls_loc=-4.0, ls_scale=0.8, heavy_df=3)
     cam = S.orbit_camera(15.0, 25.0, 2.6, 1024, 640, 55.0)
     r = Rasterizer("cuda", keep_keys=True)
-    r.forward(SceneTensors.from_numpy(scene), cam, cfg)
+    r.forward(SceneTensors.from_numpy(scene), cam, CFG)
     torch.cuda.synchronize()
     ref = _workspace_lists(r)
     touched = r.touched[: scene.n].cpu().numpy().astype(np.int64)
-    assert (touched > 256).sum() > 100
+    assert (touched > 256).sum() > 50
     got = _static_lists(r, ref[3] + 4096)
     assert got[3] == ref[3]
     for a, b in zip(got[:3], ref[:3]):
