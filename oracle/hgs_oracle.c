@@ -202,6 +202,8 @@ float orc_c_log(float x) {
 
 static float pad_f(float r) { return r * 1.0009765625f + 0.015625f; }
 
+#define ORC_ROWP 12 /* tile-set parameters per primitive */
+
 /* pixel-centre coverage of [lo, hi] -> inclusive pixel range, then tiles */
 static int c_range(float lo, float hi, int extent, int tile, int *t0, int *t1) {
   float flo = lo - 0.5f, fhi = hi - 0.5f;
@@ -219,11 +221,11 @@ static int c_range(float lo, float hi, int extent, int tile, int *t0, int *t1) {
 
 /* One primitive through the contract.  cam: R[9] t[3] fx fy cx cy.
  * Returns 1 and fills rect {tx0,tx1,ty0,ty1}, depth bits and the tile-set
- * parameters rowp (row_span) if binned. */
+ * parameters rowp (ORC_ROWP floats, row_span) if binned. */
 static int contract_one(const float mu[3], const float ls[3], const float q[4],
                         float logit, int type, const float *cam, int W, int H,
                         int tile, float near_z, float alpha_min, float dil,
-                        int rect[4], uint32_t *dbits, float rowp[8]) {
+                        int rect[4], uint32_t *dbits, float rowp[ORC_ROWP]) {
   const float *Rc = cam, *tc = cam + 9;
   const float fx = cam[12], fy = cam[13], cx = cam[14], cy = cam[15];
   float X = ((Rc[0] * mu[0] + Rc[1] * mu[1]) + Rc[2] * mu[2]) + tc[0];
@@ -264,6 +266,10 @@ static int contract_one(const float mu[3], const float ls[3], const float q[4],
   float kslope = 0.0f, wch = 0.0f, yoff = 0.0f;
   int full = 0;
   int whole = 0;
+  /* a surfel whose disc reaches the near plane (or whose image conic is
+   * degenerate): the disc in pixel-homogeneous camera coordinates */
+  int disc = 0;
+  float dP[3] = {0.0f, 0.0f, 0.0f}, dA[3] = {0.0f, 0.0f, 0.0f}, dB[3] = {0.0f, 0.0f, 0.0f};
   if (type == 1) {
     float c0 = sx * sx, c1 = sy * sy, c2 = sz * sz;
     float V[3][3];
@@ -347,6 +353,10 @@ static int contract_one(const float mu[3], const float ls[3], const float q[4],
     }
     if (whole) {
       full = 1;
+      disc = 1;
+      dP[0] = fx * X + cx * Z; dP[1] = fy * Y + cy * Z; dP[2] = Z;
+      dA[0] = fx * m0x + cx * m0z; dA[1] = fy * m0y + cy * m0z; dA[2] = m0z;
+      dB[0] = fx * m1x + cx * m1z; dB[1] = fy * m1y + cy * m1z; dB[2] = m1z;
       /* the disc reaches the near plane: a contributing hit lies in the disc
        * (camera-space extents R) at depth in (near, Z + Rz], so x/z and y/z
        * are bounded by the extents divided by the depth bounds */
@@ -380,17 +390,120 @@ static int contract_one(const float mu[3], const float ls[3], const float q[4],
   rect[0] = tx0; rect[1] = tx1; rect[2] = ty0; rect[3] = ty1;
   /* padded chord parameters: the half chord by pad_f plus 2^-10 hx for the
    * rounding of kslope (y - ctry), the half height by pad_f */
+  for (int k = 0; k < ORC_ROWP; ++k) rowp[k] = 0.0f;
+  if (disc) {
+    int fin = isfinite(dmax);
+    for (int k = 0; k < 3; ++k) fin = fin && isfinite(dP[k]) && isfinite(dA[k]) && isfinite(dB[k]);
+    if (fin) {
+      rowp[0] = dP[0]; rowp[1] = dP[1]; rowp[2] = dP[2]; rowp[3] = dmax;
+      rowp[4] = dA[0]; rowp[5] = dA[1]; rowp[6] = dA[2]; rowp[7] = near_z;
+      rowp[8] = dB[0]; rowp[9] = dB[1]; rowp[10] = dB[2]; rowp[11] = 2.0f;
+    } else {
+      rowp[11] = 1.0f;
+    }
+    return 1;
+  }
   float wp = pad_f(wch) + hx * 0x1p-10f, hyp = pad_f(hy), ihy = 1.0f / hyp;
   float yl = ctry - yoff, yr = ctry + yoff;
   if (!(isfinite(kslope) && isfinite(wp) && isfinite(yl) && isfinite(yr) && hyp > 0.0f && isfinite(ihy)))
     full = 1;
   rowp[0] = ctrx; rowp[1] = ctry; rowp[2] = kslope; rowp[3] = wp;
-  rowp[4] = ihy; rowp[5] = yl; rowp[6] = yr; rowp[7] = full ? 1.0f : 0.0f;
+  rowp[4] = ihy; rowp[5] = yl; rowp[6] = yr; rowp[11] = full ? 1.0f : 0.0f;
   return 1;
 }
 
-/* rowp: chord centre x and y, slope, padded half chord, reciprocal of the
- * padded half height, heights of the leftmost and rightmost points, full.
+/* The x-range [*xlo, *xhi] of the pixels of tile row ty whose rays hit a
+ * disc-mode surfel's disc in front of the near plane.  rowp: the disc's
+ * centre C and axes a, b in pixel-homogeneous camera coordinates P = (fx X +
+ * cx Z, fy Y + cy Z, Z), its squared radius dmax, near.  A pixel (x, y) sees
+ * P(u, v) = C + u a + v b (u^2 + v^2 <= dmax) at x = P0/P2, y = P1/P2 and
+ * depth P2; over the row's band of pixel-centre heights [ya, yb] the points
+ * seen form the disc cut by three half-planes c + p u + q v >= 0 (P1 - ya P2,
+ * yb P2 - P1, P2 - near).  x is a ratio of affine functions, so its extremes
+ * over that convex set lie at points of the circle where a plane x P2 = P0
+ * touches it, at the lines' crossings with the circle, or at the lines'
+ * crossings with each other; every candidate inside the set (with a relative
+ * tolerance of 2^-12 on each half-plane and 2^-10 on the radius) is taken.
+ * Returns 0 if none is. */
+static int disc_span(const float rp[ORC_ROWP], int ty, int tile, float *xlo, float *xhi) {
+  const float ya = (float)(ty * tile) + 0.5f, yb = ya + (float)(tile - 1);
+  const float CX = rp[0], CY = rp[1], CZ = rp[2], r2 = rp[3];
+  const float ax = rp[4], ay = rp[5], az = rp[6], nz = rp[7];
+  const float bx = rp[8], by = rp[9], bz = rp[10];
+  float c[3], p[3], q[3], tol[3];
+  c[0] = CY - ya * CZ; p[0] = ay - ya * az; q[0] = by - ya * bz;
+  c[1] = yb * CZ - CY; p[1] = yb * az - ay; q[1] = yb * bz - by;
+  c[2] = CZ - nz; p[2] = az; q[2] = bz;
+  const float rho = sqrtf(r2);
+  for (int k = 0; k < 3; ++k) tol[k] = 0x1p-12f * (fabsf(c[k]) + rho * (fabsf(p[k]) + fabsf(q[k])));
+  const float r2t = r2 * 1.0009765625f;
+  float cu[11], cv[11];
+  int onc[11], nc = 0;
+  /* (a) tangency: (CX - x CZ)^2 = r2 ((ax - x az)^2 + (bx - x bz)^2) */
+  const float A = CZ * CZ - r2 * (az * az + bz * bz);
+  const float B = CX * CZ - r2 * (ax * az + bx * bz);
+  const float Cq = CX * CX - r2 * (ax * ax + bx * bx);
+  const float dq = B * B - A * Cq;
+  if (dq >= 0.0f && A != 0.0f) {
+    const float sq = sqrtf(dq);
+    float xs[2];
+    xs[0] = (B - sq) / A;
+    xs[1] = (B + sq) / A;
+    for (int k = 0; k < 2; ++k) {
+      const float al = CX - xs[k] * CZ, be0 = ax - xs[k] * az, be1 = bx - xs[k] * bz;
+      const float bb = be0 * be0 + be1 * be1;
+      if (!(bb > 0.0f)) continue;
+      const float t = -al / bb;
+      cu[nc] = t * be0; cv[nc] = t * be1; onc[nc] = 1; ++nc;
+    }
+  }
+  /* (b) each line's crossings with the circle */
+  for (int k = 0; k < 3; ++k) {
+    const float pq = p[k] * p[k] + q[k] * q[k];
+    if (!(pq > 0.0f)) continue;
+    const float t = -c[k] / pq;
+    const float fu = t * p[k], fv = t * q[k];
+    const float d2 = (c[k] * c[k]) / pq;
+    if (!(d2 <= r2t)) continue;
+    const float h = sqrtf(fmaxf(r2 - d2, 0.0f) / pq);
+    cu[nc] = fu - h * q[k]; cv[nc] = fv + h * p[k]; onc[nc] = 1; ++nc;
+    cu[nc] = fu + h * q[k]; cv[nc] = fv - h * p[k]; onc[nc] = 1; ++nc;
+  }
+  /* (c) the lines' crossings with each other */
+  for (int i = 0; i < 3; ++i)
+    for (int j = i + 1; j < 3; ++j) {
+      const float det = p[i] * q[j] - p[j] * q[i];
+      if (det == 0.0f) continue;
+      cu[nc] = (q[i] * c[j] - q[j] * c[i]) / det;
+      cv[nc] = (p[j] * c[i] - p[i] * c[j]) / det;
+      onc[nc] = 0;
+      ++nc;
+    }
+  float lo = INFINITY, hi = -INFINITY;
+  for (int k = 0; k < nc; ++k) {
+    const float u = cu[k], v = cv[k];
+    if (!onc[k] && !(u * u + v * v <= r2t)) continue;
+    int ok = 1;
+    for (int m = 0; m < 3; ++m)
+      if (!((c[m] + p[m] * u) + q[m] * v >= -tol[m])) ok = 0;
+    if (!ok) continue;
+    const float D = (CZ + az * u) + bz * v;
+    if (!(D > 0.0f)) continue;
+    const float x = ((CX + ax * u) + bx * v) / D;
+    lo = fminf(lo, x);
+    hi = fmaxf(hi, x);
+  }
+  if (!(lo <= hi)) return 0;
+  const float pad = 0x1p-9f * fmaxf(fabsf(lo), fabsf(hi)) + 0.0625f;
+  *xlo = lo - pad;
+  *xhi = hi + pad;
+  return 1;
+}
+
+/* rowp (ellipse mode, rowp[11] = 0): chord centre x and y, slope, padded half
+ * chord, reciprocal of the padded half height, heights of the leftmost and
+ * rightmost points; rowp[11] = 1: the whole rectangle; 2: disc mode
+ * (disc_span).
  * Tile columns [*c0, *c1] of tile row ty of a binned primitive's tile set:
  * the pixel columns whose centres the padded footprint ellipse reaches in
  * the row's band of pixel-centre heights [ty tile + 0.5, ty tile + tile -
@@ -399,10 +512,22 @@ static int contract_one(const float mu[3], const float ls[3], const float q[4],
  * convex in y), the right end greatest nearest the rightmost point.  A
  * primitive marked full lists every tile of its rectangle.  Returns 0 if the
  * row lists no tile. */
-static int row_span(const float rowp[8], const int rect[4], int ty, int W, int tile, int *c0, int *c1) {
-  if (rowp[7] != 0.0f) {
+static int row_span(const float rowp[ORC_ROWP], const int rect[4], int ty, int W, int tile, int *c0, int *c1) {
+  if (rowp[11] == 1.0f) {
     *c0 = rect[0];
     *c1 = rect[1];
+    return 1;
+  }
+  if (rowp[11] == 2.0f) {
+    float xl, xr;
+    int a, b;
+    if (!disc_span(rowp, ty, tile, &xl, &xr)) return 0;
+    if (!c_range(xl, xr, W, tile, &a, &b)) return 0;
+    if (a < rect[0]) a = rect[0];
+    if (b > rect[1]) b = rect[1];
+    if (a > b) return 0;
+    *c0 = a;
+    *c1 = b;
     return 1;
   }
   const float cxe = rowp[0], cye = rowp[1], kslope = rowp[2], wp = rowp[3], ihy = rowp[4];
@@ -424,7 +549,7 @@ static int row_span(const float rowp[8], const int rect[4], int ty, int W, int t
 }
 
 /* tiles of a binned primitive's tile set */
-static int64_t set_count(const float rowp[8], const int rect[4], int W, int tile) {
+static int64_t set_count(const float rowp[ORC_ROWP], const int rect[4], int W, int tile) {
   int64_t n = 0;
   for (int ty = rect[2]; ty <= rect[3]; ++ty) {
     int a, b;
@@ -435,7 +560,7 @@ static int64_t set_count(const float rowp[8], const int rect[4], int W, int tile
 
 /* cfg32: near, alpha_min, dilation.  rect: n x 4 (tx0,tx1,ty0,ty1), -1 if not
  * binned.  touched: tiles in the primitive's tile set (0 if not binned; a
- * binned primitive whose set is empty is not binned either).  rowp (n x 8,
+ * binned primitive whose set is empty is not binned either).  rowp (n x 12,
  * may be NULL): the tile-set parameters. */
 void orc_contract_bin(int64_t n, const float *means, const float *log_scales,
                       const float *quats, const float *logits, const uint8_t *types,
@@ -445,7 +570,7 @@ void orc_contract_bin(int64_t n, const float *means, const float *log_scales,
   for (int64_t i = 0; i < n; ++i) {
     int r[4];
     uint32_t db;
-    float rp[8];
+    float rp[ORC_ROWP];
     int ok = contract_one(means + 3 * i, log_scales + 3 * i, quats + 4 * i, logits[i],
                           types[i], cam, W, H, tile, cfg32[0], cfg32[1], cfg32[2], r, &db, rp);
     depth_bits[i] = db;
@@ -453,11 +578,11 @@ void orc_contract_bin(int64_t n, const float *means, const float *log_scales,
     if (cnt > 0) {
       for (int k = 0; k < 4; ++k) rect[4 * i + k] = r[k];
       touched[i] = cnt;
-      if (rowp) memcpy(rowp + 8 * i, rp, sizeof(rp));
+      if (rowp) memcpy(rowp + ORC_ROWP * i, rp, sizeof(rp));
     } else {
       for (int k = 0; k < 4; ++k) rect[4 * i + k] = -1;
       touched[i] = 0;
-      if (rowp) memset(rowp + 8 * i, 0, sizeof(rp));
+      if (rowp) memset(rowp + ORC_ROWP * i, 0, sizeof(rp));
     }
   }
 }
@@ -474,14 +599,14 @@ void orc_contract_tiles(int64_t n, const int32_t *rect, const float *rowp, const
     const int *r = rect + 4 * i;
     for (int ty = r[2]; ty <= r[3]; ++ty) {
       int a, b;
-      if (!row_span(rowp + 8 * i, r, ty, W, tile, &a, &b)) continue;
+      if (!row_span(rowp + ORC_ROWP * i, r, ty, W, tile, &a, &b)) continue;
       for (int tx = a; tx <= b; ++tx) tiles[o++] = (uint32_t)(ty * TX + tx);
     }
   }
 }
 
 /* Whether tile (tx, ty) is in the tile set of a binned primitive. */
-static int set_has(const float rowp[8], const int rect[4], int tx, int ty, int W, int tile) {
+static int set_has(const float rowp[ORC_ROWP], const int rect[4], int tx, int ty, int W, int tile) {
   if (ty < rect[2] || ty > rect[3] || tx < rect[0] || tx > rect[1]) return 0;
   int a, b;
   return row_span(rowp, rect, ty, W, tile, &a, &b) && tx >= a && tx <= b;
@@ -505,7 +630,7 @@ typedef struct {
   double bx0, bx1, by0, by1;      /* padded continuous bbox in pixels */
   int whole;
   int rect[4];                    /* the contract's tile rectangle ... */
-  float rowp[8];                  /* ... and tile-set parameters (row_span) */
+  float rowp[ORC_ROWP];           /* ... and tile-set parameters (row_span) */
 } prim_t;
 
 typedef struct {

@@ -261,7 +261,7 @@ class _FDSession:
 def contract_bin(scene, cam, cfg, with_rowp=False):
     """FP32 binning contract for every primitive: (depth_bits u32 (N,),
     rect int32 (N,4) = tx0,tx1,ty0,ty1 (-1 if not binned), touched int64:
-    the tiles of the primitive's tile set[, rowp float32 (N,8): the tile-set
+    the tiles of the primitive's tile set[, rowp float32 (N,12): the tile-set
     parameters])."""
     n = scene.n
     arrs = [np.ascontiguousarray(scene.means, np.float32),
@@ -274,7 +274,7 @@ def contract_bin(scene, cam, cfg, with_rowp=False):
     db = np.zeros(n, np.uint32)
     rect = np.zeros((n, 4), np.int32)
     touched = np.zeros(n, np.int64)
-    rowp = np.zeros((n, 8), np.float32)
+    rowp = np.zeros((n, 12), np.float32)
     lib().orc_contract_bin(n, *[_p(a) for a in arrs], _p(cam16), cam.width, cam.height,
                            cfg.tile, _p(cfg32), _p(db), _p(rect), _p(touched), _p(rowp))
     return (db, rect, touched, rowp) if with_rowp else (db, rect, touched)

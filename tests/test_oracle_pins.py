@@ -388,10 +388,37 @@ def test_contract_is_conservative_for_surfels_reaching_the_near_plane():
                     rng.normal(1.0, 1.0, n).astype(np.float32), sh.astype(np.float32),
                     np.zeros(n, np.uint8), 0)
     cam = S.pinhole(96, 80, 70.0)
-    _assert_sets_hold_contributions(scene, cam, 1000)
-    # the branch is exercised: many discs reach the near plane
+    enc, touched = _assert_sets_hold_contributions(scene, cam, 1000)
+    # the branch is exercised: many discs reach the near plane, and their
+    # tile sets (disc mode) drop part of their rectangles
     m = means.astype(np.float64)
     assert (m[:, 2] - 3 * np.exp(ls[:, :2]).max(1) < CFG.near).sum() > 30
+    db, rect, _, rowp = O.contract_bin(scene, cam, CFG, with_rowp=True)
+    disc = (touched > 0) & (rowp[:, 11] == 2)
+    area = (rect[:, 1] - rect[:, 0] + 1) * (rect[:, 3] - rect[:, 2] + 1)
+    assert disc.sum() > 30 and touched[disc].sum() < 0.9 * area[disc].sum()
+
+
+def test_disc_mode_tile_sets_of_large_near_surfels():
+    """Large surfels crossing the near plane at every orientation, seen over
+    a wider frame: every contributing pair lies in the disc-mode tile set,
+    which keeps well under the rectangles' tiles."""
+    rng = np.random.default_rng(12)
+    n = 120
+    means = np.stack([rng.uniform(-0.6, 0.6, n), rng.uniform(-0.5, 0.5, n), rng.uniform(0.25, 1.5, n)], 1)
+    ls = np.stack([rng.normal(-0.3, 0.5, n), rng.normal(-1.5, 1.0, n), np.full(n, S.SURFEL_LOG_SZ)], 1)
+    q = rng.normal(size=(n, 4))
+    sh = np.zeros((n, 1, 3))
+    scene = S.Scene(means.astype(np.float32), ls.astype(np.float32), q.astype(np.float32),
+                    rng.normal(1.0, 1.0, n).astype(np.float32), sh.astype(np.float32),
+                    np.zeros(n, np.uint8), 0)
+    cam = S.pinhole(320, 224, 70.0)
+    enc, touched = _assert_sets_hold_contributions(scene, cam, 20000)
+    db, rect, _, rowp = O.contract_bin(scene, cam, CFG, with_rowp=True)
+    disc = (touched > 0) & (rowp[:, 11] == 2)
+    area = (rect[:, 1] - rect[:, 0] + 1) * (rect[:, 3] - rect[:, 2] + 1)
+    assert disc.sum() > 40 and touched[disc].sum() < 0.7 * area[disc].sum(), (disc.sum(), touched[disc].sum(),
+                                                                              area[disc].sum())
 
 
 def test_tile_list_structure():
