@@ -109,9 +109,9 @@ typedef struct {
  *   rect       [n,4] uint16: tile rectangle tx0, tx1, ty0, ty1 bounding the
  *              footprint (the region where alpha exp(-d/2) >= alpha_min).
  *   touched    [n] uint32: tiles in the primitive's tile set (0 = not binned).
- *   tileset    [n,8] float, A16: the tile set's parameters, private to the
+ *   tileset    [n,12] float, A16: the tile set's parameters, private to the
  *              library: per tile row of the rectangle, the columns whose
- *              pixel centres the footprint ellipse can reach. */
+ *              pixel centres the footprint can reach. */
 typedef struct {
   float *rec;
   uint32_t *depth_key;
@@ -202,8 +202,9 @@ int hgs_check(const int32_t *dev_err, int32_t *host_err, hgs_stream_t stream);
  * sequence of binary32 operations (exact rounding, no fused multiply-add).
  * The tile set lists, per tile row, the tile columns that the footprint's
  * ellipse (Eq. 1 at alpha exp(-d/2) = alpha_min, Sec. 3.1) reaches over the
- * row's pixel-centre heights, padded for rounding; a surfel whose disc
- * reaches the near plane keeps its whole rectangle.
+ * row's pixel-centre heights, padded for rounding; for a surfel whose disc
+ * reaches the near plane, the columns of the pixels whose rays hit the disc
+ * in front of the near plane.
  * Errors: HGS_ERR_INVALID_ARG for NULL pointers, n < 0, sh_degree outside
  * 0..3, a camera with non-positive size or focal, tile != 16 (UNSUPPORTED). */
 int hgs_preprocess(const hgs_scene *scene, const hgs_camera *cam, const hgs_config *cfg,

@@ -486,7 +486,7 @@ int batch_layout(int nreq, const hgs_request *reqs, int64_t capacity, BatchLayou
   L->off_key = off; off += al256(nn * 4);
   L->off_rect = off; off += al256(nn * 8);
   L->off_touched = off; off += al256(nn * 4);
-  L->off_tileset = off; off += al256(nn * 32);
+  L->off_tileset = off; off += al256(nn * 48);
   L->off_vals = off; off += al256(cc * 4);
   L->off_ranges = off; off += al256((size_t)TXmax * rows * 8);
   L->off_sort = off;
@@ -543,7 +543,7 @@ int hgs_render_batch(int nreq, const hgs_request *reqs, const hgs_config *cfg, v
     p.depth_key = key + prim;
     p.rect = rect + (size_t)prim * 4;
     p.touched = touched + prim;
-    p.tileset = tileset + (size_t)prim * 8;
+    p.tileset = tileset + (size_t)prim * 12;
     bp.req[r] = prep_args(&q.scene, ck, fk, &p);
     bp.deg[r] = q.scene.sh_degree;
     bp.row_off[r] = row;

@@ -503,13 +503,14 @@ __global__ void __launch_bounds__(kSortThreads, 8)
 // search over the lanes' exclusive prefix and its tile row in the owner's
 // row table (first column and first instance of each row, in shared
 // memory).  Sets over kBigSet tiles or kEmitRows rows are deferred to
-// k_emit_big, a block each.
+// k_emit_big, a warp each.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ TileSet load_tileset(const float *tileset, uint32_t p) {
-  const float4 *t = reinterpret_cast<const float4 *>(tileset) + 2 * (size_t)p;
+  const float4 *t = reinterpret_cast<const float4 *>(tileset) + 3 * (size_t)p;
   TileSet s;
   s.t0 = __ldg(t);
   s.t1 = __ldg(t + 1);
+  s.t2 = __ldg(t + 2);
   return s;
 }
 
@@ -637,78 +638,64 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// One block per deferred primitive: the spans and first instances of its rows
-// in shared memory (a block scan of the row widths), then its instances
-// written in order.  A rectangle spans at most kMaxTileRows rows (images are
-// at most 16384 pixels high).
-constexpr int kMaxTileRows = 1024;
+// One warp per deferred primitive: its tile rows 32 at a time (a lane per
+// row: its span, then a warp scan of the widths), and each such chunk's
+// instances written in order, a lane per instance finding its row by a
+// binary search over the chunk's first instances.
 __global__ void __launch_bounds__(256)
     k_emit_big(const uint32_t *__restrict__ ids, const uint32_t *__restrict__ offs,
                const uint16_t *__restrict__ rect, const float *__restrict__ tileset, const int64_t *counters,
                int TX, const uint32_t *__restrict__ bigq, uint32_t *__restrict__ tkeys,
                uint32_t *__restrict__ tvals) {
-  __shared__ uint32_t c0s[kMaxTileRows], firsts[kMaxTileRows];
-  __shared__ uint32_t wsum[8];
   if (counters[2]) return;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int lane = threadIdx.x & 31;
   const int64_t nbig = counters[3];
-  constexpr int kPer = kMaxTileRows / 256;
-  for (int64_t b = blockIdx.x; b < nbig; b += gridDim.x) {
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); b < nbig; b += nw) {
     const uint32_t j = bigq[b];
-    const uint32_t p = __ldg(ids + j), off = __ldg(offs + j);
+    const uint32_t p = __ldg(ids + j);
+    uint32_t base = __ldg(offs + j);
     const uint2 r = __ldg(reinterpret_cast<const uint2 *>(rect) + p);
     const int tx0 = (int)(r.x & 0xffffu), tx1 = (int)(r.x >> 16);
     const int ty0 = (int)(r.y & 0xffffu);
-    const int nrows = min((int)(r.y >> 16) - ty0 + 1, kMaxTileRows);
+    const int nrows = (int)(r.y >> 16) - ty0 + 1;
     const TileSet ts = load_tileset(tileset, p);
-    // thread tid takes rows [tid kPer, tid kPer + kPer)
-    uint32_t w[kPer];
-    uint32_t sum = 0;
-#pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-      const int row = tid * kPer + k;
-      w[k] = 0;
+    for (int r0 = 0; r0 < nrows; r0 += 32) {
+      const int row = r0 + lane;
+      uint32_t c0 = 0, w = 0;
       if (row < nrows) {
-        int c0 = 0, c1 = -1;
-        row_span(ts, ty0 + row, tx0, tx1, &c0, &c1);
-        c0s[row] = (uint32_t)c0;
-        w[k] = (uint32_t)(c1 - c0 + 1);
-        sum += w[k];
+        int a, e;
+        if (row_span(ts, ty0 + row, tx0, tx1, &a, &e)) {
+          c0 = (uint32_t)a;
+          w = (uint32_t)(e - a + 1);
+        }
       }
-    }
-    uint32_t incl = sum;
+      uint32_t incl = w;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += v;
-    }
-    if (lane == 31) wsum[warp] = incl;
-    __syncthreads();
-    uint32_t run = 0, cnt = 0;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      if (q < warp) run += wsum[q];
-      cnt += wsum[q];
-    }
-    run += incl - sum;
-#pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-      const int row = tid * kPer + k;
-      if (row < nrows) firsts[row] = run;
-      run += w[k];
-    }
-    __syncthreads();
-    for (uint32_t l = tid; l < cnt; l += blockDim.x) {
-      // the last row whose first instance is <= l
-      int a = 0, e = nrows;
-      while (e - a > 1) {
-        const int mid = (a + e) >> 1;
-        if (firsts[mid] <= l) a = mid; else e = mid;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
       }
-      tkeys[off + l] = (uint32_t)(ty0 + a) * (uint32_t)TX + c0s[a] + (l - firsts[a]);
-      tvals[off + l] = p;
+      const uint32_t first = incl - w;
+      const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+      for (uint32_t lb = 0; lb < tot; lb += 32) {  // warp-uniform trip count
+        const uint32_t l = lb + lane;
+        // the chunk row holding instance l: the last lane whose first
+        // instance is <= l (an empty row shares its successor's first)
+        int lo = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const uint32_t f = __shfl_sync(0xffffffffu, first, lo + step);
+          if (f <= l) lo += step;
+        }
+        const uint32_t fk = __shfl_sync(0xffffffffu, first, lo), ck = __shfl_sync(0xffffffffu, c0, lo);
+        if (l < tot) {
+          tkeys[base + l] = (uint32_t)(ty0 + r0 + lo) * (uint32_t)TX + ck + (l - fk);
+          tvals[base + l] = p;
+        }
+      }
+      base += tot;
     }
-    __syncthreads();
   }
 }
 

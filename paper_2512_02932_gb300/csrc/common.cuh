@@ -127,43 +127,137 @@ __device__ __forceinline__ bool pixel_tiles(float lo, float hi, int extent, int 
   return true;
 }
 
-// Tile-set parameters of a binned primitive (two float4, written by the
-// preprocess): t0 = (centre x, centre y, chord slope k, padded half chord
-// w), t1 = (1 / padded half height h, y of the leftmost point, y of the
-// rightmost point, flags).  The footprint's chord at height y is centred on
+// Tile-set parameters of a binned primitive (three float4, written by the
+// preprocess).  Ellipse mode: t0 = (centre x, centre y, chord slope k, padded
+// half chord w), t1 = (1 / padded half height h, y of the leftmost point, y
+// of the rightmost point, 0); the footprint's chord at height y is centred on
 // x + k (y - centre y) with half length w sqrt(1 - ((y - centre y) / h)^2).
-// flags (int bits): bit 0 = the whole rectangle, bits 1-15 = the tile-row
-// offset of the primitive's image in a stacked grid, bits 16-31 = the image
-// width in pixels.
+// Disc mode (a surfel reaching the near plane): the disc in
+// pixel-homogeneous camera coordinates P = (fx X + cx Z, fy Y + cy Z, Z),
+// t0 = (centre, dmax), t1 = (axis a, near), t2.xyz = axis b.  t2.w = flags
+// (int bits): bits 0-1 the mode (0 ellipse, 1 the whole rectangle, 2 disc),
+// bits 2-16 the tile-row offset of the primitive's image in a stacked grid,
+// bits 17-31 the image width in pixels.
 struct TileSet {
-  float4 t0, t1;
+  float4 t0, t1, t2;
 };
-__device__ __forceinline__ uint32_t tileset_flags(bool full, int row_off, int width) {
-  return (full ? 1u : 0u) | ((uint32_t)row_off << 1) | ((uint32_t)width << 16);
+enum { kSetEllipse = 0, kSetRect = 1, kSetDisc = 2 };
+__device__ __forceinline__ uint32_t tileset_flags(int mode, int row_off, int width) {
+  return (uint32_t)mode | ((uint32_t)row_off << 2) | ((uint32_t)width << 17);
+}
+
+// The x-range of the pixels of (image-local) tile row lty whose rays hit a
+// disc-mode surfel's disc in front of the near plane.  A pixel (x, y) sees
+// P(u, v) = C + u a + v b (u^2 + v^2 <= dmax) at x = P0/P2, y = P1/P2, depth
+// P2; over the row's band of pixel-centre heights [ya, yb] the points seen
+// form the disc cut by three half-planes c + p u + q v >= 0 (P1 - ya P2,
+// yb P2 - P1, P2 - near).  x is a ratio of affine functions, so its extremes
+// over that convex set lie at points of the circle that a plane x P2 = P0
+// touches, at the lines' crossings with the circle, or at the lines'
+// crossings with each other; every candidate inside the set (relative
+// tolerances 2^-12 on each half-plane, 2^-10 on the radius) is taken, and
+// the range padded by 2^-9 |x| + 1/16 px.  false: no candidate.
+static __device__ __noinline__ bool disc_span(const TileSet &s, int lty, float *xlo, float *xhi) {
+  const float ya = cadd((float)(lty * kTile), 0.5f), yb = cadd(ya, (float)(kTile - 1));
+  const float CX = s.t0.x, CY = s.t0.y, CZ = s.t0.z, r2 = s.t0.w;
+  const float ax = s.t1.x, ay = s.t1.y, az = s.t1.z, nz = s.t1.w;
+  const float bx = s.t2.x, by = s.t2.y, bz = s.t2.z;
+  float c[3], p[3], q[3], tol[3];
+  c[0] = csub(CY, cmul(ya, CZ)); p[0] = csub(ay, cmul(ya, az)); q[0] = csub(by, cmul(ya, bz));
+  c[1] = csub(cmul(yb, CZ), CY); p[1] = csub(cmul(yb, az), ay); q[1] = csub(cmul(yb, bz), by);
+  c[2] = csub(CZ, nz); p[2] = az; q[2] = bz;
+  const float rho = csqrt(r2);
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    tol[k] = cmul(0x1p-12f, cadd(fabsf(c[k]), cmul(rho, cadd(fabsf(p[k]), fabsf(q[k])))));
+  const float r2t = cmul(r2, 1.0009765625f);
+  float lo = __int_as_float(0x7f800000), hi = -__int_as_float(0x7f800000);
+  auto take = [&](float u, float v, bool on_circle) {
+    if (!on_circle && !(cadd(cmul(u, u), cmul(v, v)) <= r2t)) return;
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+      if (!(cadd(cadd(c[m], cmul(p[m], u)), cmul(q[m], v)) >= -tol[m])) return;
+    const float D = cadd(cadd(CZ, cmul(az, u)), cmul(bz, v));
+    if (!(D > 0.0f)) return;
+    const float x = cdiv(cadd(cadd(CX, cmul(ax, u)), cmul(bx, v)), D);
+    lo = fminf(lo, x);
+    hi = fmaxf(hi, x);
+  };
+  // (a) tangency: (CX - x CZ)^2 = r2 ((ax - x az)^2 + (bx - x bz)^2)
+  const float A = csub(cmul(CZ, CZ), cmul(r2, cadd(cmul(az, az), cmul(bz, bz))));
+  const float B = csub(cmul(CX, CZ), cmul(r2, cadd(cmul(ax, az), cmul(bx, bz))));
+  const float Cq = csub(cmul(CX, CX), cmul(r2, cadd(cmul(ax, ax), cmul(bx, bx))));
+  const float dq = csub(cmul(B, B), cmul(A, Cq));
+  if (dq >= 0.0f && A != 0.0f) {
+    const float sq = csqrt(dq);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const float xs = cdiv(k == 0 ? csub(B, sq) : cadd(B, sq), A);
+      const float al = csub(CX, cmul(xs, CZ)), be0 = csub(ax, cmul(xs, az)), be1 = csub(bx, cmul(xs, bz));
+      const float bb = cadd(cmul(be0, be0), cmul(be1, be1));
+      if (!(bb > 0.0f)) continue;
+      const float t = cdiv(-al, bb);
+      take(cmul(t, be0), cmul(t, be1), true);
+    }
+  }
+  // (b) each line's crossings with the circle
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float pq = cadd(cmul(p[k], p[k]), cmul(q[k], q[k]));
+    if (!(pq > 0.0f)) continue;
+    const float t = cdiv(-c[k], pq);
+    const float fu = cmul(t, p[k]), fv = cmul(t, q[k]);
+    const float d2 = cdiv(cmul(c[k], c[k]), pq);
+    if (!(d2 <= r2t)) continue;
+    const float h = csqrt(cdiv(fmaxf(csub(r2, d2), 0.0f), pq));
+    take(csub(fu, cmul(h, q[k])), cadd(fv, cmul(h, p[k])), true);
+    take(cadd(fu, cmul(h, q[k])), csub(fv, cmul(h, p[k])), true);
+  }
+  // (c) the lines' crossings with each other
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i + 1; j < 3; ++j) {
+      const float det = csub(cmul(p[i], q[j]), cmul(p[j], q[i]));
+      if (det == 0.0f) continue;
+      take(cdiv(csub(cmul(q[i], c[j]), cmul(q[j], c[i])), det), cdiv(csub(cmul(p[j], c[i]), cmul(p[i], c[j])), det),
+           false);
+    }
+  if (!(lo <= hi)) return false;
+  const float pad = cadd(cmul(0x1p-9f, fmaxf(fabsf(lo), fabsf(hi))), 0.0625f);
+  *xlo = csub(lo, pad);
+  *xhi = cadd(hi, pad);
+  return true;
 }
 
 // Tile columns [c0, c1] of (stacked) tile row ty of a primitive's tile set,
-// within its rectangle columns [tx0, tx1]: the pixel columns whose centres
-// the padded ellipse reaches in the row's band of pixel-centre heights
-// [16 ty + 0.5, 16 ty + 15.5].  Over the band the chord's left end is least
-// at the height nearest the leftmost point (the left end is convex in y) and
-// the right end greatest nearest the rightmost point.  false: no tile.
+// within its rectangle columns [tx0, tx1].  Ellipse mode: the pixel columns
+// whose centres the padded ellipse reaches in the row's band of pixel-centre
+// heights [16 ty + 0.5, 16 ty + 15.5]; over the band the chord's left end is
+// least at the height nearest the leftmost point (the left end is convex in
+// y) and the right end greatest nearest the rightmost point.  false: no tile.
 __device__ __forceinline__ bool row_span(const TileSet &s, int ty, int tx0, int tx1, int *c0, int *c1) {
-  const uint32_t fl = __float_as_uint(s.t1.w);
-  if (fl & 1u) {
+  const uint32_t fl = __float_as_uint(s.t2.w);
+  const uint32_t mode = fl & 3u;
+  if (mode == kSetRect) {
     *c0 = tx0;
     *c1 = tx1;
     return true;
   }
-  const int lty = ty - (int)((fl >> 1) & 0x7fffu);
-  const int width = (int)(fl >> 16);
-  const float ya = cadd((float)(lty * kTile), 0.5f), yb = cadd(ya, (float)(kTile - 1));
-  const float y1 = fminf(fmaxf(s.t1.y, ya), yb), y2 = fminf(fmaxf(s.t1.z, ya), yb);
-  const float d1 = csub(y1, s.t0.y), d2 = csub(y2, s.t0.y);
-  const float q1 = cmul(d1, s.t1.x), q2 = cmul(d2, s.t1.x);
-  const float r1 = fmaxf(csub(1.0f, cmul(q1, q1)), 0.0f), r2 = fmaxf(csub(1.0f, cmul(q2, q2)), 0.0f);
-  const float xl = csub(cadd(s.t0.x, cmul(s.t0.z, d1)), cmul(s.t0.w, csqrt(r1)));
-  const float xr = cadd(cadd(s.t0.x, cmul(s.t0.z, d2)), cmul(s.t0.w, csqrt(r2)));
+  const int lty = ty - (int)((fl >> 2) & 0x7fffu);
+  const int width = (int)(fl >> 17);
+  float xl, xr;
+  if (mode == kSetDisc) {
+    if (!disc_span(s, lty, &xl, &xr)) return false;
+  } else {
+    const float ya = cadd((float)(lty * kTile), 0.5f), yb = cadd(ya, (float)(kTile - 1));
+    const float y1 = fminf(fmaxf(s.t1.y, ya), yb), y2 = fminf(fmaxf(s.t1.z, ya), yb);
+    const float d1 = csub(y1, s.t0.y), d2 = csub(y2, s.t0.y);
+    const float q1 = cmul(d1, s.t1.x), q2 = cmul(d2, s.t1.x);
+    const float r1 = fmaxf(csub(1.0f, cmul(q1, q1)), 0.0f), r2 = fmaxf(csub(1.0f, cmul(q2, q2)), 0.0f);
+    xl = csub(cadd(s.t0.x, cmul(s.t0.z, d1)), cmul(s.t0.w, csqrt(r1)));
+    xr = cadd(cadd(s.t0.x, cmul(s.t0.z, d2)), cmul(s.t0.w, csqrt(r2)));
+  }
   int a, b;
   if (!pixel_tiles(xl, xr, width, &a, &b)) return false;
   a = max(a, tx0);

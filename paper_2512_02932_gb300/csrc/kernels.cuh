@@ -15,7 +15,7 @@ struct PrepArgs {
   uint32_t *depth_key;
   uint16_t *rect;
   uint32_t *touched;
-  float *tileset;  // [n][8]: TileSet of each binned primitive
+  float *tileset;  // [n][12]: TileSet of each binned primitive
 };
 
 struct PrepGradArgs {

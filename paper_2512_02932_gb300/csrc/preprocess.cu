@@ -32,13 +32,15 @@ struct Contract {
   uint32_t dbits;
   int tx0, tx1, ty0, ty1;
   float bx0, bx1, by0, by1;  // padded pixel box of the alpha >= alpha_min region
-  // tile set: the footprint ellipse's centre, chord slope, padded half chord
-  // and reciprocal padded half height, heights of its leftmost and rightmost
-  // points; full =
-  // the whole rectangle (a surfel reaching the near plane, or a degenerate
-  // ellipse)
+  // tile set (TileSet, common.cuh).  Ellipse mode: the footprint ellipse's
+  // centre, chord slope, padded half chord and reciprocal padded half
+  // height, heights of its leftmost and rightmost points.  Disc mode (a
+  // surfel whose disc reaches the near plane, or whose image conic is
+  // degenerate): the disc's centre and axes in pixel-homogeneous camera
+  // coordinates.  Rect mode: parameters that overflow binary32.
   float ctrx, ctry, kslope, wp, ihy, yl, yr;
-  bool full;
+  int mode;  // kSetEllipse, kSetRect or kSetDisc
+  float dP[3], dA[3], dB[3];
 };
 
 // The contract: a fixed sequence of correctly rounded binary32 operations.
@@ -89,7 +91,7 @@ __device__ bool run_contract(const float mu[3], const float ls[3], const float q
   // ctrx + kslope (y - ctry) with half length wch sqrt(1 - ((y - ctry)/hy)^2);
   // its leftmost (rightmost) point lies at y = ctry - yoff (+ yoff)
   float kslope = 0.f, wch = 0.f, yoff = 0.f;
-  bool whole = false, full = false;
+  bool whole = false, full = false, disc = false;
   if (type == 1) {
     const float c0 = cmul(o.s[0], o.s[0]), c1 = cmul(o.s[1], o.s[1]), c2 = cmul(o.s[2], o.s[2]);
     float V[3][3];
@@ -183,6 +185,16 @@ __device__ bool run_contract(const float mu[3], const float ls[3], const float q
     }
     if (whole) {
       full = true;
+      disc = true;
+      o.dP[0] = cadd(cmul(fx, o.X), cmul(cx, o.Z));
+      o.dP[1] = cadd(cmul(fy, o.Y), cmul(cy, o.Z));
+      o.dP[2] = o.Z;
+      o.dA[0] = cadd(cmul(fx, m0x), cmul(cx, m0z));
+      o.dA[1] = cadd(cmul(fy, m0y), cmul(cy, m0z));
+      o.dA[2] = m0z;
+      o.dB[0] = cadd(cmul(fx, m1x), cmul(cx, m1z));
+      o.dB[1] = cadd(cmul(fy, m1y), cmul(cy, m1z));
+      o.dB[2] = m1z;
       // The disc reaches the near plane (or its image conic is degenerate):
       // a contributing hit lies inside the disc's camera-space extents R at a
       // depth in (near, Z + R_z], which bounds x/z and y/z.
@@ -217,6 +229,13 @@ __device__ bool run_contract(const float mu[3], const float ls[3], const float q
     if (!pixel_tiles(o.bx0, o.bx1, c.W, &o.tx0, &o.tx1)) return false;
     if (!pixel_tiles(o.by0, o.by1, c.H, &o.ty0, &o.ty1)) return false;
   }
+  if (disc) {
+    bool fin = isfinite(o.dmax);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) fin = fin && isfinite(o.dP[k]) && isfinite(o.dA[k]) && isfinite(o.dB[k]);
+    o.mode = fin ? kSetDisc : kSetRect;
+    return true;
+  }
   // padded chord parameters: the half chord by pad_extent plus 2^-10 hx for
   // the rounding of kslope (y - ctry), the half height by pad_extent (its
   // reciprocal is stored)
@@ -228,8 +247,9 @@ __device__ bool run_contract(const float mu[3], const float ls[3], const float q
   o.ihy = cdiv(1.0f, hyp);
   o.yl = csub(ctry, yoff);
   o.yr = cadd(ctry, yoff);
-  o.full = full || !(isfinite(o.kslope) && isfinite(o.wp) && isfinite(o.yl) && isfinite(o.yr) && hyp > 0.0f &&
+  const bool bad = !(isfinite(o.kslope) && isfinite(o.wp) && isfinite(o.yl) && isfinite(o.yr) && hyp > 0.0f &&
                      isfinite(o.ihy));
+  o.mode = (full || bad) ? kSetRect : kSetEllipse;
   return true;
 }
 
@@ -530,8 +550,21 @@ __device__ __forceinline__ int contract_part(const PrepArgs &a, int64_t i, int r
   const bool binned = run_contract(p.mu, p.ls, p.q, p.logit, p.type, a.cam, a.cfg, o);
   a.depth_key[i] = o.dbits;
   if (!binned) return 0;
-  ts.t0 = make_float4(o.ctrx, o.ctry, o.kslope, o.wp);
-  ts.t1 = make_float4(o.ihy, o.yl, o.yr, __uint_as_float(tileset_flags(o.full, row_off, a.cam.W)));
+  const float fl = __uint_as_float(tileset_flags(o.mode, row_off, a.cam.W));
+  if (o.mode == kSetDisc) {
+    ts.t0 = make_float4(o.dP[0], o.dP[1], o.dP[2], o.dmax);
+    ts.t1 = make_float4(o.dA[0], o.dA[1], o.dA[2], a.cfg.near_z);
+    ts.t2 = make_float4(o.dB[0], o.dB[1], o.dB[2], fl);
+  } else {
+    ts.t0 = make_float4(o.ctrx, o.ctry, o.kslope, o.wp);
+    ts.t1 = make_float4(o.ihy, o.yl, o.yr, 0.0f);
+    ts.t2 = make_float4(0.0f, 0.0f, 0.0f, fl);
+  }
+  // written now (only read for a primitive whose set is not empty)
+  float4 *tsd = reinterpret_cast<float4 *>(a.tileset) + 3 * i;
+  tsd[0] = ts.t0;
+  tsd[1] = ts.t1;
+  tsd[2] = ts.t2;
   return o.ty1 - o.ty0 + 1;
 }
 
@@ -581,7 +614,7 @@ __device__ __forceinline__ uint32_t warp_set_count(const TileSet &ts, int tx0, i
 // record.
 template <int DEG>
 __device__ __forceinline__ void finish_one(const PrepArgs &a, int64_t i, int row_off, const PrimIn &p,
-                                           const Contract &o, const TileSet &ts, uint32_t count) {
+                                           const Contract &o, uint32_t count) {
   if (count == 0u) {
     a.touched[i] = 0u;
     reinterpret_cast<uint2 *>(a.rect)[i] = make_uint2(0u, 0u);
@@ -594,8 +627,6 @@ __device__ __forceinline__ void finish_one(const PrepArgs &a, int64_t i, int row
   reinterpret_cast<uint2 *>(a.rect)[i] =
       make_uint2((uint32_t)o.tx0 | ((uint32_t)o.tx1 << 16),
                  (uint32_t)(o.ty0 + row_off) | ((uint32_t)(o.ty1 + row_off) << 16));
-  reinterpret_cast<float4 *>(a.tileset)[2 * i] = ts.t0;
-  reinterpret_cast<float4 *>(a.tileset)[2 * i + 1] = ts.t1;
 
   const CamK &c = a.cam;
   // colour (Sec. 3.1): SH decoded along the view direction
@@ -681,7 +712,7 @@ __global__ void __launch_bounds__(256, 4) preprocess_fwd_kernel(PrepArgs a) {
     nrows = contract_part(a, i, 0, p, o, ts);
   }
   const uint32_t count = warp_set_count(ts, o.tx0, o.tx1, o.ty0, nrows, sts[warp], scnt[warp]);
-  if (in) finish_one<DEG>(a, i, 0, p, o, ts, count);
+  if (in) finish_one<DEG>(a, i, 0, p, o, count);
 }
 
 // Batched: the requests' primitives are concatenated; request r covers global
@@ -711,10 +742,10 @@ __global__ void __launch_bounds__(256) preprocess_batch_kernel(BatchPrepArgs b) 
   const uint32_t count = warp_set_count(ts, o.tx0, o.tx1, o.ty0 + b.row_off[r], nrows, sts[warp], scnt[warp]);
   if (!in) return;
   switch (b.deg[r]) {
-    case 0: finish_one<0>(a, i, b.row_off[r], p, o, ts, count); break;
-    case 1: finish_one<1>(a, i, b.row_off[r], p, o, ts, count); break;
-    case 2: finish_one<2>(a, i, b.row_off[r], p, o, ts, count); break;
-    default: finish_one<3>(a, i, b.row_off[r], p, o, ts, count); break;
+    case 0: finish_one<0>(a, i, b.row_off[r], p, o, count); break;
+    case 1: finish_one<1>(a, i, b.row_off[r], p, o, count); break;
+    case 2: finish_one<2>(a, i, b.row_off[r], p, o, count); break;
+    default: finish_one<3>(a, i, b.row_off[r], p, o, count); break;
   }
 }
 

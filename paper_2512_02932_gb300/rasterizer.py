@@ -135,7 +135,7 @@ class Rasterizer:
         self.depth_key = torch.empty(m, dtype=torch.int32, device=d)
         self.rect = torch.empty((m, 4), dtype=torch.int16, device=d)
         self.touched = torch.empty(m, dtype=torch.int32, device=d)
-        self.tileset = torch.empty((m, 8), dtype=torch.float32, device=d)
+        self.tileset = torch.empty((m, 12), dtype=torch.float32, device=d)
         self.grad_ws = torch.empty((m, GRAD_FLOATS), dtype=torch.float32, device=d)
         self.n = n
         self.ws = None
