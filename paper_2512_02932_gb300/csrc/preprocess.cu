@@ -45,6 +45,8 @@ struct Contract {
 
 // The contract: a fixed sequence of correctly rounded binary32 operations.
 // Returns true if the primitive is binned.
+// SETS = false (the backward) skips the tile-set parameters.
+template <bool SETS>
 __device__ bool run_contract(const float mu[3], const float ls[3], const float q[4], float logit,
                              int type, const CamK &c, const CfgK &f, Contract &o) {
   const float *Rc = c.R;
@@ -117,25 +119,27 @@ __device__ bool run_contract(const float mu[3], const float ls[3], const float q
     ctry = cadd(cmul(fy, o.yz), cy);
     hx = csqrt(cmul(o.dmax, o.s00));
     hy = csqrt(cmul(o.dmax, o.s11));
-    // det(Sigma') by Cauchy-Binet over the columns t_k = s_k J a_k (a sum of
-    // squares: no cancellation for a needle); wch^2 = dmax det / s11
-    float tX[3], tY[3];
+    if constexpr (SETS) {
+      // det(Sigma') by Cauchy-Binet over the columns t_k = s_k J a_k (a sum of
+      // squares: no cancellation for a needle); wch^2 = dmax det / s11
+      float tX[3], tY[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      tX[k] = cmul(o.s[k], cadd(cmul(j00, o.a[k][0]), cmul(j02, o.a[k][2])));
-      tY[k] = cmul(o.s[k], cadd(cmul(j11, o.a[k][1]), cmul(j12, o.a[k][2])));
+      for (int k = 0; k < 3; ++k) {
+        tX[k] = cmul(o.s[k], cadd(cmul(j00, o.a[k][0]), cmul(j02, o.a[k][2])));
+        tY[k] = cmul(o.s[k], cadd(cmul(j11, o.a[k][1]), cmul(j12, o.a[k][2])));
+      }
+      const float m01 = csub(cmul(tX[0], tY[1]), cmul(tY[0], tX[1]));
+      const float m02 = csub(cmul(tX[0], tY[2]), cmul(tY[0], tX[2]));
+      const float m12 = csub(cmul(tX[1], tY[2]), cmul(tY[1], tX[2]));
+      const float x2 = cadd(cadd(cmul(tX[0], tX[0]), cmul(tX[1], tX[1])), cmul(tX[2], tX[2]));
+      const float y2 = cadd(cadd(cmul(tY[0], tY[0]), cmul(tY[1], tY[1])), cmul(tY[2], tY[2]));
+      const float dil = f.dilation;
+      const float detS = cadd(cadd(cadd(cmul(m01, m01), cmul(m02, m02)), cmul(m12, m12)),
+                              cadd(cmul(dil, cadd(x2, y2)), cmul(dil, dil)));
+      kslope = cdiv(o.s01, o.s11);
+      wch = csqrt(cdiv(cmul(o.dmax, detS), o.s11));
+      yoff = cdiv(cmul(o.dmax, o.s01), hx);
     }
-    const float m01 = csub(cmul(tX[0], tY[1]), cmul(tY[0], tX[1]));
-    const float m02 = csub(cmul(tX[0], tY[2]), cmul(tY[0], tX[2]));
-    const float m12 = csub(cmul(tX[1], tY[2]), cmul(tY[1], tX[2]));
-    const float x2 = cadd(cadd(cmul(tX[0], tX[0]), cmul(tX[1], tX[1])), cmul(tX[2], tX[2]));
-    const float y2 = cadd(cadd(cmul(tY[0], tY[0]), cmul(tY[1], tY[1])), cmul(tY[2], tY[2]));
-    const float dil = f.dilation;
-    const float detS = cadd(cadd(cadd(cmul(m01, m01), cmul(m02, m02)), cmul(m12, m12)),
-                            cadd(cmul(dil, cadd(x2, y2)), cmul(dil, dil)));
-    kslope = cdiv(o.s01, o.s11);
-    wch = csqrt(cdiv(cmul(o.dmax, detS), o.s11));
-    yoff = cdiv(cmul(o.dmax, o.s01), hx);
   } else {
     const float m0x = cmul(o.s[0], o.a[0][0]), m0y = cmul(o.s[0], o.a[0][1]), m0z = cmul(o.s[0], o.a[0][2]);
     const float m1x = cmul(o.s[1], o.a[1][0]), m1y = cmul(o.s[1], o.a[1][1]), m1z = cmul(o.s[1], o.a[1][2]);
@@ -169,32 +173,36 @@ __device__ bool run_contract(const float mu[3], const float ls[3], const float q
           ctry = cadd(cmul(fy, cadd(o.yz, oy)), cy);
           hx = cmul(fx, cdiv(csqrt(qx), nD));
           hy = cmul(fy, cdiv(csqrt(qy), nD));
-          // the image ellipse's shape from the dual conic D: Sigma_xy =
-          // fx fy (D02 D12 - D01 D22) / D22^2 and det Sigma = fx^2 fy^2 dmax^2
-          // det(M)^2 / nD^3, M the re-centred splat frame (det D = -dmax^2
-          // det(M)^2)
-          const float D01 = csub(cmul(o.dmax, cadd(cmul(o.e0, o.f0), cmul(o.e1, o.f1))), cmul(e2, f2));
-          kslope = cdiv(cmul(fx, csub(cmul(D02, D12), cmul(D01, D22))), cmul(fy, qy));
-          const float detM = cadd(csub(cmul(o.e0, csub(cmul(o.f1, o.Z), cmul(f2, m1z))),
-                                       cmul(o.e1, csub(cmul(o.f0, o.Z), cmul(f2, m0z)))),
-                                  cmul(e2, csub(cmul(o.f0, m1z), cmul(o.f1, m0z))));
-          wch = cdiv(cmul(cmul(fx, o.dmax), fabsf(detM)), csqrt(cmul(nD, qy)));
-          yoff = cdiv(cmul(kslope, cmul(hy, hy)), hx);
+          if constexpr (SETS) {
+            // the image ellipse's shape from the dual conic D: Sigma_xy =
+            // fx fy (D02 D12 - D01 D22) / D22^2 and det Sigma = fx^2 fy^2 dmax^2
+            // det(M)^2 / nD^3, M the re-centred splat frame (det D = -dmax^2
+            // det(M)^2)
+            const float D01 = csub(cmul(o.dmax, cadd(cmul(o.e0, o.f0), cmul(o.e1, o.f1))), cmul(e2, f2));
+            kslope = cdiv(cmul(fx, csub(cmul(D02, D12), cmul(D01, D22))), cmul(fy, qy));
+            const float detM = cadd(csub(cmul(o.e0, csub(cmul(o.f1, o.Z), cmul(f2, m1z))),
+                                         cmul(o.e1, csub(cmul(o.f0, o.Z), cmul(f2, m0z)))),
+                                    cmul(e2, csub(cmul(o.f0, m1z), cmul(o.f1, m0z))));
+            wch = cdiv(cmul(cmul(fx, o.dmax), fabsf(detM)), csqrt(cmul(nD, qy)));
+            yoff = cdiv(cmul(kslope, cmul(hy, hy)), hx);
+          }
         }
       }
     }
     if (whole) {
       full = true;
       disc = true;
-      o.dP[0] = cadd(cmul(fx, o.X), cmul(cx, o.Z));
-      o.dP[1] = cadd(cmul(fy, o.Y), cmul(cy, o.Z));
-      o.dP[2] = o.Z;
-      o.dA[0] = cadd(cmul(fx, m0x), cmul(cx, m0z));
-      o.dA[1] = cadd(cmul(fy, m0y), cmul(cy, m0z));
-      o.dA[2] = m0z;
-      o.dB[0] = cadd(cmul(fx, m1x), cmul(cx, m1z));
-      o.dB[1] = cadd(cmul(fy, m1y), cmul(cy, m1z));
-      o.dB[2] = m1z;
+      if constexpr (SETS) {
+        o.dP[0] = cadd(cmul(fx, o.X), cmul(cx, o.Z));
+        o.dP[1] = cadd(cmul(fy, o.Y), cmul(cy, o.Z));
+        o.dP[2] = o.Z;
+        o.dA[0] = cadd(cmul(fx, m0x), cmul(cx, m0z));
+        o.dA[1] = cadd(cmul(fy, m0y), cmul(cy, m0z));
+        o.dA[2] = m0z;
+        o.dB[0] = cadd(cmul(fx, m1x), cmul(cx, m1z));
+        o.dB[1] = cadd(cmul(fy, m1y), cmul(cy, m1z));
+        o.dB[2] = m1z;
+      }
       // The disc reaches the near plane (or its image conic is degenerate):
       // a contributing hit lies inside the disc's camera-space extents R at a
       // depth in (near, Z + R_z], which bounds x/z and y/z.
@@ -229,6 +237,7 @@ __device__ bool run_contract(const float mu[3], const float ls[3], const float q
     if (!pixel_tiles(o.bx0, o.bx1, c.W, &o.tx0, &o.tx1)) return false;
     if (!pixel_tiles(o.by0, o.by1, c.H, &o.ty0, &o.ty1)) return false;
   }
+  if constexpr (!SETS) return true;
   if (disc) {
     bool fin = isfinite(o.dmax);
 #pragma unroll
@@ -547,7 +556,7 @@ struct PrimIn {
 // tile rows of the rectangle (0 if not binned).
 __device__ __forceinline__ int contract_part(const PrepArgs &a, int64_t i, int row_off, const PrimIn &p,
                                              Contract &o, TileSet &ts) {
-  const bool binned = run_contract(p.mu, p.ls, p.q, p.logit, p.type, a.cam, a.cfg, o);
+  const bool binned = run_contract<true>(p.mu, p.ls, p.q, p.logit, p.type, a.cam, a.cfg, o);
   a.depth_key[i] = o.dbits;
   if (!binned) return 0;
   const float fl = __uint_as_float(tileset_flags(o.mode, row_off, a.cam.W));
@@ -777,7 +786,7 @@ __device__ __forceinline__ void bwd_ctx(const PrepArgs &a, int64_t i, BwdCtx<DEG
   constexpr int NB = BwdCtx<DEG>::NB;
   float q[4], logit;
   load_params(a, i, x.mu, x.ls, q, logit, x.type);
-  run_contract(x.mu, x.ls, q, logit, x.type, a.cam, a.cfg, x.o);
+  run_contract<false>(x.mu, x.ls, q, logit, x.type, a.cam, a.cfg, x.o);
   load_sh<DEG>(a.sh, i, x.f);
   const CamK &c = a.cam;
   const float vx = x.mu[0] - c.campos[0], vy = x.mu[1] - c.campos[1], vz = x.mu[2] - c.campos[2];
