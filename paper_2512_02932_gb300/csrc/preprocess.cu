@@ -1078,6 +1078,15 @@ __global__ void __launch_bounds__(256) preprocess_bwd_kernel(PrepArgs a, PrepGra
   PGrad r;
   float out[NB * 3];
   if (binned) {
+    // the SH row and the record gradient are read after the contract's
+    // arithmetic: ask L2 for them first (a hint only)
+    if constexpr (NB > 1) {
+      const char *sp = reinterpret_cast<const char *>(a.sh + i * NB * 3);
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(sp));
+      if (NB * 12 > 96) asm volatile("prefetch.global.L2 [%0];" ::"l"(sp + 96));
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(sp + NB * 12 - 4));
+    }
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(g.rec_grad + i * kGradW));
     BwdCtx<DEG> x;
     bwd_ctx<DEG>(a, i, x);
     float G[kGradW];

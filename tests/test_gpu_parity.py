@@ -301,6 +301,28 @@ def test_surfels_reaching_the_near_plane():
     assert_grads_match(got, ref)
 
 
+def test_disc_mode_tile_sets_of_large_near_surfels():
+    """Large surfels crossing the near plane at every orientation over a
+    wider frame (the contract's disc-mode tile sets, rows spanning the
+    frame): lists bit-exact, images within tolerance."""
+    rng = np.random.default_rng(12)
+    n = 120
+    means = np.stack([rng.uniform(-0.6, 0.6, n), rng.uniform(-0.5, 0.5, n), rng.uniform(0.25, 1.5, n)], 1)
+    ls = np.stack([rng.normal(-0.3, 0.5, n), rng.normal(-1.5, 1.0, n), np.full(n, S.SURFEL_LOG_SZ)], 1)
+    q = rng.normal(size=(n, 4))
+    sh = np.zeros((n, 1, 3))
+    sh[:, 0] = rng.uniform(-1.7, 1.7, (n, 3))
+    scene = S.Scene(means.astype(np.float32), ls.astype(np.float32), q.astype(np.float32),
+                    rng.normal(1.0, 1.0, n).astype(np.float32), sh.astype(np.float32), np.zeros(n, np.uint8), 0)
+    cam = S.pinhole(320, 224, 70.0)
+    r, st, g = gpu_forward(scene, cam)
+    assert_lists_bitexact(r, scene, cam)
+    db, rect, touched, rowp = O.contract_bin(scene, cam, CFG, with_rowp=True)
+    assert ((touched > 0) & (rowp[:, 11] == 2)).sum() > 40
+    m = _oracle_maps(scene, cam)
+    assert_images_match(g, m, check_nc=True, max_excluded=0.0, label="disc mode")
+
+
 # ---------------------------------------------------------------------------
 # the autograd Function
 # ---------------------------------------------------------------------------
