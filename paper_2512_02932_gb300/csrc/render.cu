@@ -239,7 +239,7 @@ __device__ __forceinline__ float2 sel2(bool k0, bool k1, float2 a, float2 b) {
 
 struct Eval2 {
   float dx;
-  float2 dy, u, v, g, araw, at, z, inv;
+  float2 dy, u, v, q, g, araw, at, z, inv;
   bool c0, c1;
 };
 
@@ -276,6 +276,7 @@ __device__ __forceinline__ void eval_pair2(const float4 &r0, const float4 &r1, c
     q = fma2(e.u, e.u, mul2(e.v, e.v));
     alpha = -r0.w;
   }
+  e.q = q;
   const float2 x = mul2(q, f2(-0.5f * kLog2e));
   e.g = make_float2(ex2_approx(x.x), ex2_approx(x.y));
   e.araw = mul2(f2(alpha), e.g);
@@ -932,6 +933,84 @@ __device__ __forceinline__ void pair_grad2s(float (&g)[NC][16], Bwd4<NC> &s, con
   }
 }
 
+// One cotangent set, with the per-record sums kept packed over the lane's
+// two pixels (one packed FMA per term instead of two scalar ones) and in the
+// form that needs the fewest products per pair: with e = dL/d(alpha) * alpha
+// (= -2 dL/dd, zero where the pair does not contribute or alpha is clamped),
+//   G[0] = sum dL/d(alpha) G      G[1..3] = sum w dL/dC
+//   G[4..6] = sum e (u u, u v, v v)
+//   G[7..8] = sum e p2^-1 (u, v)  (3D: p2 = 1)
+//   2D only: G[9..10] = sum e q (u, v), G[11] = sum e p2^-1 q   (q = u^2 + v^2)
+// moments_to_slots maps them, linearly, to the record-gradient slots.
+__device__ __forceinline__ void pair_moments2(float2 (&G)[12], Bwd4<1> &s, const Bwd4Smem<1> &ps, int k, int lane,
+                                              const Eval2 &e, bool c0, bool c1, bool is3d, const float4 &r2,
+                                              const float4 &r3, const CfgK &cfg) {
+  const float2 at = sel2(c0, c1, e.at, f2(0.0f));
+  const float2 om = add2(f2(1.0f), neg2(at));
+  const float2 Ti = mul2(s.T, make_float2(rcp_approx(om.x), rcp_approx(om.y)));
+  s.T = sel2(c0, c1, Ti, s.T);
+  const float2 w = mul2(at, Ti);
+  const bool o0 = c0 && e.araw.x <= cfg.alpha_max, o1 = c1 && e.araw.y <= cfg.alpha_max;
+  const float2 oTi = sel2(o0, o1, Ti, f2(0.0f));
+  const float2 dC0 = ps.dC[k][0][lane], dC1 = ps.dC[k][1][lane], dC2 = ps.dC[k][2][lane];
+  const float2 cd = fma2(f2(r2.z), dC0, fma2(f2(r2.w), dC1, mul2(f2(r3.x), dC2)));
+  const float2 fsum = add2(cd, neg2(s.S[0]));
+  s.S[0] = fma2(at, fsum, s.S[0]);
+  G[1] = fma2(w, dC0, G[1]);
+  G[2] = fma2(w, dC1, G[2]);
+  G[3] = fma2(w, dC2, G[3]);
+  const float2 dato = mul2(oTi, fsum);
+  G[0] = fma2(dato, e.g, G[0]);
+  const float2 ee = mul2(dato, at);
+  const float2 eu = mul2(ee, e.u), ev = mul2(ee, e.v);
+  G[4] = fma2(eu, e.u, G[4]);
+  G[5] = fma2(eu, e.v, G[5]);
+  G[6] = fma2(ev, e.v, G[6]);
+  if (is3d) {
+    G[7] = add2(G[7], eu);
+    G[8] = add2(G[8], ev);
+  } else {
+    const float2 eq = mul2(ee, e.q), ei = mul2(ee, e.inv);
+    G[9] = fma2(eq, e.u, G[9]);
+    G[10] = fma2(eq, e.v, G[10]);
+    G[7] = fma2(ei, e.u, G[7]);
+    G[8] = fma2(ei, e.v, G[8]);
+    G[11] = fma2(ei, e.q, G[11]);
+  }
+}
+
+// The record-gradient slots of one lane's moments (the map is linear, so the
+// warp sum of the slots is the slots of the warp sum).
+//  3D: dd = -e / 2, so d h00 = -G4 / 2, d h01 (as 2 u v) = -G5, d h11 = -G6 / 2,
+//      and d x_c = -2 sum dd (W00 u) = W00 G7, d y_c = W01 G7 + W11 G8.
+//  2D: du = -e u, dv = -e v and p2 dL/dp2 = e q give the four (du, dv) (u, v)
+//      sums -G4, -G5, -G5, -G6 and (G9, G10); the centre gradient
+//      -sum p2^-1 (du Q0k + dv Q1k + e q Q2k) is Q0k G7 + Q1k G8 - Q2k G11.
+__device__ __forceinline__ void moments_to_slots(const float2 (&G)[12], bool is3d, const float4 &r1,
+                                                 const float4 &r2, float (&g)[16]) {
+  auto h = [](float2 a) { return a.x + a.y; };
+#pragma unroll
+  for (int i = 0; i < 4; ++i) g[i] = h(G[i]);
+  const float m4 = h(G[4]), m5 = h(G[5]), m6 = h(G[6]), m7 = h(G[7]), m8 = h(G[8]);
+  if (is3d) {
+    g[4] = r1.x * m7;
+    g[5] = fmaf(r1.y, m7, r1.z * m8);
+    g[7] = -0.5f * m4;
+    g[8] = -m5;
+    g[9] = -0.5f * m6;
+  } else {
+    const float m11 = h(G[11]);
+    g[4] = fmaf(r1.x, m7, fmaf(r1.z, m8, -r2.x * m11));
+    g[5] = fmaf(r1.y, m7, fmaf(r1.w, m8, -r2.y * m11));
+    g[7] = -m4;
+    g[8] = -m5;
+    g[9] = -m5;
+    g[10] = -m6;
+    g[11] = h(G[9]);
+    g[12] = h(G[10]);
+  }
+}
+
 // One tile of the rgb-only backward by one warp (all four quadrants), NC
 // cotangent sets.
 template <int NC>
@@ -1011,30 +1090,49 @@ __device__ __forceinline__ void bwd4_tile(const RenderBwdArgs &a, int tile, int 
       const float4 *r = chunk + jj * kRecF4;
       const uint32_t jrel = cs + (uint32_t)jj - start;
       const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4];
-      float gs[NC][16];
+      const bool is3d = r0.w > 0.0f;
+      if constexpr (NC == 1) {
+        float2 G[12];
 #pragma unroll
-      for (int c = 0; c < NC; ++c)
+        for (int i = 0; i < 12; ++i) G[i] = f2(0.0f);
+        bool hit = false;
 #pragma unroll
-        for (int i = 0; i < 16; ++i) gs[c][i] = 0.0f;
-      bool hit = false;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        if (!((m[k] >> jj) & 1u) || jrel >= qmax[k]) continue;
-        const float pyq = (float)(ty0 + 8 * (k >> 1) + ly) + 0.5f;
-        Eval2 e;
-        eval_pair2(r0, r1, r2, r4, px + 8.0f * (float)(k & 1), make_float2(pyq, pyq + 4.0f), a.cfg, e);
-        const uint2 l = ps.last[k][lane];
-        const bool c0 = e.c0 && jrel < l.x, c1 = e.c1 && jrel < l.y;
-        if (!__any_sync(0xffffffffu, c0 || c1)) continue;
-        hit = true;
-        pair_grad2s<NC>(gs, s[k], ps, k, lane, e, c0, c1, r0, r1, r2, r3, a.cfg);
-      }
-      if (!hit) continue;
-      const uint32_t id = sid[buf][jj];
-      if constexpr (NC == 3) {
-        reduce_record3(gs, r0.w > 0.0f, lane, a.rec_grads, id);
+        for (int k = 0; k < 4; ++k) {
+          if (!((m[k] >> jj) & 1u) || jrel >= qmax[k]) continue;
+          const float pyq = (float)(ty0 + 8 * (k >> 1) + ly) + 0.5f;
+          Eval2 e;
+          eval_pair2(r0, r1, r2, r4, px + 8.0f * (float)(k & 1), make_float2(pyq, pyq + 4.0f), a.cfg, e);
+          const uint2 l = ps.last[k][lane];
+          const bool c0 = e.c0 && jrel < l.x, c1 = e.c1 && jrel < l.y;
+          if (!__any_sync(0xffffffffu, c0 || c1)) continue;
+          hit = true;
+          pair_moments2(G, s[k], ps, k, lane, e, c0, c1, is3d, r2, r3, a.cfg);
+        }
+        if (!hit) continue;
+        float gs[16];
+        moments_to_slots(G, is3d, r1, r2, gs);
+        reduce_record<false>(gs, is3d, lane, a.rec_grads[0] + (size_t)sid[buf][jj] * kGradW);
       } else {
-        reduce_record<false>(gs[0], r0.w > 0.0f, lane, a.rec_grads[0] + (size_t)id * kGradW);
+        float gs[NC][16];
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+#pragma unroll
+          for (int i = 0; i < 16; ++i) gs[c][i] = 0.0f;
+        bool hit = false;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (!((m[k] >> jj) & 1u) || jrel >= qmax[k]) continue;
+          const float pyq = (float)(ty0 + 8 * (k >> 1) + ly) + 0.5f;
+          Eval2 e;
+          eval_pair2(r0, r1, r2, r4, px + 8.0f * (float)(k & 1), make_float2(pyq, pyq + 4.0f), a.cfg, e);
+          const uint2 l = ps.last[k][lane];
+          const bool c0 = e.c0 && jrel < l.x, c1 = e.c1 && jrel < l.y;
+          if (!__any_sync(0xffffffffu, c0 || c1)) continue;
+          hit = true;
+          pair_grad2s<NC>(gs, s[k], ps, k, lane, e, c0, c1, r0, r1, r2, r3, a.cfg);
+        }
+        if (!hit) continue;
+        reduce_record3(gs, is3d, lane, a.rec_grads, sid[buf][jj]);
       }
     }
     if (!has_next) break;
