@@ -879,7 +879,33 @@ template <int NC>
 struct Bwd4Smem {
   float2 dC[4][3 * NC][32];  // [quadrant][set * 3 + channel][lane]: the lane's two pixels
   uint2 last[4][32];         // [quadrant][lane]
+  uint32_t qmax[4];          // per quadrant: the latest contributor of any of its pixels
+  uint32_t qb[kCh];          // per staged record: the quadrants it is evaluated against
 };
+
+// Quadrant bits of staged record `lane` (lane < cnt) of the one-warp-per-tile
+// backward: bit k is set iff the record lies before quadrant k's latest
+// contributor (the first lim[k] records of the chunk do) and may hit the
+// quadrant (box overlap, then block_may_hit).  Kept in shared memory, so
+// that no mask stays in registers across the record loop.
+__device__ __forceinline__ uint32_t chunk_qbits(const float4 *buf, int cnt, int lane, float tx0, float ty0,
+                                                const uint32_t (&lim)[4], const CfgK &f) {
+  uint32_t bits = 0;
+  if (lane < cnt) {
+    const float4 *r = buf + lane * kRecF4;
+    const float4 r0 = r[0], r1 = r[1], r2 = r[2], b = r[4];
+    const float2 bxr = unpack_box(b.z), byr = unpack_box(b.w);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if ((uint32_t)lane >= lim[k]) continue;
+      const float bx = tx0 + 8.0f * (float)(k & 1), by = ty0 + 8.0f * (float)(k >> 1);
+      bool hit = bxr.x <= bx + 7.5f && bxr.y >= bx + 0.5f && byr.x <= by + 7.5f && byr.y >= by + 0.5f;
+      if (hit) hit = block_may_hit(r0, r1, r2, b, bx, by, f);
+      bits |= (hit ? 1u : 0u) << k;
+    }
+  }
+  return bits;
+}
 
 // Reverse replay of one record for the two pixels of a lane and NC cotangent
 // sets (sharing the evaluation and the transmittance step), accumulated into
@@ -1020,7 +1046,6 @@ __device__ __forceinline__ void bwd4_tile(const RenderBwdArgs &a, int tile, int 
   const int lx = lane & 7, ly = lane >> 3;
   const size_t HW = (size_t)a.cam.W * a.cam.H;
   Bwd4<NC> s[4];
-  uint32_t qmax[4];
   uint32_t wmax = 0;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
@@ -1055,8 +1080,9 @@ __device__ __forceinline__ void bwd4_tile(const RenderBwdArgs &a, int tile, int 
       s[k].S[c] = fma2(f2(a.cfg.bg[0]), d[0], fma2(f2(a.cfg.bg[1]), d[1], mul2(f2(a.cfg.bg[2]), d[2])));
     }
     ps.last[k][lane] = make_uint2(l[0], l[1]);
-    qmax[k] = __reduce_max_sync(0xffffffffu, max(l[0], l[1]));
-    wmax = max(wmax, qmax[k]);
+    const uint32_t qm = __reduce_max_sync(0xffffffffu, max(l[0], l[1]));
+    if (lane == 0) ps.qmax[k] = qm;
+    wmax = max(wmax, qm);
   }
   __syncwarp();
   if (wmax == 0) return;
@@ -1078,12 +1104,17 @@ __device__ __forceinline__ void bwd4_tile(const RenderBwdArgs &a, int tile, int 
     }
     __syncwarp();
     const float4 *chunk = &sm[buf][0];
-    uint32_t want = 0;
+    {
+      uint32_t lim[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) want |= (qmax[k] > cs - start ? 1u : 0u) << k;
-    uint32_t m[4];
-    chunk_masks<4>(chunk, (int)(ce - cs), lane, (float)tx0, (float)ty0, 0, want, a.cfg, m);
-    uint32_t any = m[0] | m[1] | m[2] | m[3];
+      for (int k = 0; k < 4; ++k) {
+        const uint32_t q = ps.qmax[k];
+        lim[k] = q > cs - start ? min((uint32_t)kCh, q - (cs - start)) : 0u;
+      }
+      ps.qb[lane] = chunk_qbits(chunk, (int)(ce - cs), lane, (float)tx0, (float)ty0, lim, a.cfg);
+    }
+    uint32_t any = __ballot_sync(0xffffffffu, ps.qb[lane] != 0u);
+    __syncwarp();
     while (any) {
       const int jj = 31 - __clz(any);
       any &= ~(1u << jj);
@@ -1091,6 +1122,7 @@ __device__ __forceinline__ void bwd4_tile(const RenderBwdArgs &a, int tile, int 
       const uint32_t jrel = cs + (uint32_t)jj - start;
       const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4];
       const bool is3d = r0.w > 0.0f;
+      const uint32_t qb = ps.qb[jj];
       if constexpr (NC == 1) {
         float2 G[12];
 #pragma unroll
@@ -1098,7 +1130,7 @@ __device__ __forceinline__ void bwd4_tile(const RenderBwdArgs &a, int tile, int 
         bool hit = false;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          if (!((m[k] >> jj) & 1u) || jrel >= qmax[k]) continue;
+          if (!((qb >> k) & 1u)) continue;
           const float pyq = (float)(ty0 + 8 * (k >> 1) + ly) + 0.5f;
           Eval2 e;
           eval_pair2(r0, r1, r2, r4, px + 8.0f * (float)(k & 1), make_float2(pyq, pyq + 4.0f), a.cfg, e);
@@ -1121,7 +1153,7 @@ __device__ __forceinline__ void bwd4_tile(const RenderBwdArgs &a, int tile, int 
         bool hit = false;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          if (!((m[k] >> jj) & 1u) || jrel >= qmax[k]) continue;
+          if (!((qb >> k) & 1u)) continue;
           const float pyq = (float)(ty0 + 8 * (k >> 1) + ly) + 0.5f;
           Eval2 e;
           eval_pair2(r0, r1, r2, r4, px + 8.0f * (float)(k & 1), make_float2(pyq, pyq + 4.0f), a.cfg, e);
