@@ -973,8 +973,12 @@ __device__ __forceinline__ void pair_moments2(float2 (&G)[12], Bwd4<1> &s, const
                                               const float4 &r3, const CfgK &cfg) {
   const float2 at = sel2(c0, c1, e.at, f2(0.0f));
   const float2 om = add2(f2(1.0f), neg2(at));
+  // a pixel the pair does not reach has at = 0, and T * rcp(1) is T (the
+  // approximate reciprocal of 1 is exactly 1 on sm_103a; no decision here
+  // depends on T, so even a rounding-level change would only perturb the
+  // gradient at the rounding level)
   const float2 Ti = mul2(s.T, make_float2(rcp_approx(om.x), rcp_approx(om.y)));
-  s.T = sel2(c0, c1, Ti, s.T);
+  s.T = Ti;
   const float2 w = mul2(at, Ti);
   const bool o0 = c0 && e.araw.x <= cfg.alpha_max, o1 = c1 && e.araw.y <= cfg.alpha_max;
   const float2 oTi = sel2(o0, o1, Ti, f2(0.0f));
