@@ -917,7 +917,7 @@ __device__ __forceinline__ void pair_grad2s(float (&g)[NC][16], Bwd4<NC> &s, con
   const float2 at = sel2(c0, c1, e.at, f2(0.0f));
   const float2 om = add2(f2(1.0f), neg2(at));
   const float2 Ti = mul2(s.T, make_float2(rcp_approx(om.x), rcp_approx(om.y)));
-  s.T = sel2(c0, c1, Ti, s.T);
+  s.T = Ti;  // T * rcp(1) = T where the pair does not reach the pixel (at = 0)
   const float2 w = mul2(at, Ti);
   const bool o0 = c0 && e.araw.x <= cfg.alpha_max, o1 = c1 && e.araw.y <= cfg.alpha_max;
   const float2 oTi = sel2(o0, o1, Ti, f2(0.0f));
