@@ -162,6 +162,7 @@ __device__ __forceinline__ void chunk_tiles(int64_t n, int64_t &t0, int64_t &t1)
 }
 
 __global__ void __launch_bounds__(kSortThreads) k_chunk_hist(PassArgs a) {
+  grid_dep();
   constexpr int W = kSortThreads / 32;
   __shared__ uint32_t h[W][256];
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -195,6 +196,7 @@ __global__ void __launch_bounds__(kSortThreads) k_chunk_hist(PassArgs a) {
 
 // one block per digit: chunk offsets = digit base + counts of earlier chunks
 __global__ void __launch_bounds__(256) k_chunk_scan(PassArgs a, int nchunks) {
+  grid_dep();
   __shared__ uint32_t wsum[8];
   __shared__ uint32_t s_base;
   const int d = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -282,6 +284,7 @@ __device__ __forceinline__ void fetch_tile(const PassArgs &a, ScatterSmem &sm, i
 
 template <int BITS>
 __global__ void __launch_bounds__(kSortThreads) k_scatter(PassArgs a) {
+  grid_dep();
   constexpr int W = kSortThreads / 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ScatterSmem &sm = *reinterpret_cast<ScatterSmem *>(smem_raw);
@@ -411,6 +414,7 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter(PassArgs a) {
 __global__ void __launch_bounds__(kSortThreads)
     k_scan_partial(const uint32_t *__restrict__ ids, const uint32_t *__restrict__ touched,
                    const int64_t *d_n, uint64_t *__restrict__ blk) {
+  grid_dep();
   __shared__ uint64_t ws[kSortThreads / 32];
   const int tid = threadIdx.x;
   int64_t b0, b1;
@@ -433,6 +437,7 @@ __global__ void __launch_bounds__(kSortThreads)
 __global__ void __launch_bounds__(1024)
     k_scan_top(uint64_t *__restrict__ blk, int nblocks, int64_t capacity, int64_t *counters, int64_t *d_count,
                int32_t *dev_err) {
+  grid_dep();
   __shared__ uint64_t wsum[32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint64_t own = tid < nblocks ? blk[tid] : 0ull;
@@ -463,6 +468,7 @@ __global__ void __launch_bounds__(1024)
 __global__ void __launch_bounds__(kSortThreads, 8)
     k_scan_final(const uint32_t *__restrict__ ids, const uint32_t *__restrict__ touched,
                  const int64_t *counters, const uint64_t *__restrict__ blk, uint32_t *__restrict__ offs) {
+  grid_dep();
   __shared__ uint32_t wsum[kSortThreads / 32];
   __shared__ uint32_t carry;
   if (counters[2]) return;
@@ -518,6 +524,7 @@ __global__ void __launch_bounds__(256)
     k_emit(const uint32_t *__restrict__ ids, const uint32_t *__restrict__ offs, const uint16_t *__restrict__ rect,
            const uint32_t *__restrict__ touched, const float *__restrict__ tileset, int64_t *counters, int TX,
            uint32_t *__restrict__ tkeys, uint32_t *__restrict__ tvals, uint32_t *__restrict__ bigq) {
+  grid_dep();
   // per warp and lane: (first column | first instance << 16) of each row of
   // the lane's primitive, rows past its last 0xffffffff; the lanes' tile sets
   __shared__ uint32_t rows[256 / 32][32][kEmitRows];
@@ -647,6 +654,7 @@ __global__ void __launch_bounds__(256)
                const uint16_t *__restrict__ rect, const float *__restrict__ tileset, const int64_t *counters,
                int TX, const uint32_t *__restrict__ bigq, uint32_t *__restrict__ tkeys,
                uint32_t *__restrict__ tvals) {
+  grid_dep();
   if (counters[2]) return;
   const int lane = threadIdx.x & 31;
   const int64_t nbig = counters[3];
@@ -701,6 +709,7 @@ __global__ void __launch_bounds__(256)
 
 // tiles no instance reached keep their initial (0xffffffff, 0): make them [0, 0)
 __global__ void __launch_bounds__(256) k_ranges_fix(uint32_t *__restrict__ ranges, int tiles) {
+  grid_dep();
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tiles; t += gridDim.x * blockDim.x) {
     uint2 *r = reinterpret_cast<uint2 *>(ranges) + t;
     if (r->x == 0xffffffffu) *r = make_uint2(0u, 0u);
@@ -710,6 +719,7 @@ __global__ void __launch_bounds__(256) k_ranges_fix(uint32_t *__restrict__ range
 __global__ void __launch_bounds__(256)
     k_keys64(const uint32_t *__restrict__ tkeys, const uint32_t *__restrict__ vals,
              const uint32_t *__restrict__ depth_key, const int64_t *counters, uint64_t *__restrict__ keys) {
+  grid_dep();
   if (counters[2]) return;
   const int64_t K = counters[1];
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < K;
@@ -735,14 +745,21 @@ static int pass_grid() {
 template <int B>
 static void scatter_bits(const PassArgs &p, int G, cudaStream_t s) {
   if (p.bits == B)
-    k_scatter<B><<<G, kSortThreads, sizeof(ScatterSmem), s>>>(p);
+    pdl_launch(k_scatter<B>, G, kSortThreads, sizeof(ScatterSmem), s, p);
   else if constexpr (B > 1)
     scatter_bits<B - 1>(p, G, s);
 }
 
-static void radix_pass(const PassArgs &p, int G, cudaStream_t s) {
-  k_chunk_hist<<<G, kSortThreads, 0, s>>>(p);
-  k_chunk_scan<<<1 << p.bits, 256, 0, s>>>(p, G);
+// Every kernel of the sort after the first is launched with programmatic
+// dependent launch (grid_dep() at its top): its blocks are already resident
+// when its predecessor finishes.  The first follows a memset and is launched
+// plainly.
+static void radix_pass(const PassArgs &p, int G, cudaStream_t s, bool first = false) {
+  if (first)
+    k_chunk_hist<<<G, kSortThreads, 0, s>>>(p);
+  else
+    pdl_launch(k_chunk_hist, G, kSortThreads, 0, s, p);
+  pdl_launch(k_chunk_scan, 1 << p.bits, 256, 0, s, p, G);
   scatter_bits<8>(p, G, s);
 }
 
@@ -766,15 +783,15 @@ int launch_bin_sort(const BinArgs &a, const BinWorkspace &ws, cudaStream_t s) {
     w.keys_out = ws.dk[p & 1];
     w.vals_out = ws.dv[p & 1];
     w.count_out = p == 0 ? &ctr[0] : nullptr;
-    radix_pass(w, G, s);
+    radix_pass(w, G, s, p == 0);
     dk_in = ws.dk[p & 1];
     dv_in = ws.dv[p & 1];
   }
   const uint32_t *ids = ws.dv[1];
   // 2) instance offsets and K (capacity check on the device)
-  k_scan_partial<<<kSortBlocks, kSortThreads, 0, s>>>(ids, a.touched, &ctr[0], ws.blk);
-  k_scan_top<<<1, 1024, 0, s>>>(ws.blk, kSortBlocks, a.capacity, ctr, a.d_count, a.dev_err);
-  k_scan_final<<<kSortBlocks, kSortThreads, 0, s>>>(ids, a.touched, ctr, ws.blk, ws.offs);
+  pdl_launch(k_scan_partial, kSortBlocks, kSortThreads, 0, s, ids, a.touched, &ctr[0], ws.blk);
+  pdl_launch(k_scan_top, 1, 1024, 0, s, ws.blk, kSortBlocks, a.capacity, ctr, a.d_count, a.dev_err);
+  pdl_launch(k_scan_final, kSortBlocks, kSortThreads, 0, s, ids, a.touched, ctr, ws.blk, ws.offs);
   // 3) emit (dk[0], free once the depth sort is done, holds the deferred
   //    queue), then the tile digits, split evenly over the passes (13 bits ->
   //    7 + 6): fewer buckets per pass give longer runs in the write-out
@@ -783,10 +800,10 @@ int launch_bin_sort(const BinArgs &a, const BinWorkspace &ws, cudaStream_t s) {
   uint32_t *vbuf[2];
   vbuf[0] = (passes % 2 == 0) ? a.vals : ws.tv;
   vbuf[1] = (passes % 2 == 0) ? ws.tv : a.vals;
-  k_emit<<<kSortBlocks, 256, 0, s>>>(ids, ws.offs, a.rect, a.touched, a.tileset, ctr, a.TX, ws.tk[0], vbuf[0],
-                                      ws.dk[0]);
-  k_emit_big<<<kSortBlocks, 256, 0, s>>>(ids, ws.offs, a.rect, a.tileset, ctr, a.TX, ws.dk[0], ws.tk[0],
-                                          vbuf[0]);
+  pdl_launch(k_emit, kSortBlocks, 256, 0, s, ids, ws.offs, a.rect, a.touched, a.tileset, ctr, a.TX, ws.tk[0],
+             vbuf[0], ws.dk[0]);
+  pdl_launch(k_emit_big, kSortBlocks, 256, 0, s, ids, ws.offs, a.rect, a.tileset, ctr, a.TX, ws.dk[0], ws.tk[0],
+             vbuf[0]);
   for (int p = 0; p < passes; ++p) {
     const bool last = p + 1 == passes;
     PassArgs w{};
@@ -805,8 +822,8 @@ int launch_bin_sort(const BinArgs &a, const BinWorkspace &ws, cudaStream_t s) {
     w.ranges = last ? a.ranges : nullptr;
     radix_pass(w, G, s);
   }
-  k_ranges_fix<<<(a.tiles + 255) / 256, 256, 0, s>>>(a.ranges, a.tiles);
-  if (a.keys) k_keys64<<<kSortBlocks, 256, 0, s>>>(ws.tk[passes & 1], a.vals, a.depth_key, ctr, a.keys);
+  pdl_launch(k_ranges_fix, (a.tiles + 255) / 256, 256, 0, s, a.ranges, a.tiles);
+  if (a.keys) pdl_launch(k_keys64, kSortBlocks, 256, 0, s, ws.tk[passes & 1], a.vals, a.depth_key, ctr, a.keys);
   return 0;
 }
 

@@ -282,6 +282,34 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return y;
 }
 
+// Programmatic dependent launch (sm_90 and later).  A kernel launched with
+// pdl_launch may become resident while its predecessor in the stream is
+// still finishing; grid_dep() at the top of such a kernel waits until the
+// predecessor has completed and its writes are visible, before any global
+// memory access, and then lets the successor's blocks be scheduled in turn
+// (they wait the same way).  Launched normally, both instructions return at
+// once.
+__device__ __forceinline__ void grid_dep() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+static inline void pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // error-free transforms for the double-float projected centre
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
   s = __fadd_rn(a, b);
