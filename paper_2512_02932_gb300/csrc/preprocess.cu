@@ -1069,6 +1069,7 @@ __device__ __forceinline__ void store_sh_rows_warp(float *sh, int64_t n, int64_t
 
 template <int DEG>
 __global__ void __launch_bounds__(256) preprocess_bwd_kernel(PrepArgs a, PrepGradArgs g) {
+  grid_dep();
   constexpr int NB = (DEG + 1) * (DEG + 1);
   constexpr bool kWarpRows = DEG == 1 || DEG == 3;
   __shared__ float4 stage[kWarpRows ? 8 : 1][kWarpRows ? 16 * NB * 3 / 4 : 1];
@@ -1150,6 +1151,7 @@ __device__ __forceinline__ void pgrad_axpy(PGrad &y, float s, const PGrad &x) {
 
 template <int DEG>
 __global__ void __launch_bounds__(128) preprocess_bwd_fdo_kernel(PrepArgs a, PrepGradFdoArgs g3) {
+  grid_dep();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
   PrepGradArgs g;
@@ -1211,10 +1213,10 @@ int launch_preprocess_bwd(const PrepArgs &a, const PrepGradArgs &g, int deg, cud
   if (a.n == 0) return 0;
   const unsigned grid = (unsigned)((a.n + 255) / 256);
   switch (deg) {
-    case 0: preprocess_bwd_kernel<0><<<grid, 256, 0, s>>>(a, g); break;
-    case 1: preprocess_bwd_kernel<1><<<grid, 256, 0, s>>>(a, g); break;
-    case 2: preprocess_bwd_kernel<2><<<grid, 256, 0, s>>>(a, g); break;
-    default: preprocess_bwd_kernel<3><<<grid, 256, 0, s>>>(a, g); break;
+    case 0: pdl_launch(preprocess_bwd_kernel<0>, grid, 256, 0, s, a, g); break;
+    case 1: pdl_launch(preprocess_bwd_kernel<1>, grid, 256, 0, s, a, g); break;
+    case 2: pdl_launch(preprocess_bwd_kernel<2>, grid, 256, 0, s, a, g); break;
+    default: pdl_launch(preprocess_bwd_kernel<3>, grid, 256, 0, s, a, g); break;
   }
   return 0;
 }
@@ -1223,10 +1225,10 @@ int launch_preprocess_bwd_fdo(const PrepArgs &a, const PrepGradFdoArgs &g, int d
   if (a.n == 0) return 0;
   const unsigned grid = (unsigned)((a.n + 127) / 128);
   switch (deg) {
-    case 0: preprocess_bwd_fdo_kernel<0><<<grid, 128, 0, s>>>(a, g); break;
-    case 1: preprocess_bwd_fdo_kernel<1><<<grid, 128, 0, s>>>(a, g); break;
-    case 2: preprocess_bwd_fdo_kernel<2><<<grid, 128, 0, s>>>(a, g); break;
-    default: preprocess_bwd_fdo_kernel<3><<<grid, 128, 0, s>>>(a, g); break;
+    case 0: pdl_launch(preprocess_bwd_fdo_kernel<0>, grid, 128, 0, s, a, g); break;
+    case 1: pdl_launch(preprocess_bwd_fdo_kernel<1>, grid, 128, 0, s, a, g); break;
+    case 2: pdl_launch(preprocess_bwd_fdo_kernel<2>, grid, 128, 0, s, a, g); break;
+    default: pdl_launch(preprocess_bwd_fdo_kernel<3>, grid, 128, 0, s, a, g); break;
   }
   return 0;
 }

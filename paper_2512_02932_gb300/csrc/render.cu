@@ -507,6 +507,7 @@ __global__ void __launch_bounds__(kFwdWarps * 32, kFwdMinBlocks) render_fwd2_ker
 __global__ void __launch_bounds__(kFwdWarps * 32, kFwdMinBlocks) render_fwd_sched_kernel(RenderArgs a,
                                                                                      const uint32_t *order,
                                                                   uint32_t *counter, int tiles) {
+  grid_dep();
   __shared__ __align__(16) float4 sm[4][2][kCh * kRecF4];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   while (true) {
@@ -834,6 +835,7 @@ __global__ void k_tile_work(const uint32_t *__restrict__ n_last, int W, int H, i
 
 // A tile's forward work estimate: its list length.
 __global__ void k_tile_len(const uint32_t *__restrict__ ranges, int tiles, uint32_t *__restrict__ work) {
+  grid_dep();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < tiles) work[t] = ranges[2 * t + 1] - ranges[2 * t];
 }
@@ -848,6 +850,7 @@ __device__ __forceinline__ int work_bucket(uint32_t w) {
 
 __global__ void __launch_bounds__(1024) k_tile_order(const uint32_t *__restrict__ work, int tiles,
                                                      uint32_t *__restrict__ order, uint32_t *__restrict__ counter) {
+  grid_dep();
   __shared__ uint32_t cnt[64];
   if (threadIdx.x < 64) cnt[threadIdx.x] = 0;
   __syncthreads();
@@ -1186,6 +1189,7 @@ __device__ __forceinline__ void bwd4_tile(const RenderBwdArgs &a, int tile, int 
 template <int NC>
 __global__ void __launch_bounds__(32, NC == 1 ? 20 : 16) render_bwd_rgb4_kernel(RenderBwdArgs a, const uint32_t *order,
                                                                               uint32_t *counter, int tiles) {
+  grid_dep();
   __shared__ __align__(16) float4 sm[2][kCh * kRecF4];
   __shared__ uint32_t sid[2][kCh];
   __shared__ Bwd4Smem<NC> ps;
@@ -1258,9 +1262,10 @@ int launch_render_fwd(const RenderArgs &a, cudaStream_t s) {
     return max(1, sms * max(per, 1));
   }();
   uint32_t *work = a.tile_sched, *order = a.tile_sched + tiles, *counter = a.tile_sched + 2 * (size_t)tiles;
-  k_tile_len<<<(tiles + 255) / 256, 256, 0, s>>>(a.ranges, tiles, work);
-  k_tile_order<<<1, 1024, 0, s>>>(work, tiles, order, counter);
-  render_fwd_sched_kernel<<<min(tiles, resident), 128, 0, s>>>(a, order, counter, tiles);
+  // programmatic dependent launches (grid_dep() at the top of each kernel)
+  pdl_launch(k_tile_len, (tiles + 255) / 256, 256, 0, s, a.ranges, tiles, work);
+  pdl_launch(k_tile_order, 1, 1024, 0, s, (const uint32_t *)work, tiles, order, counter);
+  pdl_launch(render_fwd_sched_kernel, min(tiles, resident), 128, 0, s, a, (const uint32_t *)order, counter, tiles);
   return 0;
 }
 
@@ -1291,9 +1296,11 @@ static void launch_bwd4(const RenderBwdArgs &a, int tiles, cudaStream_t s) {
     return;
   }
   uint32_t *work = a.tile_sched, *order = a.tile_sched + tiles, *counter = a.tile_sched + 2 * (size_t)tiles;
+  // (the first follows the record-gradient memset; the others are
+  // programmatic dependent launches)
   k_tile_work<<<(tiles + 7) / 8, 256, 0, s>>>(a.n_last, a.cam.W, a.cam.H, a.cam.TX, tiles, work);
-  k_tile_order<<<1, 1024, 0, s>>>(work, tiles, order, counter);
-  render_bwd_rgb4_kernel<NC><<<min(tiles, resident), 32, 0, s>>>(a, order, counter, tiles);
+  pdl_launch(k_tile_order, 1, 1024, 0, s, (const uint32_t *)work, tiles, order, counter);
+  pdl_launch(render_bwd_rgb4_kernel<NC>, min(tiles, resident), 32, 0, s, a, (const uint32_t *)order, counter, tiles);
 }
 
 int launch_render_bwd(const RenderBwdArgs &a, cudaStream_t s) {
