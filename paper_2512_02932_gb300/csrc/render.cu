@@ -27,6 +27,8 @@
 // every backward reproduces the forward's contribution decisions bit for bit.
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -246,14 +248,16 @@ struct Eval2 {
 // eval_pair for the pixels (px, py.x) and (px, py.y).  For a pixel that does
 // not contribute the fields are finite (a surfel's reciprocal is replaced by
 // 0 where the ray misses the plane's front), so a caller may blend it in with
-// weight 0.
-__device__ __forceinline__ void eval_pair2(const float4 &r0, const float4 &r1, const float4 &r2, const float4 &r4,
-                                           float px, float2 py, const CfgK &f, Eval2 &e) {
+// weight 0.  eval_pair2_t is the same for a record known to be a 3D Gaussian
+// (IS3D) or a surfel; eval_pair2 picks by the record's sign.
+template <bool IS3D>
+__device__ __forceinline__ void eval_pair2_t(const float4 &r0, const float4 &r1, const float4 &r2, const float4 &r4,
+                                             float px, float2 py, const CfgK &f, Eval2 &e) {
   e.dx = __fsub_rn(__fsub_rn(px, r0.x), r4.x);
   e.dy = add2(add2(py, f2(-r0.y)), f2(-r4.y));
   float2 q;
   float alpha;
-  if (r0.w > 0.0f) {
+  if constexpr (IS3D) {
     e.u = fma2(f2(r1.x), f2(e.dx), mul2(f2(r1.y), e.dy));
     e.v = mul2(f2(r1.z), e.dy);
     q = fma2(e.u, e.u, mul2(e.v, e.v));
@@ -283,6 +287,13 @@ __device__ __forceinline__ void eval_pair2(const float4 &r0, const float4 &r1, c
   e.c0 = e.c0 && e.araw.x >= f.alpha_min;
   e.c1 = e.c1 && e.araw.y >= f.alpha_min;
   e.at = make_float2(fminf(e.araw.x, f.alpha_max), fminf(e.araw.y, f.alpha_max));
+}
+__device__ __forceinline__ void eval_pair2(const float4 &r0, const float4 &r1, const float4 &r2, const float4 &r4,
+                                           float px, float2 py, const CfgK &f, Eval2 &e) {
+  if (r0.w > 0.0f)
+    eval_pair2_t<true>(r0, r1, r2, r4, px, py, f, e);
+  else
+    eval_pair2_t<false>(r0, r1, r2, r4, px, py, f, e);
 }
 
 // Block tests of one staged chunk against QW quadrants of a tile: bit l of
@@ -971,8 +982,9 @@ __device__ __forceinline__ void pair_grad2s(float (&g)[NC][16], Bwd4<NC> &s, con
 //   G[7..8] = sum e p2^-1 (u, v)  (3D: p2 = 1)
 //   2D only: G[9..10] = sum e q (u, v), G[11] = sum e p2^-1 q   (q = u^2 + v^2)
 // moments_to_slots maps them, linearly, to the record-gradient slots.
+template <bool IS3D>
 __device__ __forceinline__ void pair_moments2(float2 (&G)[12], Bwd4<1> &s, const Bwd4Smem<1> &ps, int k, int lane,
-                                              const Eval2 &e, bool c0, bool c1, bool is3d, const float4 &r2,
+                                              const Eval2 &e, bool c0, bool c1, const float4 &r2,
                                               const float4 &r3, const CfgK &cfg) {
   const float2 at = sel2(c0, c1, e.at, f2(0.0f));
   const float2 om = add2(f2(1.0f), neg2(at));
@@ -999,7 +1011,7 @@ __device__ __forceinline__ void pair_moments2(float2 (&G)[12], Bwd4<1> &s, const
   G[4] = fma2(eu, e.u, G[4]);
   G[5] = fma2(eu, e.v, G[5]);
   G[6] = fma2(ev, e.v, G[6]);
-  if (is3d) {
+  if constexpr (IS3D) {
     G[7] = add2(G[7], eu);
     G[8] = add2(G[8], ev);
   } else {
@@ -1019,13 +1031,14 @@ __device__ __forceinline__ void pair_moments2(float2 (&G)[12], Bwd4<1> &s, const
 //  2D: du = -e u, dv = -e v and p2 dL/dp2 = e q give the four (du, dv) (u, v)
 //      sums -G4, -G5, -G5, -G6 and (G9, G10); the centre gradient
 //      -sum p2^-1 (du Q0k + dv Q1k + e q Q2k) is Q0k G7 + Q1k G8 - Q2k G11.
-__device__ __forceinline__ void moments_to_slots(const float2 (&G)[12], bool is3d, const float4 &r1,
-                                                 const float4 &r2, float (&g)[16]) {
+template <bool IS3D>
+__device__ __forceinline__ void moments_to_slots(const float2 (&G)[12], const float4 &r1, const float4 &r2,
+                                                 float (&g)[16]) {
   auto h = [](float2 a) { return a.x + a.y; };
 #pragma unroll
   for (int i = 0; i < 4; ++i) g[i] = h(G[i]);
   const float m4 = h(G[4]), m5 = h(G[5]), m6 = h(G[6]), m7 = h(G[7]), m8 = h(G[8]);
-  if (is3d) {
+  if constexpr (IS3D) {
     g[4] = r1.x * m7;
     g[5] = fmaf(r1.y, m7, r1.z * m8);
     g[7] = -0.5f * m4;
@@ -1131,26 +1144,35 @@ __device__ __forceinline__ void bwd4_tile(const RenderBwdArgs &a, int tile, int 
       const bool is3d = r0.w > 0.0f;
       const uint32_t qb = ps.qb[jj];
       if constexpr (NC == 1) {
-        float2 G[12];
+        // the quadrant loop specialised for the record's kind
+        auto record = [&](auto kind) {
+          constexpr bool IS3D = decltype(kind)::value;
+          float2 G[12];
 #pragma unroll
-        for (int i = 0; i < 12; ++i) G[i] = f2(0.0f);
-        bool hit = false;
+          for (int i = 0; i < 12; ++i) G[i] = f2(0.0f);
+          bool hit = false;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          if (!((qb >> k) & 1u)) continue;
-          const float pyq = (float)(ty0 + 8 * (k >> 1) + ly) + 0.5f;
-          Eval2 e;
-          eval_pair2(r0, r1, r2, r4, px + 8.0f * (float)(k & 1), make_float2(pyq, pyq + 4.0f), a.cfg, e);
-          const uint2 l = ps.last[k][lane];
-          const bool c0 = e.c0 && jrel < l.x, c1 = e.c1 && jrel < l.y;
-          if (!__any_sync(0xffffffffu, c0 || c1)) continue;
-          hit = true;
-          pair_moments2(G, s[k], ps, k, lane, e, c0, c1, is3d, r2, r3, a.cfg);
-        }
-        if (!hit) continue;
-        float gs[16];
-        moments_to_slots(G, is3d, r1, r2, gs);
-        reduce_record<false>(gs, is3d, lane, a.rec_grads[0] + (size_t)sid[buf][jj] * kGradW);
+          for (int k = 0; k < 4; ++k) {
+            if (!((qb >> k) & 1u)) continue;
+            const float pyq = (float)(ty0 + 8 * (k >> 1) + ly) + 0.5f;
+            Eval2 e;
+            eval_pair2_t<IS3D>(r0, r1, r2, r4, px + 8.0f * (float)(k & 1), make_float2(pyq, pyq + 4.0f), a.cfg,
+                               e);
+            const uint2 l = ps.last[k][lane];
+            const bool c0 = e.c0 && jrel < l.x, c1 = e.c1 && jrel < l.y;
+            if (!__any_sync(0xffffffffu, c0 || c1)) continue;
+            hit = true;
+            pair_moments2<IS3D>(G, s[k], ps, k, lane, e, c0, c1, r2, r3, a.cfg);
+          }
+          if (!hit) return;
+          float gs[16];
+          moments_to_slots<IS3D>(G, r1, r2, gs);
+          reduce_record<false>(gs, IS3D, lane, a.rec_grads[0] + (size_t)sid[buf][jj] * kGradW);
+        };
+        if (is3d)
+          record(std::true_type{});
+        else
+          record(std::false_type{});
       } else {
         float gs[NC][16];
 #pragma unroll
