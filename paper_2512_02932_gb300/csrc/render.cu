@@ -924,7 +924,7 @@ __device__ __forceinline__ uint32_t chunk_qbits(const float4 *buf, int cnt, int 
 // Reverse replay of one record for the two pixels of a lane and NC cotangent
 // sets (sharing the evaluation and the transmittance step), accumulated into
 // the per-record slots g[set] (pair_grad_rgb for both pixels).
-template <int NC>
+template <int NC, bool IS3D>
 __device__ __forceinline__ void pair_grad2s(float (&g)[NC][16], Bwd4<NC> &s, const Bwd4Smem<NC> &ps, int k,
                                             int lane, const Eval2 &e, bool c0, bool c1, const float4 &r0,
                                             const float4 &r1, const float4 &r2, const float4 &r3, const CfgK &cfg) {
@@ -948,7 +948,7 @@ __device__ __forceinline__ void pair_grad2s(float (&g)[NC][16], Bwd4<NC> &s, con
     const float2 dato = mul2(oTi, fsum);
     acc(g[c][0], dato, e.g);
     const float2 dd = mul2(dato, mul2(f2(-0.5f), at));
-    if (r0.w > 0.0f) {
+    if constexpr (IS3D) {
       const float2 ddu = mul2(dd, e.u), ddv = mul2(dd, e.v);
       acc(g[c][7], ddu, e.u);
       acc(g[c][8], mul2(f2(2.0f), ddu), e.v);
@@ -1174,26 +1174,34 @@ __device__ __forceinline__ void bwd4_tile(const RenderBwdArgs &a, int tile, int 
         else
           record(std::false_type{});
       } else {
-        float gs[NC][16];
+        auto record = [&](auto kind) {
+          constexpr bool IS3D = decltype(kind)::value;
+          float gs[NC][16];
 #pragma unroll
-        for (int c = 0; c < NC; ++c)
+          for (int c = 0; c < NC; ++c)
 #pragma unroll
-          for (int i = 0; i < 16; ++i) gs[c][i] = 0.0f;
-        bool hit = false;
+            for (int i = 0; i < 16; ++i) gs[c][i] = 0.0f;
+          bool hit = false;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          if (!((qb >> k) & 1u)) continue;
-          const float pyq = (float)(ty0 + 8 * (k >> 1) + ly) + 0.5f;
-          Eval2 e;
-          eval_pair2(r0, r1, r2, r4, px + 8.0f * (float)(k & 1), make_float2(pyq, pyq + 4.0f), a.cfg, e);
-          const uint2 l = ps.last[k][lane];
-          const bool c0 = e.c0 && jrel < l.x, c1 = e.c1 && jrel < l.y;
-          if (!__any_sync(0xffffffffu, c0 || c1)) continue;
-          hit = true;
-          pair_grad2s<NC>(gs, s[k], ps, k, lane, e, c0, c1, r0, r1, r2, r3, a.cfg);
-        }
-        if (!hit) continue;
-        reduce_record3(gs, is3d, lane, a.rec_grads, sid[buf][jj]);
+          for (int k = 0; k < 4; ++k) {
+            if (!((qb >> k) & 1u)) continue;
+            const float pyq = (float)(ty0 + 8 * (k >> 1) + ly) + 0.5f;
+            Eval2 e;
+            eval_pair2_t<IS3D>(r0, r1, r2, r4, px + 8.0f * (float)(k & 1), make_float2(pyq, pyq + 4.0f), a.cfg,
+                               e);
+            const uint2 l = ps.last[k][lane];
+            const bool c0 = e.c0 && jrel < l.x, c1 = e.c1 && jrel < l.y;
+            if (!__any_sync(0xffffffffu, c0 || c1)) continue;
+            hit = true;
+            pair_grad2s<NC, IS3D>(gs, s[k], ps, k, lane, e, c0, c1, r0, r1, r2, r3, a.cfg);
+          }
+          if (!hit) return;
+          reduce_record3(gs, IS3D, lane, a.rec_grads, sid[buf][jj]);
+        };
+        if (is3d)
+          record(std::true_type{});
+        else
+          record(std::false_type{});
       }
     }
     if (!has_next) break;
