@@ -399,7 +399,9 @@ __device__ __forceinline__ void blend2(Fwd2 &s, const EvalF2 &e, const float4 &r
   const float2 a2 = mul2(e.at, keep);
   const float2 w = mul2(a2, s.T);
   s.T = mul2(s.T, add2(f2(1.0f), neg2(a2)));
-  const float2 z = make_float2(keep.x != 0.0f ? e.z.x : 0.0f, keep.y != 0.0f ? e.z.y : 0.0f);
+  // e.z is finite for every pair (see EvalF2), so a pair that does not count
+  // adds w z = 0 to the depth, as it adds 0 to the colour
+  const float2 z = e.z;
   s.C0 = fma2(w, f2(r2.z), s.C0);
   s.C1 = fma2(w, f2(r2.w), s.C1);
   s.C2 = fma2(w, f2(r3.x), s.C2);
