@@ -704,7 +704,7 @@ __device__ __forceinline__ void finish_one(const PrepArgs &a, int64_t i, int row
 }
 
 template <int DEG>
-__global__ void __launch_bounds__(256, 4) preprocess_fwd_kernel(PrepArgs a) {
+__global__ void __launch_bounds__(256, 3) preprocess_fwd_kernel(PrepArgs a) {
   __shared__ TileSet sts[8][32];
   __shared__ uint32_t scnt[8][32];
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
