@@ -374,6 +374,28 @@ __device__ __forceinline__ void load_sh(const float *sh, int64_t i, float *f) {
   }
 }
 
+// Visit the SH row p coefficient by coefficient (fn(k, f_k0, f_k1, f_k2)),
+// loading a few 16-byte pieces at a time so the row is never held whole.
+template <int DEG, class Fn>
+__device__ __forceinline__ void sh_visit(const float *p, Fn &&fn) {
+  constexpr int NB = (DEG + 1) * (DEG + 1);
+  if constexpr ((NB * 3) % 4 == 0) {
+    // four coefficients (12 floats, three float4) per step
+    const float4 *p4 = reinterpret_cast<const float4 *>(p);
+#pragma unroll
+    for (int c = 0; c < NB / 4; ++c) {
+      const float4 a = __ldg(p4 + 3 * c), b = __ldg(p4 + 3 * c + 1), d = __ldg(p4 + 3 * c + 2);
+      fn(4 * c + 0, a.x, a.y, a.z);
+      fn(4 * c + 1, a.w, b.x, b.y);
+      fn(4 * c + 2, b.z, b.w, d.x);
+      fn(4 * c + 3, d.y, d.z, d.w);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < NB; ++k) fn(k, __ldg(p + 3 * k), __ldg(p + 3 * k + 1), __ldg(p + 3 * k + 2));
+  }
+}
+
 // a d - b c with one rounding error (Kahan's FMA algorithm)
 __device__ __forceinline__ float det2(float a, float b, float c, float d) {
   const float w = __fmul_rn(b, c);
@@ -640,21 +662,19 @@ __device__ __forceinline__ void finish_one(const PrepArgs &a, int64_t i, int row
   const CamK &c = a.cam;
   // colour (Sec. 3.1): SH decoded along the view direction
   constexpr int NB = (DEG + 1) * (DEG + 1);
-  float f[NB * 3];
-  load_sh<DEG>(a.sh, i, f);
   float dx = mu[0] - c.campos[0], dy = mu[1] - c.campos[1], dz = mu[2] - c.campos[2];
   const float il = rsqrtf(dx * dx + dy * dy + dz * dz);
   dx *= il; dy *= il; dz *= il;
   float Y[NB];
   sh_eval<DEG>(dx, dy, dz, Y);
-  float col[3];
+  float col[3] = {0.5f, 0.5f, 0.5f};
+  sh_visit<DEG>(a.sh + i * NB * 3, [&](int k, float f0, float f1, float f2) {
+    col[0] = fmaf(f0, Y[k], col[0]);
+    col[1] = fmaf(f1, Y[k], col[1]);
+    col[2] = fmaf(f2, Y[k], col[2]);
+  });
 #pragma unroll
-  for (int ch = 0; ch < 3; ++ch) {
-    float v = 0.5f;
-#pragma unroll
-    for (int k = 0; k < NB; ++k) v = fmaf(f[3 * k + ch], Y[k], v);
-    col[ch] = fmaxf(v, 0.0f);
-  }
+  for (int ch = 0; ch < 3; ++ch) col[ch] = fmaxf(col[ch], 0.0f);
   // normal: smallest-scale axis (z for a surfel), facing the camera
   const int kn = normal_axis(type, ls);
   float n0, n1, n2;
@@ -770,44 +790,62 @@ struct PGrad {
 };
 
 // What the backward needs of one primitive besides its record gradient.
-template <int DEG>
+// STREAM: the SH row is read again where it is needed (twice), never held
+// whole, which keeps the one-set backward at 80 registers; else (the
+// three-set backward, which runs the chain three times) it is held.
+template <int DEG, bool STREAM>
 struct BwdCtx {
   static constexpr int NB = (DEG + 1) * (DEG + 1);
   float mu[3], ls[3];
   int type;
   Contract o;
-  float f[NB * 3], Yb[NB];
+  const float *f;                    // the primitive's SH row
+  float fr[STREAM ? 1 : NB * 3];     // its copy in registers (not STREAM)
+  float Yb[NB];
   float ux, uy, uz, il;
   bool cpos[3];  // colour channel not clamped at 0
+  template <class Fn>
+  __device__ __forceinline__ void visit_sh(Fn &&fn) const {
+    if constexpr (STREAM) {
+      sh_visit<DEG>(f, fn);
+    } else {
+#pragma unroll
+      for (int k = 0; k < NB; ++k) fn(k, fr[3 * k], fr[3 * k + 1], fr[3 * k + 2]);
+    }
+  }
 };
 
-template <int DEG>
-__device__ __forceinline__ void bwd_ctx(const PrepArgs &a, int64_t i, BwdCtx<DEG> &x) {
-  constexpr int NB = BwdCtx<DEG>::NB;
+
+template <int DEG, bool STREAM>
+__device__ __forceinline__ void bwd_ctx(const PrepArgs &a, int64_t i, BwdCtx<DEG, STREAM> &x) {
+  constexpr int NB = BwdCtx<DEG, STREAM>::NB;
   float q[4], logit;
   load_params(a, i, x.mu, x.ls, q, logit, x.type);
   run_contract<false>(x.mu, x.ls, q, logit, x.type, a.cam, a.cfg, x.o);
-  load_sh<DEG>(a.sh, i, x.f);
+  x.f = a.sh + i * NB * 3;
+  if constexpr (!STREAM) load_sh<DEG>(a.sh, i, x.fr);
   const CamK &c = a.cam;
   const float vx = x.mu[0] - c.campos[0], vy = x.mu[1] - c.campos[1], vz = x.mu[2] - c.campos[2];
   x.il = rsqrtf(vx * vx + vy * vy + vz * vz);
   x.ux = vx * x.il; x.uy = vy * x.il; x.uz = vz * x.il;
   sh_eval<DEG>(x.ux, x.uy, x.uz, x.Yb);
+  float v[3] = {0.5f, 0.5f, 0.5f};
+  x.visit_sh([&](int k, float f0, float f1, float f2) {
+    v[0] = fmaf(f0, x.Yb[k], v[0]);
+    v[1] = fmaf(f1, x.Yb[k], v[1]);
+    v[2] = fmaf(f2, x.Yb[k], v[2]);
+  });
 #pragma unroll
-  for (int ch = 0; ch < 3; ++ch) {
-    float v = 0.5f;
-#pragma unroll
-    for (int k = 0; k < NB; ++k) v = fmaf(x.f[3 * k + ch], x.Yb[k], v);
-    x.cpos[ch] = v > 0.0f;
-  }
+  for (int ch = 0; ch < 3; ++ch) x.cpos[ch] = v[ch] > 0.0f;
 }
 
 // The chain from a record gradient G (layout: common.cuh) to the raw
 // parameters: projection (App. C), camera, rotation, activations and the SH
 // colour.  Linear in G.
-template <int DEG>
-__device__ __forceinline__ PGrad chain_grad(const PrepArgs &a, const BwdCtx<DEG> &ctx, const float (&G)[kGradW]) {
-  constexpr int NB = BwdCtx<DEG>::NB;
+template <int DEG, bool STREAM>
+__device__ __forceinline__ PGrad chain_grad(const PrepArgs &a, const BwdCtx<DEG, STREAM> &ctx,
+                                            const float (&G)[kGradW]) {
+  constexpr int NB = BwdCtx<DEG, STREAM>::NB;
   const CamK &c = a.cam;
   const Contract &o = ctx.o;
   const int type = ctx.type;
@@ -982,8 +1020,9 @@ __device__ __forceinline__ PGrad chain_grad(const PrepArgs &a, const BwdCtx<DEG>
   for (int ch = 0; ch < 3; ++ch) r.dv[ch] = ctx.cpos[ch] ? G[1 + ch] : 0.0f;
   if (DEG > 0) {
     float wk[NB];
-#pragma unroll
-    for (int k = 0; k < NB; ++k) wk[k] = r.dv[0] * ctx.f[3 * k] + r.dv[1] * ctx.f[3 * k + 1] + r.dv[2] * ctx.f[3 * k + 2];
+    ctx.visit_sh([&](int k, float f0, float f1, float f2) {
+      wk[k] = r.dv[0] * f0 + r.dv[1] * f1 + r.dv[2] * f2;
+    });
     float gd[3];
     sh_grad<DEG>(ctx.ux, ctx.uy, ctx.uz, wk, gd);
     const float dotp = gd[0] * ctx.ux + gd[1] * ctx.uy + gd[2] * ctx.uz;
@@ -1068,7 +1107,7 @@ __device__ __forceinline__ void store_sh_rows_warp(float *sh, int64_t n, int64_t
 }
 
 template <int DEG>
-__global__ void __launch_bounds__(256) preprocess_bwd_kernel(PrepArgs a, PrepGradArgs g) {
+__global__ void __launch_bounds__(256, 3) preprocess_bwd_kernel(PrepArgs a, PrepGradArgs g) {
   grid_dep();
   constexpr int NB = (DEG + 1) * (DEG + 1);
   constexpr bool kWarpRows = DEG == 1 || DEG == 3;
@@ -1088,11 +1127,11 @@ __global__ void __launch_bounds__(256) preprocess_bwd_kernel(PrepArgs a, PrepGra
       asm volatile("prefetch.global.L2 [%0];" ::"l"(sp + NB * 12 - 4));
     }
     asm volatile("prefetch.global.L2 [%0];" ::"l"(g.rec_grad + i * kGradW));
-    BwdCtx<DEG> x;
-    bwd_ctx<DEG>(a, i, x);
+    BwdCtx<DEG, true> x;
+    bwd_ctx<DEG, true>(a, i, x);
     float G[kGradW];
     load_rec_grad(g.rec_grad, i, G);
-    r = chain_grad<DEG>(a, x, G);
+    r = chain_grad<DEG, true>(a, x, G);
 #pragma unroll
     for (int k = 0; k < NB; ++k)
 #pragma unroll
@@ -1161,16 +1200,16 @@ __global__ void __launch_bounds__(128) preprocess_bwd_fdo_kernel(PrepArgs a, Pre
     store_zero_grad<DEG>(g, i);
     return;
   }
-  BwdCtx<DEG> x;
-  bwd_ctx<DEG>(a, i, x);
+  BwdCtx<DEG, false> x;
+  bwd_ctx<DEG, false>(a, i, x);
   float yy = 0.0f;
 #pragma unroll
-  for (int k = 0; k < BwdCtx<DEG>::NB; ++k) yy = fmaf(x.Yb[k], x.Yb[k], yy);
+  for (int k = 0; k < BwdCtx<DEG, false>::NB; ++k) yy = fmaf(x.Yb[k], x.Yb[k], yy);
   float G[kGradW];
   load_rec_grad(g3.rec_low, i, G);
-  PGrad pl = chain_grad<DEG>(a, x, G);
+  PGrad pl = chain_grad<DEG, false>(a, x, G);
   load_rec_grad(g3.rec_high, i, G);
-  PGrad ph = chain_grad<DEG>(a, x, G);
+  PGrad ph = chain_grad<DEG, false>(a, x, G);
   const float lh = pgrad_dot(pl, ph, yy);
   if (lh < 0.0f) {
     if (x.type == 0) {
@@ -1181,7 +1220,7 @@ __global__ void __launch_bounds__(128) preprocess_bwd_fdo_kernel(PrepArgs a, Pre
     if (g3.n_conflicts) atomicAdd(g3.n_conflicts, 1ull);
   }
   load_rec_grad(g3.rec_color, i, G);
-  PGrad r = chain_grad<DEG>(a, x, G);
+  PGrad r = chain_grad<DEG, false>(a, x, G);
   pgrad_axpy(r, 1.0f, pl);
   pgrad_axpy(r, 1.0f, ph);
   store_pgrad<DEG>(g, i, r, x.Yb);
