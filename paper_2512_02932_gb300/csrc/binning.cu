@@ -659,15 +659,35 @@ __global__ void __launch_bounds__(256)
   const int lane = threadIdx.x & 31;
   const int64_t nbig = counters[3];
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); b < nbig; b += nw) {
-    const uint32_t j = bigq[b];
-    const uint32_t p = __ldg(ids + j);
+  // software pipeline over the warp's primitives: the next one's queue
+  // entry and id are loaded, and its rectangle, set and offset prefetched
+  // into L2, while the current one is written (the three dependent loads
+  // at the head of each primitive otherwise leave the warp waiting)
+  const int64_t b0 = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  uint32_t jn = 0, pn = 0;
+  if (b0 < nbig) {
+    jn = bigq[b0];
+    pn = __ldg(ids + jn);
+  }
+  for (int64_t b = b0; b < nbig; b += nw) {
+    const uint32_t j = jn, p = pn;
+    const bool more = b + nw < nbig;
+    if (more) {
+      jn = bigq[b + nw];
+      pn = __ldg(ids + jn);
+    }
     uint32_t base = __ldg(offs + j);
     const uint2 r = __ldg(reinterpret_cast<const uint2 *>(rect) + p);
     const int tx0 = (int)(r.x & 0xffffu), tx1 = (int)(r.x >> 16);
     const int ty0 = (int)(r.y & 0xffffu);
     const int nrows = (int)(r.y >> 16) - ty0 + 1;
     const TileSet ts = load_tileset(tileset, p);
+    if (more && lane < 3) {  // hints only
+      const void *h = lane == 0   ? static_cast<const void *>(reinterpret_cast<const uint2 *>(rect) + pn)
+                      : lane == 1 ? static_cast<const void *>(reinterpret_cast<const float4 *>(tileset) + 3 * (size_t)pn)
+                                  : static_cast<const void *>(offs + jn);
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(h));
+    }
     for (int r0 = 0; r0 < nrows; r0 += 32) {
       const int row = r0 + lane;
       uint32_t c0 = 0, w = 0;
