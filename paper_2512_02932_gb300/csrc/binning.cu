@@ -651,31 +651,42 @@ __global__ void __launch_bounds__(256)
 // binary search over the chunk's first instances.
 __global__ void __launch_bounds__(256)
     k_emit_big(const uint32_t *__restrict__ ids, const uint32_t *__restrict__ offs,
-               const uint16_t *__restrict__ rect, const float *__restrict__ tileset, const int64_t *counters,
+               const uint16_t *__restrict__ rect, const float *__restrict__ tileset, int64_t *counters,
                int TX, const uint32_t *__restrict__ bigq, uint32_t *__restrict__ tkeys,
                uint32_t *__restrict__ tvals) {
   grid_dep();
   if (counters[2]) return;
   const int lane = threadIdx.x & 31;
   const int64_t nbig = counters[3];
+  // Warps take the deferred primitives a batch at a time from a counter
+  // (their sizes run from a few rows to the whole frame, so a fixed stride
+  // left the busiest warp with 2.4 times the mean work); a batch is sized
+  // for about four per warp, 1 to 8 primitives.  Within a batch, the next
+  // primitive's queue entry and id are loaded, and its rectangle, set and
+  // offset prefetched into L2, while the current one is written.
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-  // software pipeline over the warp's primitives: the next one's queue
-  // entry and id are loaded, and its rectangle, set and offset prefetched
-  // into L2, while the current one is written (the three dependent loads
-  // at the head of each primitive otherwise leave the warp waiting)
-  const int64_t b0 = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int64_t kBigBatch = max((int64_t)1, min((int64_t)8, nbig / (4 * nw)));
+  unsigned long long *next = reinterpret_cast<unsigned long long *>(&counters[4]);
+  int64_t b = 0, bend = 0;
   uint32_t jn = 0, pn = 0;
-  if (b0 < nbig) {
-    jn = bigq[b0];
-    pn = __ldg(ids + jn);
-  }
-  for (int64_t b = b0; b < nbig; b += nw) {
-    const uint32_t j = jn, p = pn;
-    const bool more = b + nw < nbig;
-    if (more) {
-      jn = bigq[b + nw];
+  while (true) {
+    if (b >= bend) {
+      unsigned long long t = 0;
+      if (lane == 0) t = atomicAdd(next, (unsigned long long)kBigBatch);
+      t = __shfl_sync(0xffffffffu, t, 0);
+      if ((int64_t)t >= nbig) break;
+      b = (int64_t)t;
+      bend = min(nbig, b + kBigBatch);
+      jn = bigq[b];
       pn = __ldg(ids + jn);
     }
+    const uint32_t j = jn, p = pn;
+    const bool more = b + 1 < bend;
+    if (more) {
+      jn = bigq[b + 1];
+      pn = __ldg(ids + jn);
+    }
+    ++b;
     uint32_t base = __ldg(offs + j);
     const uint2 r = __ldg(reinterpret_cast<const uint2 *>(rect) + p);
     const int tx0 = (int)(r.x & 0xffffu), tx1 = (int)(r.x >> 16);
@@ -784,7 +795,8 @@ static void radix_pass(const PassArgs &p, int G, cudaStream_t s, bool first = fa
 }
 
 int launch_bin_sort(const BinArgs &a, const BinWorkspace &ws, cudaStream_t s) {
-  int64_t *ctr = ws.counters;  // 0 = binned primitives, 1 = K, 2 = overflow, 3 = deferred primitives
+  int64_t *ctr = ws.counters;  // 0 = binned primitives, 1 = K, 2 = overflow, 3 = deferred primitives,
+                               // 4 = deferred primitives handed out
   cudaMemsetAsync(ctr, 0, ws.head_bytes, s);
   const int G = pass_grid();
   // 1) depth digits over the binned primitives (the first pass compacts)
