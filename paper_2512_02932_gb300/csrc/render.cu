@@ -949,28 +949,52 @@ __device__ __forceinline__ void pair_grad2s(float (&g)[NC][16], Bwd4<NC> &s, con
     acc(g[c][3], w, dC2);
     const float2 dato = mul2(oTi, fsum);
     acc(g[c][0], dato, e.g);
-    const float2 dd = mul2(dato, mul2(f2(-0.5f), at));
+    // the moments of pair_moments2 in scalar slots (moments_to_slots3 maps
+    // them to the record-gradient slots once per record):
+    //   [4] sum e p2^-1 u  [5] sum e p2^-1 v  [7] sum e u u  [8] sum e u v
+    //   [9] sum e v v; surfels also [10] sum e p2^-1 q  [11] sum e q u
+    //   [12] sum e q v      (e = dL/d(alpha) alpha, 3D: p2 = 1)
+    const float2 ee = mul2(dato, at);
+    const float2 eu = mul2(ee, e.u), ev = mul2(ee, e.v);
+    acc(g[c][7], eu, e.u);
+    acc(g[c][8], eu, e.v);
+    acc(g[c][9], ev, e.v);
     if constexpr (IS3D) {
-      const float2 ddu = mul2(dd, e.u), ddv = mul2(dd, e.v);
-      acc(g[c][7], ddu, e.u);
-      acc(g[c][8], mul2(f2(2.0f), ddu), e.v);
-      acc(g[c][9], ddv, e.v);
-      const float2 dd2 = mul2(dd, f2(-2.0f));
-      acc(g[c][4], mul2(dd2, e.u), f2(r1.x));
-      acc(g[c][5], dd2, fma2(e.u, f2(r1.y), mul2(e.v, f2(r1.z))));
+      g[c][4] += eu.x + eu.y;
+      g[c][5] += ev.x + ev.y;
     } else {
-      const float2 du = mul2(mul2(f2(2.0f), e.u), dd), dv = mul2(mul2(f2(2.0f), e.v), dd);
-      const float2 dp0 = mul2(du, e.inv), dp1 = mul2(dv, e.inv);
-      const float2 dq2 = neg2(fma2(du, e.u, mul2(dv, e.v)));
-      const float2 dp2 = mul2(dq2, e.inv);
-      acc(g[c][7], du, e.u);
-      acc(g[c][8], du, e.v);
-      acc(g[c][9], dv, e.u);
-      acc(g[c][10], dv, e.v);
-      acc(g[c][11], dq2, e.u);
-      acc(g[c][12], dq2, e.v);
-      acc(g[c][4], fma2(dp0, f2(-r1.x), fma2(dp1, f2(-r1.z), mul2(dp2, f2(-r2.x)))), f2(1.0f));
-      acc(g[c][5], fma2(dp0, f2(-r1.y), fma2(dp1, f2(-r1.w), mul2(dp2, f2(-r2.y)))), f2(1.0f));
+      const float2 eq = mul2(ee, e.q), ei = mul2(ee, e.inv);
+      acc(g[c][11], eq, e.u);
+      acc(g[c][12], eq, e.v);
+      acc(g[c][4], ei, e.u);
+      acc(g[c][5], ei, e.v);
+      acc(g[c][10], ei, e.q);
+    }
+  }
+}
+
+// The three-set moments of pair_grad2s mapped, per set, to the
+// record-gradient slots (the same linear map as moments_to_slots).
+template <int NC, bool IS3D>
+__device__ __forceinline__ void moments_to_slots3(float (&g)[NC][16], const float4 &r1, const float4 &r2) {
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const float m4 = g[c][4], m5 = g[c][5], m7 = g[c][7], m8 = g[c][8], m9 = g[c][9];
+    if constexpr (IS3D) {
+      g[c][4] = r1.x * m4;
+      g[c][5] = fmaf(r1.y, m4, r1.z * m5);
+      g[c][7] = -0.5f * m7;
+      g[c][8] = -m8;
+      g[c][9] = -0.5f * m9;
+    } else {
+      const float m10 = g[c][10];
+      g[c][4] = fmaf(r1.x, m4, fmaf(r1.z, m5, -r2.x * m10));
+      g[c][5] = fmaf(r1.y, m4, fmaf(r1.w, m5, -r2.y * m10));
+      g[c][7] = -m7;
+      g[c][8] = -m8;
+      g[c][9] = -m8;
+      g[c][10] = -m9;
+      // [11], [12] are already the p2 dL/dp2 sums
     }
   }
 }
@@ -1198,6 +1222,7 @@ __device__ __forceinline__ void bwd4_tile(const RenderBwdArgs &a, int tile, int 
             pair_grad2s<NC, IS3D>(gs, s[k], ps, k, lane, e, c0, c1, r0, r1, r2, r3, a.cfg);
           }
           if (!hit) return;
+          moments_to_slots3<NC, IS3D>(gs, r1, r2);
           reduce_record3(gs, IS3D, lane, a.rec_grads, sid[buf][jj]);
         };
         if (is3d)
