@@ -772,19 +772,27 @@ __device__ __forceinline__ void reduce_record(float (&g)[16], bool is3d, int lan
     if ((lane & 1) == 0) atomicAdd(row + comp, v);
     return;
   }
-  // slots 0-5, 7, 8 in one transpose; then 9 (3D) or 9-12 (2D)
+  // slots 0-5, 7, 8 in one transpose; then 9 (3D) or 9-12 (2D).  One
+  // atomic instruction adds all of them: lanes 4i hold the transpose's
+  // slots, lane 1 (3D) or lanes 8i + 1 (2D) the others.
   float a[8] = {g[0], g[1], g[2], g[3], g[4], g[5], g[7], g[8]};
   const int s8 = (lane >> 2) & 7;
   const float v8 = sum8(a, lane);
-  if ((lane & 3) == 0) atomicAdd(row + (s8 < 6 ? s8 : s8 + 1), v8);
+  float vt;
+  int st;
+  bool tail;
   if (is3d) {
-    const float v = sum1(g[9]);
-    if (lane == 0) atomicAdd(row + 9, v);
+    vt = sum1(g[9]);
+    st = 9;
+    tail = lane == 1;
   } else {
     float b[4] = {g[9], g[10], g[11], g[12]};
-    const float v4 = sum4(b, lane);
-    if ((lane & 7) == 0) atomicAdd(row + 9 + ((lane >> 3) & 3), v4);
+    vt = sum4(b, lane);
+    st = 9 + ((lane >> 3) & 3);
+    tail = (lane & 7) == 1;
   }
+  const bool head = (lane & 3) == 0;
+  if (head || tail) atomicAdd(row + (head ? (s8 < 6 ? s8 : s8 + 1) : st), head ? v8 : vt);
 }
 
 // Reverse walk over a warp's part of one tile list (shared by both backward
