@@ -20,19 +20,29 @@ namespace hgs {
 // Adam (bias-corrected form): m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
 // p -= (lr / (1 - b1^t)) m / (sqrt(v) / sqrt(1 - b2^t) + eps)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float adam_one(float &p, float g, float &m, float &v, const AdamArgs &a, float lr) {
+// step = lr / (1 - b1^t) and isb2 = 1 / sqrt(1 - b2^t) are the same for every
+// element of a group, so each thread forms them once (one division per
+// element remains).
+struct AdamStep {
+  float head, tail, isb2;
+};
+__device__ __forceinline__ AdamStep adam_step(const AdamArgs &a, const AdamGroup &g) {
+  return AdamStep{g.lr / a.bc1, g.lr_tail / a.bc1, 1.0f / a.sqrt_bc2};
+}
+__device__ __forceinline__ float adam_one(float &p, float g, float &m, float &v, const AdamArgs &a, float step,
+                                          float isb2) {
   m = fmaf(a.beta1, m, a.omb1 * g);
   v = fmaf(a.beta2, v, a.omb2 * g * g);
-  p -= (lr / a.bc1) * m / (sqrtf(v) / a.sqrt_bc2 + a.eps);
+  p -= step * m / fmaf(sqrtf(v), isb2, a.eps);
   return p;
 }
 
-// Learning rate of the element whose position in its row of `period` is r
+// Step size of the element whose position in its row of `period` is r
 // (r < period + 3 is reduced once).
-__device__ __forceinline__ float lr_at(const AdamGroup &g, uint32_t r) {
-  if (g.period <= 0) return g.lr;
+__device__ __forceinline__ float step_at(const AdamGroup &g, const AdamStep &st, uint32_t r) {
+  if (g.period <= 0) return st.head;
   if (r >= (uint32_t)g.period) r -= (uint32_t)g.period;
-  return r < (uint32_t)g.head ? g.lr : g.lr_tail;
+  return r < (uint32_t)g.head ? st.head : st.tail;
 }
 
 // The row position advances by a fixed stride per grid step, so it is kept
@@ -44,6 +54,7 @@ __global__ void __launch_bounds__(256) adam_kernel(AdamArgs a, AdamGroup grp) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t P = grp.period > 0 ? (uint64_t)grp.period : 1;
+  const AdamStep st = adam_step(a, grp);
   int64_t done = 0;
   if (vec) {
     const int64_t n4 = n / 4;
@@ -55,10 +66,10 @@ __global__ void __launch_bounds__(256) adam_kernel(AdamArgs a, AdamGroup grp) {
     for (int64_t k = tid; k < n4; k += stride) {
       float4 p = Pp[k], m = M[k], v = V[k];
       const float4 g = __ldg(G + k);
-      adam_one(p.x, g.x, m.x, v.x, a, lr_at(grp, r));
-      adam_one(p.y, g.y, m.y, v.y, a, lr_at(grp, r + 1));
-      adam_one(p.z, g.z, m.z, v.z, a, lr_at(grp, r + 2));
-      adam_one(p.w, g.w, m.w, v.w, a, lr_at(grp, r + 3));
+      adam_one(p.x, g.x, m.x, v.x, a, step_at(grp, st, r), st.isb2);
+      adam_one(p.y, g.y, m.y, v.y, a, step_at(grp, st, r + 1), st.isb2);
+      adam_one(p.z, g.z, m.z, v.z, a, step_at(grp, st, r + 2), st.isb2);
+      adam_one(p.w, g.w, m.w, v.w, a, step_at(grp, st, r + 3), st.isb2);
       Pp[k] = p; M[k] = m; V[k] = v;
       r += inc;
       if (r >= (uint32_t)P) r -= (uint32_t)P;
@@ -67,7 +78,7 @@ __global__ void __launch_bounds__(256) adam_kernel(AdamArgs a, AdamGroup grp) {
   }
   for (int64_t k = done + tid; k < n; k += stride) {
     float p = grp.param[k], m = grp.m[k], v = grp.v[k];
-    adam_one(p, grp.grad[k], m, v, a, lr_at(grp, (uint32_t)((uint64_t)k % P)));
+    adam_one(p, grp.grad[k], m, v, a, step_at(grp, st, (uint32_t)((uint64_t)k % P)), st.isb2);
     grp.param[k] = p; grp.m[k] = m; grp.v[k] = v;
   }
 }
